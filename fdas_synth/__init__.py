@@ -1,0 +1,139 @@
+"""Seeded synthetic inputs shaped like the paper's FDAS workloads.
+
+This module is the only code shared by the CUDA path's tests, the benchmark and the CPU
+oracle, and it holds none of the method's arithmetic: it only draws time series (Gaussian
+noise plus injected accelerated signals), so that both sides see the same float32 input.
+
+The paper's inputs (SIGPROC ``fake`` filterbanks and a GMRT observation) are not available;
+these generators stand in for them.  Seeds follow ``20220624 + 1000 * config + series``
+and every draw uses numpy's PCG64.
+
+Signal model: phase in cycles phi(u) = phi0 + r0 u + z0 u^2 / 2 over u = t / T in [0, 1),
+so r0 is the start frequency in Fourier bins and z0 = fdot T^2 the drift in bins over the
+observation (Eq. fdotz: acceleration = z c / (f T^2)).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEED_BASE = 20220624
+C_LIGHT = 299_792_458.0
+
+
+def seed_for(config_index: int, series_index: int = 0) -> int:
+    return SEED_BASE + 1000 * int(config_index) + int(series_index)
+
+
+def rng_for(config_index: int, series_index: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed_for(config_index, series_index)))
+
+
+def noise(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Unit-variance white Gaussian noise, float64 (the caller casts once at the end)."""
+    return rng.standard_normal(n)
+
+
+def chirp(n: int, amp: float, r0: float, z0: float, phase: float = 0.0) -> np.ndarray:
+    """amp * cos(2 pi (r0 u + z0 u^2 / 2) + phase), u = j / n, float64."""
+    u = np.arange(n, dtype=np.float64) / n
+    cyc = r0 * u + 0.5 * z0 * u * u
+    cyc -= np.floor(cyc)
+    return amp * np.cos(2.0 * np.pi * cyc + phase)
+
+
+def pulse_train(n: int, r0: float, z0: float, duty: float, snr: float, phase0: float) -> np.ndarray:
+    """Gaussian pulses (FWHM = duty x period) on the phase phi(u) = phase0 + r0 u + z0 u^2/2,
+    mean removed and scaled so that sqrt(sum s_j^2) = snr in units of the noise sigma."""
+    u = np.arange(n, dtype=np.float64) / n
+    cyc = phase0 + r0 * u + 0.5 * z0 * u * u
+    d = cyc - np.round(cyc)
+    w = duty / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    s = np.exp(-0.5 * (d / w) ** 2)
+    s -= s.mean()
+    return s * (snr / math.sqrt(float(np.dot(s, s))))
+
+
+def accel_to_z(accel: float, f: float, tobs: float) -> float:
+    """Eq. fdotz inverted: z = a f T^2 / c."""
+    return accel * f * tobs * tobs / C_LIGHT
+
+
+def z_to_accel(z: float, f: float, tobs: float) -> float:
+    """Eq. fdotz: a = z c / (f T^2)."""
+    return z * C_LIGHT / (f * tobs * tobs)
+
+
+@dataclasses.dataclass
+class Train:
+    period_s: float
+    r0: float
+    z0: float
+    duty: float
+    snr: float
+    phase0: float
+
+
+@dataclasses.dataclass
+class Workload:
+    """One series of a workload: its float32 samples and what was injected."""
+    name: str
+    n: int
+    tsamp: float
+    zmax: int
+    taps: int
+    seg_len: int
+    series: np.ndarray
+    trains: list
+    max_harm: int = 1
+    thr: tuple = (30.0, 30.0, 30.0, 30.0, 30.0)
+
+    @property
+    def nb(self) -> int:
+        return self.n // 2
+
+    @property
+    def K(self) -> int:
+        return self.zmax + 1
+
+
+def single_chirp_workload(seed_config: int = 0, n: int = 1 << 16, amp: float = 0.05,
+                          r0: float = 8000.3, z0: float = 6.2, zmax: int = 16, taps: int = 64,
+                          seg_len: int = 1024, with_noise: bool = True) -> Workload:
+    """Plain FP32 FDAS case: N = 2^16 N(0,1) samples plus one sinusoid of amplitude 0.05 at
+    bin 8000.3 with z = +6.2; 17 templates (zmax 16), 64 taps, 1024-bin segments."""
+    x = chirp(n, amp, r0, z0)
+    if with_noise:
+        x = x + noise(n, rng_for(seed_config, 0))
+    return Workload("single_chirp_n65536_z16_m64_s1024", n, 1.0 / n, zmax, taps, seg_len,
+                    x.astype(np.float32), [Train(0.0, r0, z0, 0.0, 0.0, 0.0)])
+
+
+def draw_trains(rng: np.random.Generator, count: int, n: int, tsamp: float,
+                zlim: float = 80.0, duty: float = 0.05, snr=(5.0, 30.0),
+                period=(1e-3, 20e-3)) -> list:
+    tobs = n * tsamp
+    out = []
+    for _ in range(count):
+        p = math.exp(rng.uniform(math.log(period[0]), math.log(period[1])))
+        out.append(Train(p, tobs / p, float(rng.uniform(-zlim, zlim)), duty,
+                         float(rng.uniform(snr[0], snr[1])), float(rng.uniform(0.0, 1.0))))
+    return out
+
+
+def pulse_train_workload(config_index: int = 1, n: int = 1 << 23, tsamp: float = 64e-6,
+                         n_trains: int = 8, zmax: int = 84, taps: int = 256,
+                         seg_len: int = 8192, series_index: int = 0, zlim: float = 80.0,
+                         duty: float = 0.05, snr=(5.0, 30.0)) -> Workload:
+    """Precision case: N = 2^23 Gaussian-noise samples at 64 us with 8 injected pulse trains
+    (period log-uniform 1-20 ms, 5% duty Gaussian pulses, z uniform in [-80, 80], per-train
+    SNR 5-30); 85 templates (zmax 84), 256 taps, 8192-bin segments."""
+    rng = rng_for(config_index, series_index)
+    x = noise(n, rng)
+    trains = draw_trains(rng, n_trains, n, tsamp, zlim=zlim, duty=duty, snr=snr)
+    for t in trains:
+        x += pulse_train(n, t.r0, t.z0, t.duty, t.snr, t.phase0)
+    name = f"pulse_trains_n{n}_z{zmax}_m{taps}_s{seg_len}"
+    return Workload(name, n, tsamp, zmax, taps, seg_len, x.astype(np.float32), trains)
