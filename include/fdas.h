@@ -1,0 +1,196 @@
+/*
+ * libfdas — GB300 (sm_103a) Fourier Domain Acceleration Search hot path.
+ *
+ * The library turns the time series of one dispersion-measure trial into the
+ * frequency/frequency-derivative (f-z) power plane and its harmonic-summed peak list,
+ * following arXiv:2206.12205 (White et al., "Bits missing: finding exotic pulsars using
+ * bfloat16 on NVIDIA GPUs"):
+ *
+ *   x[N] --(long real FFT, FP32; Sec. 3)--> X[Nb]                          fdas_spectrum
+ *        --(overlap-save correlation with K acceleration templates;
+ *           Sec. 2.1, Fig. fdas_flow "blue box"; BF16 variant Sec. 3)--> P[K][Nb]   fdas_plane
+ *        --(harmonic sum + threshold + local maxima; Sec. 2.1)--> peaks        fdas_peaks
+ *
+ * fdas_search runs all three.  Every step runs in this library's CUDA kernels.
+ *
+ * Conventions used by every entry point:
+ *   - Nb = N/2 frequency bins (the Nyquist bin is dropped), bin 0 (DC) is set to zero.
+ *   - Spectrum normalisation: Xhat = X * sqrt(2/sigma2), sigma2 = mean |X_k|^2 over
+ *     k = 1..Nb-1 (or the fixed value in fdas_config.sigma2), so that noise-only plane
+ *     cells follow chi^2 with 2 degrees of freedom (Sec. 5.1).
+ *   - Templates: K = zmax + 1 rows at z_i = -zmax + 2i (z = fdot T^2 in bins, Eq. fdotz);
+ *     m taps at q = -m/2 .. m/2-1 of the response of a constant-fdot sinusoid
+ *     I(q, z) = int_0^1 exp(i pi (z u^2 - 2 q u)) du, scaled to unit norm (Sec. 3.3).
+ *   - Plane: P[i][r] = | sum_q Xhat[r+q] conj(T_i(q)) |^2, r = 0..Nb-1, row-major [K][Nb]
+ *     (r contiguous); Xhat is zero outside [0, Nb).  Element type is float for
+ *     FDAS_FP32 and bfloat16 (the upper 16 bits of the float) for the BF16 precisions.
+ *   - All device pointers are CUDA device addresses on the current device; the caller
+ *     owns them.  Streams are cudaStream_t values passed as void* (NULL = default
+ *     stream).  Calls are asynchronous unless stated.  Nothing inside fdas_spectrum,
+ *     fdas_plane, fdas_peaks or fdas_search allocates memory.
+ *   - Errors are returned as fdas_status; nothing is thrown across the ABI.  Device-side
+ *     conditions (peak-list overflow, a wait that ran out) are recorded in a sticky
+ *     per-plan status word read by fdas_device_status.
+ */
+#ifndef FDAS_H
+#define FDAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FDAS_OK = 0,
+    FDAS_E_INVALID = 1,      /* an argument is out of range or a pointer is NULL          */
+    FDAS_E_UNSUPPORTED = 2,  /* a valid request this build does not implement             */
+    FDAS_E_NOMEM = 3,        /* a plan-time allocation failed                             */
+    FDAS_E_CUDA = 4,         /* a CUDA call or kernel launch failed (fdas_last_error)     */
+    FDAS_E_OVERFLOW = 5,     /* more peaks than fdas_config.max_peaks                     */
+    FDAS_E_TIMEOUT = 6,      /* a bounded device wait gave up                             */
+    FDAS_E_STATE = 7         /* call out of order (e.g. a search before make_templates)   */
+} fdas_status;
+
+typedef enum {
+    FDAS_FP32 = 0,           /* FP32 plane, FP32 CUDA-core FFTs                           */
+    FDAS_BF16 = 1,           /* BF16 spectrum/templates, tensor-core DFT stages with FP32
+                                accumulation, BF16 plane (Sec. 3)                          */
+    FDAS_BF16_SPLIT = 2      /* compensated hi+lo BF16 products, BF16 plane               */
+} fdas_precision;
+
+/* Device status bits (fdas_device_status). */
+#define FDAS_DEV_PEAK_OVERFLOW 0x1
+#define FDAS_DEV_TIMEOUT       0x2
+
+/* Search configuration for one series (one DM trial). */
+typedef struct {
+    int64_t n_samples;   /* N: power of two, 2^11 .. 2^27                                  */
+    int32_t zmax;        /* even, 0 .. 1022; K = zmax + 1 template rows                    */
+    int32_t taps;        /* m: even, 2 .. seg_len/2                                        */
+    int32_t seg_len;     /* S: overlap-save segment, 1024, 2048, 4096 or 8192 bins; the
+                            plane does not depend on it (linear-correlation identity)       */
+    int32_t precision;   /* fdas_precision                                                 */
+    int32_t max_harm;    /* highest harmonic-sum level: 1, 2, 4, 8 or 16                   */
+    float   thr[5];      /* peak thresholds on S_H for H = 1, 2, 4, 8, 16                   */
+    int32_t max_peaks;   /* capacity of the caller's peak buffer, >= 0                      */
+    double  sigma2;      /* 0: estimate sigma2 from the spectrum; > 0: use this value       */
+} fdas_config;
+
+/* One peak record, 16 bytes, ordered by (series, harm, zi, r) in the output list. */
+typedef struct {
+    uint32_t series;     /* series index (0 for single-series calls)                        */
+    uint32_t r;          /* frequency bin of the fundamental                                 */
+    int16_t  zi;         /* template row; z = -zmax + 2 zi                                   */
+    uint8_t  harm;       /* harmonic-sum level H (1, 2, 4, 8, 16)                            */
+    uint8_t  pad;        /* 0                                                                */
+    float    power;      /* S_H(r, zi): the summed normalised power                          */
+} fdas_peak;
+
+/* Sizes derived by fdas_plan. */
+typedef struct {
+    int64_t nb;              /* N/2 frequency bins                                           */
+    int32_t K;               /* template rows                                                */
+    int32_t seg_valid;       /* L = S - m + 1 plane bins kept per segment                     */
+    int64_t n_seg;           /* ceil(Nb / L) overlap-save segments                            */
+    int32_t plane_elem_bytes;/* 4 (FP32) or 2 (BF16)                                          */
+    int64_t plane_bytes;     /* K * Nb * plane_elem_bytes                                     */
+    size_t  workspace_bytes; /* caller-provided scratch for fdas_search                       */
+    int64_t cells;           /* K * Nb                                                        */
+} fdas_plan_info;
+
+typedef struct fdas_plan_s *fdas_plan_t;
+
+/*
+ * Validate cfg, derive sizes and create a plan (host only: no device work, no device
+ * allocation).  On success *plan receives a new plan and *workspace_bytes (nullable) the
+ * size of the scratch buffer fdas_search needs.
+ * Errors: FDAS_E_INVALID for a NULL pointer or a value outside the ranges above;
+ * FDAS_E_UNSUPPORTED for a precision this build does not implement.
+ */
+fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspace_bytes);
+
+/* Copy the derived sizes of a plan into *info.  Host only. */
+fdas_status fdas_plan_get_info(fdas_plan_t plan, fdas_plan_info *info);
+
+/*
+ * Build the template bank on the current device (Sec. 3.3: templates generated once, then
+ * converted to the working precision).  Allocates plan-owned device memory (freed by
+ * fdas_destroy): the responses I(q, z_i) are integrated in FP64 (Gauss-Legendre), scaled
+ * to unit norm, and their length-S DFTs G_i(k) = (1/S) sum_d T_i(d - m/2) e^{-2 pi i d k/S}
+ * stored in FP32 (and in BF16 hi/lo for the BF16 precisions).  Synchronises the stream.
+ * Errors: FDAS_E_NOMEM, FDAS_E_CUDA.
+ */
+fdas_status fdas_make_templates(fdas_plan_t plan, void *stream);
+
+/*
+ * Long real FFT [Sec. 3, kept in FP32]: d_series holds N float samples; d_xhat receives
+ * Nb complex values (interleaved float re, im) of the normalised spectrum Xhat with
+ * Xhat[0] = 0.  d_workspace: fdas_plan's workspace_bytes.  d_sigma2 (nullable, device):
+ * receives sigma2 as a double.
+ * Errors: FDAS_E_INVALID (NULL pointer), FDAS_E_STATE (no templates yet), FDAS_E_CUDA.
+ */
+fdas_status fdas_spectrum(fdas_plan_t plan, const float *d_series, void *d_workspace,
+                          float *d_xhat, double *d_sigma2, void *stream);
+
+/*
+ * The f-z plane from a normalised spectrum [Sec. 2.1 overlap-save; Fig. fdas_flow blue
+ * box]: segment FFTs of length S with stride L, per-template complex multiply, inverse
+ * FFT, |.|^2 and overlap discard.  d_xhat: Nb interleaved complex floats.  d_plane:
+ * K*Nb elements of the plan's plane type.  This is the step the throughput metric times.
+ * Errors: FDAS_E_INVALID, FDAS_E_STATE, FDAS_E_CUDA.
+ */
+fdas_status fdas_plane(fdas_plan_t plan, const float *d_xhat, void *d_workspace,
+                       void *d_plane, void *stream);
+
+/*
+ * Harmonic sums and peak list of a plane [Sec. 2.1]: for H = 1, 2, 4, .. max_harm,
+ * S_H(r, i) = sum_{h=1..H} P(h r, i_h) with z_{i_h} = h z_i (summed in FP32 in the order
+ * h = 1..H), defined where |H z_i| <= zmax and H r < Nb.  A cell is a peak when
+ * S_H > thr[level] and it beats each defined 3x3 neighbour (strictly for neighbours earlier
+ * in row-major (i, r) order, or equal for later ones).  Peaks are written to d_peaks in
+ * (harm, zi, r) order, at most max_peaks of them; *d_npeaks (device int32) receives the
+ * true count, and a count above max_peaks also sets FDAS_DEV_PEAK_OVERFLOW.
+ * Errors: FDAS_E_INVALID, FDAS_E_STATE, FDAS_E_CUDA.
+ */
+fdas_status fdas_peaks(fdas_plan_t plan, const void *d_plane, void *d_workspace,
+                       fdas_peak *d_peaks, int32_t *d_npeaks, void *stream);
+
+/*
+ * Whole path for one series: fdas_spectrum (into the workspace), fdas_plane, fdas_peaks.
+ * d_plane must hold plane_bytes.  Same errors as the three steps.
+ */
+fdas_status fdas_search(fdas_plan_t plan, const float *d_series, void *d_workspace,
+                        void *d_plane, fdas_peak *d_peaks, int32_t *d_npeaks, void *stream);
+
+/*
+ * Copy the frequency-domain template bank G[K][S] (interleaved complex float, FP32) to the
+ * device buffer d_out (K*S*8 bytes).  For verification.
+ * Errors: FDAS_E_INVALID, FDAS_E_STATE, FDAS_E_CUDA.
+ */
+fdas_status fdas_get_templates(fdas_plan_t plan, float *d_out, void *stream);
+
+/*
+ * Read (and clear when clear != 0) the plan's sticky device status word
+ * (FDAS_DEV_* bits).  Synchronises the device.  Errors: FDAS_E_INVALID, FDAS_E_CUDA.
+ */
+fdas_status fdas_device_status(fdas_plan_t plan, int32_t *bits, int clear);
+
+/* Text of the last CUDA error seen by this plan ("" if none).  Host only. */
+const char *fdas_last_error(fdas_plan_t plan);
+
+/* Free a plan and its device memory (NULL is ignored).  Synchronises the device. */
+void fdas_destroy(fdas_plan_t plan);
+
+/* Static text for a status code. */
+const char *fdas_status_string(fdas_status s);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int fdas_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDAS_H */

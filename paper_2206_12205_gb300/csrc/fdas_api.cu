@@ -1,0 +1,258 @@
+// libfdas C-ABI: plan validation, workspace layout and the entry points of include/fdas.h.
+// The entry points only check arguments and enqueue kernels; all numerical work happens
+// in the kernels of k0..k4.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "fdas_internal.cuh"
+
+using fdas::Plan;
+
+struct fdas_plan_s : public fdas::Plan {};
+
+namespace {
+
+Plan *P(fdas_plan_t h) { return static_cast<Plan *>(h); }
+
+constexpr size_t ALIGN = 256;
+size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+int ilog2(int64_t x) {
+    int l = 0;
+    while ((int64_t(1) << l) < x) l++;
+    return l;
+}
+
+fdas_status record(Plan *p, cudaError_t e) {
+    if (e == cudaSuccess) return FDAS_OK;
+    if (p) p->last_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();   // clear a non-sticky error
+    return e == cudaErrorMemoryAllocation ? FDAS_E_NOMEM : FDAS_E_CUDA;
+}
+
+bool plane_is_bf16(const Plan *p) { return p->cfg.precision != FDAS_FP32; }
+
+}  // namespace
+
+extern "C" {
+
+int fdas_version(void) { return 100; }
+
+const char *fdas_status_string(fdas_status s) {
+    switch (s) {
+        case FDAS_OK: return "ok";
+        case FDAS_E_INVALID: return "invalid argument";
+        case FDAS_E_UNSUPPORTED: return "unsupported configuration";
+        case FDAS_E_NOMEM: return "out of memory";
+        case FDAS_E_CUDA: return "CUDA error";
+        case FDAS_E_OVERFLOW: return "peak list overflow";
+        case FDAS_E_TIMEOUT: return "device wait timed out";
+        case FDAS_E_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspace_bytes) {
+    if (!cfg || !plan) return FDAS_E_INVALID;
+    *plan = nullptr;
+    const fdas_config c = *cfg;
+    if (!is_pow2(c.n_samples) || c.n_samples < (int64_t(1) << 11) || c.n_samples > (int64_t(1) << 27))
+        return FDAS_E_INVALID;
+    if (c.zmax < 0 || c.zmax > 1022 || (c.zmax & 1)) return FDAS_E_INVALID;
+    if (!(c.seg_len == 1024 || c.seg_len == 2048 || c.seg_len == 4096 || c.seg_len == 8192)) return FDAS_E_INVALID;
+    if (c.taps < 2 || (c.taps & 1) || c.taps > c.seg_len / 2) return FDAS_E_INVALID;
+    if (!(c.max_harm == 1 || c.max_harm == 2 || c.max_harm == 4 || c.max_harm == 8 || c.max_harm == 16))
+        return FDAS_E_INVALID;
+    if (c.max_peaks < 0) return FDAS_E_INVALID;
+    if (!(c.sigma2 >= 0.0)) return FDAS_E_INVALID;   // also rejects NaN
+    for (int l = 0; l < 5; l++)
+        if (c.thr[l] != c.thr[l]) return FDAS_E_INVALID;
+    if (c.precision != FDAS_FP32 && c.precision != FDAS_BF16 && c.precision != FDAS_BF16_SPLIT)
+        return FDAS_E_INVALID;
+    if (c.precision != FDAS_FP32) return FDAS_E_UNSUPPORTED;
+
+    fdas_plan_s *p = new (std::nothrow) fdas_plan_s();
+    if (!p) return FDAS_E_NOMEM;
+    p->cfg = c;
+    p->N = c.n_samples;
+    p->nb = p->N / 2;
+    p->K = c.zmax + 1;
+    p->m = c.taps;
+    p->S = c.seg_len;
+    p->logS = ilog2(p->S);
+    p->L = p->S - p->m + 1;
+    p->n_seg = (p->nb + p->L - 1) / p->L;
+    p->M = p->nb;
+    const int lgM = ilog2(p->M);
+    p->M1 = 1 << ((lgM + 1) / 2);
+    p->M2 = 1 << (lgM / 2);
+    const fdas::LevelTable lt = fdas::make_levels(*p);
+    p->n_levels = lt.n_levels;
+    p->n_tiles = lt.lev[lt.n_levels - 1].tile0 + (int64_t)lt.lev[lt.n_levels - 1].rows * lt.lev[lt.n_levels - 1].chunks;
+    p->n_part = p->M1 / 2;
+    // workspace layout
+    size_t off = 0;
+    p->ws_x = off;     off = align_up(off + sizeof(float2) * (size_t)p->nb);
+    p->ws_tmp = off;   off = align_up(off + sizeof(float2) * (size_t)p->M);
+    p->ws_part = off;  off = align_up(off + sizeof(double) * (size_t)p->n_part);
+    p->ws_scale = off; off = align_up(off + 16);
+    p->ws_y = off;     off = align_up(off + sizeof(float2) * (size_t)p->n_seg * p->S);
+    p->ws_tiles = off; off = align_up(off + align_up(sizeof(int32_t) * (size_t)p->n_tiles) + sizeof(int64_t) * (size_t)p->n_tiles);
+    p->ws_bytes = off;
+    p->device = -1;
+    *plan = p;
+    if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+    return FDAS_OK;
+}
+
+fdas_status fdas_plan_get_info(fdas_plan_t plan, fdas_plan_info *info) {
+    if (!plan || !info) return FDAS_E_INVALID;
+    const Plan *p = P(plan);
+    info->nb = p->nb;
+    info->K = p->K;
+    info->seg_valid = p->L;
+    info->n_seg = p->n_seg;
+    info->plane_elem_bytes = plane_is_bf16(p) ? 2 : 4;
+    info->cells = (int64_t)p->K * p->nb;
+    info->plane_bytes = info->cells * info->plane_elem_bytes;
+    info->workspace_bytes = p->ws_bytes;
+    return FDAS_OK;
+}
+
+fdas_status fdas_make_templates(fdas_plan_t plan, void *stream) {
+    if (!plan) return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->templates_ready) return FDAS_OK;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) return record(p, e);
+    const size_t nbank = (size_t)p->K * p->S;
+    const int64_t nhi = std::max<int64_t>(1, p->N >> fdas::TW_LO_BITS);
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    };
+    alloc((void **)&p->d_tw, sizeof(float2) * fdas::TW_MAX);
+    alloc((void **)&p->d_twn_lo, sizeof(float2) * ((size_t)1 << fdas::TW_LO_BITS));
+    alloc((void **)&p->d_twn_hi, sizeof(float2) * (size_t)nhi);
+    alloc((void **)&p->d_G, sizeof(float2) * nbank);
+    if (plane_is_bf16(p)) {
+        alloc((void **)&p->d_Gbf, sizeof(__nv_bfloat162) * nbank);
+        if (p->cfg.precision == FDAS_BF16_SPLIT) alloc((void **)&p->d_Gbf_lo, sizeof(__nv_bfloat162) * nbank);
+    }
+    alloc((void **)&p->d_status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = fdas::launch_make_templates(*p, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return record(p, e);
+    p->templates_ready = true;
+    return FDAS_OK;
+}
+
+static fdas_status ready(Plan *p) {
+    if (!p->templates_ready) return FDAS_E_STATE;
+    return FDAS_OK;
+}
+
+fdas_status fdas_spectrum(fdas_plan_t plan, const float *d_series, void *d_workspace, float *d_xhat,
+                          double *d_sigma2, void *stream) {
+    if (!plan || !d_series || !d_workspace || !d_xhat) return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    if (fdas_status s = ready(p)) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(d_workspace);
+    cudaError_t e = fdas::launch_spectrum(*p, d_series, ws, st);
+    if (e == cudaSuccess) e = fdas::launch_apply_scale(*p, ws, d_xhat, d_sigma2, st);
+    return record(p, e);
+}
+
+fdas_status fdas_plane(fdas_plan_t plan, const float *d_xhat, void *d_workspace, void *d_plane, void *stream) {
+    if (!plan || !d_xhat || !d_workspace || !d_plane) return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    if (fdas_status s = ready(p)) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(d_workspace);
+    const float2 *x = reinterpret_cast<const float2 *>(d_xhat);
+    cudaError_t e;
+    if (plane_is_bf16(p))
+        e = fdas::launch_plane_bf16(*p, x, nullptr, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
+    else
+        e = fdas::launch_plane_fp32(*p, x, nullptr, ws, static_cast<float *>(d_plane), st);
+    return record(p, e);
+}
+
+fdas_status fdas_peaks(fdas_plan_t plan, const void *d_plane, void *d_workspace, fdas_peak *d_peaks,
+                       int32_t *d_npeaks, void *stream) {
+    if (!plan || !d_plane || !d_workspace || !d_npeaks || (!d_peaks && P(plan)->cfg.max_peaks > 0))
+        return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    if (fdas_status s = ready(p)) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = fdas::launch_peaks(*p, d_plane, plane_is_bf16(p), static_cast<char *>(d_workspace), d_peaks,
+                                       d_npeaks, 0u, st);
+    return record(p, e);
+}
+
+fdas_status fdas_search(fdas_plan_t plan, const float *d_series, void *d_workspace, void *d_plane,
+                        fdas_peak *d_peaks, int32_t *d_npeaks, void *stream) {
+    if (!plan || !d_series || !d_workspace || !d_plane || !d_npeaks || (!d_peaks && P(plan)->cfg.max_peaks > 0))
+        return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    if (fdas_status s = ready(p)) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(d_workspace);
+    cudaError_t e = fdas::launch_spectrum(*p, d_series, ws, st);
+    const float2 *x = reinterpret_cast<const float2 *>(ws + p->ws_x);
+    const float *scale = reinterpret_cast<const float *>(ws + p->ws_scale + 8);
+    if (e == cudaSuccess) {
+        if (plane_is_bf16(p))
+            e = fdas::launch_plane_bf16(*p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
+        else
+            e = fdas::launch_plane_fp32(*p, x, scale, ws, static_cast<float *>(d_plane), st);
+    }
+    if (e == cudaSuccess) e = fdas::launch_peaks(*p, d_plane, plane_is_bf16(p), ws, d_peaks, d_npeaks, 0u, st);
+    return record(p, e);
+}
+
+fdas_status fdas_get_templates(fdas_plan_t plan, float *d_out, void *stream) {
+    if (!plan || !d_out) return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    if (fdas_status s = ready(p)) return s;
+    cudaError_t e = cudaMemcpyAsync(d_out, p->d_G, sizeof(float2) * (size_t)p->K * p->S, cudaMemcpyDeviceToDevice,
+                                    static_cast<cudaStream_t>(stream));
+    return record(p, e);
+}
+
+fdas_status fdas_device_status(fdas_plan_t plan, int32_t *bits, int clear) {
+    if (!plan || !bits) return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    *bits = 0;
+    if (!p->d_status) return FDAS_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(bits, p->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && clear) e = cudaMemset(p->d_status, 0, sizeof(int32_t));
+    return record(p, e);
+}
+
+const char *fdas_last_error(fdas_plan_t plan) {
+    if (!plan) return "";
+    return P(plan)->last_error.c_str();
+}
+
+void fdas_destroy(fdas_plan_t plan) {
+    if (!plan) return;
+    Plan *p = P(plan);
+    if (p->device >= 0) {
+        cudaDeviceSynchronize();
+        cudaFree(p->d_tw);
+        cudaFree(p->d_twn_lo);
+        cudaFree(p->d_twn_hi);
+        cudaFree(p->d_G);
+        cudaFree(p->d_Gbf);
+        cudaFree(p->d_Gbf_lo);
+        cudaFree(p->d_status);
+    }
+    delete static_cast<fdas_plan_s *>(plan);
+}
+
+}  // extern "C"

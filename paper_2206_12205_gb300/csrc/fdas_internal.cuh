@@ -1,0 +1,77 @@
+// Internal declarations shared by the libfdas translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/fdas.h"
+
+namespace fdas {
+
+// Largest overlap-save / block-FFT length; the block-FFT twiddle table has this many
+// entries and a length-L FFT reads every (TW_MAX/L)-th of them.
+constexpr int TW_MAX = 8192;
+// Two-level twiddle split for the long FFT: W_N^e = hi[e >> TW_LO_BITS] * lo[e & mask].
+constexpr int TW_LO_BITS = 13;
+
+struct Plan {
+    fdas_config cfg;
+    int64_t N, nb, n_seg;
+    int K, m, S, L;
+    int logS;
+    // long real FFT split: M = N/2 = M1 * M2 (four-step)
+    int64_t M;
+    int M1, M2;
+    // harmonic-sum levels and peak tiles
+    int n_levels;
+    int64_t n_tiles;
+    // workspace layout (byte offsets inside the caller's workspace)
+    size_t ws_x, ws_tmp, ws_part, ws_scale, ws_y, ws_tiles, ws_bytes;
+    int n_part;
+    // plan-owned device memory
+    int device;
+    float2 *d_tw;          // TW_MAX block-FFT twiddles W_TW_MAX^j
+    float2 *d_twn_lo;      // W_N^j, j < 2^TW_LO_BITS
+    float2 *d_twn_hi;      // W_N^(j << TW_LO_BITS), j < max(1, N >> TW_LO_BITS)
+    float2 *d_G;           // [K][S] FP32 template bank
+    __nv_bfloat162 *d_Gbf; // [K][S] BF16 template bank (hi), BF16 precisions
+    __nv_bfloat162 *d_Gbf_lo; // [K][S] BF16 residual (lo), split precision
+    int32_t *d_status;     // sticky device status word
+    bool templates_ready;
+    std::string last_error;
+};
+
+// Peak tiles: one tile = one (level, row, r-chunk).  Chunks hold PEAK_TILE cells.
+constexpr int PEAK_TILE = 2048;
+constexpr int PEAK_THREADS = 256;
+
+struct LevelDesc {
+    int H;          // harmonic count
+    int i_lo, rows; // valid rows [i_lo, i_lo + rows)
+    int64_t rmax;   // last valid r (H r < nb)
+    int64_t chunks; // r-chunks per row
+    int64_t tile0;  // first tile index of this level
+    float thr;
+};
+struct LevelTable {
+    LevelDesc lev[5];
+    int n_levels;
+};
+
+LevelTable make_levels(const Plan &p);
+
+// ---- launchers (each returns cudaGetLastError() of its launches) ----
+cudaError_t launch_make_templates(Plan &p, cudaStream_t st);
+cudaError_t launch_spectrum(const Plan &p, const float *d_series, char *ws, cudaStream_t st);
+cudaError_t launch_apply_scale(const Plan &p, const char *ws, float *d_xhat, double *d_sigma2,
+                               cudaStream_t st);
+cudaError_t launch_plane_fp32(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
+                              float *d_plane, cudaStream_t st);
+cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
+                              __nv_bfloat16 *d_plane, cudaStream_t st);
+cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
+                         fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st);
+
+}  // namespace fdas

@@ -1,0 +1,212 @@
+// K0: acceleration template bank (Sec. 2.1 and Sec. 3.3 "Template conversion").
+//
+// The paper generates its templates once in single precision and converts them to the
+// working precision with a GPU kernel.  Here the responses are integrated in FP64 on the
+// GPU and rounded once, at the end, to each working precision:
+//   1. taps:      I(q, z_i) = int_0^1 exp(i pi (z_i u^2 - 2 q u)) du for q = -m/2..m/2-1,
+//                 z_i = -zmax + 2i, by composite 20-point Gauss-Legendre quadrature with
+//                 panels no wider than one phase cycle (FP64, exact to rounding);
+//   2. normalise: T_i = I(., z_i) / sqrt(eta_i), eta_i = sum_q |I(q, z_i)|^2;
+//   3. transform: G_i(k) = (1/S) sum_{d<m} T_i(d - m/2) exp(-2 pi i d k / S), k < S, as a
+//                 direct FP64 DFT (m terms per output), stored as FP32 and as BF16 hi/lo.
+// With G in hand, the overlap-save correlation of a segment spectrum Yhat is
+// conj(FFT(conj(Yhat) * G)) (see the plane kernels), so the inverse FFT becomes a forward one.
+#include <cmath>
+#include <vector>
+
+#include "fdas_internal.cuh"
+
+namespace fdas {
+
+namespace {
+
+constexpr int GL_N = 20;
+struct GaussLegendre {
+    double x[GL_N];
+    double w[GL_N];
+};
+
+// Nodes and weights on [-1, 1]: Newton iteration on the Legendre polynomial P_n.
+GaussLegendre gauss_legendre_nodes() {
+    GaussLegendre g;
+    const int n = GL_N;
+    for (int i = 0; i < n; i++) {
+        double x = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dpn = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double a = 1.0, b = x;
+            for (int k = 2; k <= n; k++) {
+                double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+                a = b;
+                b = c;
+            }
+            dpn = n * (x * b - a) / (x * x - 1.0);
+            double step = b / dpn;
+            x -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        double a = 1.0, b = x;
+        for (int k = 2; k <= n; k++) {
+            double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+            a = b;
+            b = c;
+        }
+        dpn = n * (x * b - a) / (x * x - 1.0);
+        g.x[i] = x;
+        g.w[i] = 2.0 / ((1.0 - x * x) * dpn * dpn);
+    }
+    return g;
+}
+
+__global__ void k0_taps(double2 *__restrict__ taps, int K, int m, int zmax, GaussLegendre gl) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= K * m) return;
+    const int i = idx / m, t = idx - i * m;
+    const double z = -(double)zmax + 2.0 * i;
+    const double q = (double)(t - m / 2);
+    const int panels = (int)ceil(fabs(z) + fabs(q)) + 4;
+    const double h = 1.0 / panels;
+    double re = 0.0, im = 0.0;
+    for (int p = 0; p < panels; p++) {
+        const double mid = (p + 0.5) * h;
+#pragma unroll 4
+        for (int g = 0; g < GL_N; g++) {
+            const double u = fma(0.5 * h, gl.x[g], mid);
+            double s, c;
+            sincospi(u * (z * u - 2.0 * q), &s, &c);
+            const double wt = 0.5 * h * gl.w[g];
+            re = fma(wt, c, re);
+            im = fma(wt, s, im);
+        }
+    }
+    taps[idx] = make_double2(re, im);
+}
+
+// One block per template row: eta = sum |I|^2 (fixed-order tree), then scale to unit norm.
+__global__ void k0_normalise(double2 *__restrict__ taps, int m, double *__restrict__ eta_out) {
+    __shared__ double red[256];
+    double2 *row = taps + (size_t)blockIdx.x * m;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) acc += row[t].x * row[t].x + row[t].y * row[t].y;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double eta = red[0];
+    const double inv = 1.0 / sqrt(eta);
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        row[t].x *= inv;
+        row[t].y *= inv;
+    }
+    if (threadIdx.x == 0 && eta_out) eta_out[blockIdx.x] = eta;
+}
+
+// G_i(k) = (1/S) sum_d T_i(d - m/2) W_S^{d k}: direct FP64 DFT, rounded once to each format.
+__global__ void k0_dft(const double2 *__restrict__ taps, int m, int S, const double2 *__restrict__ wS,
+                       float2 *__restrict__ G, __nv_bfloat162 *__restrict__ Ghi,
+                       __nv_bfloat162 *__restrict__ Glo) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (k >= S) return;
+    const double2 *row = taps + (size_t)i * m;
+    double re = 0.0, im = 0.0;
+    for (int d = 0; d < m; d++) {
+        const double2 tv = row[d];
+        const double2 w = wS[((long long)d * k) & (S - 1)];
+        re = fma(tv.x, w.x, fma(-tv.y, w.y, re));
+        im = fma(tv.x, w.y, fma(tv.y, w.x, im));
+    }
+    re /= (double)S;
+    im /= (double)S;
+    const float fr = (float)re, fi = (float)im;
+    G[(size_t)i * S + k] = make_float2(fr, fi);
+    if (Ghi) {
+        // hi = BF16 rounding of the FP32 value (the paper's conversion); lo = BF16 of the
+        // FP64 remainder, so hi + lo carries about 16 significant bits.
+        const __nv_bfloat16 hr = __float2bfloat16_rn(fr), hi_i = __float2bfloat16_rn(fi);
+        Ghi[(size_t)i * S + k] = __halves2bfloat162(hr, hi_i);
+        if (Glo) {
+            const double rr = re - (double)__bfloat162float(hr);
+            const double ri = im - (double)__bfloat162float(hi_i);
+            Glo[(size_t)i * S + k] = __halves2bfloat162(__float2bfloat16_rn((float)rr),
+                                                        __float2bfloat16_rn((float)ri));
+        }
+    }
+}
+
+// exp(-2 pi i j / n) in FP64; f = 2j/n is exact for a power-of-two n and is reduced to
+// (-1, 1] before the libm call, so the argument error stays below pi * 2^-53.
+double2 host_unit(int64_t j, int64_t n) {
+    j %= n;
+    double f = 2.0 * (double)j / (double)n;
+    if (f > 1.0) f -= 2.0;
+    return make_double2(std::cos(M_PI * f), -std::sin(M_PI * f));
+}
+
+}  // namespace
+
+cudaError_t launch_make_templates(Plan &p, cudaStream_t st) {
+    const int K = p.K, m = p.m, S = p.S;
+    cudaError_t e;
+    // --- twiddle tables (host FP64 -> FP32) ---
+    {
+        std::vector<float2> tw(TW_MAX);
+        for (int j = 0; j < TW_MAX; j++) {
+            double2 w = host_unit(j, TW_MAX);
+            tw[j] = make_float2((float)w.x, (float)w.y);
+        }
+        e = cudaMemcpyAsync(p.d_tw, tw.data(), sizeof(float2) * TW_MAX, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        const int64_t nlo = (int64_t)1 << TW_LO_BITS;
+        const int64_t nhi = std::max<int64_t>(1, p.N >> TW_LO_BITS);
+        std::vector<float2> lo(nlo), hi(nhi);
+        for (int64_t j = 0; j < nlo; j++) {
+            double2 w = host_unit(j % p.N, p.N);
+            lo[j] = make_float2((float)w.x, (float)w.y);
+        }
+        for (int64_t j = 0; j < nhi; j++) {
+            double2 w = host_unit((j << TW_LO_BITS) % p.N, p.N);
+            hi[j] = make_float2((float)w.x, (float)w.y);
+        }
+        e = cudaMemcpyAsync(p.d_twn_lo, lo.data(), sizeof(float2) * nlo, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(p.d_twn_hi, hi.data(), sizeof(float2) * nhi, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        // the host vectors go out of scope: finish the copies first
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+    }
+    // --- template bank ---
+    double2 *d_taps = nullptr, *d_wS = nullptr;
+    double *d_eta = nullptr;
+    e = cudaMalloc(&d_taps, sizeof(double2) * (size_t)K * m);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&d_wS, sizeof(double2) * (size_t)S);
+    if (e != cudaSuccess) { cudaFree(d_taps); return e; }
+    e = cudaMalloc(&d_eta, sizeof(double) * (size_t)K);
+    if (e != cudaSuccess) { cudaFree(d_taps); cudaFree(d_wS); return e; }
+    {
+        std::vector<double2> wS(S);
+        for (int j = 0; j < S; j++) wS[j] = host_unit(j, S);
+        e = cudaMemcpyAsync(d_wS, wS.data(), sizeof(double2) * S, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e == cudaSuccess) {
+        const GaussLegendre gl = gauss_legendre_nodes();
+        const int n = K * m;
+        k0_taps<<<(n + 127) / 128, 128, 0, st>>>(d_taps, K, m, p.cfg.zmax, gl);
+        k0_normalise<<<K, 256, 0, st>>>(d_taps, m, d_eta);
+        dim3 grid((S + 255) / 256, K);
+        k0_dft<<<grid, 256, 0, st>>>(d_taps, m, S, d_wS, p.d_G, p.d_Gbf, p.d_Gbf_lo);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFree(d_taps);
+    cudaFree(d_wS);
+    cudaFree(d_eta);
+    return e;
+}
+
+}  // namespace fdas

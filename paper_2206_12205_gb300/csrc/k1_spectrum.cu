@@ -1,0 +1,198 @@
+// K1: the long real FFT of one series, kept in FP32 (Sec. 3: it does not scale with the
+// number of templates and reduced precision hurts it most), DC zeroed (Sec. 3.2), Nyquist
+// dropped, and the noise normalisation sigma2 = mean_{k=1..Nb-1} |X_k|^2.
+//
+// A real series x[N] is read as the complex series z_n = x_{2n} + i x_{2n+1} of length
+// M = N/2 = M1*M2, transformed by a four-step FFT, then split:
+//   pass A (one CTA per column n2):  FFT_M1 over n1 of z[n1*M2 + n2], times W_M^{n2 k1},
+//                                    stored as a contiguous row B[n2*M1 + k1];
+//   pass B (one CTA per row pair):   FFT_M2 over n2 of B[n2*M1 + k1] gives Z[k1 + M1*k2];
+//                                    with Z for rows k1 and M1-k1 both in shared memory,
+//                                    X_k = (Z_k + conj Z_{M-k})/2 - (i/2) W_N^k (Z_k - conj Z_{M-k}),
+//                                    k < M, and a per-CTA FP64 partial of sum |X_k|^2;
+//   finalize (one CTA):              fixed-order sum of the partials -> sigma2, scale.
+// Twiddles W_N^e come from a two-level FP32 table (W_N^e = hi[e >> 13] * lo[e & 8191]).
+#include "block_fft.cuh"
+#include "fdas_internal.cuh"
+
+namespace fdas {
+
+namespace {
+
+__device__ __forceinline__ float2 twN(const float2 *__restrict__ lo, const float2 *__restrict__ hi, int64_t e) {
+    return cmul(__ldg(hi + (e >> TW_LO_BITS)), __ldg(lo + (e & ((1 << TW_LO_BITS) - 1))));
+}
+
+template <int M1>
+__global__ void __launch_bounds__(M1 / 32) k1_pass_a(const float2 *__restrict__ z, const float2 *__restrict__ tw,
+                                                     const float2 *__restrict__ lo, const float2 *__restrict__ hi,
+                                                     float2 *__restrict__ B, int M2) {
+    constexpr int T = M1 / 32;
+    extern __shared__ float2 sm[];        // fft_smem_entries(M1) entries
+    const int t = threadIdx.x;
+    const int n2 = blockIdx.x;
+    float2 v[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __ldg(z + (int64_t)(t + i * T) * M2 + n2);
+    block_fft<M1>(v, sm, tw, t);
+    float2 *row = B + (int64_t)n2 * M1;
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const int k1 = t + i * T;
+        // W_M^{n2 k1} = W_N^{2 n2 k1}
+        row[k1] = cmul(v[i], twN(lo, hi, 2 * (int64_t)n2 * k1));
+    }
+}
+
+template <int M2>
+__global__ void __launch_bounds__(2 * (M2 / 32)) k1_pass_b(const float2 *__restrict__ B, const float2 *__restrict__ tw,
+                                                           const float2 *__restrict__ lo, const float2 *__restrict__ hi,
+                                                           float2 *__restrict__ X, double *__restrict__ partial, int M1) {
+    constexpr int T = M2 / 32;
+    constexpr int E = fft_smem_entries(M2);
+    extern __shared__ float2 smb[];       // 2 * E entries
+    __shared__ double red[2 * T];
+    const int half = threadIdx.x / T, t = threadIdx.x - half * T;
+    const int p = blockIdx.x;             // row pair
+    const int rowA = p, rowB = (p == 0) ? M1 / 2 : M1 - p;
+    const int row = half ? rowB : rowA;
+    float2 *sm = smb + half * E;
+    float2 v[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __ldg(B + (int64_t)(t + i * T) * M1 + row);
+    block_fft<M2>(v, sm, tw, t);
+    // the last FFT stage works in registers and the previous exchange ended with a barrier
+#pragma unroll
+    for (int i = 0; i < 32; i++) sm[fft_pad(t + i * T)] = v[i];
+    __syncthreads();
+    // partner of k = row + M1 k2 is M - k = pr + M1 k2' (row 0 pairs with itself)
+    const int pr = (row == 0) ? 0 : M1 - row;
+    const float2 *smp = smb + ((pr == rowA) ? 0 : E);
+    const int64_t M = (int64_t)M1 * M2;
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const int k2 = t + i * T;
+        const int k2p = (row == 0) ? ((M2 - k2) & (M2 - 1)) : (M2 - 1 - k2);
+        const float2 zk = v[i];
+        const float2 zc = smp[fft_pad(k2p)];
+        // E = (Z_k + conj Z_{M-k})/2, O = (Z_k - conj Z_{M-k})/(2i)
+        const float2 ev = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+        const float2 dv = make_float2(0.5f * (zk.x - zc.x), 0.5f * (zk.y + zc.y));
+        const float2 ov = make_float2(dv.y, -dv.x);
+        const int64_t k = row + (int64_t)M1 * k2;
+        float2 xk = cadd(ev, cmul(twN(lo, hi, k), ov));
+        if (k == 0) xk = make_float2(0.f, 0.f);
+        X[k] = xk;
+        acc += (double)xk.x * xk.x + (double)xk.y * xk.y;
+    }
+    (void)M;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = T; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[p] = red[0];
+}
+
+// sigma2 = (sum of partials, fixed order) / (Nb - 1) unless fixed; scale = sqrt(2 / sigma2).
+__global__ void k1_finalize(const double *__restrict__ partial, int n, int64_t nb, double sigma2_fixed,
+                            double *__restrict__ sigma2_out, float *__restrict__ scale_out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) acc += partial[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double sigma2 = sigma2_fixed > 0.0 ? sigma2_fixed : red[0] / (double)(nb - 1);
+        *sigma2_out = sigma2;
+        *scale_out = (float)sqrt(2.0 / sigma2);
+    }
+}
+
+__global__ void k1_apply_scale(const float2 *__restrict__ X, const float *__restrict__ scale, float2 *__restrict__ out,
+                               int64_t nb) {
+    const float s = *scale;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nb; k += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = X[k];
+        out[k] = make_float2(v.x * s, v.y * s);
+    }
+}
+
+template <int M1>
+cudaError_t run_pass_a(const Plan &p, const float2 *z, float2 *B, cudaStream_t st) {
+    const size_t smem = sizeof(float2) * fft_smem_entries(M1);
+    auto kern = k1_pass_a<M1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<p.M2, M1 / 32, smem, st>>>(z, p.d_tw, p.d_twn_lo, p.d_twn_hi, B, p.M2);
+    return cudaGetLastError();
+}
+
+template <int M2>
+cudaError_t run_pass_b(const Plan &p, const float2 *B, float2 *X, double *partial, cudaStream_t st) {
+    const size_t smem = 2 * sizeof(float2) * fft_smem_entries(M2);
+    auto kern = k1_pass_b<M2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<p.M1 / 2, 2 * (M2 / 32), smem, st>>>(B, p.d_tw, p.d_twn_lo, p.d_twn_hi, X, partial, p.M1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_spectrum(const Plan &p, const float *d_series, char *ws, cudaStream_t st) {
+    const float2 *z = reinterpret_cast<const float2 *>(d_series);
+    float2 *B = reinterpret_cast<float2 *>(ws + p.ws_tmp);
+    float2 *X = reinterpret_cast<float2 *>(ws + p.ws_x);
+    double *partial = reinterpret_cast<double *>(ws + p.ws_part);
+    double *sigma2 = reinterpret_cast<double *>(ws + p.ws_scale);
+    float *scale = reinterpret_cast<float *>(ws + p.ws_scale + 8);
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (p.M1) {
+        case 32: e = run_pass_a<32>(p, z, B, st); break;
+        case 64: e = run_pass_a<64>(p, z, B, st); break;
+        case 128: e = run_pass_a<128>(p, z, B, st); break;
+        case 256: e = run_pass_a<256>(p, z, B, st); break;
+        case 512: e = run_pass_a<512>(p, z, B, st); break;
+        case 1024: e = run_pass_a<1024>(p, z, B, st); break;
+        case 2048: e = run_pass_a<2048>(p, z, B, st); break;
+        case 4096: e = run_pass_a<4096>(p, z, B, st); break;
+        case 8192: e = run_pass_a<8192>(p, z, B, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaErrorInvalidValue;
+    switch (p.M2) {
+        case 32: e = run_pass_b<32>(p, B, X, partial, st); break;
+        case 64: e = run_pass_b<64>(p, B, X, partial, st); break;
+        case 128: e = run_pass_b<128>(p, B, X, partial, st); break;
+        case 256: e = run_pass_b<256>(p, B, X, partial, st); break;
+        case 512: e = run_pass_b<512>(p, B, X, partial, st); break;
+        case 1024: e = run_pass_b<1024>(p, B, X, partial, st); break;
+        case 2048: e = run_pass_b<2048>(p, B, X, partial, st); break;
+        case 4096: e = run_pass_b<4096>(p, B, X, partial, st); break;
+        case 8192: e = run_pass_b<8192>(p, B, X, partial, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    k1_finalize<<<1, 256, 0, st>>>(partial, p.M1 / 2, p.nb, p.cfg.sigma2, sigma2, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_scale(const Plan &p, const char *ws, float *d_xhat, double *d_sigma2, cudaStream_t st) {
+    const float2 *X = reinterpret_cast<const float2 *>(ws + p.ws_x);
+    const float *scale = reinterpret_cast<const float *>(ws + p.ws_scale + 8);
+    const double *sigma2 = reinterpret_cast<const double *>(ws + p.ws_scale);
+    const int64_t blocks = std::min<int64_t>((p.nb + 255) / 256, 152 * 16);
+    k1_apply_scale<<<(int)blocks, 256, 0, st>>>(X, scale, reinterpret_cast<float2 *>(d_xhat), p.nb);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && d_sigma2)
+        e = cudaMemcpyAsync(d_sigma2, sigma2, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    return e;
+}
+
+}  // namespace fdas

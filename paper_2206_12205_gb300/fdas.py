@@ -1,0 +1,321 @@
+"""ctypes binding to libfdas (include/fdas.h): the same entry points, argument marshalling only.
+
+Every step of the path runs in libfdas' CUDA kernels.  torch tensors supply device memory
+and streams; this module checks their device, dtype and size, passes raw pointers, and
+turns fdas_status codes into exceptions.  If the library is missing this module raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+FDAS_OK, FDAS_E_INVALID, FDAS_E_UNSUPPORTED, FDAS_E_NOMEM, FDAS_E_CUDA, FDAS_E_OVERFLOW, FDAS_E_TIMEOUT, FDAS_E_STATE = range(8)
+FDAS_FP32, FDAS_BF16, FDAS_BF16_SPLIT = 0, 1, 2
+FDAS_DEV_PEAK_OVERFLOW, FDAS_DEV_TIMEOUT = 0x1, 0x2
+PRECISIONS = {"fp32": FDAS_FP32, "bf16": FDAS_BF16, "bf16_split": FDAS_BF16_SPLIT}
+
+# every symbol include/fdas.h declares
+EXPORTED = (
+    "fdas_plan", "fdas_plan_get_info", "fdas_make_templates", "fdas_spectrum", "fdas_plane",
+    "fdas_peaks", "fdas_search", "fdas_get_templates", "fdas_device_status", "fdas_last_error",
+    "fdas_destroy", "fdas_status_string", "fdas_version",
+)
+
+PEAK_DTYPE = np.dtype([("series", "<u4"), ("r", "<u4"), ("zi", "<i2"), ("harm", "u1"),
+                       ("pad", "u1"), ("power", "<f4")])
+assert PEAK_DTYPE.itemsize == 16
+
+
+class FdasError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {status_string(status)} ({status})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int64), ("zmax", ctypes.c_int32), ("taps", ctypes.c_int32),
+                ("seg_len", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_harm", ctypes.c_int32),
+                ("thr", ctypes.c_float * 5), ("max_peaks", ctypes.c_int32), ("sigma2", ctypes.c_double)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int64), ("K", ctypes.c_int32), ("seg_valid", ctypes.c_int32),
+                ("n_seg", ctypes.c_int64), ("plane_elem_bytes", ctypes.c_int32), ("plane_bytes", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_size_t), ("cells", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libfdas.so from the package's _build directory (built by __graft_entry__.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libfdas.so is not built ({path}); run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    V, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    S = ctypes.c_int
+    sig = {
+        "fdas_plan": (S, [ctypes.POINTER(_Config), ctypes.POINTER(V), ctypes.POINTER(SZ)]),
+        "fdas_plan_get_info": (S, [V, ctypes.POINTER(_Info)]),
+        "fdas_make_templates": (S, [V, V]),
+        "fdas_spectrum": (S, [V, V, V, V, V, V]),
+        "fdas_plane": (S, [V, V, V, V, V]),
+        "fdas_peaks": (S, [V, V, V, V, V, V]),
+        "fdas_search": (S, [V, V, V, V, V, V, V]),
+        "fdas_get_templates": (S, [V, V, V]),
+        "fdas_device_status": (S, [V, ctypes.POINTER(I32), ctypes.c_int]),
+        "fdas_last_error": (ctypes.c_char_p, [V]),
+        "fdas_destroy": (None, [V]),
+        "fdas_status_string": (ctypes.c_char_p, [S]),
+        "fdas_version": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _ = I64
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().fdas_status_string(int(status)).decode()
+
+
+def fdas_version() -> int:
+    return int(load().fdas_version())
+
+
+# ----------------------------------------------------------------------------- helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev_ptr(t, name: str, dtype=None, min_bytes: int = 0) -> int:
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    nbytes = t.numel() * t.element_size()
+    if nbytes < min_bytes:
+        raise ValueError(f"{name}: {nbytes} bytes < required {min_bytes}")
+    return int(t.data_ptr())
+
+
+def _check(status: int, where: str, plan=None):
+    if status != FDAS_OK:
+        detail = ""
+        if plan is not None and plan.handle:
+            detail = (load().fdas_last_error(plan.handle) or b"").decode()
+        raise FdasError(status, where, detail)
+
+
+@dataclasses.dataclass
+class PlanInfo:
+    nb: int
+    K: int
+    seg_valid: int
+    n_seg: int
+    plane_elem_bytes: int
+    plane_bytes: int
+    workspace_bytes: int
+    cells: int
+
+
+class Plan:
+    """Owns an fdas_plan_t.  Create with fdas_plan(); freed by fdas_destroy() or GC."""
+
+    def __init__(self, handle: int, cfg: dict, info: PlanInfo):
+        self.handle = handle
+        self.cfg = cfg
+        self.info = info
+
+    @property
+    def precision(self) -> int:
+        return self.cfg["precision"]
+
+    def plane_dtype(self):
+        torch = _torch()
+        return torch.float32 if self.info.plane_elem_bytes == 4 else torch.bfloat16
+
+    def __del__(self):
+        try:
+            fdas_destroy(self)
+        except Exception:
+            pass
+
+
+def make_config(n_samples: int, zmax: int, taps: int, seg_len: int, precision="fp32", max_harm: int = 1,
+                thr: Sequence[float] = (30.0,) * 5, max_peaks: int = 1 << 16, sigma2: float = 0.0) -> dict:
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    thr = list(thr) + [float(thr[-1])] * (5 - len(thr))
+    return dict(n_samples=int(n_samples), zmax=int(zmax), taps=int(taps), seg_len=int(seg_len),
+                precision=int(precision), max_harm=int(max_harm), thr=[float(v) for v in thr[:5]],
+                max_peaks=int(max_peaks), sigma2=float(sigma2))
+
+
+# ----------------------------------------------------------------------------- entry points
+def fdas_plan(cfg: dict) -> Plan:
+    lib = load()
+    c = _Config()
+    for k in ("n_samples", "zmax", "taps", "seg_len", "precision", "max_harm", "max_peaks", "sigma2"):
+        setattr(c, k, cfg[k])
+    for i, v in enumerate(cfg["thr"]):
+        c.thr[i] = v
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    _check(lib.fdas_plan(ctypes.byref(c), ctypes.byref(h), ctypes.byref(ws)), "fdas_plan")
+    inf = _Info()
+    _check(lib.fdas_plan_get_info(h, ctypes.byref(inf)), "fdas_plan_get_info")
+    info = PlanInfo(inf.nb, inf.K, inf.seg_valid, inf.n_seg, inf.plane_elem_bytes, inf.plane_bytes,
+                    inf.workspace_bytes, inf.cells)
+    return Plan(h.value, dict(cfg), info)
+
+
+def fdas_make_templates(plan: Plan, stream=None):
+    _check(load().fdas_make_templates(plan.handle, _stream_ptr(stream)), "fdas_make_templates", plan)
+
+
+def fdas_spectrum(plan: Plan, series, workspace, xhat, sigma2=None, stream=None):
+    torch = _torch()
+    n = plan.cfg["n_samples"]
+    args = (plan.handle,
+            _dev_ptr(series, "series", torch.float32, 4 * n),
+            _dev_ptr(workspace, "workspace", None, plan.info.workspace_bytes),
+            _dev_ptr(xhat, "xhat", torch.float32, 8 * plan.info.nb),
+            _dev_ptr(sigma2, "sigma2", torch.float64, 8) if sigma2 is not None else None,
+            _stream_ptr(stream))
+    _check(load().fdas_spectrum(*args), "fdas_spectrum", plan)
+
+
+def fdas_plane(plan: Plan, xhat, workspace, plane, stream=None):
+    torch = _torch()
+    args = (plan.handle,
+            _dev_ptr(xhat, "xhat", torch.float32, 8 * plan.info.nb),
+            _dev_ptr(workspace, "workspace", None, plan.info.workspace_bytes),
+            _dev_ptr(plane, "plane", plan.plane_dtype(), plan.info.plane_bytes),
+            _stream_ptr(stream))
+    _check(load().fdas_plane(*args), "fdas_plane", plan)
+
+
+def fdas_peaks(plan: Plan, plane, workspace, peaks, npeaks, stream=None):
+    torch = _torch()
+    args = (plan.handle,
+            _dev_ptr(plane, "plane", plan.plane_dtype(), plan.info.plane_bytes),
+            _dev_ptr(workspace, "workspace", None, plan.info.workspace_bytes),
+            _dev_ptr(peaks, "peaks", torch.uint8, 16 * plan.cfg["max_peaks"]) if peaks is not None else None,
+            _dev_ptr(npeaks, "npeaks", torch.int32, 4),
+            _stream_ptr(stream))
+    _check(load().fdas_peaks(*args), "fdas_peaks", plan)
+
+
+def fdas_search(plan: Plan, series, workspace, plane, peaks, npeaks, stream=None):
+    torch = _torch()
+    n = plan.cfg["n_samples"]
+    args = (plan.handle,
+            _dev_ptr(series, "series", torch.float32, 4 * n),
+            _dev_ptr(workspace, "workspace", None, plan.info.workspace_bytes),
+            _dev_ptr(plane, "plane", plan.plane_dtype(), plan.info.plane_bytes),
+            _dev_ptr(peaks, "peaks", torch.uint8, 16 * plan.cfg["max_peaks"]) if peaks is not None else None,
+            _dev_ptr(npeaks, "npeaks", torch.int32, 4),
+            _stream_ptr(stream))
+    _check(load().fdas_search(*args), "fdas_search", plan)
+
+
+def fdas_get_templates(plan: Plan, out, stream=None):
+    torch = _torch()
+    K, S = plan.info.K, plan.cfg["seg_len"]
+    _check(load().fdas_get_templates(plan.handle, _dev_ptr(out, "out", torch.float32, 8 * K * S),
+                                     _stream_ptr(stream)), "fdas_get_templates", plan)
+
+
+def fdas_device_status(plan: Plan, clear: bool = True) -> int:
+    bits = ctypes.c_int32(0)
+    _check(load().fdas_device_status(plan.handle, ctypes.byref(bits), 1 if clear else 0), "fdas_device_status", plan)
+    return int(bits.value)
+
+
+def fdas_destroy(plan: Plan):
+    if plan.handle:
+        load().fdas_destroy(plan.handle)
+        plan.handle = None
+
+
+# ----------------------------------------------------------------------------- conveniences
+def peaks_to_numpy(peaks_u8, npeaks: int) -> np.ndarray:
+    """View the first npeaks records of a uint8 peak buffer (device or host) as PEAK_DTYPE."""
+    a = peaks_u8[: 16 * npeaks].cpu().numpy() if hasattr(peaks_u8, "cpu") else np.asarray(peaks_u8)[: 16 * npeaks]
+    return a.view(PEAK_DTYPE).copy()
+
+
+class Search:
+    """One configured series search with its device buffers (torch-owned)."""
+
+    def __init__(self, cfg: dict, device="cuda", stream=None):
+        torch = _torch()
+        self.plan = fdas_plan(cfg)
+        self.device = torch.device(device)
+        fdas_make_templates(self.plan, stream)
+        inf = self.plan.info
+        self.workspace = torch.empty(inf.workspace_bytes, dtype=torch.uint8, device=self.device)
+        self.plane = torch.empty(inf.cells, dtype=self.plan.plane_dtype(), device=self.device)
+        self.xhat = torch.empty(2 * inf.nb, dtype=torch.float32, device=self.device)
+        self.sigma2 = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.peaks = torch.zeros(16 * max(1, cfg["max_peaks"]), dtype=torch.uint8, device=self.device)
+        self.npeaks = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def plane_2d(self):
+        return self.plane.view(self.plan.info.K, self.plan.info.nb)
+
+    def search(self, series, stream=None):
+        fdas_search(self.plan, series, self.workspace, self.plane, self.peaks, self.npeaks, stream)
+
+    def spectrum(self, series, stream=None):
+        fdas_spectrum(self.plan, series, self.workspace, self.xhat, self.sigma2, stream)
+        return self.xhat
+
+    def plane_from_spectrum(self, xhat, stream=None):
+        fdas_plane(self.plan, xhat, self.workspace, self.plane, stream)
+        return self.plane
+
+    def find_peaks(self, stream=None):
+        fdas_peaks(self.plan, self.plane, self.workspace, self.peaks, self.npeaks, stream)
+
+    def peak_list(self) -> np.ndarray:
+        n = int(self.npeaks.item())
+        n = min(n, self.plan.cfg["max_peaks"])
+        return peaks_to_numpy(self.peaks, n)

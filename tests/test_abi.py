@@ -1,0 +1,114 @@
+"""libfdas C-ABI on the CPU: the library loads, exports every symbol include/fdas.h declares,
+validates configurations on the host, derives sizes, and reports errors without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2206_12205_gb300 as fd
+from paper_2206_12205_gb300 import fdas as fb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fd.build.build()
+    return fd.load()
+
+
+def _declared_symbols():
+    with open(os.path.join(ROOT, "include", "fdas.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdas_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_symbols()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(fb.EXPORTED) == names
+
+
+def test_version_and_status_strings(lib):
+    assert fd.fdas_version() == 100
+    for code in range(8):
+        assert fd.status_string(code) and fd.status_string(code) != "unknown status"
+    assert fd.status_string(99) == "unknown status"
+
+
+def test_struct_layouts(lib):
+    assert ctypes.sizeof(fb._Config) == 64      # int64, 5 x int32, float[5], int32, pad, double
+    assert fb.PEAK_DTYPE.itemsize == 16
+
+
+@pytest.mark.parametrize("n,zmax,m,S", [(1 << 16, 16, 64, 1024), (1 << 23, 84, 256, 8192),
+                                         (1 << 11, 0, 2, 1024), (1 << 27, 1022, 4096, 8192),
+                                         (1 << 12, 8, 512, 1024), (1 << 13, 2, 16, 2048)])
+def test_plan_sizes(lib, n, zmax, m, S):
+    p = fd.fdas_plan(fd.make_config(n, zmax, m, S, max_harm=16))
+    nb, L = n // 2, S - m + 1
+    assert p.info.nb == nb and p.info.K == zmax + 1 and p.info.seg_valid == L
+    assert p.info.n_seg == -(-nb // L)
+    assert p.info.cells == (zmax + 1) * nb and p.info.plane_bytes == 4 * p.info.cells
+    assert p.info.workspace_bytes >= 8 * nb * 2 + 8 * p.info.n_seg * S
+    fd.fdas_destroy(p)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n=1 << 16 | 1), dict(n=1 << 10), dict(n=1 << 28), dict(zmax=15), dict(zmax=-2), dict(zmax=1024),
+    dict(m=63), dict(m=0), dict(m=513), dict(S=512), dict(S=3000), dict(S=16384), dict(max_harm=3),
+    dict(max_harm=32), dict(max_peaks=-1), dict(sigma2=-1.0), dict(sigma2=float("nan")), dict(precision=7),
+    dict(thr=(float("nan"),) * 5)])
+def test_plan_rejects_invalid(lib, kw):
+    a = dict(n=1 << 16, zmax=16, m=64, S=1024, max_harm=1, max_peaks=10, sigma2=0.0, precision=0, thr=(30.0,) * 5)
+    a.update(kw)
+    cfg = fd.make_config(a["n"], a["zmax"], a["m"], a["S"], precision=a["precision"], max_harm=a["max_harm"],
+                         thr=a["thr"], max_peaks=a["max_peaks"], sigma2=a["sigma2"])
+    with pytest.raises(fd.FdasError) as ei:
+        fd.fdas_plan(cfg)
+    assert ei.value.status == fb.FDAS_E_INVALID
+
+
+def test_null_arguments_rejected(lib):
+    assert lib.fdas_plan(None, None, None) == fb.FDAS_E_INVALID
+    p = fd.fdas_plan(fd.make_config(1 << 16, 16, 64, 1024))
+    for fn, nargs in (("fdas_spectrum", 6), ("fdas_plane", 5), ("fdas_peaks", 6), ("fdas_search", 7),
+                      ("fdas_get_templates", 3)):
+        assert getattr(lib, fn)(p.handle, *([None] * (nargs - 1))) == fb.FDAS_E_INVALID
+        assert getattr(lib, fn)(None, *([None] * (nargs - 1))) == fb.FDAS_E_INVALID
+    assert lib.fdas_make_templates(None, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_device_status(None, None, 0) == fb.FDAS_E_INVALID
+    assert lib.fdas_last_error(None) == b""
+    lib.fdas_destroy(None)
+    fd.fdas_destroy(p)
+
+
+def test_calls_before_templates_are_out_of_order(lib):
+    p = fd.fdas_plan(fd.make_config(1 << 16, 16, 64, 1024))
+    fake = ctypes.c_void_p(1 << 20)        # never dereferenced: the state check comes first
+    assert lib.fdas_plane(p.handle, fake, fake, fake, None) == fb.FDAS_E_STATE
+    assert lib.fdas_search(p.handle, fake, fake, fake, fake, fake, None) == fb.FDAS_E_STATE
+    fd.fdas_destroy(p)
+
+
+def test_make_templates_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    p = fd.fdas_plan(fd.make_config(1 << 16, 16, 64, 1024))
+    status = lib.fdas_make_templates(p.handle, None)
+    assert status in (fb.FDAS_E_CUDA, fb.FDAS_E_NOMEM)
+    assert lib.fdas_last_error(p.handle)
+    fd.fdas_destroy(p)
+
+
+def test_binding_refuses_host_tensors(lib):
+    import torch
+    p = fd.fdas_plan(fd.make_config(1 << 16, 16, 64, 1024))
+    with pytest.raises(ValueError):
+        fd.fdas_plane(p, torch.zeros(10), torch.zeros(10), torch.zeros(10))
+    fd.fdas_destroy(p)

@@ -1,0 +1,246 @@
+"""GPU parity: libfdas (through its C-ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP32 path):
+  - plane:     max_cells |P - P_ref| / max(P_ref, 2) <= 1e-5 (2 = mean noise power; a purely
+               relative error is unbounded where P_ref ~ 0);
+  - spectrum:  max |Xhat - Xhat_ref| <= 2e-6 * max|Xhat_ref| + 2e-5 (FP32 long FFT, log2 N levels);
+  - templates: max |G - G_ref| <= 1e-6 * max|G_ref| (one FP32 rounding of an FP64 value);
+  - peaks:     bit-exact (r, zi, H, power) against the oracle's float given-plane mode.
+"""
+import numpy as np
+import pytest
+import torch
+
+import fdas_synth as synth
+import oracle
+import paper_2206_12205_gb300 as fd
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fd.build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def _floor_err(p, ref):
+    return float(np.max(np.abs(p - ref) / np.maximum(ref, 2.0)))
+
+
+def _search(n, zmax, m, S, **kw):
+    return fd.Search(fd.make_config(n, zmax, m, S, **kw), device="cuda")
+
+
+def _to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _xhat_f32(xhat_c128):
+    return np.ascontiguousarray(xhat_c128.astype(np.complex64)).view(np.float32)
+
+
+# ------------------------------------------------------------------ templates (K0)
+@pytest.mark.parametrize("zmax,m,S", [(16, 64, 1024), (84, 256, 8192), (0, 2, 1024), (6, 512, 1024)])
+def test_templates_match_oracle(zmax, m, S):
+    s = _search(1 << 12, zmax, m, S)
+    K = zmax + 1
+    out = torch.empty(2 * K * S, dtype=torch.float32, device="cuda")
+    fd.fdas_get_templates(s.plan, out)
+    G = out.cpu().numpy().view(np.complex64).reshape(K, S).astype(np.complex128)
+    T, _ = oracle.templates(zmax, m)
+    c = np.zeros((K, S), dtype=np.complex128)
+    c[:, :m] = T
+    ref = np.fft.fft(c, axis=1) / S
+    assert np.abs(G - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ spectrum (K1)
+@pytest.mark.parametrize("n", [1 << 11, 1 << 12, 1 << 13, 1 << 16, 1 << 20])
+def test_spectrum_matches_oracle(n):
+    x = (synth.noise(n, synth.rng_for(50, n.bit_length())) + synth.chirp(n, 0.3, n / 7.3, 3.0)).astype(np.float32)
+    x[: n // 3] += 5.0                                 # a DC offset and a step: DC must still vanish
+    s = _search(n, 8, 32, 1024)
+    xh = s.spectrum(_to_dev(x))
+    torch.cuda.synchronize()
+    got = xh.cpu().numpy().view(np.complex64).astype(np.complex128)
+    ref, s2 = oracle.spectrum(x)
+    assert got[0] == 0
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max() + 2e-5
+    assert abs(s.sigma2.item() - s2) <= 1e-5 * s2
+
+
+def test_spectrum_fixed_sigma2():
+    n = 1 << 14
+    x = synth.chirp(n, 0.1, 2000.0, 0.0).astype(np.float32)
+    s = _search(n, 4, 16, 1024, sigma2=float(n))
+    got = s.spectrum(_to_dev(x)).cpu().numpy().view(np.complex64)
+    ref, _ = oracle.spectrum(x, sigma2=float(n))
+    assert s.sigma2.item() == float(n)
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ plane (K2 + K3)
+@pytest.mark.parametrize("n,zmax,m,S", [
+    (1 << 16, 16, 64, 1024),      # the plain FP32 workload's shape
+    (1 << 12, 0, 2, 1024),        # one template, minimal taps
+    (1 << 12, 4, 512, 1024),      # maximal taps: L = S/2 + 1
+    (1 << 13, 10, 100, 2048),     # m not a power of two, ragged last segment
+    (1 << 14, 20, 128, 4096),
+    (1 << 15, 6, 64, 8192),       # several segments of the largest size
+    (1 << 11, 2, 8, 8192),        # Nb < S: one zero-padded segment
+])
+def test_plane_shared_spectrum(n, zmax, m, S):
+    """fdas_plane on the oracle's spectrum (rounded to FP32) vs the oracle's FP64 plane of
+    that same rounded spectrum."""
+    x = (synth.noise(n, synth.rng_for(51, S)) + synth.chirp(n, 0.2, n / 9.1, zmax / 2.0)).astype(np.float32)
+    xr, _ = oracle.spectrum(x)
+    xr32 = _xhat_f32(xr)
+    xin = xr32.view(np.complex64).astype(np.complex128)
+    s = _search(n, zmax, m, S)
+    s.plane_from_spectrum(_to_dev(xr32))
+    torch.cuda.synchronize()
+    got = s.plane_2d().cpu().numpy().astype(np.float64)
+    ref = oracle.plane(xin, zmax, m)
+    assert _floor_err(got, ref) <= 1e-5
+
+
+def test_single_chirp_end_to_end():
+    """The plain FP32 workload end to end (long FFT included): plane within 1e-5 of the FP64
+    oracle, the injected signal at (8000, z = +6), peak list above 30."""
+    w = synth.single_chirp_workload()
+    s = _search(w.n, w.zmax, w.taps, w.seg_len, max_harm=1, thr=(30.0,), max_peaks=1024)
+    s.search(_to_dev(w.series))
+    torch.cuda.synchronize()
+    got = s.plane_2d().cpu().numpy().astype(np.float64)
+    ref = oracle.search(w.series, w.zmax, w.taps, 1, (30.0,))
+    assert _floor_err(got, ref["plane"]) <= 1e-5
+    i, r = np.unravel_index(np.argmax(got), got.shape)
+    assert (int(r), -w.zmax + 2 * int(i)) == (8000, 6)
+    pk = s.peak_list()
+    assert any(p["r"] == 8000 and p["zi"] == 11 for p in pk)
+    want = ref["peaks"]
+    # the FP64 oracle's peak set equals ours up to cells within 1e-5 of the threshold
+    close = lambda v: abs(v - 30.0) <= 1e-4 * 30.0
+    a = {(p["zi"], p["r"]) for p in pk if not close(p["power"])}
+    b = {(p["zi"], p["r"]) for p in want if not close(p["power"])}
+    assert a == b
+
+
+# ------------------------------------------------------------------ peaks (K4)
+def _peaks_equal(got, want):
+    assert len(got) == len(want)
+    for g, w in zip(got, want):
+        assert (int(g["harm"]), int(g["zi"]), int(g["r"])) == (int(w["h"]), int(w["zi"]), int(w["r"]))
+        assert np.float32(g["power"]).tobytes() == np.float32(w["power"]).tobytes()
+
+
+@pytest.mark.parametrize("max_harm", [1, 2, 4, 8, 16])
+def test_peaks_bit_exact_given_plane(max_harm):
+    n, zmax, m, S = 1 << 16, 32, 64, 1024
+    x = synth.noise(n, synth.rng_for(52, max_harm))
+    for h in range(1, 6):                             # a harmonic-rich accelerated signal
+        x += synth.chirp(n, 0.08 / h, 1234.0 * h, 6.0 * h)
+    x = x.astype(np.float32)
+    thr = (12.0, 18.0, 28.0, 45.0, 70.0)
+    s = _search(n, zmax, m, S, max_harm=max_harm, thr=thr, max_peaks=1 << 16)
+    s.search(_to_dev(x))
+    torch.cuda.synchronize()
+    got = s.peak_list()
+    want, cnt = oracle.peaks_f32(s.plane_2d().cpu().numpy(), zmax, max_harm, thr)
+    assert int(s.npeaks.item()) == cnt > 0
+    _peaks_equal(got, want)
+    assert fd.fdas_device_status(s.plan) == 0
+
+
+def test_peaks_ties_plateaus_and_overflow():
+    n, zmax, m, S = 1 << 14, 4, 16, 1024
+    s = _search(n, zmax, m, S, max_harm=2, thr=(1.0, 1.0), max_peaks=5)
+    K, nb = zmax + 1, n // 2
+    pl = np.zeros((K, nb), dtype=np.float32)
+    pl[2, 100] = pl[2, 101] = 9.0                     # plateau in a row
+    pl[1, 300] = pl[2, 300] = 7.0                     # plateau in a column
+    pl[0, 0] = 5.0                                    # corner cell
+    pl[4, nb - 1] = 5.0                               # last cell
+    pl[2, 4000:4010] = 3.0                            # a flat run
+    pl[3, 1500] = 6.0; pl[4, 3000] = 6.0              # a harmonic pair (z = 2 -> 4, r -> 2r)
+    s.plane.copy_(torch.from_numpy(pl.ravel()))
+    s.find_peaks()
+    torch.cuda.synchronize()
+    want, cnt = oracle.peaks_f32(pl, zmax, 2, (1.0, 1.0), max_out=5)
+    assert int(s.npeaks.item()) == cnt and cnt > 5
+    _peaks_equal(s.peak_list(), want)
+    assert fd.fdas_device_status(s.plan) & fd.fdas.FDAS_DEV_PEAK_OVERFLOW
+    assert fd.fdas_device_status(s.plan) == 0         # cleared by the previous read
+
+
+def test_bf16_plane_peaks_quick_cast():
+    """The peak kernel widens BF16 planes by bit placement (Sec. 3.1 quick cast): given the
+    same values, BF16 and FP32 planes give the same peaks."""
+    n, zmax = 1 << 13, 8
+    rng = np.random.default_rng(3)
+    pl = rng.exponential(2.0, size=(zmax + 1, n // 2)).astype(np.float32)
+    bits = pl.view(np.uint32) & np.uint32(0xFFFF0000)
+    pl_bf = bits.view(np.float32)                     # values exactly representable in BF16
+    s = _search(n, zmax, 16, 1024, max_harm=4, thr=(9.0, 14.0, 22.0), max_peaks=1 << 14)
+    s.plane.copy_(torch.from_numpy(pl_bf.ravel()))
+    s.find_peaks()
+    torch.cuda.synchronize()
+    want, _ = oracle.peaks_f32(pl_bf, zmax, 4, (9.0, 14.0, 22.0))
+    _peaks_equal(s.peak_list(), want)
+
+
+# ------------------------------------------------------------------ full size, sampled
+@pytest.fixture(scope="module")
+def pulse_train_case():
+    w = synth.pulse_train_workload()
+    s = _search(w.n, w.zmax, w.taps, w.seg_len, max_harm=1, thr=(40.0,), max_peaks=1 << 16)
+    s.search(_to_dev(w.series))
+    xh = s.spectrum(_to_dev(w.series))
+    torch.cuda.synchronize()
+    return w, s, xh.cpu().numpy().view(np.complex64).astype(np.complex128)
+
+
+def test_full_size_spectrum(pulse_train_case):
+    w, s, xh = pulse_train_case
+    ref, s2 = oracle.spectrum(w.series)
+    assert np.abs(xh - ref).max() <= 2e-6 * np.abs(ref).max() + 2e-5
+    assert abs(s.sigma2.item() - s2) <= 1e-5 * s2
+
+
+def test_full_size_plane_sampled(pulse_train_case):
+    """N = 2^23, 85 templates, 256 taps, 8192-bin segments, in the launch configuration the
+    benchmark times: sampled cells (random, segment edges, the ragged tail, each train's
+    fundamental) against the oracle evaluated cell by cell on the same spectrum."""
+    w, s, xh = pulse_train_case
+    K, nb, L = w.K, w.nb, w.seg_len - w.taps + 1
+    rng = np.random.default_rng(7)
+    zi = list(rng.integers(0, K, 3000))
+    r = list(rng.integers(0, nb, 3000))
+    for j in (0, 1, 2, 100, nb // L - 1, nb // L):    # segment starts and ends
+        for t in (0, 1, L - 2, L - 1):
+            rr = j * L + t
+            if 0 <= rr < nb:
+                zi += [0, K // 2, K - 1]
+                r += [rr] * 3
+    for rr in range(nb - 5, nb):                      # the ragged tail
+        zi += [0, K - 1]
+        r += [rr] * 2
+    for tr in w.trains:
+        i0 = int(np.clip(round((tr.z0 + w.zmax) / 2), 0, K - 1))
+        for dr in range(-2, 3):
+            zi.append(i0)
+            r.append(int(np.clip(round(tr.r0) + dr, 0, nb - 1)))
+    zi = np.array(zi)
+    r = np.array(r)
+    T, _ = oracle.templates(w.zmax, w.taps)
+    ref = oracle.plane_cells(xh, w.zmax, w.taps, T, zi, r)
+    plane = s.plane_2d()
+    idx = torch.from_numpy(zi * nb + r).cuda()
+    got = plane.reshape(-1)[idx].cpu().numpy().astype(np.float64)
+    assert _floor_err(got, ref) <= 1e-5
+    # the whole-plane noise law: mean power 2 (chi^2, 2 dof) away from injected signals
+    assert abs(float(plane.double().mean().item()) - 2.0) < 0.1
