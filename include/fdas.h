@@ -177,6 +177,34 @@ fdas_status fdas_get_templates(fdas_plan_t plan, float *d_out, void *stream);
  */
 fdas_status fdas_device_status(fdas_plan_t plan, int32_t *bits, int clear);
 
+/* Per-stage device times of profiled calls (CUDA events on the caller's stream). */
+typedef struct {
+    int64_t calls;          /* entry-point calls that launched work since the last reset        */
+    int64_t launches;       /* libfdas kernels launched by those calls                          */
+    int64_t n_timed[4];     /* timed launch groups per stage: spectrum, segments, correlate, peaks */
+    double  ms[4];          /* their summed event times in milliseconds                         */
+} fdas_profile;
+
+/* Stage indices of fdas_profile.ms / n_timed. */
+#define FDAS_STAGE_SPECTRUM  0   /* K1: long real FFT + normalisation                            */
+#define FDAS_STAGE_SEGMENTS  1   /* K2: segment FFTs                                              */
+#define FDAS_STAGE_CORRELATE 2   /* K3: multiply, inverse FFT, |.|^2, overlap discard            */
+#define FDAS_STAGE_PEAKS     3   /* K4: harmonic sums and peak list                               */
+
+/*
+ * Turn per-stage timing on (enable != 0) or off.  Enabling creates CUDA events (plan-owned)
+ * so that every later stage launch is bracketed by an event pair on its stream; at most
+ * 512 launch groups per stage are timed between reads.  Launch counting is always on.
+ * Errors: FDAS_E_INVALID, FDAS_E_CUDA.
+ */
+fdas_status fdas_profile_enable(fdas_plan_t plan, int enable);
+
+/*
+ * Synchronise the device, add up the recorded event pairs into *out, and reset the
+ * counters when reset != 0.  Errors: FDAS_E_INVALID, FDAS_E_CUDA.
+ */
+fdas_status fdas_profile_read(fdas_plan_t plan, fdas_profile *out, int reset);
+
 /* Text of the last CUDA error seen by this plan ("" if none).  Host only. */
 const char *fdas_last_error(fdas_plan_t plan);
 

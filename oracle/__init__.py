@@ -176,7 +176,8 @@ def _peaks(fn, plane_arr, zmax, max_harm, thr, max_out, pdtype):
     K, nb = plane_arr.shape
     if K != zmax + 1:
         raise ValueError("plane rows must be zmax + 1")
-    thr = np.zeros(5, dtype=np.float64) + np.asarray(thr, dtype=np.float64)
+    thr = list(np.atleast_1d(np.asarray(thr, dtype=np.float64)))
+    thr = np.array((thr + [thr[-1]] * 5)[:5], dtype=np.float64)   # one threshold per level
     cap = max(int(max_out), 1)
     h = np.empty(cap, np.int32)
     zi = np.empty(cap, np.int32)

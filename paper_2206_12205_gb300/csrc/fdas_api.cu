@@ -161,6 +161,7 @@ fdas_status fdas_spectrum(fdas_plan_t plan, const float *d_series, void *d_works
     if (fdas_status s = ready(p)) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(d_workspace);
+    p->prof.calls++;
     cudaError_t e = fdas::launch_spectrum(*p, d_series, ws, st);
     if (e == cudaSuccess) e = fdas::launch_apply_scale(*p, ws, d_xhat, d_sigma2, st);
     return record(p, e);
@@ -173,6 +174,7 @@ fdas_status fdas_plane(fdas_plan_t plan, const float *d_xhat, void *d_workspace,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(d_workspace);
     const float2 *x = reinterpret_cast<const float2 *>(d_xhat);
+    p->prof.calls++;
     cudaError_t e;
     if (plane_is_bf16(p))
         e = fdas::launch_plane_bf16(*p, x, nullptr, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
@@ -188,6 +190,7 @@ fdas_status fdas_peaks(fdas_plan_t plan, const void *d_plane, void *d_workspace,
     Plan *p = P(plan);
     if (fdas_status s = ready(p)) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    p->prof.calls++;
     cudaError_t e = fdas::launch_peaks(*p, d_plane, plane_is_bf16(p), static_cast<char *>(d_workspace), d_peaks,
                                        d_npeaks, 0u, st);
     return record(p, e);
@@ -201,6 +204,7 @@ fdas_status fdas_search(fdas_plan_t plan, const float *d_series, void *d_workspa
     if (fdas_status s = ready(p)) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(d_workspace);
+    p->prof.calls++;
     cudaError_t e = fdas::launch_spectrum(*p, d_series, ws, st);
     const float2 *x = reinterpret_cast<const float2 *>(ws + p->ws_x);
     const float *scale = reinterpret_cast<const float *>(ws + p->ws_scale + 8);
@@ -234,6 +238,53 @@ fdas_status fdas_device_status(fdas_plan_t plan, int32_t *bits, int clear) {
     return record(p, e);
 }
 
+fdas_status fdas_profile_enable(fdas_plan_t plan, int enable) {
+    if (!plan) return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    fdas::Profiler &pr = p->prof;
+    if (enable && !pr.on) {
+        for (int s = 0; s < fdas::PROF_STAGES; s++)
+            for (int i = 0; i < fdas::PROF_CAP; i++)
+                for (int k = 0; k < 2; k++) {
+                    if (pr.ev[s][i][k]) continue;
+                    cudaError_t e = cudaEventCreate(&pr.ev[s][i][k]);
+                    if (e != cudaSuccess) return record(p, e);
+                }
+        for (int s = 0; s < fdas::PROF_STAGES; s++) pr.n[s] = 0;
+    }
+    pr.on = enable != 0;
+    return FDAS_OK;
+}
+
+fdas_status fdas_profile_read(fdas_plan_t plan, fdas_profile *out, int reset) {
+    if (!plan || !out) return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    fdas::Profiler &pr = p->prof;
+    std::memset(out, 0, sizeof(*out));
+    out->calls = pr.calls;
+    out->launches = pr.launches;
+    if (pr.n[0] + pr.n[1] + pr.n[2] + pr.n[3] > 0) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return record(p, e);
+        for (int s = 0; s < fdas::PROF_STAGES; s++) {
+            double acc = 0.0;
+            for (int i = 0; i < pr.n[s]; i++) {
+                float ms = 0.f;
+                e = cudaEventElapsedTime(&ms, pr.ev[s][i][0], pr.ev[s][i][1]);
+                if (e != cudaSuccess) return record(p, e);
+                acc += ms;
+            }
+            out->ms[s] = acc;
+            out->n_timed[s] = pr.n[s];
+        }
+    }
+    if (reset) {
+        pr.calls = pr.launches = 0;
+        for (int s = 0; s < fdas::PROF_STAGES; s++) pr.n[s] = 0;
+    }
+    return FDAS_OK;
+}
+
 const char *fdas_last_error(fdas_plan_t plan) {
     if (!plan) return "";
     return P(plan)->last_error.c_str();
@@ -252,6 +303,10 @@ void fdas_destroy(fdas_plan_t plan) {
         cudaFree(p->d_Gbf_lo);
         cudaFree(p->d_status);
     }
+    for (int s = 0; s < fdas::PROF_STAGES; s++)
+        for (int i = 0; i < fdas::PROF_CAP; i++)
+            for (int k = 0; k < 2; k++)
+                if (p->prof.ev[s][i][k]) cudaEventDestroy(p->prof.ev[s][i][k]);
     delete static_cast<fdas_plan_s *>(plan);
 }
 

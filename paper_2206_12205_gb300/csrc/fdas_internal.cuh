@@ -16,6 +16,25 @@ constexpr int TW_MAX = 8192;
 // Two-level twiddle split for the long FFT: W_N^e = hi[e >> TW_LO_BITS] * lo[e & mask].
 constexpr int TW_LO_BITS = 13;
 
+// Per-stage CUDA-event timing (fdas_profile_enable / fdas_profile_read).
+constexpr int PROF_STAGES = 4;
+constexpr int PROF_CAP = 512;
+struct Profiler {
+    bool on = false;
+    cudaEvent_t ev[PROF_STAGES][PROF_CAP][2] = {};
+    int n[PROF_STAGES] = {};
+    int64_t calls = 0, launches = 0;
+    void begin(int stage, cudaStream_t st) {
+        if (on && n[stage] < PROF_CAP) cudaEventRecord(ev[stage][n[stage]][0], st);
+    }
+    void end(int stage, cudaStream_t st) {
+        if (on && n[stage] < PROF_CAP) {
+            cudaEventRecord(ev[stage][n[stage]][1], st);
+            n[stage]++;
+        }
+    }
+};
+
 struct Plan {
     fdas_config cfg;
     int64_t N, nb, n_seg;
@@ -41,6 +60,7 @@ struct Plan {
     int32_t *d_status;     // sticky device status word
     bool templates_ready;
     std::string last_error;
+    mutable Profiler prof;
 };
 
 // Peak tiles: one tile = one (level, row, r-chunk).  Chunks hold PEAK_TILE cells.

@@ -153,6 +153,8 @@ cudaError_t launch_spectrum(const Plan &p, const float *d_series, char *ws, cuda
     double *partial = reinterpret_cast<double *>(ws + p.ws_part);
     double *sigma2 = reinterpret_cast<double *>(ws + p.ws_scale);
     float *scale = reinterpret_cast<float *>(ws + p.ws_scale + 8);
+    p.prof.begin(FDAS_STAGE_SPECTRUM, st);
+    p.prof.launches += 3;
     cudaError_t e = cudaErrorInvalidValue;
     switch (p.M1) {
         case 32: e = run_pass_a<32>(p, z, B, st); break;
@@ -180,6 +182,7 @@ cudaError_t launch_spectrum(const Plan &p, const float *d_series, char *ws, cuda
     }
     if (e != cudaSuccess) return e;
     k1_finalize<<<1, 256, 0, st>>>(partial, p.M1 / 2, p.nb, p.cfg.sigma2, sigma2, scale);
+    p.prof.end(FDAS_STAGE_SPECTRUM, st);
     return cudaGetLastError();
 }
 
@@ -189,6 +192,7 @@ cudaError_t launch_apply_scale(const Plan &p, const char *ws, float *d_xhat, dou
     const double *sigma2 = reinterpret_cast<const double *>(ws + p.ws_scale);
     const int64_t blocks = std::min<int64_t>((p.nb + 255) / 256, 152 * 16);
     k1_apply_scale<<<(int)blocks, 256, 0, st>>>(X, scale, reinterpret_cast<float2 *>(d_xhat), p.nb);
+    p.prof.launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && d_sigma2)
         e = cudaMemcpyAsync(d_sigma2, sigma2, sizeof(double), cudaMemcpyDeviceToDevice, st);

@@ -181,6 +181,8 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
     int32_t *tile_count = reinterpret_cast<int32_t *>(ws + p.ws_tiles);
     int64_t *tile_off = reinterpret_cast<int64_t *>(ws + p.ws_tiles + ((sizeof(int32_t) * p.n_tiles + 255) & ~size_t(255)));
     const int64_t n = p.n_tiles;            // < 2^31: one block per tile on a 1-D grid
+    p.prof.begin(FDAS_STAGE_PEAKS, st);
+    p.prof.launches += 3;
     k4_tiles<E, false><<<(unsigned)n, PEAK_THREADS, 0, st>>>(plane, p.nb, p.cfg.zmax, lt, tile_count, tile_off,
                                                              peaks, p.cfg.max_peaks, series);
     cudaError_t e = cudaGetLastError();
@@ -190,6 +192,7 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
     if (e != cudaSuccess) return e;
     k4_tiles<E, true><<<(unsigned)n, PEAK_THREADS, 0, st>>>(plane, p.nb, p.cfg.zmax, lt, tile_count, tile_off,
                                                             peaks, p.cfg.max_peaks, series);
+    p.prof.end(FDAS_STAGE_PEAKS, st);
     return cudaGetLastError();
 }
 

@@ -25,8 +25,9 @@ PRECISIONS = {"fp32": FDAS_FP32, "bf16": FDAS_BF16, "bf16_split": FDAS_BF16_SPLI
 EXPORTED = (
     "fdas_plan", "fdas_plan_get_info", "fdas_make_templates", "fdas_spectrum", "fdas_plane",
     "fdas_peaks", "fdas_search", "fdas_get_templates", "fdas_device_status", "fdas_last_error",
-    "fdas_destroy", "fdas_status_string", "fdas_version",
+    "fdas_destroy", "fdas_status_string", "fdas_version", "fdas_profile_enable", "fdas_profile_read",
 )
+STAGES = ("spectrum", "segments", "correlate", "peaks")
 
 PEAK_DTYPE = np.dtype([("series", "<u4"), ("r", "<u4"), ("zi", "<i2"), ("harm", "u1"),
                        ("pad", "u1"), ("power", "<f4")])
@@ -52,6 +53,11 @@ class _Info(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int64), ("K", ctypes.c_int32), ("seg_valid", ctypes.c_int32),
                 ("n_seg", ctypes.c_int64), ("plane_elem_bytes", ctypes.c_int32), ("plane_bytes", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_size_t), ("cells", ctypes.c_int64)]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int64), ("launches", ctypes.c_int64), ("n_timed", ctypes.c_int64 * 4),
+                ("ms", ctypes.c_double * 4)]
 
 
 _lib = None
@@ -88,6 +94,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "fdas_destroy": (None, [V]),
         "fdas_status_string": (ctypes.c_char_p, [S]),
         "fdas_version": (ctypes.c_int, []),
+        "fdas_profile_enable": (S, [V, ctypes.c_int]),
+        "fdas_profile_read": (S, [V, ctypes.POINTER(_Profile), ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -267,6 +275,19 @@ def fdas_device_status(plan: Plan, clear: bool = True) -> int:
     bits = ctypes.c_int32(0)
     _check(load().fdas_device_status(plan.handle, ctypes.byref(bits), 1 if clear else 0), "fdas_device_status", plan)
     return int(bits.value)
+
+
+def fdas_profile_enable(plan: Plan, enable: bool = True):
+    _check(load().fdas_profile_enable(plan.handle, 1 if enable else 0), "fdas_profile_enable", plan)
+
+
+def fdas_profile_read(plan: Plan, reset: bool = True) -> dict:
+    """Per-stage event times (ms, summed) and launch counts since the last reset."""
+    pr = _Profile()
+    _check(load().fdas_profile_read(plan.handle, ctypes.byref(pr), 1 if reset else 0), "fdas_profile_read", plan)
+    return {"calls": int(pr.calls), "launches": int(pr.launches),
+            "ms": {STAGES[i]: float(pr.ms[i]) for i in range(4)},
+            "n_timed": {STAGES[i]: int(pr.n_timed[i]) for i in range(4)}}
 
 
 def fdas_destroy(plan: Plan):
