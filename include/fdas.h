@@ -145,6 +145,29 @@ fdas_status fdas_plane(fdas_plan_t plan, const float *d_xhat, void *d_workspace,
                        void *d_plane, void *stream);
 
 /*
+ * fdas_plane for callers that must not allocate device memory at call time (no counterpart
+ * in the paper).  Such callers include code running while a CUDA stream is being captured
+ * into a graph, real-time pipelines that reserve all device memory at start-up and forbid
+ * allocation later, and hosts whose own allocator owns the device's memory.  The result is
+ * the same plane as fdas_plane; the segment spectra live in a library-owned static device
+ * array of FDAS_STATIC_SCRATCH_BYTES (reserved on every GPU that loads the library, until the
+ * process exits) instead of the workspace.
+ *   - Only FDAS_FP32 plans with n_seg * S * 8 <= FDAS_STATIC_SCRATCH_BYTES are accepted
+ *     (e.g. S = 8192 up to N = 2^23); larger ones return FDAS_E_UNSUPPORTED with the sizes in
+ *     fdas_last_error.
+ *   - The first call on a device looks up the array's device address (once per device, with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU (different streams,
+ *     or different plans at once) race on it.  Each call overwrites the whole part it reads,
+ *     so no clearing is needed between calls.
+ *   - Allocates nothing; the plan's templates must exist (fdas_make_templates, which does
+ *     allocate, called earlier), else FDAS_E_STATE.
+ * Errors: FDAS_E_INVALID, FDAS_E_STATE, FDAS_E_UNSUPPORTED, FDAS_E_CUDA.
+ */
+#define FDAS_STATIC_SCRATCH_BYTES ((size_t)40 << 20)
+fdas_status fdas_plane_static(fdas_plan_t plan, const float *d_xhat, void *d_plane, void *stream);
+
+/*
  * Harmonic sums and peak list of a plane [Sec. 2.1]: for H = 1, 2, 4, .. max_harm,
  * S_H(r, i) = sum_{h=1..H} P(h r, i_h) with z_{i_h} = h z_i (summed in FP32 in the order
  * h = 1..H), defined where |H z_i| <= zmax and H r < Nb.  A cell is a peak when

@@ -9,6 +9,6 @@ from . import build  # noqa: F401
 from .fdas import (  # noqa: F401
     FDAS_BF16, FDAS_BF16_SPLIT, FDAS_FP32, PEAK_DTYPE, PRECISIONS, FdasError, Plan, Search,
     fdas_destroy, fdas_device_status, fdas_get_templates, fdas_make_templates, fdas_peaks,
-    fdas_plan, fdas_plane, fdas_profile_enable, fdas_profile_read, fdas_search, fdas_spectrum, fdas_version, load, make_config,
+    fdas_plan, fdas_plane, fdas_plane_static, fdas_profile_enable, fdas_profile_read, fdas_search, fdas_spectrum, fdas_version, load, make_config,
     peaks_to_numpy, status_string,
 )

@@ -89,6 +89,9 @@ cudaError_t launch_apply_scale(const Plan &p, const char *ws, float *d_xhat, dou
                                cudaStream_t st);
 cudaError_t launch_plane_fp32(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
                               float *d_plane, cudaStream_t st);
+// The same kernels with the segment spectra (n_seg * S complex64) at d_yhat instead of the workspace.
+cudaError_t launch_plane_fp32_scratch(const Plan &p, const float2 *d_x, const float *d_scale, float2 *d_yhat,
+                                      float *d_plane, cudaStream_t st);
 cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
                               __nv_bfloat16 *d_plane, cudaStream_t st);
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,

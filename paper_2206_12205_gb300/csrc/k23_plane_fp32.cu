@@ -112,4 +112,15 @@ cudaError_t launch_plane_fp32(const Plan &p, const float2 *d_x, const float *d_s
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_plane_fp32_scratch(const Plan &p, const float2 *d_x, const float *d_scale, float2 *d_yhat,
+                                      float *d_plane, cudaStream_t st) {
+    switch (p.S) {
+        case 1024: return run_plane<1024>(p, d_x, d_scale, d_yhat, d_plane, st);
+        case 2048: return run_plane<2048>(p, d_x, d_scale, d_yhat, d_plane, st);
+        case 4096: return run_plane<4096>(p, d_x, d_scale, d_yhat, d_plane, st);
+        case 8192: return run_plane<8192>(p, d_x, d_scale, d_yhat, d_plane, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace fdas

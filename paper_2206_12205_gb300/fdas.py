@@ -26,7 +26,9 @@ EXPORTED = (
     "fdas_plan", "fdas_plan_get_info", "fdas_make_templates", "fdas_spectrum", "fdas_plane",
     "fdas_peaks", "fdas_search", "fdas_get_templates", "fdas_device_status", "fdas_last_error",
     "fdas_destroy", "fdas_status_string", "fdas_version", "fdas_profile_enable", "fdas_profile_read",
+    "fdas_plane_static",
 )
+STATIC_SCRATCH_BYTES = 40 << 20
 STAGES = ("spectrum", "segments", "correlate", "peaks")
 
 PEAK_DTYPE = np.dtype([("series", "<u4"), ("r", "<u4"), ("zi", "<i2"), ("harm", "u1"),
@@ -96,6 +98,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "fdas_version": (ctypes.c_int, []),
         "fdas_profile_enable": (S, [V, ctypes.c_int]),
         "fdas_profile_read": (S, [V, ctypes.POINTER(_Profile), ctypes.c_int]),
+        "fdas_plane_static": (S, [V, V, V, V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -238,6 +241,18 @@ def fdas_plane(plan: Plan, xhat, workspace, plane, stream=None):
             _dev_ptr(plane, "plane", plan.plane_dtype(), plan.info.plane_bytes),
             _stream_ptr(stream))
     _check(load().fdas_plane(*args), "fdas_plane", plan)
+
+
+def fdas_plane_static(plan: Plan, xhat, plane, stream=None):
+    """fdas_plane without a workspace: for callers that may not allocate device memory at call
+    time (stream capture, pre-reserved real-time pipelines, hosts owning the memory pool).
+    Its scratch is a library-owned static device array; concurrent calls race on it."""
+    torch = _torch()
+    args = (plan.handle,
+            _dev_ptr(xhat, "xhat", torch.float32, 8 * plan.info.nb),
+            _dev_ptr(plane, "plane", plan.plane_dtype(), plan.info.plane_bytes),
+            _stream_ptr(stream))
+    _check(load().fdas_plane_static(*args), "fdas_plane_static", plan)
 
 
 def fdas_peaks(plan: Plan, plane, workspace, peaks, npeaks, stream=None):
