@@ -89,7 +89,7 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     p->M2 = 1 << (lgM / 2);
     const fdas::LevelTable lt = fdas::make_levels(*p);
     p->n_levels = lt.n_levels;
-    p->n_tiles = lt.lev[lt.n_levels - 1].tile0 + (int64_t)lt.lev[lt.n_levels - 1].rows * lt.lev[lt.n_levels - 1].chunks;
+    p->n_units = lt.lev[lt.n_levels - 1].unit0 + (int64_t)lt.lev[lt.n_levels - 1].rows * lt.lev[lt.n_levels - 1].chunks;
     p->n_part = p->M1 / 2;
     // workspace layout
     size_t off = 0;
@@ -98,7 +98,11 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     p->ws_part = off;  off = align_up(off + sizeof(double) * (size_t)p->n_part);
     p->ws_scale = off; off = align_up(off + 16);
     p->ws_y = off;     off = align_up(off + sizeof(float2) * (size_t)p->n_seg * p->S);
-    p->ws_tiles = off; off = align_up(off + align_up(sizeof(int32_t) * (size_t)p->n_tiles) + sizeof(int64_t) * (size_t)p->n_tiles);
+    const size_t n_scan_blocks = (size_t)((p->n_units + fdas::PEAK_SCAN_BLOCK - 1) / fdas::PEAK_SCAN_BLOCK);
+    p->ws_ucount = off; off = align_up(off + sizeof(int32_t) * (size_t)p->n_units);
+    p->ws_uoff = off;   off = align_up(off + sizeof(int32_t) * (size_t)p->n_units);
+    p->ws_umask = off;  off = align_up(off + sizeof(uint32_t) * (fdas::PEAK_CHUNK / 32) * (size_t)p->n_units);
+    p->ws_ublock = off; off = align_up(off + sizeof(int64_t) * n_scan_blocks);
     p->ws_bytes = off;
     p->device = -1;
     *plan = p;

@@ -43,11 +43,11 @@ struct Plan {
     // long real FFT split: M = N/2 = M1 * M2 (four-step)
     int64_t M;
     int M1, M2;
-    // harmonic-sum levels and peak tiles
+    // harmonic-sum levels and peak units (level, row, chunk)
     int n_levels;
-    int64_t n_tiles;
+    int64_t n_units;
     // workspace layout (byte offsets inside the caller's workspace)
-    size_t ws_x, ws_tmp, ws_part, ws_scale, ws_y, ws_tiles, ws_bytes;
+    size_t ws_x, ws_tmp, ws_part, ws_scale, ws_y, ws_ucount, ws_uoff, ws_umask, ws_ublock, ws_bytes;
     int n_part;
     // plan-owned device memory
     int device;
@@ -63,16 +63,19 @@ struct Plan {
     mutable Profiler prof;
 };
 
-// Peak tiles: one tile = one (level, row, r-chunk).  Chunks hold PEAK_TILE cells.
-constexpr int PEAK_TILE = 2048;
-constexpr int PEAK_THREADS = 256;
+// Peak search geometry: tiles of PEAK_ROWS rows x PEAK_CHUNK bins; a unit is one
+// (level, row, chunk) with a count and a PEAK_CHUNK-bit mask; the offset scan works on blocks
+// of PEAK_SCAN_BLOCK units.
+constexpr int PEAK_ROWS = 8;
+constexpr int PEAK_CHUNK = 512;
+constexpr int PEAK_SCAN_BLOCK = 4096;
 
 struct LevelDesc {
     int H;          // harmonic count
     int i_lo, rows; // valid rows [i_lo, i_lo + rows)
     int64_t rmax;   // last valid r (H r < nb)
     int64_t chunks; // r-chunks per row
-    int64_t tile0;  // first tile index of this level
+    int64_t unit0;  // first unit index of this level
     float thr;
 };
 struct LevelTable {

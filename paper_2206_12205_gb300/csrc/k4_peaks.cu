@@ -6,15 +6,20 @@
 // summed in FP32 in the order h = 1..H (BF16 planes are widened by placing the 16 stored
 // bits in the top half of a float, the paper's quick cast of Sec. 3.1), defined where
 // |H z_i| <= zmax and H r < Nb.  Peak: S_H > thr and a 3x3 local maximum (strictly above
-// earlier neighbours in row-major (i, r) order, >= later ones).
+// earlier neighbours in row-major (i, r) order, >= later ones, undefined neighbours ignored).
 //
-// The list comes out in (H, i, r) order without a sort: the work is cut into tiles
-// (level, row, chunk of PEAK_TILE bins), enumerated in that order;
-//   pass 1 counts the peaks of every tile,
-//   pass 2 (one CTA) turns the counts into exclusive offsets and the total,
-//   pass 3 recomputes each tile and writes its peaks at offset + rank within the tile.
-// A tile stages S_H for its row and the two neighbouring rows, bins r0-1 .. r1+1, in
-// shared memory; undefined neighbours hold -inf and never block a peak.
+// The defined regions nest (level 2H's lies inside level H's), so one pass builds every level
+// in place: a tile of RB rows x CB bins (plus a one-cell halo) is loaded once into shared
+// memory as S_1 = P, peaks of level 1 are detected, then S_2 = S_1 + P(2r, i_2) is formed in
+// place (cells outside level 2's region become -inf), and so on up to max_harm.  The running
+// sum adds the terms in the order h = 1..H, so every S_H is bit-identical to the direct sum.
+//
+// Output order (H, i, r) without a sort: a "unit" is (level, row, chunk of CB bins), units
+// are numbered in that order, and
+//   pass A (k4_detect) writes each unit's peak count and, when non-zero, its CB-bit mask;
+//   pass B (k4_scan_blocks, k4_scan_top) turns the counts into exclusive offsets + total;
+//   pass C (k4_emit, one warp per unit, empty units skipped) recomputes S_H at the few
+//   marked cells and writes the records at offset + rank.
 #include <cmath>
 
 #include "fdas_internal.cuh"
@@ -22,6 +27,12 @@
 namespace fdas {
 
 namespace {
+
+constexpr int RB = PEAK_ROWS;            // rows per tile (one warp each)
+constexpr int CB = PEAK_CHUNK;           // bins per tile / unit
+constexpr int SW = CB + 2;               // staged row width with the halo
+constexpr int WORDS = CB / 32;           // mask words per unit
+constexpr int SCAN_BLOCK = PEAK_SCAN_BLOCK;
 
 __device__ __forceinline__ float ld_plane(const float *p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float ld_plane(const __nv_bfloat16 *p, int64_t i) {
@@ -40,137 +51,222 @@ __device__ __forceinline__ float harm_sum(const E *plane, int64_t nb, int zmax, 
     return s;
 }
 
-struct TileRef {
-    int lev, row;
-    int64_t r0, r1;
+__device__ __forceinline__ bool row_in_level(int i, int K, int zmax, int H) {
+    const int z = -zmax + 2 * i;
+    return i >= 0 && i < K && abs(H * z) <= zmax;
+}
+
+template <typename E>
+__global__ void __launch_bounds__(RB * 32) k4_detect(const E *__restrict__ plane, int64_t nb, int zmax, int K,
+                                                     LevelTable lt, int n_rb, int32_t *__restrict__ unit_count,
+                                                     uint32_t *__restrict__ unit_mask) {
+    __shared__ float S[RB + 2][SW];
+    const int tile = blockIdx.x;
+    const int rb = tile % n_rb;                    // row blocks of one chunk run side by side (halo rows hit L2)
+    const int64_t chunk = tile / n_rb;
+    const int i0 = rb * RB;
+    const int64_t r0 = chunk * CB;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = i0 + warp;
+
+    // level 1: S_1 = P on rows i0-1 .. i0+RB, bins r0-1 .. r0+CB
+    for (int idx = threadIdx.x; idx < (RB + 2) * SW; idx += RB * 32) {
+        const int ri = idx / SW, c = idx - ri * SW;
+        const int i = i0 - 1 + ri;
+        const int64_t r = r0 - 1 + c;
+        S[ri][c] = (i >= 0 && i < K && r >= 0 && r < nb) ? ld_plane(plane, (int64_t)i * nb + r) : -INFINITY;
+    }
+    __syncthreads();
+
+    for (int l = 0; l < lt.n_levels; l++) {
+        const LevelDesc &d = lt.lev[l];
+        const int H = d.H;
+        if (r0 > d.rmax) break;                                     // regions nest: nothing further
+        const int rlo = max(i0 - 1, d.i_lo), rhi = min(i0 + RB, d.i_lo + d.rows - 1);
+        if (rlo > rhi) break;
+        if (l > 0) {
+            // S_H = S_{H/2} + sum_{h = H/2+1 .. H} P(h r, i_h) inside level H's region, -inf outside
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < (RB + 2) * SW; idx += RB * 32) {
+                const int ri = idx / SW, c = idx - ri * SW;
+                const int i = i0 - 1 + ri;
+                const int64_t r = r0 - 1 + c;
+                float s = -INFINITY;
+                if (row_in_level(i, K, zmax, H) && r >= 0 && r <= d.rmax) {
+                    s = S[ri][c];
+                    const int z = -zmax + 2 * i;
+                    for (int h = H / 2 + 1; h <= H; h++)
+                        s = __fadd_rn(s, ld_plane(plane, (int64_t)((h * z + zmax) >> 1) * nb + (int64_t)h * r));
+                }
+                S[ri][c] = s;
+            }
+            __syncthreads();
+        }
+        // detection: warp `warp` owns row i0 + warp; lane handles bins r0 + lane + 32 e
+        if (row_in_level(row, K, zmax, H)) {
+            int cnt = 0;
+            uint32_t words[WORDS];
+#pragma unroll
+            for (int e = 0; e < WORDS; e++) {
+                const int c = 1 + lane + 32 * e;
+                const int64_t r = r0 + lane + 32 * e;
+                bool pk = false;
+                if (r <= d.rmax) {
+                    const float v = S[warp + 1][c];
+                    if (v > d.thr) {
+                        pk = v > S[warp][c - 1] && v > S[warp][c] && v > S[warp][c + 1] && v > S[warp + 1][c - 1] &&
+                             v >= S[warp + 1][c + 1] && v >= S[warp + 2][c - 1] && v >= S[warp + 2][c] &&
+                             v >= S[warp + 2][c + 1];
+                    }
+                }
+                words[e] = __ballot_sync(0xffffffffu, pk);
+                cnt += __popc(words[e]);
+            }
+            const int64_t u = d.unit0 + (int64_t)(row - d.i_lo) * d.chunks + chunk;
+            if (lane == 0) unit_count[u] = cnt;
+            if (cnt > 0 && lane < WORDS) {
+                uint32_t w = 0;
+#pragma unroll
+                for (int e = 0; e < WORDS; e++)
+                    if (e == lane) w = words[e];
+                unit_mask[u * WORDS + lane] = w;
+            }
+        }
+    }
+}
+
+// First-level scan: exclusive prefix of the counts inside each block of SCAN_BLOCK units.
+__global__ void __launch_bounds__(1024) k4_scan_blocks(const int32_t *__restrict__ cnt, int64_t n,
+                                                       int32_t *__restrict__ off, int64_t *__restrict__ block_sum) {
+    __shared__ int32_t warp_tot[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x * 4;
+    int32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = (base + k < n) ? cnt[base + k] : 0;
+    const int32_t sum = v[0] + v[1] + v[2] + v[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t t = warp_tot[lane], ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        warp_tot[lane] = ti - t;                 // exclusive warp offsets
+        if (lane == 31) block_sum[blockIdx.x] = ti;
+    }
+    __syncthreads();
+    int32_t run = warp_tot[warp] + incl - sum;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (base + k < n) off[base + k] = run;
+        run += v[k];
+    }
+}
+
+// Second level (one CTA, fixed order): block offsets in place, total count, overflow flag.
+__global__ void __launch_bounds__(1024) k4_scan_top(int64_t *__restrict__ block_sum, int64_t nblocks,
+                                                    int32_t *__restrict__ npeaks, int max_peaks,
+                                                    int32_t *__restrict__ status) {
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t b0 = 0; b0 < nblocks; b0 += 1024) {
+        const int64_t b = b0 + threadIdx.x;
+        const int64_t v = (b < nblocks) ? block_sum[b] : 0;
+        int64_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        int64_t before = carry;
+        for (int w = 0; w < warp; w++) before += warp_tot[w];
+        if (b < nblocks) block_sum[b] = before + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int64_t total = carry;
+        *npeaks = (int32_t)(total < 0x7fffffff ? total : 0x7fffffff);
+        if (total > max_peaks) atomicOr(status, FDAS_DEV_PEAK_OVERFLOW);
+    }
+}
+
+struct UnitRef {
+    int l, row;
+    int64_t chunk;
 };
 
-__device__ __forceinline__ TileRef locate(const LevelTable &lt, int64_t tile) {
+__device__ __forceinline__ UnitRef unit_of(const LevelTable &lt, int64_t u) {
     int l = 0;
 #pragma unroll
     for (int k = 1; k < 5; k++)
-        if (k < lt.n_levels && tile >= lt.lev[k].tile0) l = k;
+        if (k < lt.n_levels && u >= lt.lev[k].unit0) l = k;
     const LevelDesc &d = lt.lev[l];
-    const int64_t local = tile - d.tile0;
-    TileRef t;
-    t.lev = l;
-    t.row = d.i_lo + (int)(local / d.chunks);
-    t.r0 = (local % d.chunks) * PEAK_TILE;
-    t.r1 = min(t.r0 + PEAK_TILE - 1, d.rmax);
-    return t;
+    const int64_t local = u - d.unit0;
+    UnitRef ref;
+    ref.l = l;
+    ref.row = d.i_lo + (int)(local / d.chunks);
+    ref.chunk = local % d.chunks;
+    return ref;
 }
 
-template <typename E, bool WRITE>
-__global__ void __launch_bounds__(PEAK_THREADS) k4_tiles(const E *__restrict__ plane, int64_t nb, int zmax, LevelTable lt,
-                                                         int32_t *__restrict__ tile_count,
-                                                         const int64_t *__restrict__ tile_off,
-                                                         fdas_peak *__restrict__ out, int max_peaks, uint32_t series) {
-    constexpr int W = PEAK_TILE + 2;
-    constexpr int PER = PEAK_TILE / PEAK_THREADS;
-    __shared__ float s[3][W];
-    __shared__ int warp_tot[PEAK_THREADS / 32];
-    const int64_t tile = blockIdx.x;
-    const TileRef tr = locate(lt, tile);
-    const LevelDesc &d = lt.lev[tr.lev];
-    const int H = d.H;
-    const int ncol = (int)(tr.r1 - tr.r0 + 3);
-    for (int di = 0; di < 3; di++) {
-        const int ii = tr.row - 1 + di;
-        const bool row_ok = ii >= d.i_lo && ii < d.i_lo + d.rows;
-        for (int c = threadIdx.x; c < ncol; c += PEAK_THREADS) {
-            const int64_t r = tr.r0 - 1 + c;
-            s[di][c] = (row_ok && r >= 0 && r <= d.rmax) ? harm_sum(plane, nb, zmax, H, ii, r) : -INFINITY;
+// One warp per non-empty unit: records at (block offset + in-block offset + rank).
+template <typename E>
+__global__ void __launch_bounds__(256) k4_emit(const E *__restrict__ plane, int64_t nb, int zmax, LevelTable lt,
+                                               int64_t n_units, const int32_t *__restrict__ unit_count,
+                                               const int32_t *__restrict__ unit_off,
+                                               const int64_t *__restrict__ block_off,
+                                               const uint32_t *__restrict__ unit_mask, fdas_peak *__restrict__ out,
+                                               int max_peaks, uint32_t series) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp_id; u < n_units; u += n_warps) {
+        const int32_t cnt = unit_count[u];
+        if (cnt == 0) continue;                                  // warp-uniform
+        const int64_t base = block_off[u / SCAN_BLOCK] + unit_off[u];
+        const UnitRef ref = unit_of(lt, u);
+        const int H = lt.lev[ref.l].H;
+        const uint32_t w = lane < WORDS ? unit_mask[u * WORDS + lane] : 0u;
+        int incl = __popc(w);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
-    }
-    __syncthreads();
-    const float thr = d.thr;
-    unsigned mask = 0;
-    int cnt = 0;
-    const int c0 = threadIdx.x * PER;
-#pragma unroll
-    for (int e = 0; e < PER; e++) {
-        const int c = c0 + e + 1;
-        if (tr.r0 + c0 + e > tr.r1) break;
-        const float v = s[1][c];
-        if (!(v > thr)) continue;
-        // earlier neighbours: previous row (all three) and the left cell: strictly greater
-        bool pk = v > s[0][c - 1] && v > s[0][c] && v > s[0][c + 1] && v > s[1][c - 1];
-        // later neighbours: right cell and next row: greater or equal
-        pk = pk && v >= s[1][c + 1] && v >= s[2][c - 1] && v >= s[2][c] && v >= s[2][c + 1];
-        if (pk) {
-            mask |= 1u << e;
-            cnt++;
+        int64_t pos = base + incl - __popc(w);
+        uint32_t bits = w;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (pos < max_peaks) {
+                const int64_t r = ref.chunk * CB + lane * 32 + b;
+                fdas_peak pk;
+                pk.series = series;
+                pk.r = (uint32_t)r;
+                pk.zi = (int16_t)ref.row;
+                pk.harm = (uint8_t)H;
+                pk.pad = 0;
+                pk.power = harm_sum(plane, nb, zmax, H, ref.row, r);
+                out[pos] = pk;
+            }
+            pos++;
         }
-    }
-    // block-wide exclusive scan of cnt (warp shuffles, then warp totals)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) warp_tot[warp] = incl;
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < PEAK_THREADS / 32; w++) {
-        if (w < warp) before += warp_tot[w];
-        total += warp_tot[w];
-    }
-    const int excl = before + incl - cnt;
-    if (!WRITE) {
-        if (threadIdx.x == 0) tile_count[tile] = total;
-        return;
-    }
-    int64_t pos = tile_off[tile] + excl;
-#pragma unroll
-    for (int e = 0; e < PER; e++) {
-        if (!(mask & (1u << e))) continue;
-        if (pos < max_peaks) {
-            fdas_peak pk;
-            pk.series = series;
-            pk.r = (uint32_t)(tr.r0 + c0 + e);
-            pk.zi = (int16_t)tr.row;
-            pk.harm = (uint8_t)H;
-            pk.pad = 0;
-            pk.power = s[1][c0 + e + 1];
-            out[pos] = pk;
-        }
-        pos++;
-    }
-}
-
-// Exclusive scan of the tile counts (one CTA, fixed order) and the total peak count.
-__global__ void __launch_bounds__(1024) k4_scan(const int32_t *__restrict__ cnt, int64_t n, int64_t *__restrict__ off,
-                                                int32_t *__restrict__ npeaks, int max_peaks,
-                                                int32_t *__restrict__ status) {
-    __shared__ int64_t warp_tot[32];
-    const int64_t per = (n + 1023) / 1024;
-    const int64_t b = threadIdx.x * per, e = min(n, b + per);
-    int64_t sum = 0;
-    for (int64_t k = b; k < e; k++) sum += cnt[k];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int64_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) warp_tot[warp] = incl;
-    __syncthreads();
-    int64_t before = 0, total = 0;
-    for (int w = 0; w < 32; w++) {
-        if (w < warp) before += warp_tot[w];
-        total += warp_tot[w];
-    }
-    int64_t run = before + incl - sum;
-    for (int64_t k = b; k < e; k++) {
-        off[k] = run;
-        run += cnt[k];
-    }
-    if (threadIdx.x == 0) {
-        *npeaks = (int32_t)(total < 0x7fffffff ? total : 0x7fffffff);
-        if (total > max_peaks) atomicOr(status, FDAS_DEV_PEAK_OVERFLOW);
     }
 }
 
@@ -178,20 +274,23 @@ template <typename E>
 cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks, int32_t *npeaks, uint32_t series,
                       cudaStream_t st) {
     const LevelTable lt = make_levels(p);
-    int32_t *tile_count = reinterpret_cast<int32_t *>(ws + p.ws_tiles);
-    int64_t *tile_off = reinterpret_cast<int64_t *>(ws + p.ws_tiles + ((sizeof(int32_t) * p.n_tiles + 255) & ~size_t(255)));
-    const int64_t n = p.n_tiles;            // < 2^31: one block per tile on a 1-D grid
+    int32_t *unit_count = reinterpret_cast<int32_t *>(ws + p.ws_ucount);
+    int32_t *unit_off = reinterpret_cast<int32_t *>(ws + p.ws_uoff);
+    uint32_t *unit_mask = reinterpret_cast<uint32_t *>(ws + p.ws_umask);
+    int64_t *block_off = reinterpret_cast<int64_t *>(ws + p.ws_ublock);
+    const int n_rb = (p.K + RB - 1) / RB;
+    const int64_t chunks1 = lt.lev[0].chunks;
+    const int64_t n_units = p.n_units;
+    const int64_t n_blocks = (n_units + SCAN_BLOCK - 1) / SCAN_BLOCK;
     p.prof.begin(FDAS_STAGE_PEAKS, st);
-    p.prof.launches += 3;
-    k4_tiles<E, false><<<(unsigned)n, PEAK_THREADS, 0, st>>>(plane, p.nb, p.cfg.zmax, lt, tile_count, tile_off,
-                                                             peaks, p.cfg.max_peaks, series);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k4_scan<<<1, 1024, 0, st>>>(tile_count, n, tile_off, npeaks, p.cfg.max_peaks, p.d_status);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k4_tiles<E, true><<<(unsigned)n, PEAK_THREADS, 0, st>>>(plane, p.nb, p.cfg.zmax, lt, tile_count, tile_off,
-                                                            peaks, p.cfg.max_peaks, series);
+    p.prof.launches += 4;
+    k4_detect<E><<<(unsigned)(n_rb * chunks1), RB * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, n_rb, unit_count,
+                                                                  unit_mask);
+    k4_scan_blocks<<<(unsigned)n_blocks, 1024, 0, st>>>(unit_count, n_units, unit_off, block_off);
+    k4_scan_top<<<1, 1024, 0, st>>>(block_off, n_blocks, npeaks, p.cfg.max_peaks, p.d_status);
+    const int64_t emit_blocks = std::min<int64_t>((n_units + 7) / 8, 152 * 16);
+    k4_emit<E><<<(unsigned)emit_blocks, 256, 0, st>>>(plane, p.nb, p.cfg.zmax, lt, n_units, unit_count, unit_off,
+                                                       block_off, unit_mask, peaks, p.cfg.max_peaks, series);
     p.prof.end(FDAS_STAGE_PEAKS, st);
     return cudaGetLastError();
 }
@@ -200,7 +299,7 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
 
 LevelTable make_levels(const Plan &p) {
     LevelTable lt{};
-    int64_t tile0 = 0;
+    int64_t unit0 = 0;
     int n = 0;
     for (int l = 0; l < 5; l++) {
         const int H = 1 << l;
@@ -212,10 +311,10 @@ LevelTable make_levels(const Plan &p) {
         d.i_lo = (p.cfg.zmax - zl) / 2;
         d.rows = zl + 1;
         d.rmax = (p.nb - 1) / H;
-        d.chunks = (d.rmax + 1 + PEAK_TILE - 1) / PEAK_TILE;
-        d.tile0 = tile0;
+        d.chunks = (d.rmax + 1 + PEAK_CHUNK - 1) / PEAK_CHUNK;
+        d.unit0 = unit0;
         d.thr = p.cfg.thr[l];
-        tile0 += (int64_t)d.rows * d.chunks;
+        unit0 += (int64_t)d.rows * d.chunks;
         n++;
     }
     lt.n_levels = n;

@@ -194,10 +194,13 @@ def test_bf16_plane_peaks_quick_cast():
 
 
 # ------------------------------------------------------------------ full size, sampled
+FULL_THR = (40.0, 44.0, 51.0, 64.0, 88.0)   # about one noise peak per harmonic level
+
+
 @pytest.fixture(scope="module")
 def pulse_train_case():
     w = synth.pulse_train_workload()
-    s = _search(w.n, w.zmax, w.taps, w.seg_len, max_harm=1, thr=(40.0,), max_peaks=1 << 16)
+    s = _search(w.n, w.zmax, w.taps, w.seg_len, max_harm=16, thr=FULL_THR, max_peaks=1 << 16)
     s.search(_to_dev(w.series))
     xh = s.spectrum(_to_dev(w.series))
     torch.cuda.synchronize()
@@ -244,3 +247,13 @@ def test_full_size_plane_sampled(pulse_train_case):
     assert _floor_err(got, ref) <= 1e-5
     # the whole-plane noise law: mean power 2 (chi^2, 2 dof) away from injected signals
     assert abs(float(plane.double().mean().item()) - 2.0) < 0.1
+
+
+def test_full_size_peaks_bit_exact(pulse_train_case):
+    """16-harmonic peak list of the full-size plane, bit-exact against the oracle's float
+    given-plane mode, and every injected train's fundamental found near its (r0, z0)."""
+    w, s, _ = pulse_train_case
+    got = s.peak_list()
+    want, cnt = oracle.peaks_f32(s.plane_2d().cpu().numpy(), w.zmax, 16, FULL_THR)
+    assert int(s.npeaks.item()) == cnt
+    _peaks_equal(got, want)
