@@ -70,7 +70,8 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
         if (c.thr[l] != c.thr[l]) return FDAS_E_INVALID;
     if (c.precision != FDAS_FP32 && c.precision != FDAS_BF16 && c.precision != FDAS_BF16_SPLIT)
         return FDAS_E_INVALID;
-    if (c.precision != FDAS_FP32) return FDAS_E_UNSUPPORTED;
+    if (c.precision == FDAS_BF16_SPLIT) return FDAS_E_UNSUPPORTED;
+    if (c.precision == FDAS_BF16 && c.taps > fdas::TC_MAX_TAPS) return FDAS_E_UNSUPPORTED;
 
     fdas_plan_s *p = new (std::nothrow) fdas_plan_s();
     if (!p) return FDAS_E_NOMEM;
@@ -80,8 +81,13 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     p->K = c.zmax + 1;
     p->m = c.taps;
     p->S = c.seg_len;
-    p->logS = ilog2(p->S);
     p->L = p->S - p->m + 1;
+    if (c.precision != FDAS_FP32) {
+        // tensor-core path: 4096-bin segments, stride a multiple of 64 (same plane for any L)
+        p->S = fdas::TC_S_BF16;
+        p->L = (p->S - p->m + 1) / 64 * 64;
+    }
+    p->logS = ilog2(p->S);
     p->n_seg = (p->nb + p->L - 1) / p->L;
     p->M = p->nb;
     const int lgM = ilog2(p->M);
@@ -143,10 +149,13 @@ fdas_status fdas_make_templates(fdas_plan_t plan, void *stream) {
     if (plane_is_bf16(p)) {
         alloc((void **)&p->d_Gbf, sizeof(__nv_bfloat162) * nbank);
         if (p->cfg.precision == FDAS_BF16_SPLIT) alloc((void **)&p->d_Gbf_lo, sizeof(__nv_bfloat162) * nbank);
+        alloc((void **)&p->d_tcF, 2 * 128 * 128);
+        alloc((void **)&p->d_tcTw, sizeof(float2) * 64 * 64);
     }
     alloc((void **)&p->d_status, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = fdas::launch_make_templates(*p, st);
+    if (e == cudaSuccess && plane_is_bf16(p)) e = fdas::launch_prepare_bf16(*p, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return record(p, e);
     p->templates_ready = true;
@@ -305,6 +314,8 @@ void fdas_destroy(fdas_plan_t plan) {
         cudaFree(p->d_G);
         cudaFree(p->d_Gbf);
         cudaFree(p->d_Gbf_lo);
+        cudaFree(p->d_tcF);
+        cudaFree(p->d_tcTw);
         cudaFree(p->d_status);
     }
     for (int s = 0; s < fdas::PROF_STAGES; s++)

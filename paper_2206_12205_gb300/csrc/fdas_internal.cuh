@@ -15,6 +15,9 @@ namespace fdas {
 constexpr int TW_MAX = 8192;
 // Two-level twiddle split for the long FFT: W_N^e = hi[e >> TW_LO_BITS] * lo[e & mask].
 constexpr int TW_LO_BITS = 13;
+// Segment length of the BF16 tensor-core path (64 x 64 four-step DFT) and its largest tap count.
+constexpr int TC_S_BF16 = 4096;
+constexpr int TC_MAX_TAPS = 2048;
 
 // Per-stage CUDA-event timing (fdas_profile_enable / fdas_profile_read).
 constexpr int PROF_STAGES = 4;
@@ -57,6 +60,8 @@ struct Plan {
     float2 *d_G;           // [K][S] FP32 template bank
     __nv_bfloat162 *d_Gbf; // [K][S] BF16 template bank (hi), BF16 precisions
     __nv_bfloat162 *d_Gbf_lo; // [K][S] BF16 residual (lo), split precision
+    void *d_tcF;           // real-ified radix-64 DFT matrix, BF16, K-major operand image (32 KB)
+    float2 *d_tcTw;        // W_4096^{n2 k1}, [k1][n2] (32 KB)
     int32_t *d_status;     // sticky device status word
     bool templates_ready;
     std::string last_error;
@@ -97,6 +102,7 @@ cudaError_t launch_plane_fp32_scratch(const Plan &p, const float2 *d_x, const fl
                                       float *d_plane, cudaStream_t st);
 cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
                               __nv_bfloat16 *d_plane, cudaStream_t st);
+cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st);
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
                          fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st);
 
