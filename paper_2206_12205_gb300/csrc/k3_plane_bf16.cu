@@ -15,9 +15,10 @@
 // where F' is the radix-64 DFT real-ified with re/im interleaved (row 2k+p, column 2n+s), so
 // the real and imaginary parts of one value sit in adjacent TMEM lanes (adjacent threads).
 //
-// One persistent CTA per slot (2 per SM: 97 KB shared memory, 256 of 512 TMEM columns each)
-// walks a contiguous range of (segment, template pair) items, so a segment's spectrum stays in
-// L1.  Every mbarrier wait is bounded; a timeout sets FDAS_DEV_TIMEOUT and the CTA stops
+// B1 and B2 share one shared-memory tile and D1 and D2 one set of TMEM columns: each is
+// rewritten only after the MMA that reads it (or the loads that drain it) has completed.  One
+// persistent CTA per slot (3 per SM: 64 KB shared memory, 128 of 512 TMEM columns each) walks a
+// contiguous range of (segment, template pair) items, so a segment's spectrum stays in L1.  Every mbarrier wait is bounded; a timeout sets FDAS_DEV_TIMEOUT and the CTA stops
 // after its MMAs have drained, freeing its TMEM.
 #include <cmath>
 #include <cstring>
@@ -37,9 +38,10 @@ constexpr int TC_N = TC_G * TC_R;                // GEMM N (columns)
 constexpr int TC_M = 2 * TC_R;                   // GEMM M (real-ified rows)
 constexpr int TC_K = 2 * TC_R;                   // GEMM K
 constexpr int TC_THREADS = 256;
-constexpr uint32_t TILE_BYTES = TC_M * TC_K * 2;  // 32 KB: F', B1, B2 are all 128 x 128 BF16
-constexpr uint32_t SMEM_BYTES = 3 * TILE_BYTES + 64;
-constexpr uint32_t TMEM_COLS = 2 * TC_N;          // D1 and D2
+constexpr uint32_t TILE_BYTES = TC_M * TC_K * 2;  // 32 KB: F' and B are 128 x 128 BF16
+constexpr uint32_t SMEM_BYTES = 2 * TILE_BYTES + 64;
+constexpr uint32_t TMEM_COLS = TC_N;              // D1 and D2 share the columns
+constexpr int CTAS_PER_SM = 3;                    // 64 KB shared memory, 128 TMEM columns each
 constexpr long long WAIT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
 
 static_assert(TC_S_BF16 == TC_R * TC_R, "segment length must be 64 x 64");
@@ -105,9 +107,9 @@ __global__ void __launch_bounds__(TC_THREADS) k3_plane_tc(const __nv_bfloat162 *
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sF = smem;
     unsigned char *sB1 = smem + TILE_BYTES;
-    unsigned char *sB2 = smem + 2 * TILE_BYTES;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 3 * TILE_BYTES);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 3 * TILE_BYTES + 16);
+    unsigned char *sB2 = sB1;                      // B2 overwrites B1 once stage 1 has read it
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * TILE_BYTES);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 2 * TILE_BYTES + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(TC_THREADS) k3_plane_tc(const __nv_bfloat162 *
     tc::fence_after_thread_sync();
 
     const uint32_t tbase = *tslot;
-    const uint32_t tD1 = tbase, tD2 = tbase + TC_N;
+    const uint32_t tD1 = tbase, tD2 = tbase;       // D2 overwrites D1 once it has been read
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     const uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_N);
     const uint32_t aF = tc::smem_u32(sF), aB1 = tc::smem_u32(sB1), aB2 = tc::smem_u32(sB2);
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(TC_THREADS) k3_plane_tc(const __nv_bfloat162 *
             const bool zvalid = z < K;
             const __nv_bfloat162 *Yj = Y + j * TC_S_BF16;
             const __nv_bfloat162 *Gz = G + (int64_t)(zvalid ? z : 0) * TC_S_BF16;
-#pragma unroll 2
+#pragma unroll 8
             for (int b = tid >> 7; b < 16; b += 2) {
                 uint32_t w[4];
 #pragma unroll
@@ -320,7 +322,7 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
     const int64_t n_items = p.n_seg * n_groups;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
-    const int64_t ctas = std::min<int64_t>(n_items, 2 * (int64_t)sms);
+    const int64_t ctas = std::min<int64_t>(n_items, CTAS_PER_SM * (int64_t)sms);
     const int64_t per = (n_items + ctas - 1) / ctas;
     const int64_t grid = (n_items + per - 1) / per;
     p.prof.begin(FDAS_STAGE_CORRELATE, st);

@@ -56,6 +56,30 @@ __device__ __forceinline__ bool row_in_level(int i, int K, int zmax, int H) {
     return i >= 0 && i < K && abs(H * z) <= zmax;
 }
 
+// Add the harmonics h = H/2+1 .. H to S_{H/2} for the cells of one staged row (thread-strided
+// columns); all loads of a cell are issued before its ordered sum.
+template <typename E, int H>
+__device__ __forceinline__ void level_update(float *Srow, const E *__restrict__ plane, int64_t nb, int zmax, int z,
+                                             bool row_ok, int64_t r0, int64_t rmax) {
+    constexpr int NH = H / 2;
+    const E *base[NH];
+#pragma unroll
+    for (int q = 0; q < NH; q++) base[q] = plane + (int64_t)((((NH + 1 + q) * z) + zmax) >> 1) * nb;
+    for (int c = threadIdx.x; c < SW; c += RB * 32) {
+        const int64_t r = r0 - 1 + c;
+        float s = -INFINITY;
+        if (row_ok && r >= 0 && r <= rmax) {
+            float v[NH];
+#pragma unroll
+            for (int q = 0; q < NH; q++) v[q] = ld_plane(base[q], (int64_t)(NH + 1 + q) * r);
+            s = Srow[c];
+#pragma unroll
+            for (int q = 0; q < NH; q++) s = __fadd_rn(s, v[q]);
+        }
+        Srow[c] = s;
+    }
+}
+
 template <typename E>
 __global__ void __launch_bounds__(RB * 32) k4_detect(const E *__restrict__ plane, int64_t nb, int zmax, int K,
                                                      LevelTable lt, int n_rb, int32_t *__restrict__ unit_count,
@@ -70,11 +94,15 @@ __global__ void __launch_bounds__(RB * 32) k4_detect(const E *__restrict__ plane
     const int row = i0 + warp;
 
     // level 1: S_1 = P on rows i0-1 .. i0+RB, bins r0-1 .. r0+CB
-    for (int idx = threadIdx.x; idx < (RB + 2) * SW; idx += RB * 32) {
-        const int ri = idx / SW, c = idx - ri * SW;
+#pragma unroll 1
+    for (int ri = 0; ri < RB + 2; ri++) {
         const int i = i0 - 1 + ri;
-        const int64_t r = r0 - 1 + c;
-        S[ri][c] = (i >= 0 && i < K && r >= 0 && r < nb) ? ld_plane(plane, (int64_t)i * nb + r) : -INFINITY;
+        const bool row_ok = i >= 0 && i < K;
+        const E *prow = plane + (int64_t)(row_ok ? i : 0) * nb;
+        for (int c = threadIdx.x; c < SW; c += RB * 32) {
+            const int64_t r = r0 - 1 + c;
+            S[ri][c] = (row_ok && r >= 0 && r < nb) ? ld_plane(prow, r) : -INFINITY;
+        }
     }
     __syncthreads();
 
@@ -87,18 +115,17 @@ __global__ void __launch_bounds__(RB * 32) k4_detect(const E *__restrict__ plane
         if (l > 0) {
             // S_H = S_{H/2} + sum_{h = H/2+1 .. H} P(h r, i_h) inside level H's region, -inf outside
             __syncthreads();
-            for (int idx = threadIdx.x; idx < (RB + 2) * SW; idx += RB * 32) {
-                const int ri = idx / SW, c = idx - ri * SW;
+#pragma unroll 1
+            for (int ri = 0; ri < RB + 2; ri++) {
                 const int i = i0 - 1 + ri;
-                const int64_t r = r0 - 1 + c;
-                float s = -INFINITY;
-                if (row_in_level(i, K, zmax, H) && r >= 0 && r <= d.rmax) {
-                    s = S[ri][c];
-                    const int z = -zmax + 2 * i;
-                    for (int h = H / 2 + 1; h <= H; h++)
-                        s = __fadd_rn(s, ld_plane(plane, (int64_t)((h * z + zmax) >> 1) * nb + (int64_t)h * r));
+                const bool row_ok = row_in_level(i, K, zmax, H);
+                const int z = -zmax + 2 * i;
+                switch (H) {
+                    case 2: level_update<E, 2>(S[ri], plane, nb, zmax, z, row_ok, r0, d.rmax); break;
+                    case 4: level_update<E, 4>(S[ri], plane, nb, zmax, z, row_ok, r0, d.rmax); break;
+                    case 8: level_update<E, 8>(S[ri], plane, nb, zmax, z, row_ok, r0, d.rmax); break;
+                    default: level_update<E, 16>(S[ri], plane, nb, zmax, z, row_ok, r0, d.rmax); break;
                 }
-                S[ri][c] = s;
             }
             __syncthreads();
         }
@@ -106,12 +133,12 @@ __global__ void __launch_bounds__(RB * 32) k4_detect(const E *__restrict__ plane
         if (row_in_level(row, K, zmax, H)) {
             int cnt = 0;
             uint32_t words[WORDS];
+            const int cmax = (int)min((int64_t)CB, d.rmax - r0 + 1);   // valid bins in this chunk
 #pragma unroll
             for (int e = 0; e < WORDS; e++) {
                 const int c = 1 + lane + 32 * e;
-                const int64_t r = r0 + lane + 32 * e;
                 bool pk = false;
-                if (r <= d.rmax) {
+                if (lane + 32 * e < cmax) {
                     const float v = S[warp + 1][c];
                     if (v > d.thr) {
                         pk = v > S[warp][c - 1] && v > S[warp][c] && v > S[warp][c + 1] && v > S[warp + 1][c - 1] &&
