@@ -25,7 +25,9 @@
  *     (r contiguous); Xhat is zero outside [0, Nb).  Element type is float for
  *     FDAS_FP32 and bfloat16 (the upper 16 bits of the float) for the BF16 precisions.
  *   - All device pointers are CUDA device addresses on the current device; the caller
- *     owns them.  Streams are cudaStream_t values passed as void* (NULL = default
+ *     owns them.  Alignment: series and spectra 8 bytes, plane 16 bytes, workspace 256
+ *     bytes, peak list and counts 4 bytes (cudaMalloc'd and torch buffers satisfy all of
+ *     these); a misaligned pointer is rejected with FDAS_E_INVALID.  Streams are cudaStream_t values passed as void* (NULL = default
  *     stream).  Calls are asynchronous unless stated.  Nothing inside fdas_spectrum,
  *     fdas_plane, fdas_peaks or fdas_search allocates memory.
  *   - Errors are returned as fdas_status; nothing is thrown across the ABI.  Device-side

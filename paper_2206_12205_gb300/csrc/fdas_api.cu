@@ -33,6 +33,12 @@ fdas_status record(Plan *p, cudaError_t e) {
 
 bool plane_is_bf16(const Plan *p) { return p->cfg.precision != FDAS_FP32; }
 
+// Alignment the kernels' vector accesses rely on (documented in fdas.h).
+bool aligned(const void *ptr, uintptr_t a) { return (reinterpret_cast<uintptr_t>(ptr) & (a - 1)) == 0; }
+bool args_aligned(const void *series, const void *xhat, const void *ws, const void *plane, const void *peaks) {
+    return aligned(series, 8) && aligned(xhat, 8) && aligned(ws, 256) && aligned(plane, 16) && aligned(peaks, 4);
+}
+
 }  // namespace
 
 extern "C" {
@@ -170,6 +176,7 @@ static fdas_status ready(Plan *p) {
 fdas_status fdas_spectrum(fdas_plan_t plan, const float *d_series, void *d_workspace, float *d_xhat,
                           double *d_sigma2, void *stream) {
     if (!plan || !d_series || !d_workspace || !d_xhat) return FDAS_E_INVALID;
+    if (!args_aligned(d_series, d_xhat, d_workspace, nullptr, nullptr)) return FDAS_E_INVALID;
     Plan *p = P(plan);
     if (fdas_status s = ready(p)) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -182,6 +189,7 @@ fdas_status fdas_spectrum(fdas_plan_t plan, const float *d_series, void *d_works
 
 fdas_status fdas_plane(fdas_plan_t plan, const float *d_xhat, void *d_workspace, void *d_plane, void *stream) {
     if (!plan || !d_xhat || !d_workspace || !d_plane) return FDAS_E_INVALID;
+    if (!args_aligned(nullptr, d_xhat, d_workspace, d_plane, nullptr)) return FDAS_E_INVALID;
     Plan *p = P(plan);
     if (fdas_status s = ready(p)) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -200,6 +208,7 @@ fdas_status fdas_peaks(fdas_plan_t plan, const void *d_plane, void *d_workspace,
                        int32_t *d_npeaks, void *stream) {
     if (!plan || !d_plane || !d_workspace || !d_npeaks || (!d_peaks && P(plan)->cfg.max_peaks > 0))
         return FDAS_E_INVALID;
+    if (!args_aligned(nullptr, nullptr, d_workspace, d_plane, d_peaks) || !aligned(d_npeaks, 4)) return FDAS_E_INVALID;
     Plan *p = P(plan);
     if (fdas_status s = ready(p)) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -213,6 +222,7 @@ fdas_status fdas_search(fdas_plan_t plan, const float *d_series, void *d_workspa
                         fdas_peak *d_peaks, int32_t *d_npeaks, void *stream) {
     if (!plan || !d_series || !d_workspace || !d_plane || !d_npeaks || (!d_peaks && P(plan)->cfg.max_peaks > 0))
         return FDAS_E_INVALID;
+    if (!args_aligned(d_series, nullptr, d_workspace, d_plane, d_peaks) || !aligned(d_npeaks, 4)) return FDAS_E_INVALID;
     Plan *p = P(plan);
     if (fdas_status s = ready(p)) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -46,6 +46,7 @@ cudaError_t scratch_on_current_device(void **out) {
 
 extern "C" fdas_status fdas_plane_static(fdas_plan_t plan, const float *d_xhat, void *d_plane, void *stream) {
     if (!plan || !d_xhat || !d_plane) return FDAS_E_INVALID;
+    if ((reinterpret_cast<uintptr_t>(d_xhat) & 7) || (reinterpret_cast<uintptr_t>(d_plane) & 15)) return FDAS_E_INVALID;
     fdas::Plan *p = static_cast<fdas::Plan *>(plan);
     if (!p->templates_ready) return FDAS_E_STATE;
     if (p->cfg.precision != FDAS_FP32) {

@@ -15,11 +15,11 @@
 // where F' is the radix-64 DFT real-ified with re/im interleaved (row 2k+p, column 2n+s), so
 // the real and imaginary parts of one value sit in adjacent TMEM lanes (adjacent threads).
 //
-// B1 and B2 share one shared-memory tile and D1 and D2 one set of TMEM columns: each is
-// rewritten only after the MMA that reads it (or the loads that drain it) has completed.  One
-// persistent CTA per slot (3 per SM: 64 KB shared memory, 128 of 512 TMEM columns each) walks a
-// contiguous range of (segment, template pair) items, so a segment's spectrum stays in L1.  Every mbarrier wait is bounded; a timeout sets FDAS_DEV_TIMEOUT and the CTA stops
-// after its MMAs have drained, freeing its TMEM.
+// One persistent, warp-specialised CTA per SM walks a contiguous range of (segment, template
+// pair) items with producer, MMA and two epilogue roles overlapped through double-buffered
+// shared-memory tiles and TMEM accumulators (layout below the helpers).  Every mbarrier wait
+// is bounded; a timeout sets FDAS_DEV_TIMEOUT, all roles stop, the issued MMAs drain and the
+// TMEM is released.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -37,11 +37,7 @@ constexpr int TC_G = 2;                          // templates per item
 constexpr int TC_N = TC_G * TC_R;                // GEMM N (columns)
 constexpr int TC_M = 2 * TC_R;                   // GEMM M (real-ified rows)
 constexpr int TC_K = 2 * TC_R;                   // GEMM K
-constexpr int TC_THREADS = 256;
-constexpr uint32_t TILE_BYTES = TC_M * TC_K * 2;  // 32 KB: F' and B are 128 x 128 BF16
-constexpr uint32_t SMEM_BYTES = 2 * TILE_BYTES + 64;
-constexpr uint32_t TMEM_COLS = TC_N;              // D1 and D2 share the columns
-constexpr int CTAS_PER_SM = 3;                    // 64 KB shared memory, 128 TMEM columns each
+constexpr uint32_t TILE_BYTES = TC_M * TC_K * 2;  // 32 KB: F' and every B tile are 128 x 128 BF16
 constexpr long long WAIT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
 
 static_assert(TC_S_BF16 == TC_R * TC_R, "segment length must be 64 x 64");
@@ -97,170 +93,241 @@ __device__ __forceinline__ void pair_exchange(const uint32_t (&r)[16], int rho, 
     }
 }
 
-__global__ void __launch_bounds__(TC_THREADS) k3_plane_tc(const __nv_bfloat162 *__restrict__ Y,
-                                                          const __nv_bfloat162 *__restrict__ G,
-                                                          const uint4 *__restrict__ Fimg,
-                                                          const float2 *__restrict__ tw,
-                                                          __nv_bfloat16 *__restrict__ plane, int K, int64_t nb,
-                                                          int L, int64_t n_items, int n_groups,
-                                                          int64_t items_per_cta, int32_t *__restrict__ status) {
+// ---------------------------------------------------------------------------------------
+// Warp-specialised persistent kernel (one CTA per SM, 13 warps):
+//   warp 0      TMEM allocation; lane 0 issues the MMAs (stage 1 of item i+1 before stage 2 of i)
+//   warps 1-4   producer:   B1[slot] = conj(Yhat_j) * G_z
+//   warps 5-8   epilogue 1: D1[slot] (TMEM) -> twiddle -> B2[slot]
+//   warps 9-12  epilogue 2: D2[slot] (TMEM) -> |.|^2 -> BF16 plane
+// Two slots of B1, B2 (shared memory) and D1, D2 (TMEM, 4 x 128 of the 512 columns).
+// Hand-offs are mbarriers, one per slot:
+//   b1_full  (128 producer arrivals)   s1_done (MMA commit: D1 ready, B1 free)
+//   b2_full  (128 epilogue-1 arrivals: B2 ready, D1 drained)
+//   s2_done  (MMA commit: D2 ready, B2 free)   d2_free (128 epilogue-2 arrivals: D2 drained)
+// The k-th use of a slot waits for phase parity k & 1; every wait is bounded and also gives
+// up when another role has aborted.
+constexpr int WS_THREADS = 13 * 32;
+constexpr uint32_t WS_TILE = TILE_BYTES;                     // 32 KB
+constexpr uint32_t OFF_F = 0;
+constexpr uint32_t OFF_B1 = OFF_F + WS_TILE;                 // 2 slots
+constexpr uint32_t OFF_B2 = OFF_B1 + 2 * WS_TILE;            // 2 slots
+constexpr uint32_t OFF_TW = OFF_B2 + 2 * WS_TILE;            // twiddles, 4096 x float2 = 32 KB
+constexpr uint32_t OFF_BAR = OFF_TW + TC_S_BF16 * 8;
+constexpr uint32_t WS_SMEM = OFF_BAR + 16 * 8 + 32;
+constexpr uint32_t WS_TMEM_COLS = 512;
+
+struct WsBars {
+    uint64_t b1_full[2], s1_done[2], b2_full[2], s2_done[2], d2_free[2], drain;
+};
+
+__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    const long long t0 = clock64();
+    while (!tc::mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat162 *__restrict__ Y,
+                                                             const __nv_bfloat162 *__restrict__ G,
+                                                             const uint4 *__restrict__ Fimg,
+                                                             const float2 *__restrict__ tw,
+                                                             __nv_bfloat16 *__restrict__ plane, int K, int64_t nb,
+                                                             int L, int64_t n_items, int n_groups,
+                                                             int64_t items_per_cta, int32_t *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sF = smem;
-    unsigned char *sB1 = smem + TILE_BYTES;
-    unsigned char *sB2 = sB1;                      // B2 overwrites B1 once stage 1 has read it
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * TILE_BYTES);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 2 * TILE_BYTES + 16);
+    WsBars *bars = reinterpret_cast<WsBars *>(smem + OFF_BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + OFF_BAR + sizeof(WsBars));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + OFF_BAR + sizeof(WsBars) + 8);
+    float2 *sTw = reinterpret_cast<float2 *>(smem + OFF_TW);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
-        tc::tmem_alloc(tslot, TMEM_COLS);
+        tc::tmem_alloc(tslot, WS_TMEM_COLS);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(&bar[0], 1);
-        tc::mbar_init(&bar[1], 1);
+        for (int s = 0; s < 2; s++) {
+            tc::mbar_init(&bars->b1_full[s], 128);
+            tc::mbar_init(&bars->s1_done[s], 1);
+            tc::mbar_init(&bars->b2_full[s], 128);
+            tc::mbar_init(&bars->s2_done[s], 1);
+            tc::mbar_init(&bars->d2_free[s], 128);
+        }
+        tc::mbar_init(&bars->drain, 1);
+        *abort_flag = 0;
     }
-    for (int i = tid; i < (int)(TILE_BYTES / 16); i += TC_THREADS) reinterpret_cast<uint4 *>(sF)[i] = __ldg(Fimg + i);
+    for (int i = tid; i < (int)(WS_TILE / 16); i += WS_THREADS)
+        reinterpret_cast<uint4 *>(smem + OFF_F)[i] = __ldg(Fimg + i);
+    for (int i = tid; i < TC_S_BF16; i += WS_THREADS) sTw[i] = __ldg(tw + i);
     tc::fence_proxy_async_smem();
     tc::fence_before_thread_sync();
     __syncthreads();
     tc::fence_after_thread_sync();
 
     const uint32_t tbase = *tslot;
-    const uint32_t tD1 = tbase, tD2 = tbase;       // D2 overwrites D1 once it has been read
-    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    const uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_N);
-    const uint32_t aF = tc::smem_u32(sF), aB1 = tc::smem_u32(sB1), aB2 = tc::smem_u32(sB2);
-    const int row = 32 * (warp & 3) + lane;      // TMEM lane = GEMM row (k, p)
-    const int kk = row >> 1, rho = row & 1;
-    const int zl_epi = warp >> 2;                 // warps 0-3: first template, 4-7: second
-
-    uint32_t phase = 0;
-    int pending = 0;                               // MMA groups committed but not yet waited for
-    bool ok = true;
     const int64_t it0 = (int64_t)blockIdx.x * items_per_cta;
     const int64_t it1 = min(n_items, it0 + items_per_cta);
-    for (int64_t it = it0; it < it1; it++) {
-        const int64_t j = it / n_groups;
-        const int z0 = (int)(it % n_groups) * TC_G;
+    const int64_t n_my = it1 - it0;
 
-        // ---- B1[(n1, s), (zl, n2)] = conj(Yhat_j[64 n1 + n2]) * G_{z0+zl}[64 n1 + n2]
-        {
-            const int c = tid & (TC_N - 1);
-            const int zl = c >> 6, n2 = c & 63;
-            const int z = z0 + zl;
+    if (warp == 0) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0 && n_my > 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_N);
+            const uint32_t aF = tc::smem_u32(smem + OFF_F);
+            auto issue = [&](uint32_t dcol, uint32_t bsm) {
+#pragma unroll
+                for (int s = 0; s < TC_K / 16; s++)
+                    tc::mma_bf16(tbase + dcol, tc::smem_desc(aF + s * TC_M * 32, TC_M * 16, 128),
+                                 tc::smem_desc(bsm + s * TC_N * 32, TC_N * 16, 128), idesc, s > 0 ? 1u : 0u);
+            };
+            bool ok = ws_wait(&bars->b1_full[0], 0, abort_flag);
+            if (ok) {
+                tc::fence_after_thread_sync();
+                issue(0 * TC_N, tc::smem_u32(smem + OFF_B1));
+                tc::mma_commit(&bars->s1_done[0]);
+            }
+            for (int64_t k = 0; k < n_my && ok; k++) {
+                const int sl = (int)(k & 1);
+                const uint32_t par = (uint32_t)((k >> 1) & 1);
+                if (k + 1 < n_my) {                                    // stage 1 of the next item
+                    const int sn = (int)((k + 1) & 1);
+                    ok = ws_wait(&bars->b1_full[sn], (uint32_t)(((k + 1) >> 1) & 1), abort_flag);
+                    if (!ok) break;
+                    tc::fence_after_thread_sync();
+                    issue(sn * TC_N, tc::smem_u32(smem + OFF_B1 + sn * WS_TILE));
+                    tc::mma_commit(&bars->s1_done[sn]);
+                }
+                ok = ws_wait(&bars->b2_full[sl], par, abort_flag);     // B2 ready, D1 drained
+                if (ok && k >= 2) ok = ws_wait(&bars->d2_free[sl], par ^ 1u, abort_flag);
+                if (!ok) break;
+                tc::fence_after_thread_sync();
+                issue((2 + sl) * TC_N, tc::smem_u32(smem + OFF_B2 + sl * WS_TILE));
+                tc::mma_commit(&bars->s2_done[sl]);
+            }
+            // drain: every MMA issued above has completed before TMEM can be released
+            tc::mma_commit(&bars->drain);
+            tc::mbar_wait_bounded(&bars->drain, 0, WAIT_CYCLES);
+        }
+        __syncwarp();
+    } else if (warp <= 4) {
+        // ---------------------------------------------------------------- producer
+        const int pt = tid - 32;                        // 0..127: B1 column (zl, n2)
+        const int zl = pt >> 6, n2 = pt & 63;
+        for (int64_t k = 0; k < n_my; k++) {
+            const int64_t it = it0 + k;
+            const int64_t j = it / n_groups;
+            const int z = (int)(it % n_groups) * TC_G + zl;
+            const int sl = (int)(k & 1);
+            if (k >= 2 && !ws_wait(&bars->s1_done[sl], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
             const bool zvalid = z < K;
             const __nv_bfloat162 *Yj = Y + j * TC_S_BF16;
             const __nv_bfloat162 *Gz = G + (int64_t)(zvalid ? z : 0) * TC_S_BF16;
+            unsigned char *b1 = smem + OFF_B1 + sl * WS_TILE;
 #pragma unroll 8
-            for (int b = tid >> 7; b < 16; b += 2) {
+            for (int b = 0; b < 16; b++) {
                 uint32_t w[4];
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const int n = 64 * (4 * b + q) + n2;
-                    const float2 y = unpack_bf16x2(Yj[n]);
+                    const float2 y = unpack_bf16x2(__ldg(Yj + n));
                     const float2 g = zvalid ? unpack_bf16x2(__ldg(Gz + n)) : make_float2(0.f, 0.f);
                     w[q] = pack_bf16x2(y.x * g.x + y.y * g.y, y.x * g.y - y.y * g.x);
                 }
-                *reinterpret_cast<uint4 *>(sB1 + tc::kmajor_offset(TC_N, c, 8 * b)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4 *>(b1 + tc::kmajor_offset(TC_N, pt, 8 * b)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
+            tc::fence_proxy_async_smem();
+            mbar_arrive(&bars->b1_full[sl]);
         }
-        tc::fence_proxy_async_smem();
-        tc::fence_before_thread_sync();
-        __syncthreads();
-        tc::fence_after_thread_sync();
-
-        // ---- stage 1: D1 = F' B1
-        if (tid == 0) {
-#pragma unroll
-            for (int s = 0; s < TC_K / 16; s++)
-                tc::mma_bf16(tD1, tc::smem_desc(aF + s * TC_M * 32, TC_M * 16, 128),
-                             tc::smem_desc(aB1 + s * TC_N * 32, TC_N * 16, 128), idesc, s > 0 ? 1u : 0u);
-            tc::mma_commit(&bar[0]);
-        }
-        pending = 1;
-        ok = __syncthreads_and(tc::mbar_wait_bounded(&bar[0], phase, WAIT_CYCLES));
-        if (!ok) break;
-        pending = 0;
-        tc::fence_after_thread_sync();
-
-        // ---- twiddle: B2[(n2, s), (zl, k1)] = W_S^{n2 k1} D1[(k1, .), (zl, n2)]
+    } else {
+        // ---------------------------------------------------------------- epilogues
+        const bool epi1 = warp <= 8;
+        const int quad = warp & 3;                      // TMEM lane quadrant this warp may access
+        const int row = 32 * quad + lane;               // GEMM row (k, p)
+        const int kk = row >> 1, rho = row & 1;
+        const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+        for (int64_t k = 0; k < n_my; k++) {
+            const int64_t it = it0 + k;
+            const int sl = (int)(k & 1);
+            const uint32_t par = (uint32_t)((k >> 1) & 1);
+            if (epi1) {
+                if (!ws_wait(&bars->s1_done[sl], par, abort_flag)) break;
+                if (k >= 2 && !ws_wait(&bars->s2_done[sl], par ^ 1u, abort_flag)) break;   // B2[sl] free
+                tc::fence_after_thread_sync();
+                unsigned char *b2 = smem + OFF_B2 + sl * WS_TILE;
 #pragma unroll 1
-        for (int ch = 0; ch < 4; ch++) {
-            uint32_t r[16];
-            tc::tmem_ld16(tD1 + lane_base + zl_epi * TC_R + 16 * ch, r);
-            tc::tmem_ld_wait();
-            float re[8], im[8];
-            pair_exchange(r, rho, re, im);
-            const int n2_0 = 16 * ch + 8 * rho;
-            const float4 *twp = reinterpret_cast<const float4 *>(tw + kk * TC_R + n2_0);
-            uint32_t w[8];
+                for (int ch = 0; ch < 8; ch++) {
+                    const int zl = ch >> 2;
+                    uint32_t r[16];
+                    tc::tmem_ld16(tbase + lane_base + sl * TC_N + 16 * ch, r);
+                    tc::tmem_ld_wait();
+                    float re[8], im[8];
+                    pair_exchange(r, rho, re, im);
+                    const int n2_0 = 16 * (ch & 3) + 8 * rho;
+                    const float4 *twp = reinterpret_cast<const float4 *>(sTw + kk * TC_R + n2_0);
+                    uint32_t w[8];
 #pragma unroll
-            for (int q2 = 0; q2 < 4; q2++) {
-                const float4 t2 = __ldg(twp + q2);
-                const int q = 2 * q2;
-                w[q] = pack_bf16x2(re[q] * t2.x - im[q] * t2.y, re[q] * t2.y + im[q] * t2.x);
-                w[q + 1] = pack_bf16x2(re[q + 1] * t2.z - im[q + 1] * t2.w, re[q + 1] * t2.w + im[q + 1] * t2.z);
-            }
-            const int c2 = zl_epi * TC_R + kk;
-            *reinterpret_cast<uint4 *>(sB2 + tc::kmajor_offset(TC_N, c2, 2 * n2_0)) = make_uint4(w[0], w[1], w[2], w[3]);
-            *reinterpret_cast<uint4 *>(sB2 + tc::kmajor_offset(TC_N, c2, 2 * n2_0 + 8)) =
-                make_uint4(w[4], w[5], w[6], w[7]);
-        }
-        tc::fence_proxy_async_smem();
-        tc::fence_before_thread_sync();
-        __syncthreads();
-        tc::fence_after_thread_sync();
-
-        // ---- stage 2: D2 = F' B2
-        if (tid == 0) {
-#pragma unroll
-            for (int s = 0; s < TC_K / 16; s++)
-                tc::mma_bf16(tD2, tc::smem_desc(aF + s * TC_M * 32, TC_M * 16, 128),
-                             tc::smem_desc(aB2 + s * TC_N * 32, TC_N * 16, 128), idesc, s > 0 ? 1u : 0u);
-            tc::mma_commit(&bar[1]);
-        }
-        pending = 2;
-        ok = __syncthreads_and(tc::mbar_wait_bounded(&bar[1], phase, WAIT_CYCLES));
-        if (!ok) break;
-        pending = 0;
-        tc::fence_after_thread_sync();
-
-        // ---- |X|^2 for X[k1 + 64 k2], k1 = 16 ch + 8 p + q: eight consecutive bins per thread
-        {
-            const int z = z0 + zl_epi;
-            const int64_t r0 = j * L;
-#pragma unroll 1
-            for (int ch = 0; ch < 4; ch++) {
-                uint32_t r[16];
-                tc::tmem_ld16(tD2 + lane_base + zl_epi * TC_R + 16 * ch, r);
-                tc::tmem_ld_wait();
-                float re[8], im[8];
-                pair_exchange(r, rho, re, im);
-                const int t = 64 * kk + 16 * ch + 8 * rho;
-                const int64_t rr = r0 + t;
-                if (z < K && t < L && rr < nb) {
-                    uint4 o;
-                    o.x = pack_bf16x2(re[0] * re[0] + im[0] * im[0], re[1] * re[1] + im[1] * im[1]);
-                    o.y = pack_bf16x2(re[2] * re[2] + im[2] * im[2], re[3] * re[3] + im[3] * im[3]);
-                    o.z = pack_bf16x2(re[4] * re[4] + im[4] * im[4], re[5] * re[5] + im[5] * im[5]);
-                    o.w = pack_bf16x2(re[6] * re[6] + im[6] * im[6], re[7] * re[7] + im[7] * im[7]);
-                    *reinterpret_cast<uint4 *>(plane + (int64_t)z * nb + rr) = o;
+                    for (int q2 = 0; q2 < 4; q2++) {
+                        const float4 t2 = twp[q2];
+                        const int q = 2 * q2;
+                        w[q] = pack_bf16x2(re[q] * t2.x - im[q] * t2.y, re[q] * t2.y + im[q] * t2.x);
+                        w[q + 1] = pack_bf16x2(re[q + 1] * t2.z - im[q + 1] * t2.w, re[q + 1] * t2.w + im[q + 1] * t2.z);
+                    }
+                    const int c2 = zl * TC_R + kk;
+                    *reinterpret_cast<uint4 *>(b2 + tc::kmajor_offset(TC_N, c2, 2 * n2_0)) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4 *>(b2 + tc::kmajor_offset(TC_N, c2, 2 * n2_0 + 8)) =
+                        make_uint4(w[4], w[5], w[6], w[7]);
                 }
+                tc::fence_before_thread_sync();
+                tc::fence_proxy_async_smem();
+                mbar_arrive(&bars->b2_full[sl]);
+            } else {
+                if (!ws_wait(&bars->s2_done[sl], par, abort_flag)) break;
+                tc::fence_after_thread_sync();
+                const int64_t j = it / n_groups;
+                const int z0 = (int)(it % n_groups) * TC_G;
+                const int64_t r0 = j * L;
+#pragma unroll 1
+                for (int ch = 0; ch < 8; ch++) {
+                    const int zl = ch >> 2;
+                    const int z = z0 + zl;
+                    uint32_t r[16];
+                    tc::tmem_ld16(tbase + lane_base + (2 + sl) * TC_N + 16 * ch, r);
+                    tc::tmem_ld_wait();
+                    float re[8], im[8];
+                    pair_exchange(r, rho, re, im);
+                    const int t = 64 * kk + 16 * (ch & 3) + 8 * rho;
+                    const int64_t rr = r0 + t;
+                    if (z < K && t < L && rr < nb) {
+                        uint4 o;
+                        o.x = pack_bf16x2(re[0] * re[0] + im[0] * im[0], re[1] * re[1] + im[1] * im[1]);
+                        o.y = pack_bf16x2(re[2] * re[2] + im[2] * im[2], re[3] * re[3] + im[3] * im[3]);
+                        o.z = pack_bf16x2(re[4] * re[4] + im[4] * im[4], re[5] * re[5] + im[5] * im[5]);
+                        o.w = pack_bf16x2(re[6] * re[6] + im[6] * im[6], re[7] * re[7] + im[7] * im[7]);
+                        *reinterpret_cast<uint4 *>(plane + (int64_t)z * nb + rr) = o;
+                    }
+                }
+                tc::fence_before_thread_sync();
+                mbar_arrive(&bars->d2_free[sl]);
             }
         }
-        tc::fence_before_thread_sync();
-        __syncthreads();
-        phase ^= 1;
-    }
-    if (!ok) {
-        if (tid == 0) atomicOr(status, FDAS_DEV_TIMEOUT);
-        // let the outstanding MMAs drain (bounded) before the TMEM is released
-        tc::mbar_wait_bounded(&bar[pending == 2 ? 1 : 0], phase, WAIT_CYCLES);
     }
     tc::fence_before_thread_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tbase, TMEM_COLS);
+    if (tid == 0 && *abort_flag) atomicOr(status, FDAS_DEV_TIMEOUT);
+    if (warp == 0) {
+        tc::fence_after_thread_sync();
+        tc::tmem_dealloc(tbase, WS_TMEM_COLS);
+    }
 }
 
 }  // namespace
@@ -311,7 +378,7 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
     const size_t smem2 = sizeof(float2) * fft_smem_entries(TC_S_BF16);
     cudaError_t e = cudaFuncSetAttribute(k2_segments_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k3_plane_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    e = cudaFuncSetAttribute(k3_plane_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM);
     if (e != cudaSuccess) return e;
     p.prof.begin(FDAS_STAGE_SEGMENTS, st);
     k2_segments_bf16<<<(unsigned)p.n_seg, TC_S_BF16 / 32, smem2, st>>>(d_x, d_scale, p.d_tw, Y, p.nb, p.L, p.m / 2);
@@ -322,11 +389,11 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
     const int64_t n_items = p.n_seg * n_groups;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
-    const int64_t ctas = std::min<int64_t>(n_items, CTAS_PER_SM * (int64_t)sms);
+    const int64_t ctas = std::min<int64_t>(n_items, (int64_t)sms);     // one persistent CTA per SM
     const int64_t per = (n_items + ctas - 1) / ctas;
     const int64_t grid = (n_items + per - 1) / per;
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
-    k3_plane_tc<<<(unsigned)grid, TC_THREADS, SMEM_BYTES, st>>>(Y, p.d_Gbf, reinterpret_cast<const uint4 *>(p.d_tcF),
+    k3_plane_tc<<<(unsigned)grid, WS_THREADS, WS_SMEM, st>>>(Y, p.d_Gbf, reinterpret_cast<const uint4 *>(p.d_tcF),
                                                                p.d_tcTw, d_plane, p.K, p.nb, p.L, n_items, n_groups,
                                                                per, p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);

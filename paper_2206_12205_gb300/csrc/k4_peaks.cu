@@ -40,6 +40,31 @@ __device__ __forceinline__ float ld_plane(const __nv_bfloat16 *p, int64_t i) {
     return __uint_as_float(((unsigned)bits) << 16);
 }
 
+// 16-byte vector of plane values widened to float: 4 FP32 or 8 BF16 elements.
+template <typename E>
+struct Vec;
+template <>
+struct Vec<float> {
+    static constexpr int N = 4;
+    __device__ __forceinline__ static void load(const float *p, float (&o)[4]) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+};
+template <>
+struct Vec<__nv_bfloat16> {
+    static constexpr int N = 8;
+    __device__ __forceinline__ static void load(const __nv_bfloat16 *p, float (&o)[8]) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            o[2 * k] = __uint_as_float(w[k] << 16);
+            o[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+        }
+    }
+};
+
 template <typename E>
 __device__ __forceinline__ float harm_sum(const E *plane, int64_t nb, int zmax, int H, int i, int64_t r) {
     const int z = -zmax + 2 * i;
@@ -65,7 +90,11 @@ __device__ __forceinline__ void level_update(float *Srow, const E *__restrict__ 
     const E *base[NH];
 #pragma unroll
     for (int q = 0; q < NH; q++) base[q] = plane + (int64_t)((((NH + 1 + q) * z) + zmax) >> 1) * nb;
-    for (int c = threadIdx.x; c < SW; c += RB * 32) {
+    constexpr int NC = (SW + RB * 32 - 1) / (RB * 32);
+#pragma unroll
+    for (int cc = 0; cc < NC; cc++) {
+        const int c = threadIdx.x + cc * RB * 32;
+        if (c >= SW) break;
         const int64_t r = r0 - 1 + c;
         float s = -INFINITY;
         if (row_ok && r >= 0 && r <= rmax) {
@@ -93,15 +122,42 @@ __global__ void __launch_bounds__(RB * 32) k4_detect(const E *__restrict__ plane
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = i0 + warp;
 
-    // level 1: S_1 = P on rows i0-1 .. i0+RB, bins r0-1 .. r0+CB
-#pragma unroll 1
-    for (int ri = 0; ri < RB + 2; ri++) {
-        const int i = i0 - 1 + ri;
-        const bool row_ok = i >= 0 && i < K;
-        const E *prow = plane + (int64_t)(row_ok ? i : 0) * nb;
-        for (int c = threadIdx.x; c < SW; c += RB * 32) {
+    // level 1: S_1 = P on rows i0-1 .. i0+RB, bins r0-1 .. r0+CB.  The chunk interior
+    // [r0, r0 + CB) is 16-byte aligned (r0 is a multiple of CB, Nb a power of two): vector loads,
+    // all issued before the shared-memory stores; the two halo columns are loaded singly.
+    {
+        constexpr int EPV = Vec<E>::N;
+        constexpr int VPR = CB / EPV;                       // vectors per row
+        constexpr int NV = ((RB + 2) * VPR + RB * 32 - 1) / (RB * 32);
+        float vals[NV][EPV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            const int v = threadIdx.x + k * RB * 32;
+            const int ri = v / VPR, q = v % VPR;
+            const int i = i0 - 1 + ri;
+            const int64_t r = r0 + (int64_t)q * EPV;
+            if (ri < RB + 2 && i >= 0 && i < K && r < nb) {
+                Vec<E>::load(plane + (int64_t)i * nb + r, vals[k]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < EPV; e++) vals[k][e] = -INFINITY;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            const int v = threadIdx.x + k * RB * 32;
+            const int ri = v / VPR, q = v % VPR;
+            if (ri < RB + 2) {
+#pragma unroll
+                for (int e = 0; e < EPV; e++) S[ri][1 + q * EPV + e] = vals[k][e];
+            }
+        }
+        if (threadIdx.x < 2 * (RB + 2)) {
+            const int ri = threadIdx.x >> 1;
+            const int c = (threadIdx.x & 1) ? SW - 1 : 0;
+            const int i = i0 - 1 + ri;
             const int64_t r = r0 - 1 + c;
-            S[ri][c] = (row_ok && r >= 0 && r < nb) ? ld_plane(prow, r) : -INFINITY;
+            S[ri][c] = (i >= 0 && i < K && r >= 0 && r < nb) ? ld_plane(plane + (int64_t)i * nb, r) : -INFINITY;
         }
     }
     __syncthreads();

@@ -112,3 +112,17 @@ def test_binding_refuses_host_tensors(lib):
     with pytest.raises(ValueError):
         fd.fdas_plane(p, torch.zeros(10), torch.zeros(10), torch.zeros(10))
     fd.fdas_destroy(p)
+
+
+def test_misaligned_pointers_rejected(lib):
+    p = fd.fdas_plan(fd.make_config(1 << 16, 16, 64, 1024))
+    p_ptr = p.handle
+    base = 1 << 20                                # never dereferenced: argument checks come first
+    ok = ctypes.c_void_p(base)
+    odd = ctypes.c_void_p(base + 4)               # 4-byte aligned only
+    assert lib.fdas_plane(p_ptr, ok, ok, odd, None) == fb.FDAS_E_INVALID      # plane needs 16
+    assert lib.fdas_plane(p_ptr, odd, ok, ok, None) == fb.FDAS_E_INVALID      # spectrum needs 8
+    assert lib.fdas_plane(p_ptr, ok, odd, ok, None) == fb.FDAS_E_INVALID      # workspace needs 256
+    assert lib.fdas_plane_static(p_ptr, ok, odd, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_search(p_ptr, odd, ok, ok, ok, ok, None) == fb.FDAS_E_INVALID
+    fd.fdas_destroy(p)
