@@ -96,22 +96,28 @@ __device__ __forceinline__ void pair_exchange(const uint32_t (&r)[16], int rho, 
 // ---------------------------------------------------------------------------------------
 // Warp-specialised persistent kernel (one CTA per SM, 13 warps):
 //   warp 0      TMEM allocation; lane 0 issues the MMAs (stage 1 of item i+1 before stage 2 of i)
-//   warps 1-4   producer:   B1[slot] = conj(Yhat_j) * G_z
-//   warps 5-8   epilogue 1: D1[slot] (TMEM) -> twiddle -> B2[slot]
-//   warps 9-12  epilogue 2: D2[slot] (TMEM) -> |.|^2 -> BF16 plane
+//   warps 1-8   producer:   B1[slot] = conj(Yhat_j) * G_z, one 4 x 4 (n1, n2) block per thread
+//               with all of its 16-byte loads in flight at once
+//   warps 9-12  epilogue 1: D1[slot] (TMEM) -> twiddle -> B2[slot]
+//   warps 13-16 epilogue 2: D2[slot] (TMEM) -> |.|^2 -> BF16 plane
 // Two slots of B1, B2 (shared memory) and D1, D2 (TMEM, 4 x 128 of the 512 columns).
 // Hand-offs are mbarriers, one per slot:
-//   b1_full  (128 producer arrivals)   s1_done (MMA commit: D1 ready, B1 free)
+//   b1_full  (256 producer arrivals)   s1_done (MMA commit: D1 ready, B1 free)
 //   b2_full  (128 epilogue-1 arrivals: B2 ready, D1 drained)
 //   s2_done  (MMA commit: D2 ready, B2 free)   d2_free (128 epilogue-2 arrivals: D2 drained)
 // The k-th use of a slot waits for phase parity k & 1; every wait is bounded and also gives
 // up when another role has aborted.
-constexpr int WS_THREADS = 13 * 32;
-constexpr uint32_t WS_TILE = TILE_BYTES;                     // 32 KB
-constexpr uint32_t OFF_F = 0;
-constexpr uint32_t OFF_B1 = OFF_F + WS_TILE;                 // 2 slots
-constexpr uint32_t OFF_B2 = OFF_B1 + 2 * WS_TILE;            // 2 slots
-constexpr uint32_t OFF_TW = OFF_B2 + 2 * WS_TILE;            // twiddles, 4096 x float2 = 32 KB
+constexpr int WS_PRODUCERS = 256;                            // warps 1-8
+constexpr int WS_E1 = 1 + WS_PRODUCERS / 32;                 // first epilogue-1 warp (9)
+constexpr int WS_E2 = WS_E1 + 4;                             // first epilogue-2 warp (13)
+constexpr int WS_THREADS = (WS_E2 + 4) * 32;                 // 17 warps
+// B tiles: K-major, core matrices 144 B apart along N and 16 x 144 B apart along K
+constexpr uint32_t B_SBO = 144, B_LBO = 16 * B_SBO;
+constexpr uint32_t B_TILE = 16 * B_LBO;                      // 36 KB (K = 128 = 16 core matrices)
+constexpr uint32_t OFF_F = 0;                                // F': dense, 32 KB
+constexpr uint32_t OFF_B1 = OFF_F + TILE_BYTES;              // 2 slots
+constexpr uint32_t OFF_B2 = OFF_B1 + 2 * B_TILE;             // 2 slots
+constexpr uint32_t OFF_TW = OFF_B2 + 2 * B_TILE;             // twiddles, 4096 x float2 = 32 KB
 constexpr uint32_t OFF_BAR = OFF_TW + TC_S_BF16 * 8;
 constexpr uint32_t WS_SMEM = OFF_BAR + 16 * 8 + 32;
 constexpr uint32_t WS_TMEM_COLS = 512;
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
     }
     if (tid == 0) {
         for (int s = 0; s < 2; s++) {
-            tc::mbar_init(&bars->b1_full[s], 128);
+            tc::mbar_init(&bars->b1_full[s], WS_PRODUCERS);
             tc::mbar_init(&bars->s1_done[s], 1);
             tc::mbar_init(&bars->b2_full[s], 128);
             tc::mbar_init(&bars->s2_done[s], 1);
@@ -165,7 +171,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
         tc::mbar_init(&bars->drain, 1);
         *abort_flag = 0;
     }
-    for (int i = tid; i < (int)(WS_TILE / 16); i += WS_THREADS)
+    for (int i = tid; i < (int)(TILE_BYTES / 16); i += WS_THREADS)
         reinterpret_cast<uint4 *>(smem + OFF_F)[i] = __ldg(Fimg + i);
     for (int i = tid; i < TC_S_BF16; i += WS_THREADS) sTw[i] = __ldg(tw + i);
     tc::fence_proxy_async_smem();
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
 #pragma unroll
                 for (int s = 0; s < TC_K / 16; s++)
                     tc::mma_bf16(tbase + dcol, tc::smem_desc(aF + s * TC_M * 32, TC_M * 16, 128),
-                                 tc::smem_desc(bsm + s * TC_N * 32, TC_N * 16, 128), idesc, s > 0 ? 1u : 0u);
+                                 tc::smem_desc(bsm + s * 2 * B_LBO, B_LBO, B_SBO), idesc, s > 0 ? 1u : 0u);
             };
             bool ok = ws_wait(&bars->b1_full[0], 0, abort_flag);
             if (ok) {
@@ -203,14 +209,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
                     ok = ws_wait(&bars->b1_full[sn], (uint32_t)(((k + 1) >> 1) & 1), abort_flag);
                     if (!ok) break;
                     tc::fence_after_thread_sync();
-                    issue(sn * TC_N, tc::smem_u32(smem + OFF_B1 + sn * WS_TILE));
+                    issue(sn * TC_N, tc::smem_u32(smem + OFF_B1 + sn * B_TILE));
                     tc::mma_commit(&bars->s1_done[sn]);
                 }
                 ok = ws_wait(&bars->b2_full[sl], par, abort_flag);     // B2 ready, D1 drained
                 if (ok && k >= 2) ok = ws_wait(&bars->d2_free[sl], par ^ 1u, abort_flag);
                 if (!ok) break;
                 tc::fence_after_thread_sync();
-                issue((2 + sl) * TC_N, tc::smem_u32(smem + OFF_B2 + sl * WS_TILE));
+                issue((2 + sl) * TC_N, tc::smem_u32(smem + OFF_B2 + sl * B_TILE));
                 tc::mma_commit(&bars->s2_done[sl]);
             }
             // drain: every MMA issued above has completed before TMEM can be released
@@ -218,38 +224,57 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
             tc::mbar_wait_bounded(&bars->drain, 0, WAIT_CYCLES);
         }
         __syncwarp();
-    } else if (warp <= 4) {
+    } else if (warp < WS_E1) {
         // ---------------------------------------------------------------- producer
-        const int pt = tid - 32;                        // 0..127: B1 column (zl, n2)
-        const int zl = pt >> 6, n2 = pt & 63;
+        // thread -> block (n1 = 4 n1q .. 4 n1q + 3, n2 = 4 n2q .. 4 n2q + 3) of both templates
+        const int pt = tid - 32;
+        const int n2q = pt & 15, n1q = pt >> 4;
         for (int64_t k = 0; k < n_my; k++) {
             const int64_t it = it0 + k;
             const int64_t j = it / n_groups;
-            const int z = (int)(it % n_groups) * TC_G + zl;
+            const int z0 = (int)(it % n_groups) * TC_G;
             const int sl = (int)(k & 1);
+            const uint4 *Yj = reinterpret_cast<const uint4 *>(Y + j * TC_S_BF16);
+            uint4 yv[4], gv[TC_G][4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) yv[q] = __ldg(Yj + (64 * (4 * n1q + q) + 4 * n2q) / 4);
+#pragma unroll
+            for (int zl = 0; zl < TC_G; zl++) {
+                const int z = z0 + zl;
+                const uint4 *Gz = reinterpret_cast<const uint4 *>(G + (int64_t)(z < K ? z : 0) * TC_S_BF16);
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    gv[zl][q] = z < K ? __ldg(Gz + (64 * (4 * n1q + q) + 4 * n2q) / 4) : make_uint4(0, 0, 0, 0);
+            }
             if (k >= 2 && !ws_wait(&bars->s1_done[sl], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
-            const bool zvalid = z < K;
-            const __nv_bfloat162 *Yj = Y + j * TC_S_BF16;
-            const __nv_bfloat162 *Gz = G + (int64_t)(zvalid ? z : 0) * TC_S_BF16;
-            unsigned char *b1 = smem + OFF_B1 + sl * WS_TILE;
-#pragma unroll 8
-            for (int b = 0; b < 16; b++) {
-                uint32_t w[4];
+            unsigned char *b1 = smem + OFF_B1 + sl * B_TILE;
+#pragma unroll
+            for (int zl = 0; zl < TC_G; zl++) {
+                uint32_t w[4][4];                                  // [n2 offset e][n1 offset q]
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    const int n = 64 * (4 * b + q) + n2;
-                    const float2 y = unpack_bf16x2(__ldg(Yj + n));
-                    const float2 g = zvalid ? unpack_bf16x2(__ldg(Gz + n)) : make_float2(0.f, 0.f);
-                    w[q] = pack_bf16x2(y.x * g.x + y.y * g.y, y.x * g.y - y.y * g.x);
+                    const uint32_t ys[4] = {yv[q].x, yv[q].y, yv[q].z, yv[q].w};
+                    const uint32_t gs[4] = {gv[zl][q].x, gv[zl][q].y, gv[zl][q].z, gv[zl][q].w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const float2 y = unpack_bf16x2(*reinterpret_cast<const __nv_bfloat162 *>(&ys[e]));
+                        const float2 g = unpack_bf16x2(*reinterpret_cast<const __nv_bfloat162 *>(&gs[e]));
+                        w[e][q] = pack_bf16x2(y.x * g.x + y.y * g.y, y.x * g.y - y.y * g.x);
+                    }
                 }
-                *reinterpret_cast<uint4 *>(b1 + tc::kmajor_offset(TC_N, pt, 8 * b)) = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int c = zl * TC_R + 4 * n2q + e;
+                    *reinterpret_cast<uint4 *>(b1 + tc::kmajor_offset_strided(B_SBO, B_LBO, c, 8 * n1q)) =
+                        make_uint4(w[e][0], w[e][1], w[e][2], w[e][3]);
+                }
             }
             tc::fence_proxy_async_smem();
             mbar_arrive(&bars->b1_full[sl]);
         }
     } else {
         // ---------------------------------------------------------------- epilogues
-        const bool epi1 = warp <= 8;
+        const bool epi1 = warp < WS_E2;
         const int quad = warp & 3;                      // TMEM lane quadrant this warp may access
         const int row = 32 * quad + lane;               // GEMM row (k, p)
         const int kk = row >> 1, rho = row & 1;
@@ -262,15 +287,19 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
                 if (!ws_wait(&bars->s1_done[sl], par, abort_flag)) break;
                 if (k >= 2 && !ws_wait(&bars->s2_done[sl], par ^ 1u, abort_flag)) break;   // B2[sl] free
                 tc::fence_after_thread_sync();
-                unsigned char *b2 = smem + OFF_B2 + sl * WS_TILE;
+                unsigned char *b2 = smem + OFF_B2 + sl * B_TILE;
 #pragma unroll 1
-                for (int ch = 0; ch < 8; ch++) {
+                for (int ch2 = 0; ch2 < 8; ch2 += 2) {
+                  uint32_t rr2[2][16];
+                  tc::tmem_ld16(tbase + lane_base + sl * TC_N + 16 * ch2, rr2[0]);
+                  tc::tmem_ld16(tbase + lane_base + sl * TC_N + 16 * ch2 + 16, rr2[1]);
+                  tc::tmem_ld_wait();
+#pragma unroll
+                  for (int hh = 0; hh < 2; hh++) {
+                    const int ch = ch2 + hh;
                     const int zl = ch >> 2;
-                    uint32_t r[16];
-                    tc::tmem_ld16(tbase + lane_base + sl * TC_N + 16 * ch, r);
-                    tc::tmem_ld_wait();
                     float re[8], im[8];
-                    pair_exchange(r, rho, re, im);
+                    pair_exchange(rr2[hh], rho, re, im);
                     const int n2_0 = 16 * (ch & 3) + 8 * rho;
                     const float4 *twp = reinterpret_cast<const float4 *>(sTw + kk * TC_R + n2_0);
                     uint32_t w[8];
@@ -282,10 +311,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
                         w[q + 1] = pack_bf16x2(re[q + 1] * t2.z - im[q + 1] * t2.w, re[q + 1] * t2.w + im[q + 1] * t2.z);
                     }
                     const int c2 = zl * TC_R + kk;
-                    *reinterpret_cast<uint4 *>(b2 + tc::kmajor_offset(TC_N, c2, 2 * n2_0)) =
+                    *reinterpret_cast<uint4 *>(b2 + tc::kmajor_offset_strided(B_SBO, B_LBO, c2, 2 * n2_0)) =
                         make_uint4(w[0], w[1], w[2], w[3]);
-                    *reinterpret_cast<uint4 *>(b2 + tc::kmajor_offset(TC_N, c2, 2 * n2_0 + 8)) =
+                    *reinterpret_cast<uint4 *>(b2 + tc::kmajor_offset_strided(B_SBO, B_LBO, c2, 2 * n2_0 + 8)) =
                         make_uint4(w[4], w[5], w[6], w[7]);
+                  }
                 }
                 tc::fence_before_thread_sync();
                 tc::fence_proxy_async_smem();
@@ -297,14 +327,18 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
                 const int z0 = (int)(it % n_groups) * TC_G;
                 const int64_t r0 = j * L;
 #pragma unroll 1
-                for (int ch = 0; ch < 8; ch++) {
+                for (int ch2 = 0; ch2 < 8; ch2 += 2) {
+                  uint32_t rr2[2][16];
+                  tc::tmem_ld16(tbase + lane_base + (2 + sl) * TC_N + 16 * ch2, rr2[0]);
+                  tc::tmem_ld16(tbase + lane_base + (2 + sl) * TC_N + 16 * ch2 + 16, rr2[1]);
+                  tc::tmem_ld_wait();
+#pragma unroll
+                  for (int hh = 0; hh < 2; hh++) {
+                    const int ch = ch2 + hh;
                     const int zl = ch >> 2;
                     const int z = z0 + zl;
-                    uint32_t r[16];
-                    tc::tmem_ld16(tbase + lane_base + (2 + sl) * TC_N + 16 * ch, r);
-                    tc::tmem_ld_wait();
                     float re[8], im[8];
-                    pair_exchange(r, rho, re, im);
+                    pair_exchange(rr2[hh], rho, re, im);
                     const int t = 64 * kk + 16 * (ch & 3) + 8 * rho;
                     const int64_t rr = r0 + t;
                     if (z < K && t < L && rr < nb) {
@@ -315,6 +349,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
                         o.w = pack_bf16x2(re[6] * re[6] + im[6] * im[6], re[7] * re[7] + im[7] * im[7]);
                         *reinterpret_cast<uint4 *>(plane + (int64_t)z * nb + rr) = o;
                     }
+                  }
                 }
                 tc::fence_before_thread_sync();
                 mbar_arrive(&bars->d2_free[sl]);

@@ -23,6 +23,13 @@ __host__ __device__ constexpr uint32_t kmajor_offset(uint32_t R, uint32_t row, u
     return ((k >> 3) * (R >> 3) + (row >> 3)) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
 }
 
+// The same layout with core matrices SBO bytes apart along R and LBO bytes apart along K
+// (any multiples of 16); a stride that is not a multiple of 128 spreads the 16-byte rows of
+// neighbouring core matrices over different shared-memory banks.
+__host__ __device__ constexpr uint32_t kmajor_offset_strided(uint32_t sbo, uint32_t lbo, uint32_t row, uint32_t k) {
+    return (k >> 3) * lbo + (row >> 3) * sbo + (row & 7u) * 16u + (k & 7u) * 2u;
+}
+
 // ---------------------------------------------------------------- mbarrier
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
