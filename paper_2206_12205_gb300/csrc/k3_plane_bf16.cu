@@ -7,13 +7,8 @@
 // With x = conj(Yhat_j) * G_z (length S, n = 64 n1 + n2) the plane row segment is
 // |X|^2 with the four-step DFT
 //     X[k1 + 64 k2] = sum_{n2} W_64^{n2 k2} W_S^{n2 k1} sum_{n1} W_64^{n1 k1} x[64 n1 + n2],
-// computed for two templates at a time as two real GEMMs of 128 x 128 x 128:
-//   stage 1  D1[(k1,p), (z,n2)] = F'[(k1,p), (n1,s)] . B1[(n1,s), (z,n2)],  B1 = x (BF16)
-//   twiddle  B2[(n2,s), (z,k1)] = W_S^{n2 k1} D1[k1, (z, n2)]               (CUDA cores, BF16)
-//   stage 2  D2[(k2,p), (z,k1)] = F'[(k2,p), (n2,s)] . B2[(n2,s), (z,k1)]
-//   output   P[z][jL + k1 + 64 k2] = |D2[k2, (z, k1)]|^2 for k1 + 64 k2 < L   (BF16, 16-byte stores)
-// where F' is the radix-64 DFT real-ified with re/im interleaved (row 2k+p, column 2n+s), so
-// the real and imaginary parts of one value sit in adjacent TMEM lanes (adjacent threads).
+// computed for two templates at a time as two real GEMMs of 128 x 128 x 128 (below), where F'
+// is the radix-64 DFT real-ified with re/im interleaved (row 2k+p, column 2n+s).
 //
 // One persistent, warp-specialised CTA per SM walks a contiguous range of (segment, template
 // pair) items with producer, MMA and two epilogue roles overlapped through double-buffered
@@ -75,49 +70,40 @@ __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_bf16(const float2 
     for (int i = 0; i < 32; i++) out[t + i * T] = __floats2bfloat162_rn(v[i].x, v[i].y);
 }
 
-// Split the re (even lane) / im (odd lane) halves of a 16-column TMEM chunk so that each
-// thread of the pair ends up with 8 complex values: the even lane keeps columns 0..7, the
-// odd lane columns 8..15.
-__device__ __forceinline__ void pair_exchange(const uint32_t (&r)[16], int rho, float (&re)[8], float (&im)[8]) {
-#pragma unroll
-    for (int q = 0; q < 8; q++) {
-        const float send = rho == 0 ? __uint_as_float(r[8 + q]) : __uint_as_float(r[q]);
-        const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
-        if (rho == 0) {
-            re[q] = __uint_as_float(r[q]);
-            im[q] = recv;
-        } else {
-            re[q] = recv;
-            im[q] = __uint_as_float(r[8 + q]);
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------------------
-// Warp-specialised persistent kernel (one CTA per SM, 13 warps):
-//   warp 0      TMEM allocation; lane 0 issues the MMAs (stage 1 of item i+1 before stage 2 of i)
-//   warps 1-8   producer:   B1[slot] = conj(Yhat_j) * G_z, one 4 x 4 (n1, n2) block per thread
-//               with all of its 16-byte loads in flight at once
-//   warps 9-12  epilogue 1: D1[slot] (TMEM) -> twiddle -> B2[slot]
-//   warps 13-16 epilogue 2: D2[slot] (TMEM) -> |.|^2 -> BF16 plane
-// Two slots of B1, B2 (shared memory) and D1, D2 (TMEM, 4 x 128 of the 512 columns).
+// Warp-specialised persistent kernel, one CTA per SM, 25 warps.  Both GEMMs run transposed,
+// data as the A operand (M = 128 rows = two templates x 64) and F' as the B operand:
+//   stage 1  D1t[(z,n2), (k1,p)] = B1[(z,n2), (n1,s)] . F'^T        (B1 = x, from the producer)
+//   stage 2  D2t[(z,k1), (k2,p)] = A2[(z,k1), (n2,s)] . F'^T        (A2 = twiddled D1t, transposed)
+// so a thread's TMEM row holds the real and imaginary parts of its values side by side.
+//   warp 0       TMEM allocation; lane 0 issues the MMAs (stage 1 of item i+1 before stage 2 of i)
+//   warps 1-8    producer:   B1[slot] = conj(Yhat_j) * G_z, one 4 x 4 (n1, n2) block per thread
+//                with all of its 16-byte loads in flight at once
+//   warps 9-16   epilogue 1: D1t[slot] -> W_S^{n2 k1} -> A2[slot] (warps 9-12 and 13-16 take the
+//                two halves of k1)
+//   warps 17-24  epilogue 2: D2t[slot] -> |.|^2 -> BF16 plane (halves of k2)
+// Two slots of B1, A2 (shared memory) and D1t, D2t (TMEM, 4 x 128 of the 512 columns).
 // Hand-offs are mbarriers, one per slot:
-//   b1_full  (256 producer arrivals)   s1_done (MMA commit: D1 ready, B1 free)
-//   b2_full  (128 epilogue-1 arrivals: B2 ready, D1 drained)
-//   s2_done  (MMA commit: D2 ready, B2 free)   d2_free (128 epilogue-2 arrivals: D2 drained)
+//   b1_full  (256 producer arrivals)   s1_done (MMA commit: D1t ready, B1 free)
+//   b2_full  (256 epilogue-1 arrivals: A2 ready, D1t drained)
+//   s2_done  (MMA commit: D2t ready, A2 free)   d2_free (256 epilogue-2 arrivals: D2t drained)
 // The k-th use of a slot waits for phase parity k & 1; every wait is bounded and also gives
 // up when another role has aborted.
 constexpr int WS_PRODUCERS = 256;                            // warps 1-8
 constexpr int WS_E1 = 1 + WS_PRODUCERS / 32;                 // first epilogue-1 warp (9)
-constexpr int WS_E2 = WS_E1 + 4;                             // first epilogue-2 warp (13)
-constexpr int WS_THREADS = (WS_E2 + 4) * 32;                 // 17 warps
-// B tiles: K-major, core matrices 144 B apart along N and 16 x 144 B apart along K
+constexpr int WS_E2 = WS_E1 + 8;                             // first epilogue-2 warp (17)
+constexpr int WS_THREADS = (WS_E2 + 8) * 32;                 // 25 warps
+// B1 tiles (stage-1 A operand): core matrices 144 B apart along M, 16 x 144 B along K
 constexpr uint32_t B_SBO = 144, B_LBO = 16 * B_SBO;
-constexpr uint32_t B_TILE = 16 * B_LBO;                      // 36 KB (K = 128 = 16 core matrices)
-constexpr uint32_t OFF_F = 0;                                // F': dense, 32 KB
+constexpr uint32_t B_TILE = 16 * B_LBO;                      // 36 KB
+// A2 tiles (stage-2 A operand): 128 B along M, 2064 B (16 mod 128) along K
+constexpr uint32_t A2_SBO = 128, A2_LBO = 16 * 128 + 16;
+constexpr uint32_t A2_TILE = 16 * A2_LBO;                    // 32.25 KB
+constexpr uint32_t F_LBO = TC_M * 16, F_SBO = 128;           // F': dense
+constexpr uint32_t OFF_F = 0;
 constexpr uint32_t OFF_B1 = OFF_F + TILE_BYTES;              // 2 slots
-constexpr uint32_t OFF_B2 = OFF_B1 + 2 * B_TILE;             // 2 slots
-constexpr uint32_t OFF_TW = OFF_B2 + 2 * B_TILE;             // twiddles, 4096 x float2 = 32 KB
+constexpr uint32_t OFF_A2 = OFF_B1 + 2 * B_TILE;             // 2 slots
+constexpr uint32_t OFF_TW = OFF_A2 + 2 * A2_TILE;            // twiddles, 4096 x float2 = 32 KB
 constexpr uint32_t OFF_BAR = OFF_TW + TC_S_BF16 * 8;
 constexpr uint32_t WS_SMEM = OFF_BAR + 16 * 8 + 32;
 constexpr uint32_t WS_TMEM_COLS = 512;
@@ -164,9 +150,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
         for (int s = 0; s < 2; s++) {
             tc::mbar_init(&bars->b1_full[s], WS_PRODUCERS);
             tc::mbar_init(&bars->s1_done[s], 1);
-            tc::mbar_init(&bars->b2_full[s], 128);
+            tc::mbar_init(&bars->b2_full[s], 256);
             tc::mbar_init(&bars->s2_done[s], 1);
-            tc::mbar_init(&bars->d2_free[s], 128);
+            tc::mbar_init(&bars->d2_free[s], 256);
         }
         tc::mbar_init(&bars->drain, 1);
         *abort_flag = 0;
@@ -188,17 +174,17 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0 && n_my > 0) {
             const uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_N);
-            const uint32_t aF = tc::smem_u32(smem + OFF_F);
-            auto issue = [&](uint32_t dcol, uint32_t bsm) {
+            const uint32_t bF = tc::smem_u32(smem + OFF_F);
+            auto issue = [&](uint32_t dcol, uint32_t asm_, uint32_t albo, uint32_t asbo) {
 #pragma unroll
                 for (int s = 0; s < TC_K / 16; s++)
-                    tc::mma_bf16(tbase + dcol, tc::smem_desc(aF + s * TC_M * 32, TC_M * 16, 128),
-                                 tc::smem_desc(bsm + s * 2 * B_LBO, B_LBO, B_SBO), idesc, s > 0 ? 1u : 0u);
+                    tc::mma_bf16(tbase + dcol, tc::smem_desc(asm_ + s * 2 * albo, albo, asbo),
+                                 tc::smem_desc(bF + s * 2 * F_LBO, F_LBO, F_SBO), idesc, s > 0 ? 1u : 0u);
             };
             bool ok = ws_wait(&bars->b1_full[0], 0, abort_flag);
             if (ok) {
                 tc::fence_after_thread_sync();
-                issue(0 * TC_N, tc::smem_u32(smem + OFF_B1));
+                issue(0, tc::smem_u32(smem + OFF_B1), B_LBO, B_SBO);
                 tc::mma_commit(&bars->s1_done[0]);
             }
             for (int64_t k = 0; k < n_my && ok; k++) {
@@ -209,14 +195,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
                     ok = ws_wait(&bars->b1_full[sn], (uint32_t)(((k + 1) >> 1) & 1), abort_flag);
                     if (!ok) break;
                     tc::fence_after_thread_sync();
-                    issue(sn * TC_N, tc::smem_u32(smem + OFF_B1 + sn * B_TILE));
+                    issue(sn * TC_N, tc::smem_u32(smem + OFF_B1 + sn * B_TILE), B_LBO, B_SBO);
                     tc::mma_commit(&bars->s1_done[sn]);
                 }
-                ok = ws_wait(&bars->b2_full[sl], par, abort_flag);     // B2 ready, D1 drained
+                ok = ws_wait(&bars->b2_full[sl], par, abort_flag);     // A2 ready, D1t drained
                 if (ok && k >= 2) ok = ws_wait(&bars->d2_free[sl], par ^ 1u, abort_flag);
                 if (!ok) break;
                 tc::fence_after_thread_sync();
-                issue((2 + sl) * TC_N, tc::smem_u32(smem + OFF_B2 + sl * B_TILE));
+                issue((2 + sl) * TC_N, tc::smem_u32(smem + OFF_A2 + sl * A2_TILE), A2_LBO, A2_SBO);
                 tc::mma_commit(&bars->s2_done[sl]);
             }
             // drain: every MMA issued above has completed before TMEM can be released
@@ -276,80 +262,75 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
         // ---------------------------------------------------------------- epilogues
         const bool epi1 = warp < WS_E2;
         const int quad = warp & 3;                      // TMEM lane quadrant this warp may access
-        const int row = 32 * quad + lane;               // GEMM row (k, p)
-        const int kk = row >> 1, rho = row & 1;
+        const int half = ((warp - (epi1 ? WS_E1 : WS_E2)) >> 2) & 1;   // which 64 of the 128 columns
+        const int lrow = 32 * quad + lane;              // TMEM lane = GEMM row = (zl, n2) or (zl, k1)
+        const int zl = lrow >> 6, idx = lrow & 63;
         const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
         for (int64_t k = 0; k < n_my; k++) {
             const int64_t it = it0 + k;
             const int sl = (int)(k & 1);
             const uint32_t par = (uint32_t)((k >> 1) & 1);
             if (epi1) {
+                // idx = n2; columns (k1, p) for k1 in [32 half, 32 half + 32)
                 if (!ws_wait(&bars->s1_done[sl], par, abort_flag)) break;
-                if (k >= 2 && !ws_wait(&bars->s2_done[sl], par ^ 1u, abort_flag)) break;   // B2[sl] free
+                if (k >= 2 && !ws_wait(&bars->s2_done[sl], par ^ 1u, abort_flag)) break;   // A2[sl] free
                 tc::fence_after_thread_sync();
-                unsigned char *b2 = smem + OFF_B2 + sl * B_TILE;
+                unsigned char *a2 = smem + OFF_A2 + sl * A2_TILE;
+                const float2 *twr = sTw + idx * TC_R;                       // W_S^{n2 k1}, symmetric
 #pragma unroll 1
-                for (int ch2 = 0; ch2 < 8; ch2 += 2) {
-                  uint32_t rr2[2][16];
-                  tc::tmem_ld16(tbase + lane_base + sl * TC_N + 16 * ch2, rr2[0]);
-                  tc::tmem_ld16(tbase + lane_base + sl * TC_N + 16 * ch2 + 16, rr2[1]);
-                  tc::tmem_ld_wait();
+                for (int ch2 = 0; ch2 < 4; ch2 += 2) {
+                    uint32_t rr[2][16];
+                    tc::tmem_ld16(tbase + lane_base + sl * TC_N + 64 * half + 16 * ch2, rr[0]);
+                    tc::tmem_ld16(tbase + lane_base + sl * TC_N + 64 * half + 16 * ch2 + 16, rr[1]);
+                    tc::tmem_ld_wait();
 #pragma unroll
-                  for (int hh = 0; hh < 2; hh++) {
-                    const int ch = ch2 + hh;
-                    const int zl = ch >> 2;
-                    float re[8], im[8];
-                    pair_exchange(rr2[hh], rho, re, im);
-                    const int n2_0 = 16 * (ch & 3) + 8 * rho;
-                    const float4 *twp = reinterpret_cast<const float4 *>(sTw + kk * TC_R + n2_0);
-                    uint32_t w[8];
+                    for (int hh = 0; hh < 2; hh++) {
+                        const int k1_0 = 32 * half + 8 * (ch2 + hh);
+                        const float4 *tp = reinterpret_cast<const float4 *>(twr + k1_0);
 #pragma unroll
-                    for (int q2 = 0; q2 < 4; q2++) {
-                        const float4 t2 = twp[q2];
-                        const int q = 2 * q2;
-                        w[q] = pack_bf16x2(re[q] * t2.x - im[q] * t2.y, re[q] * t2.y + im[q] * t2.x);
-                        w[q + 1] = pack_bf16x2(re[q + 1] * t2.z - im[q + 1] * t2.w, re[q + 1] * t2.w + im[q + 1] * t2.z);
+                        for (int q2 = 0; q2 < 4; q2++) {
+                            const float4 t2 = tp[q2];
+#pragma unroll
+                            for (int u = 0; u < 2; u++) {
+                                const int q = 2 * q2 + u;
+                                const float re = __uint_as_float(rr[hh][2 * q]), im = __uint_as_float(rr[hh][2 * q + 1]);
+                                const float tx = u ? t2.z : t2.x, ty = u ? t2.w : t2.y;
+                                const uint32_t wv = pack_bf16x2(re * tx - im * ty, re * ty + im * tx);
+                                const int row = zl * TC_R + k1_0 + q;
+                                *reinterpret_cast<uint32_t *>(a2 + tc::kmajor_offset_strided(A2_SBO, A2_LBO, row, 2 * idx)) = wv;
+                            }
+                        }
                     }
-                    const int c2 = zl * TC_R + kk;
-                    *reinterpret_cast<uint4 *>(b2 + tc::kmajor_offset_strided(B_SBO, B_LBO, c2, 2 * n2_0)) =
-                        make_uint4(w[0], w[1], w[2], w[3]);
-                    *reinterpret_cast<uint4 *>(b2 + tc::kmajor_offset_strided(B_SBO, B_LBO, c2, 2 * n2_0 + 8)) =
-                        make_uint4(w[4], w[5], w[6], w[7]);
-                  }
                 }
                 tc::fence_before_thread_sync();
                 tc::fence_proxy_async_smem();
                 mbar_arrive(&bars->b2_full[sl]);
             } else {
+                // idx = k1; columns (k2, p) for k2 in [32 half, 32 half + 32)
                 if (!ws_wait(&bars->s2_done[sl], par, abort_flag)) break;
                 tc::fence_after_thread_sync();
                 const int64_t j = it / n_groups;
-                const int z0 = (int)(it % n_groups) * TC_G;
+                const int z = (int)(it % n_groups) * TC_G + zl;
                 const int64_t r0 = j * L;
+                __nv_bfloat16 *prow = plane + (int64_t)(z < K ? z : 0) * nb + r0 + idx;
 #pragma unroll 1
-                for (int ch2 = 0; ch2 < 8; ch2 += 2) {
-                  uint32_t rr2[2][16];
-                  tc::tmem_ld16(tbase + lane_base + (2 + sl) * TC_N + 16 * ch2, rr2[0]);
-                  tc::tmem_ld16(tbase + lane_base + (2 + sl) * TC_N + 16 * ch2 + 16, rr2[1]);
-                  tc::tmem_ld_wait();
+                for (int ch2 = 0; ch2 < 4; ch2 += 2) {
+                    uint32_t rr[2][16];
+                    tc::tmem_ld16(tbase + lane_base + (2 + sl) * TC_N + 64 * half + 16 * ch2, rr[0]);
+                    tc::tmem_ld16(tbase + lane_base + (2 + sl) * TC_N + 64 * half + 16 * ch2 + 16, rr[1]);
+                    tc::tmem_ld_wait();
 #pragma unroll
-                  for (int hh = 0; hh < 2; hh++) {
-                    const int ch = ch2 + hh;
-                    const int zl = ch >> 2;
-                    const int z = z0 + zl;
-                    float re[8], im[8];
-                    pair_exchange(rr2[hh], rho, re, im);
-                    const int t = 64 * kk + 16 * (ch & 3) + 8 * rho;
-                    const int64_t rr = r0 + t;
-                    if (z < K && t < L && rr < nb) {
-                        uint4 o;
-                        o.x = pack_bf16x2(re[0] * re[0] + im[0] * im[0], re[1] * re[1] + im[1] * im[1]);
-                        o.y = pack_bf16x2(re[2] * re[2] + im[2] * im[2], re[3] * re[3] + im[3] * im[3]);
-                        o.z = pack_bf16x2(re[4] * re[4] + im[4] * im[4], re[5] * re[5] + im[5] * im[5]);
-                        o.w = pack_bf16x2(re[6] * re[6] + im[6] * im[6], re[7] * re[7] + im[7] * im[7]);
-                        *reinterpret_cast<uint4 *>(plane + (int64_t)z * nb + rr) = o;
+                    for (int hh = 0; hh < 2; hh++) {
+                        const int k2_0 = 32 * half + 8 * (ch2 + hh);
+#pragma unroll
+                        for (int q = 0; q < 8; q++) {
+                            const int t = idx + 64 * (k2_0 + q);
+                            if (z < K && t < L && r0 + t < nb) {
+                                const float re = __uint_as_float(rr[hh][2 * q]), im = __uint_as_float(rr[hh][2 * q + 1]);
+                                prow[64 * (k2_0 + q)] = __float2bfloat16_rn(re * re + im * im);
+                            }
+                        }
                     }
-                  }
                 }
                 tc::fence_before_thread_sync();
                 mbar_arrive(&bars->d2_free[sl]);
