@@ -103,8 +103,11 @@ constexpr uint32_t F_LBO = TC_M * 16, F_SBO = 128;           // F': dense
 constexpr uint32_t OFF_F = 0;
 constexpr uint32_t OFF_B1 = OFF_F + TILE_BYTES;              // 2 slots
 constexpr uint32_t OFF_A2 = OFF_B1 + 2 * B_TILE;             // 2 slots
-constexpr uint32_t OFF_TW = OFF_A2 + 2 * A2_TILE;            // twiddles, 4096 x float2 = 32 KB
-constexpr uint32_t OFF_BAR = OFF_TW + TC_S_BF16 * 8;
+// twiddles W_S^{n2 k1}, one row per n2 padded to 66 entries (528 B = 16 mod 128) so that the
+// 16-byte row reads of a warp's 32 different rows spread over all banks
+constexpr int TW_LD = TC_R + 2;
+constexpr uint32_t OFF_TW = OFF_A2 + 2 * A2_TILE;
+constexpr uint32_t OFF_BAR = OFF_TW + TC_R * TW_LD * 8;
 constexpr uint32_t WS_SMEM = OFF_BAR + 16 * 8 + 32;
 constexpr uint32_t WS_TMEM_COLS = 512;
 
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
     }
     for (int i = tid; i < (int)(TILE_BYTES / 16); i += WS_THREADS)
         reinterpret_cast<uint4 *>(smem + OFF_F)[i] = __ldg(Fimg + i);
-    for (int i = tid; i < TC_S_BF16; i += WS_THREADS) sTw[i] = __ldg(tw + i);
+    for (int i = tid; i < TC_S_BF16; i += WS_THREADS) sTw[(i / TC_R) * TW_LD + (i % TC_R)] = __ldg(tw + i);
     tc::fence_proxy_async_smem();
     tc::fence_before_thread_sync();
     __syncthreads();
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
                 if (k >= 2 && !ws_wait(&bars->s2_done[sl], par ^ 1u, abort_flag)) break;   // A2[sl] free
                 tc::fence_after_thread_sync();
                 unsigned char *a2 = smem + OFF_A2 + sl * A2_TILE;
-                const float2 *twr = sTw + idx * TC_R;                       // W_S^{n2 k1}, symmetric
+                const float2 *twr = sTw + idx * TW_LD;                      // W_S^{n2 k1}, row n2
 #pragma unroll 1
                 for (int ch2 = 0; ch2 < 4; ch2 += 2) {
                     uint32_t rr[2][16];
