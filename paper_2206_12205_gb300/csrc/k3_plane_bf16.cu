@@ -246,9 +246,13 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
                     const uint32_t gs[4] = {gv[zl][q].x, gv[zl][q].y, gv[zl][q].z, gv[zl][q].w};
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
-                        const float2 y = unpack_bf16x2(*reinterpret_cast<const __nv_bfloat162 *>(&ys[e]));
-                        const float2 g = unpack_bf16x2(*reinterpret_cast<const __nv_bfloat162 *>(&gs[e]));
-                        w[e][q] = pack_bf16x2(y.x * g.x + y.y * g.y, y.x * g.y - y.y * g.x);
+                        // conj(y) g = (yr, yr) (gr, gi) + (yi, yi) (gi, -gr), in packed BF16 arithmetic
+                        const __nv_bfloat162 y = *reinterpret_cast<const __nv_bfloat162 *>(&ys[e]);
+                        const __nv_bfloat162 g = *reinterpret_cast<const __nv_bfloat162 *>(&gs[e]);
+                        __nv_bfloat162 gb = __lowhigh2highlow(g);
+                        *reinterpret_cast<uint32_t *>(&gb) ^= 0x80000000u;
+                        const __nv_bfloat162 x = __hfma2(__high2bfloat162(y), gb, __hmul2(__low2bfloat162(y), g));
+                        w[e][q] = *reinterpret_cast<const uint32_t *>(&x);
                     }
                 }
 #pragma unroll

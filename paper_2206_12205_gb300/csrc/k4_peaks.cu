@@ -30,7 +30,9 @@ namespace {
 
 constexpr int RB = PEAK_ROWS;            // rows per tile (one warp each)
 constexpr int CB = PEAK_CHUNK;           // bins per tile / unit
-constexpr int SW = CB + 2;               // staged row width with the halo
+constexpr int SW = CB + 2;               // staged cells per row: bins r0-1 .. r0+CB
+constexpr int SOFF = 3;                  // staged cell c sits at S[row][c + SOFF]: the interior
+constexpr int SWP = CB + 8;              // (c = 1 .. CB) starts on a 16-byte boundary; row pitch
 constexpr int WORDS = CB / 32;           // mask words per unit
 constexpr int SCAN_BLOCK = PEAK_SCAN_BLOCK;
 
@@ -81,39 +83,53 @@ __device__ __forceinline__ bool row_in_level(int i, int K, int zmax, int H) {
     return i >= 0 && i < K && abs(H * z) <= zmax;
 }
 
-// Add the harmonics h = H/2+1 .. H to S_{H/2} for the cells of one staged row (thread-strided
-// columns); all loads of a cell are issued before its ordered sum.
+// S_H = S_{H/2} + sum_{h = H/2+1 .. H} P(h r, i_h) for every staged cell inside level H's region
+// (-inf outside).  Each thread takes cells tid, tid + 256, ...; a batch of KB cells issues all
+// of its KB x H/2 = 16 loads before the ordered sums, keeping many independent loads in flight.
 template <typename E, int H>
-__device__ __forceinline__ void level_update(float *Srow, const E *__restrict__ plane, int64_t nb, int zmax, int z,
-                                             bool row_ok, int64_t r0, int64_t rmax) {
+__device__ __forceinline__ void level_update(float (*S)[SWP], const E *__restrict__ plane, int64_t nb, int zmax,
+                                             int K, int i0, int64_t r0, int64_t rmax) {
     constexpr int NH = H / 2;
-    const E *base[NH];
+    constexpr int CELLS = (RB + 2) * SW;
+    constexpr int PER = (CELLS + RB * 32 - 1) / (RB * 32);
+    constexpr int KB = 16 / NH;
+    for (int k0 = 0; k0 < PER; k0 += KB) {
+        float v[KB][NH];
+        bool ok[KB];
 #pragma unroll
-    for (int q = 0; q < NH; q++) base[q] = plane + (int64_t)((((NH + 1 + q) * z) + zmax) >> 1) * nb;
-    constexpr int NC = (SW + RB * 32 - 1) / (RB * 32);
+        for (int kb = 0; kb < KB; kb++) {
+            const int cell = threadIdx.x + (k0 + kb) * RB * 32;
+            const int ri = cell / SW, c = cell - ri * SW;
+            const int i = i0 - 1 + ri;
+            const int64_t r = r0 - 1 + c;
+            ok[kb] = (k0 + kb < PER) && cell < CELLS && row_in_level(i, K, zmax, H) && r >= 0 && r <= rmax;
+            const int z = -zmax + 2 * i;
 #pragma unroll
-    for (int cc = 0; cc < NC; cc++) {
-        const int c = threadIdx.x + cc * RB * 32;
-        if (c >= SW) break;
-        const int64_t r = r0 - 1 + c;
-        float s = -INFINITY;
-        if (row_ok && r >= 0 && r <= rmax) {
-            float v[NH];
-#pragma unroll
-            for (int q = 0; q < NH; q++) v[q] = ld_plane(base[q], (int64_t)(NH + 1 + q) * r);
-            s = Srow[c];
-#pragma unroll
-            for (int q = 0; q < NH; q++) s = __fadd_rn(s, v[q]);
+            for (int q = 0; q < NH; q++)
+                v[kb][q] = ok[kb] ? ld_plane(plane + (int64_t)(((NH + 1 + q) * z + zmax) >> 1) * nb, (int64_t)(NH + 1 + q) * r)
+                                  : 0.0f;
         }
-        Srow[c] = s;
+#pragma unroll
+        for (int kb = 0; kb < KB; kb++) {
+            const int cell = threadIdx.x + (k0 + kb) * RB * 32;
+            if (k0 + kb >= PER || cell >= CELLS) continue;
+            const int ri = cell / SW, c = cell - ri * SW;
+            float sum = -INFINITY;
+            if (ok[kb]) {
+                sum = S[ri][c + SOFF];
+#pragma unroll
+                for (int q = 0; q < NH; q++) sum = __fadd_rn(sum, v[kb][q]);
+            }
+            S[ri][c + SOFF] = sum;
+        }
     }
 }
 
 template <typename E>
-__global__ void __launch_bounds__(RB * 32) k4_detect(const E *__restrict__ plane, int64_t nb, int zmax, int K,
+__global__ void __launch_bounds__(RB * 32, 4) k4_detect(const E *__restrict__ plane, int64_t nb, int zmax, int K,
                                                      LevelTable lt, int n_rb, int32_t *__restrict__ unit_count,
                                                      uint32_t *__restrict__ unit_mask) {
-    __shared__ float S[RB + 2][SW];
+    __shared__ __align__(16) float S[RB + 2][SWP];
     const int tile = blockIdx.x;
     const int rb = tile % n_rb;                    // row blocks of one chunk run side by side (halo rows hit L2)
     const int64_t chunk = tile / n_rb;
@@ -149,7 +165,9 @@ __global__ void __launch_bounds__(RB * 32) k4_detect(const E *__restrict__ plane
             const int ri = v / VPR, q = v % VPR;
             if (ri < RB + 2) {
 #pragma unroll
-                for (int e = 0; e < EPV; e++) S[ri][1 + q * EPV + e] = vals[k][e];
+                for (int e = 0; e < EPV; e += 4)
+                    *reinterpret_cast<float4 *>(&S[ri][1 + SOFF + q * EPV + e]) =
+                        make_float4(vals[k][e], vals[k][e + 1], vals[k][e + 2], vals[k][e + 3]);
             }
         }
         if (threadIdx.x < 2 * (RB + 2)) {
@@ -157,7 +175,7 @@ __global__ void __launch_bounds__(RB * 32) k4_detect(const E *__restrict__ plane
             const int c = (threadIdx.x & 1) ? SW - 1 : 0;
             const int i = i0 - 1 + ri;
             const int64_t r = r0 - 1 + c;
-            S[ri][c] = (i >= 0 && i < K && r >= 0 && r < nb) ? ld_plane(plane + (int64_t)i * nb, r) : -INFINITY;
+            S[ri][c + SOFF] = (i >= 0 && i < K && r >= 0 && r < nb) ? ld_plane(plane + (int64_t)i * nb, r) : -INFINITY;
         }
     }
     __syncthreads();
@@ -171,17 +189,11 @@ __global__ void __launch_bounds__(RB * 32) k4_detect(const E *__restrict__ plane
         if (l > 0) {
             // S_H = S_{H/2} + sum_{h = H/2+1 .. H} P(h r, i_h) inside level H's region, -inf outside
             __syncthreads();
-#pragma unroll 1
-            for (int ri = 0; ri < RB + 2; ri++) {
-                const int i = i0 - 1 + ri;
-                const bool row_ok = row_in_level(i, K, zmax, H);
-                const int z = -zmax + 2 * i;
-                switch (H) {
-                    case 2: level_update<E, 2>(S[ri], plane, nb, zmax, z, row_ok, r0, d.rmax); break;
-                    case 4: level_update<E, 4>(S[ri], plane, nb, zmax, z, row_ok, r0, d.rmax); break;
-                    case 8: level_update<E, 8>(S[ri], plane, nb, zmax, z, row_ok, r0, d.rmax); break;
-                    default: level_update<E, 16>(S[ri], plane, nb, zmax, z, row_ok, r0, d.rmax); break;
-                }
+            switch (H) {
+                case 2: level_update<E, 2>(S, plane, nb, zmax, K, i0, r0, d.rmax); break;
+                case 4: level_update<E, 4>(S, plane, nb, zmax, K, i0, r0, d.rmax); break;
+                case 8: level_update<E, 8>(S, plane, nb, zmax, K, i0, r0, d.rmax); break;
+                default: level_update<E, 16>(S, plane, nb, zmax, K, i0, r0, d.rmax); break;
             }
             __syncthreads();
         }
@@ -192,7 +204,7 @@ __global__ void __launch_bounds__(RB * 32) k4_detect(const E *__restrict__ plane
             const int cmax = (int)min((int64_t)CB, d.rmax - r0 + 1);   // valid bins in this chunk
 #pragma unroll
             for (int e = 0; e < WORDS; e++) {
-                const int c = 1 + lane + 32 * e;
+                const int c = 1 + SOFF + lane + 32 * e;
                 bool pk = false;
                 if (lane + 32 * e < cmax) {
                     const float v = S[warp + 1][c];
