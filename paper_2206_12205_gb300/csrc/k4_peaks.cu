@@ -84,43 +84,54 @@ __device__ __forceinline__ bool row_in_level(int i, int K, int zmax, int H) {
 }
 
 // S_H = S_{H/2} + sum_{h = H/2+1 .. H} P(h r, i_h) for every staged cell inside level H's region
-// (-inf outside).  Each thread takes cells tid, tid + 256, ...; a batch of KB cells issues all
-// of its KB x H/2 = 16 loads before the ordered sums, keeping many independent loads in flight.
+// (-inf outside).  A thread owns columns tid, tid + 256, tid + 512 of every staged row; the row
+// pointers of each harmonic are formed once per row, and a batch of rows issues all of its
+// loads before the ordered sums, so that about 16 independent loads are in flight per thread.
 template <typename E, int H>
 __device__ __forceinline__ void level_update(float (*S)[SWP], const E *__restrict__ plane, int64_t nb, int zmax,
                                              int K, int i0, int64_t r0, int64_t rmax) {
     constexpr int NH = H / 2;
-    constexpr int CELLS = (RB + 2) * SW;
-    constexpr int PER = (CELLS + RB * 32 - 1) / (RB * 32);
-    constexpr int KB = 16 / NH;
-    for (int k0 = 0; k0 < PER; k0 += KB) {
-        float v[KB][NH];
-        bool ok[KB];
+    constexpr int NC = (SW + RB * 32 - 1) / (RB * 32);            // columns per thread (3)
+    constexpr int RBAT = (16 / (NH * NC)) > 0 ? 16 / (NH * NC) : 1;
+    for (int ri0 = 0; ri0 < RB + 2; ri0 += RBAT) {
+        float v[RBAT][NC][NH];
+        bool ok[RBAT][NC];
 #pragma unroll
-        for (int kb = 0; kb < KB; kb++) {
-            const int cell = threadIdx.x + (k0 + kb) * RB * 32;
-            const int ri = cell / SW, c = cell - ri * SW;
+        for (int rb = 0; rb < RBAT; rb++) {
+            const int ri = ri0 + rb;
             const int i = i0 - 1 + ri;
-            const int64_t r = r0 - 1 + c;
-            ok[kb] = (k0 + kb < PER) && cell < CELLS && row_in_level(i, K, zmax, H) && r >= 0 && r <= rmax;
+            const bool row_ok = ri < RB + 2 && row_in_level(i, K, zmax, H);
             const int z = -zmax + 2 * i;
+            const E *base[NH];
 #pragma unroll
             for (int q = 0; q < NH; q++)
-                v[kb][q] = ok[kb] ? ld_plane(plane + (int64_t)(((NH + 1 + q) * z + zmax) >> 1) * nb, (int64_t)(NH + 1 + q) * r)
-                                  : 0.0f;
+                base[q] = plane + (row_ok ? (int64_t)(((NH + 1 + q) * z + zmax) >> 1) * nb : 0);
+#pragma unroll
+            for (int cc = 0; cc < NC; cc++) {
+                const int c = threadIdx.x + cc * RB * 32;
+                const int64_t r = r0 - 1 + c;
+                ok[rb][cc] = row_ok && c < SW && r >= 0 && r <= rmax;
+#pragma unroll
+                for (int q = 0; q < NH; q++)
+                    v[rb][cc][q] = ok[rb][cc] ? ld_plane(base[q], (int64_t)(NH + 1 + q) * r) : 0.0f;
+            }
         }
 #pragma unroll
-        for (int kb = 0; kb < KB; kb++) {
-            const int cell = threadIdx.x + (k0 + kb) * RB * 32;
-            if (k0 + kb >= PER || cell >= CELLS) continue;
-            const int ri = cell / SW, c = cell - ri * SW;
-            float sum = -INFINITY;
-            if (ok[kb]) {
-                sum = S[ri][c + SOFF];
+        for (int rb = 0; rb < RBAT; rb++) {
+            const int ri = ri0 + rb;
+            if (ri >= RB + 2) break;
 #pragma unroll
-                for (int q = 0; q < NH; q++) sum = __fadd_rn(sum, v[kb][q]);
+            for (int cc = 0; cc < NC; cc++) {
+                const int c = threadIdx.x + cc * RB * 32;
+                if (c >= SW) break;
+                float sum = -INFINITY;
+                if (ok[rb][cc]) {
+                    sum = S[ri][c + SOFF];
+#pragma unroll
+                    for (int q = 0; q < NH; q++) sum = __fadd_rn(sum, v[rb][cc][q]);
+                }
+                S[ri][c + SOFF] = sum;
             }
-            S[ri][c + SOFF] = sum;
         }
     }
 }
@@ -202,6 +213,16 @@ __global__ void __launch_bounds__(RB * 32, 4) k4_detect(const E *__restrict__ pl
             int cnt = 0;
             uint32_t words[WORDS];
             const int cmax = (int)min((int64_t)CB, d.rmax - r0 + 1);   // valid bins in this chunk
+            // fast path: nothing in the row segment above the threshold -> an empty unit
+            float vmax = -INFINITY;
+#pragma unroll
+            for (int e = 0; e < WORDS; e++)
+                if (lane + 32 * e < cmax) vmax = fmaxf(vmax, S[warp + 1][1 + SOFF + lane + 32 * e]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            if (!(vmax > d.thr)) {
+                if (lane == 0) unit_count[d.unit0 + (int64_t)(row - d.i_lo) * d.chunks + chunk] = 0;
+            } else {
 #pragma unroll
             for (int e = 0; e < WORDS; e++) {
                 const int c = 1 + SOFF + lane + 32 * e;
@@ -225,6 +246,7 @@ __global__ void __launch_bounds__(RB * 32, 4) k4_detect(const E *__restrict__ pl
                 for (int e = 0; e < WORDS; e++)
                     if (e == lane) w = words[e];
                 unit_mask[u * WORDS + lane] = w;
+            }
             }
         }
     }
