@@ -22,8 +22,11 @@
  *     m taps at q = -m/2 .. m/2-1 of the response of a constant-fdot sinusoid
  *     I(q, z) = int_0^1 exp(i pi (z u^2 - 2 q u)) du, scaled to unit norm (Sec. 3.3).
  *   - Plane: P[i][r] = | sum_q Xhat[r+q] conj(T_i(q)) |^2, r = 0..Nb-1, row-major [K][Nb]
- *     (r contiguous); Xhat is zero outside [0, Nb).  Element type is float for
- *     FDAS_FP32 and bfloat16 (the upper 16 bits of the float) for the BF16 precisions.
+ *     (r contiguous); Xhat is zero outside [0, Nb).  Element type is bfloat16 (the upper
+ *     16 bits of the float) for FDAS_BF16 and float otherwise.
+ *   - The tensor-core precisions (FDAS_BF16, FDAS_BF16_SPLIT) run their overlap-save with
+ *     4096-bin segments whatever seg_len says (the plane does not depend on it) and accept
+ *     at most 2048 taps.
  *   - All device pointers are CUDA device addresses on the current device; the caller
  *     owns them.  Alignment: series and spectra 8 bytes, plane 16 bytes, workspace 256
  *     bytes, peak list and counts 4 bytes (cudaMalloc'd and torch buffers satisfy all of
@@ -59,7 +62,8 @@ typedef enum {
     FDAS_FP32 = 0,           /* FP32 plane, FP32 CUDA-core FFTs                           */
     FDAS_BF16 = 1,           /* BF16 spectrum/templates, tensor-core DFT stages with FP32
                                 accumulation, BF16 plane (Sec. 3)                          */
-    FDAS_BF16_SPLIT = 2      /* compensated hi+lo BF16 products, BF16 plane               */
+    FDAS_BF16_SPLIT = 2      /* compensated hi+lo BF16 operands (three products per MMA step,
+                                about 16 significant bits), FP32 plane                      */
 } fdas_precision;
 
 /* Device status bits (fdas_device_status). */
@@ -96,7 +100,7 @@ typedef struct {
     int32_t K;               /* template rows                                                */
     int32_t seg_valid;       /* L = S - m + 1 plane bins kept per segment                     */
     int64_t n_seg;           /* ceil(Nb / L) overlap-save segments                            */
-    int32_t plane_elem_bytes;/* 4 (FP32) or 2 (BF16)                                          */
+    int32_t plane_elem_bytes;/* 2 for FDAS_BF16, else 4                                       */
     int64_t plane_bytes;     /* K * Nb * plane_elem_bytes                                     */
     size_t  workspace_bytes; /* caller-provided scratch for fdas_search                       */
     int64_t cells;           /* K * Nb                                                        */

@@ -31,7 +31,8 @@ fdas_status record(Plan *p, cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? FDAS_E_NOMEM : FDAS_E_CUDA;
 }
 
-bool plane_is_bf16(const Plan *p) { return p->cfg.precision != FDAS_FP32; }
+bool plane_is_bf16(const Plan *p) { return p->cfg.precision == FDAS_BF16; }
+bool uses_tensor_path(const Plan *p) { return p->cfg.precision != FDAS_FP32; }
 
 // Alignment the kernels' vector accesses rely on (documented in fdas.h).
 bool aligned(const void *ptr, uintptr_t a) { return (reinterpret_cast<uintptr_t>(ptr) & (a - 1)) == 0; }
@@ -39,6 +40,16 @@ bool args_aligned(const void *series, const void *xhat, const void *ws, const vo
     return aligned(series, 8) && aligned(xhat, 8) && aligned(ws, 256) && aligned(plane, 16) && aligned(peaks, 4);
 }
 
+}  // namespace
+
+namespace {
+cudaError_t launch_plane_any(Plan *p, const float2 *x, const float *scale, char *ws, void *d_plane, cudaStream_t st) {
+    switch (p->cfg.precision) {
+        case FDAS_BF16: return fdas::launch_plane_bf16(*p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
+        case FDAS_BF16_SPLIT: return fdas::launch_plane_split(*p, x, scale, ws, static_cast<float *>(d_plane), st);
+        default: return fdas::launch_plane_fp32(*p, x, scale, ws, static_cast<float *>(d_plane), st);
+    }
+}
 }  // namespace
 
 extern "C" {
@@ -76,8 +87,7 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
         if (c.thr[l] != c.thr[l]) return FDAS_E_INVALID;
     if (c.precision != FDAS_FP32 && c.precision != FDAS_BF16 && c.precision != FDAS_BF16_SPLIT)
         return FDAS_E_INVALID;
-    if (c.precision == FDAS_BF16_SPLIT) return FDAS_E_UNSUPPORTED;
-    if (c.precision == FDAS_BF16 && c.taps > fdas::TC_MAX_TAPS) return FDAS_E_UNSUPPORTED;
+    if (c.precision != FDAS_FP32 && c.taps > fdas::TC_MAX_TAPS) return FDAS_E_UNSUPPORTED;
 
     fdas_plan_s *p = new (std::nothrow) fdas_plan_s();
     if (!p) return FDAS_E_NOMEM;
@@ -152,16 +162,16 @@ fdas_status fdas_make_templates(fdas_plan_t plan, void *stream) {
     alloc((void **)&p->d_twn_lo, sizeof(float2) * ((size_t)1 << fdas::TW_LO_BITS));
     alloc((void **)&p->d_twn_hi, sizeof(float2) * (size_t)nhi);
     alloc((void **)&p->d_G, sizeof(float2) * nbank);
-    if (plane_is_bf16(p)) {
+    if (uses_tensor_path(p)) {
         alloc((void **)&p->d_Gbf, sizeof(__nv_bfloat162) * nbank);
         if (p->cfg.precision == FDAS_BF16_SPLIT) alloc((void **)&p->d_Gbf_lo, sizeof(__nv_bfloat162) * nbank);
-        alloc((void **)&p->d_tcF, 2 * 128 * 128);
+        alloc((void **)&p->d_tcF, 2 * 2 * 128 * 128);
         alloc((void **)&p->d_tcTw, sizeof(float2) * 64 * 64);
     }
     alloc((void **)&p->d_status, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = fdas::launch_make_templates(*p, st);
-    if (e == cudaSuccess && plane_is_bf16(p)) e = fdas::launch_prepare_bf16(*p, st);
+    if (e == cudaSuccess && uses_tensor_path(p)) e = fdas::launch_prepare_bf16(*p, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return record(p, e);
     p->templates_ready = true;
@@ -196,11 +206,7 @@ fdas_status fdas_plane(fdas_plan_t plan, const float *d_xhat, void *d_workspace,
     char *ws = static_cast<char *>(d_workspace);
     const float2 *x = reinterpret_cast<const float2 *>(d_xhat);
     p->prof.calls++;
-    cudaError_t e;
-    if (plane_is_bf16(p))
-        e = fdas::launch_plane_bf16(*p, x, nullptr, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
-    else
-        e = fdas::launch_plane_fp32(*p, x, nullptr, ws, static_cast<float *>(d_plane), st);
+    const cudaError_t e = launch_plane_any(p, x, nullptr, ws, d_plane, st);
     return record(p, e);
 }
 
@@ -231,12 +237,7 @@ fdas_status fdas_search(fdas_plan_t plan, const float *d_series, void *d_workspa
     cudaError_t e = fdas::launch_spectrum(*p, d_series, ws, st);
     const float2 *x = reinterpret_cast<const float2 *>(ws + p->ws_x);
     const float *scale = reinterpret_cast<const float *>(ws + p->ws_scale + 8);
-    if (e == cudaSuccess) {
-        if (plane_is_bf16(p))
-            e = fdas::launch_plane_bf16(*p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
-        else
-            e = fdas::launch_plane_fp32(*p, x, scale, ws, static_cast<float *>(d_plane), st);
-    }
+    if (e == cudaSuccess) e = launch_plane_any(p, x, scale, ws, d_plane, st);
     if (e == cudaSuccess) e = fdas::launch_peaks(*p, d_plane, plane_is_bf16(p), ws, d_peaks, d_npeaks, 0u, st);
     return record(p, e);
 }

@@ -60,7 +60,7 @@ struct Plan {
     float2 *d_G;           // [K][S] FP32 template bank
     __nv_bfloat162 *d_Gbf; // [K][S] BF16 template bank (hi), BF16 precisions
     __nv_bfloat162 *d_Gbf_lo; // [K][S] BF16 residual (lo), split precision
-    void *d_tcF;           // real-ified radix-64 DFT matrix, BF16, K-major operand image (32 KB)
+    void *d_tcF;           // real-ified radix-64 DFT matrix, BF16 K-major operand images: hi, then lo (2 x 32 KB)
     float2 *d_tcTw;        // W_4096^{n2 k1}, [k1][n2] (32 KB)
     int32_t *d_status;     // sticky device status word
     bool templates_ready;
@@ -103,6 +103,11 @@ cudaError_t launch_plane_fp32_scratch(const Plan &p, const float2 *d_x, const fl
 cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
                               __nv_bfloat16 *d_plane, cudaStream_t st);
 cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st);
+// FP32 segment spectra for 4096-bin segments (the split-BF16 path's input).
+cudaError_t launch_segments_fp32(const Plan &p, const float2 *d_x, const float *d_scale, float2 *d_yhat,
+                                 cudaStream_t st);
+cudaError_t launch_plane_split(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
+                               cudaStream_t st);
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
                          fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st);
 

@@ -112,6 +112,19 @@ cudaError_t launch_plane_fp32(const Plan &p, const float2 *d_x, const float *d_s
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_segments_fp32(const Plan &p, const float2 *d_x, const float *d_scale, float2 *d_yhat,
+                                 cudaStream_t st) {
+    if (p.S != 4096) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float2) * fft_smem_entries(4096);
+    cudaError_t e = cudaFuncSetAttribute(k2_segments<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    p.prof.begin(FDAS_STAGE_SEGMENTS, st);
+    k2_segments<4096><<<(unsigned)p.n_seg, 4096 / 32, smem, st>>>(d_x, d_scale, p.d_tw, d_yhat, p.nb, p.L, p.m / 2);
+    p.prof.end(FDAS_STAGE_SEGMENTS, st);
+    p.prof.launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_plane_fp32_scratch(const Plan &p, const float2 *d_x, const float *d_scale, float2 *d_yhat,
                                       float *d_plane, cudaStream_t st) {
     switch (p.S) {

@@ -42,8 +42,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-__device__ __forceinline__ float2 unpack_bf16x2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
-
 // Segment FFTs (FP32 CUDA-core block FFT), stored as BF16 pairs for the tensor stages.
 __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_bf16(const float2 *__restrict__ X,
                                                                    const float *__restrict__ scale_ptr,
@@ -353,6 +351,181 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Compensated split-BF16 variant (accuracy recovery): every operand v is carried as
+// v_hi + v_lo with v_hi = bf16(v), v_lo = bf16(v - v_hi) (about 16 significant bits), and each
+// product as a_hi b_hi + a_lo b_hi + a_hi b_lo (the a_lo b_lo term, ~2^-18 relative, is
+// dropped): three MMAs per K step, FP32 accumulation in TMEM.  Inputs are the FP32 segment
+// spectra and the FP32 templates; the plane is stored in FP32.  Same transposed two-stage
+// DFT as above, one item at a time per CTA (synchronous), 8 warps.
+constexpr int SP_THREADS = 256;
+constexpr uint32_t SP_OFF_FHI = 0;
+constexpr uint32_t SP_OFF_FLO = TILE_BYTES;
+constexpr uint32_t SP_OFF_AHI = 2 * TILE_BYTES;                      // A tiles (B1 layout / A2 layout)
+constexpr uint32_t SP_TILE = B_TILE > A2_TILE ? B_TILE : A2_TILE;
+constexpr uint32_t SP_OFF_ALO = SP_OFF_AHI + SP_TILE;
+constexpr uint32_t SP_OFF_BAR = SP_OFF_ALO + SP_TILE;
+constexpr uint32_t SP_SMEM = SP_OFF_BAR + 64;
+
+__device__ __forceinline__ void split_bf16x2(float re, float im, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(re - hf.x, im - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+__global__ void __launch_bounds__(SP_THREADS, 1) k3_plane_tc_split(const float2 *__restrict__ Y,
+                                                                   const float2 *__restrict__ G,
+                                                                   const uint4 *__restrict__ Fhi_img,
+                                                                   const uint4 *__restrict__ Flo_img,
+                                                                   const float2 *__restrict__ tw,
+                                                                   float *__restrict__ plane, int K, int64_t nb, int L,
+                                                                   int64_t n_items, int n_groups, int64_t items_per_cta,
+                                                                   int32_t *__restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + SP_OFF_BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + SP_OFF_BAR + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, TC_N);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) tc::mbar_init(bar, 1);
+    for (int i = tid; i < (int)(TILE_BYTES / 16); i += SP_THREADS) {
+        reinterpret_cast<uint4 *>(smem + SP_OFF_FHI)[i] = __ldg(Fhi_img + i);
+        reinterpret_cast<uint4 *>(smem + SP_OFF_FLO)[i] = __ldg(Flo_img + i);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_thread_sync();
+    __syncthreads();
+    tc::fence_after_thread_sync();
+    const uint32_t tD = *tslot;
+    const uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_N);
+    const uint32_t fhi = tc::smem_u32(smem + SP_OFF_FHI), flo = tc::smem_u32(smem + SP_OFF_FLO);
+    const uint32_t ahi = tc::smem_u32(smem + SP_OFF_AHI), alo = tc::smem_u32(smem + SP_OFF_ALO);
+    unsigned char *sAhi = smem + SP_OFF_AHI, *sAlo = smem + SP_OFF_ALO;
+    const int quad = warp & 3, half = warp >> 2;
+    const int lrow = 32 * quad + lane, zl_e = lrow >> 6, idx = lrow & 63;
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    auto mma3 = [&](uint32_t a_hi, uint32_t a_lo, uint32_t albo, uint32_t asbo) {
+#pragma unroll 1
+        for (int s = 0; s < TC_K / 16; s++) {
+            const uint64_t dh = tc::smem_desc(a_hi + s * 2 * albo, albo, asbo);
+            const uint64_t dl = tc::smem_desc(a_lo + s * 2 * albo, albo, asbo);
+            const uint64_t bh = tc::smem_desc(fhi + s * 2 * F_LBO, F_LBO, F_SBO);
+            const uint64_t bl = tc::smem_desc(flo + s * 2 * F_LBO, F_LBO, F_SBO);
+            tc::mma_bf16(tD, dh, bh, idesc, s > 0 ? 1u : 0u);
+            tc::mma_bf16(tD, dl, bh, idesc, 1u);
+            tc::mma_bf16(tD, dh, bl, idesc, 1u);
+        }
+        tc::mma_commit(bar);
+    };
+
+    const int64_t it0 = (int64_t)blockIdx.x * items_per_cta;
+    const int64_t it1 = min(n_items, it0 + items_per_cta);
+    for (int64_t it = it0; it < it1 && ok; it++) {
+        const int64_t j = it / n_groups;
+        const int z0 = (int)(it % n_groups) * TC_G;
+        // ---- x = conj(Yhat_j) G_z in FP32, split, as the stage-1 A tile (B1 layout)
+        {
+            const int n2q = tid & 15, n1q = tid >> 4;
+            const float2 *Yj = Y + j * TC_S_BF16;
+#pragma unroll
+            for (int zl = 0; zl < TC_G; zl++) {
+                const int z = z0 + zl;
+                const float2 *Gz = G + (int64_t)(z < K ? z : 0) * TC_S_BF16;
+                uint32_t wh[4][4], wl[4][4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int n = 64 * (4 * n1q + q) + 4 * n2q + e;
+                        const float2 y = __ldg(Yj + n);
+                        const float2 g = z < K ? __ldg(Gz + n) : make_float2(0.f, 0.f);
+                        split_bf16x2(y.x * g.x + y.y * g.y, y.x * g.y - y.y * g.x, wh[e][q], wl[e][q]);
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int c = zl * TC_R + 4 * n2q + e;
+                    const uint32_t off = tc::kmajor_offset_strided(B_SBO, B_LBO, c, 8 * n1q);
+                    *reinterpret_cast<uint4 *>(sAhi + off) = make_uint4(wh[e][0], wh[e][1], wh[e][2], wh[e][3]);
+                    *reinterpret_cast<uint4 *>(sAlo + off) = make_uint4(wl[e][0], wl[e][1], wl[e][2], wl[e][3]);
+                }
+            }
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_thread_sync();
+        __syncthreads();
+        tc::fence_after_thread_sync();
+        if (tid == 0) mma3(ahi, alo, B_LBO, B_SBO);
+        ok = __syncthreads_and(tc::mbar_wait_bounded(bar, phase, WAIT_CYCLES));
+        phase ^= 1;
+        if (!ok) break;
+        tc::fence_after_thread_sync();
+        // ---- twiddle, split, as the stage-2 A tile (A2 layout); row (z, k1), K (n2, s)
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ch++) {
+            uint32_t rr[16];
+            tc::tmem_ld16(tD + lane_base + 64 * half + 16 * ch, rr);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int k1 = 32 * half + 8 * ch + q;
+                const float2 t = __ldg(tw + idx * TC_R + k1);
+                const float re = __uint_as_float(rr[2 * q]), im = __uint_as_float(rr[2 * q + 1]);
+                uint32_t h, l;
+                split_bf16x2(re * t.x - im * t.y, re * t.y + im * t.x, h, l);
+                const uint32_t off = tc::kmajor_offset_strided(A2_SBO, A2_LBO, zl_e * TC_R + k1, 2 * idx);
+                *reinterpret_cast<uint32_t *>(sAhi + off) = h;
+                *reinterpret_cast<uint32_t *>(sAlo + off) = l;
+            }
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_thread_sync();
+        __syncthreads();
+        tc::fence_after_thread_sync();
+        if (tid == 0) mma3(ahi, alo, A2_LBO, A2_SBO);
+        ok = __syncthreads_and(tc::mbar_wait_bounded(bar, phase, WAIT_CYCLES));
+        phase ^= 1;
+        if (!ok) break;
+        tc::fence_after_thread_sync();
+        // ---- |X|^2 -> FP32 plane; thread row (z, k1), columns (k2, p)
+        {
+            const int z = z0 + zl_e;
+            const int64_t r0 = j * L;
+#pragma unroll 1
+            for (int ch = 0; ch < 4; ch++) {
+                uint32_t rr[16];
+                tc::tmem_ld16(tD + lane_base + 64 * half + 16 * ch, rr);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int k2 = 32 * half + 8 * ch + q;
+                    const int t = idx + 64 * k2;
+                    if (z < K && t < L && r0 + t < nb) {
+                        const float re = __uint_as_float(rr[2 * q]), im = __uint_as_float(rr[2 * q + 1]);
+                        plane[(int64_t)z * nb + r0 + t] = re * re + im * im;
+                    }
+                }
+            }
+        }
+        tc::fence_before_thread_sync();
+        __syncthreads();
+    }
+    if (!ok) {
+        if (tid == 0) atomicOr(status, FDAS_DEV_TIMEOUT);
+        tc::mbar_wait_bounded(bar, phase ^ 1, WAIT_CYCLES);   // the MMAs still in flight
+    }
+    tc::fence_before_thread_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tD, TC_N);
+}
+
 }  // namespace
 
 namespace {
@@ -367,7 +540,7 @@ uint16_t host_bf16(float f) {
 // Host tables of the tensor path: F'[(k,p),(n,s)] (W_64^{kn} real-ified, re/im interleaved) as a
 // K-major BF16 operand image, and the four-step twiddles W_4096^{n2 k1}; FP64 then rounded.
 cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st) {
-    std::vector<uint16_t> img(TC_M * TC_K, 0);
+    std::vector<uint16_t> img(TC_M * TC_K, 0), img_lo(TC_M * TC_K, 0);
     for (int k = 0; k < TC_R; k++)
         for (int n = 0; n < TC_R; n++) {
             const int e = (k * n) % TC_R;
@@ -375,9 +548,16 @@ cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st) {
             if (f > 1.0) f -= 2.0;
             const double wr = std::cos(M_PI * f), wi = -std::sin(M_PI * f);
             const float v[2][2] = {{(float)wr, (float)-wi}, {(float)wi, (float)wr}};
+            const double vd[2][2] = {{wr, -wi}, {wi, wr}};
             for (int pr = 0; pr < 2; pr++)
-                for (int sg = 0; sg < 2; sg++)
-                    img[tc::kmajor_offset(TC_M, 2 * k + pr, 2 * n + sg) / 2] = host_bf16(v[pr][sg]);
+                for (int sg = 0; sg < 2; sg++) {
+                    const uint32_t o = tc::kmajor_offset(TC_M, 2 * k + pr, 2 * n + sg) / 2;
+                    img[o] = host_bf16(v[pr][sg]);
+                    uint32_t hb = (uint32_t)img[o] << 16;
+                    float hf;
+                    std::memcpy(&hf, &hb, 4);
+                    img_lo[o] = host_bf16((float)(vd[pr][sg] - (double)hf));
+                }
         }
     std::vector<float2> tw(TC_R * TC_R);
     for (int k1 = 0; k1 < TC_R; k1++)
@@ -388,6 +568,9 @@ cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st) {
             tw[k1 * TC_R + n2] = make_float2((float)std::cos(M_PI * f), (float)-std::sin(M_PI * f));
         }
     cudaError_t e = cudaMemcpyAsync(p.d_tcF, img.data(), img.size() * 2, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<char *>(p.d_tcF) + img.size() * 2, img_lo.data(), img_lo.size() * 2,
+                            cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p.d_tcTw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -424,4 +607,34 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
     return cudaGetLastError();
 }
 
+}  // namespace fdas
+
+namespace fdas {
+cudaError_t launch_plane_fp32_scratch(const Plan &p, const float2 *d_x, const float *d_scale, float2 *d_yhat,
+                                      float *d_plane, cudaStream_t st);
+cudaError_t launch_plane_split(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
+                               cudaStream_t st) {
+    if (p.S != TC_S_BF16) return cudaErrorInvalidValue;
+    float2 *Y = reinterpret_cast<float2 *>(ws + p.ws_y);
+    // FP32 segment spectra (4096-bin CUDA-core block FFT), then the compensated tensor stages
+    cudaError_t e = launch_segments_fp32(p, d_x, d_scale, Y, st);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k3_plane_tc_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM);
+    if (e != cudaSuccess) return e;
+    const int n_groups = (p.K + TC_G - 1) / TC_G;
+    const int64_t n_items = p.n_seg * n_groups;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
+    const int64_t ctas = std::min<int64_t>(n_items, (int64_t)sms);
+    const int64_t per = (n_items + ctas - 1) / ctas;
+    const int64_t grid = (n_items + per - 1) / per;
+    const uint4 *F = reinterpret_cast<const uint4 *>(p.d_tcF);
+    p.prof.begin(FDAS_STAGE_CORRELATE, st);
+    k3_plane_tc_split<<<(unsigned)grid, SP_THREADS, SP_SMEM, st>>>(Y, p.d_G, F, F + TILE_BYTES / 16, p.d_tcTw,
+                                                                   d_plane, p.K, p.nb, p.L, n_items, n_groups, per,
+                                                                   p.d_status);
+    p.prof.end(FDAS_STAGE_CORRELATE, st);
+    p.prof.launches += 1;
+    return cudaGetLastError();
+}
 }  // namespace fdas

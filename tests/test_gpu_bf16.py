@@ -195,3 +195,34 @@ def test_bf16_full_size_peaks_vs_fp32(bf16_full):
     thr_by_h = {1 << l: thr[l] for l in range(5)}
     worst = match_peaks(ref, s.peak_list(), thr_by_h, 3.0)
     assert worst <= 3.0
+
+
+# ------------------------------------------------------------------ split-BF16 (accuracy recovery)
+@pytest.mark.parametrize("n,zmax,m", [(1 << 16, 16, 64), (1 << 18, 84, 256), (1 << 12, 2, 32)])
+def test_split_bf16_plane_matches_oracle(n, zmax, m):
+    """Compensated hi+lo BF16 operands (~16 significant bits, three products per MMA step):
+    floor-relative plane error ~2^-16 per operand rounding -> bound 5e-4 (FP32 path: 1e-5,
+    plain BF16: a few 1e-3)."""
+    x = (synth.noise(n, synth.rng_for(62, n.bit_length())) + synth.chirp(n, 0.25, n / 13.3, zmax * 0.6)).astype(np.float32)
+    s = fd.Search(fd.make_config(n, zmax, m, 8192, precision="bf16_split"), device="cuda")
+    assert s.plan.info.plane_elem_bytes == 4
+    xh = s.spectrum(torch.from_numpy(x).cuda()).clone()
+    s.plane_from_spectrum(xh)
+    torch.cuda.synchronize()
+    got = s.plane_2d().cpu().numpy().astype(np.float64)
+    ref = oracle.plane(xh.cpu().numpy().view(np.complex64).astype(np.complex128), zmax, m)
+    err = np.abs(got - ref) / np.maximum(ref, 2.0)
+    print(f"split-bf16 floor-relative error: max {err.max():.2e} rms {np.sqrt(np.mean(err ** 2)):.2e}")
+    assert err.max() <= 5e-4
+    assert fd.fdas_device_status(s.plan) == 0
+
+
+def test_split_bf16_search_peaks():
+    w = synth.single_chirp_workload()
+    s = fd.Search(fd.make_config(w.n, w.zmax, w.taps, w.seg_len, precision="bf16_split", max_harm=1, thr=(30.0,),
+                                 max_peaks=4096), device="cuda")
+    s.search(torch.from_numpy(w.series).cuda())
+    torch.cuda.synchronize()
+    ref = oracle.search(w.series, w.zmax, w.taps, 1, (30.0,))
+    worst = match_peaks(ref["peaks"], s.peak_list(), {1: 30.0}, 0.1)
+    assert worst <= 0.1
