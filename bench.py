@@ -40,6 +40,17 @@ FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
 
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:        # fallback figures for GB300 when the measured file is absent
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+MEASURED = _measured_peaks()
+
+
 def parse_args():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -49,6 +60,7 @@ def parse_args():
     ap.add_argument("--precision", choices=("auto", "fp32", "bf16", "bf16_split"), default="auto")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the other-precision comparison runs")
     ap.add_argument("--quick", action="store_true", help="no clocks, e2e or CPU baseline (profiling runs)")
     ap.add_argument("--n-log2", type=int, default=23,
                     help="series length 2^n (23 = the benchmark workload; smaller only for profiler captures)")
@@ -69,8 +81,8 @@ def config_json(w, precision: str):
         "n_samples": w.n, "tsamp_s": w.tsamp, "zmax": w.zmax, "templates": w.K, "taps": w.taps,
         "seg_len": w.seg_len, "max_harm": MAX_HARM, "thresholds": list(THRESHOLDS),
         "precision": precision, "cells_per_step": w.K * w.nb, "series_per_gpu": 1,
-        "l2": "a 256 MiB buffer is written before every timed step (L2 is 129 MB); the 1.43 GB FP32 "
-              "plane written each step is also larger than L2",
+        "l2": "a 256 MiB buffer is written before every timed step (L2 is 129 MB); the plane written "
+              "each step (0.71 GB BF16, 1.43 GB FP32) is also larger than L2",
     }
 
 
@@ -125,6 +137,73 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ rooflines
+def _peaks_file():
+    return os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def _traffic(kernel: str, workload: str):
+    try:
+        with open(_peaks_file()) as f:
+            return json.load(f).get(f"{kernel}:{workload}")
+    except Exception:
+        return None
+
+
+def roofline_correlate(w, precision: str, prof):
+    """The plane kernel: FP32 CUDA-core FFT (ALU-bound) or the tensor-core DFT stages."""
+    n = max(1, prof["n_timed"]["correlate"])
+    ms = prof["ms"]["correlate"] / n
+    if precision == "fp32":
+        S, L = w.seg_len, w.seg_len - w.taps + 1
+        n_seg = math.ceil(w.nb / L)
+        flops = n_seg * w.K * (5.0 * S * math.log2(S) + 6.0 * S + 3.0 * L)
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070 / 1e3
+        ach = flops / (ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": _traffic("k3_plane_fp32", w.name), "kernel": "k3_plane_fp32<8192>",
+                "avg_launch_ms": ms, "flops_per_launch": flops,
+                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz (no measured FP32 figure)"}
+    S = 4096
+    L = (S - w.taps + 1) // 64 * 64
+    n_seg = math.ceil(w.nb / L)
+    items = n_seg * math.ceil(w.K / 2)
+    per_item = 2 * (2 * 128 * 128 * 128)                       # two 128x128x128 real GEMMs
+    flops = items * per_item * (3 if precision == "bf16_split" else 1)
+    peak = MEASURED["bf16_tflops_sustained"]
+    ach = flops / (ms / 1e3) / 1e12
+    kern = "k3_plane_tc_split" if precision == "bf16_split" else "k3_plane_tc"
+    plane_b = w.K * w.nb * (4 if precision == "bf16_split" else 2)
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": _traffic(kern, w.name), "kernel": kern, "avg_launch_ms": ms, "flops_per_launch": flops,
+            "peak_note": "of measured: MEASURED_PEAKS bf16_tflops_sustained (cuBLAS bf16 under the power cap)",
+            "hbm_GBps_algorithmic": (plane_b + n_seg * S * 4) / (ms / 1e3) / 1e9}
+
+
+def roofline_stage(w, precision: str, stage: str, prof):
+    """HBM roofline of a bandwidth-shaped stage (peak search or the long FFT)."""
+    n = max(1, prof["n_timed"][stage])
+    ms = prof["ms"][stage] / n
+    eb = 2 if precision == "bf16" else 4
+    if stage == "peaks":
+        # the plane once, plus the H/2 new harmonic terms per cell of each level 2..16
+        gathers = 0
+        for l in range(1, 5):
+            H = 1 << l
+            zl = (w.zmax // H) // 2 * 2
+            gathers += (zl + 1) * (w.nb // H) * (H // 2)
+        nbytes = (w.K * w.nb + gathers) * eb
+        kern = "k4_detect"
+    else:
+        nbytes = 6 * 8 * (w.nb)                                 # three passes, complex64 in and out
+        kern = "k1_spectrum"
+    ach = nbytes / (ms / 1e3) / 1e9
+    peak = MEASURED["hbm_gbs"]
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": _traffic(kern, w.name), "kernel": kern, "avg_launch_ms": ms, "bytes_per_launch": nbytes,
+            "peak_note": "of measured: MEASURED_PEAKS hbm_gbs (copy bandwidth)"}
 
 
 # ------------------------------------------------------------------------------ oracle timing
@@ -243,48 +322,50 @@ def own_arm(args):
             pass
 
     w = workload(rank, args.n_log2)
-    cfg = fd.make_config(w.n, w.zmax, w.taps, w.seg_len, precision=precision, max_harm=MAX_HARM,
-                         thr=THRESHOLDS, max_peaks=MAX_PEAKS)
-    s = fd.Search(cfg, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     x_host = torch.from_numpy(w.series).pin_memory()
     x_dev = x_host.to(dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        s.search(x_dev, stream)
-    torch.cuda.synchronize()
+    def timed_run(prec: str, steps: int, warmup: int, sample_clocks: bool):
+        """Exactly `steps` timed searches, L2 flushed before each, CUDA events per step."""
+        cfg_ = fd.make_config(w.n, w.zmax, w.taps, w.seg_len, precision=prec, max_harm=MAX_HARM,
+                              thr=THRESHOLDS, max_peaks=MAX_PEAKS)
+        s_ = fd.Search(cfg_, device=dev)
+        for _ in range(warmup):
+            s_.search(x_dev, stream)
+        torch.cuda.synchronize()
+        clocks_ = ClockSampler(local) if sample_clocks else None
+        fd.fdas_profile_enable(s_.plan, True)
+        fd.fdas_profile_read(s_.plan, reset=True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        if clocks_:
+            clocks_.start()
+            time.sleep(0.3)
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            s_.search(x_dev, stream)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk_ = clocks_.stop() if clocks_ else None
+        prof_ = fd.fdas_profile_read(s_.plan, reset=True)
+        fd.fdas_profile_enable(s_.plan, False)
+        tot = sum(a_.elapsed_time(b_) for a_, b_ in zip(starts, ends))
+        t_ = torch.tensor([tot], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+        return s_, float(t_.item()), prof_, clk_
 
-    # ---- timed region: exactly K steps, inputs resident in HBM, L2 flushed before each
-    clocks = ClockSampler(local) if not args.quick else None
-    fd.fdas_profile_enable(s.plan, True)
-    fd.fdas_profile_read(s.plan, reset=True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if clocks:
-        clocks.start()
-        time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        starts[k].record(stream)
-        s.search(x_dev, stream)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop() if clocks else None
-    prof = fd.fdas_profile_read(s.plan, reset=True)
-    fd.fdas_profile_enable(s.plan, False)
-    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    s, total_ms, prof, clk = timed_run(precision, args.steps, args.warmup, not args.quick)
     cells = w.K * w.nb
     value = world * cells * args.steps / (total_ms / 1e3)
 
@@ -314,34 +395,28 @@ def own_arm(args):
                "h2d_bytes_per_step": int(x_host.numel() * 4), "d2h_bytes_per_step": int(4 + 16 * MAX_PEAKS),
                "steps": e_steps}
 
-    # ---- roofline of the dominant kernel (the per-template correlation, K3)
-    n_k3 = max(1, prof["n_timed"]["correlate"])
-    k3_ms = prof["ms"]["correlate"] / n_k3
-    S, L, K = w.seg_len, w.seg_len - w.taps + 1, w.K
-    n_seg = math.ceil(w.nb / L)
-    fft_flops = 5.0 * S * math.log2(S) + 6.0 * S + 3.0 * L        # radix-2 count + multiply + |.|^2
-    plane_bytes_per_cell = 4 if precision == "fp32" else 2
-    if precision == "fp32":
-        clock_ghz = 2.070
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_ghz / 1e3    # TFLOP/s
-        achieved = n_seg * K * fft_flops / (k3_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k3_plane_fp32",
-                "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz max SM clock",
-                "flops_per_launch": n_seg * K * fft_flops,
-                "avg_launch_ms": k3_ms,
-                "hbm_GBps_algorithmic": (K * w.nb * plane_bytes_per_cell + n_seg * S * 8) / (k3_ms / 1e3) / 1e9}
-    else:
-        roof = None
-    peaks_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if roof is not None and os.path.exists(peaks_path):
-        try:
-            with open(peaks_path) as f:
-                tr = json.load(f).get(f"{roof['kernel']}:{w.name}")
-            if tr:
-                roof["traffic"] = tr
-        except Exception:
-            pass
+    # ---- the other precisions on the same GPU and workload (the metric's comparison)
+    paths = {}
+    if not args.quick and not args.no_compare:
+        for prec in ("fp32", "bf16", "bf16_split"):
+            if prec == precision:
+                continue
+            cmp_steps = max(3, min(args.steps, 100))
+            s_c, ms_c, prof_c, _ = timed_run(prec, cmp_steps, args.warmup, False)
+            paths[prec] = {"value": world * cells * cmp_steps / (ms_c / 1e3), "unit": UNIT,
+                           "ms_per_step": ms_c / cmp_steps, "steps": cmp_steps,
+                           "stages_ms_per_step": {k: v / cmp_steps for k, v in prof_c["ms"].items()},
+                           "roofline_correlate": roofline_correlate(w, prec, prof_c)}
+            del s_c
+        paths[precision] = {"value": value, "unit": UNIT, "ms_per_step": total_ms / args.steps}
+        if "fp32" in paths and "bf16" in paths:
+            paths["speedup_bf16_over_fp32"] = paths["bf16"]["value"] / paths["fp32"]["value"]
+
+    # ---- roofline of the dominant kernel of the step (largest per-step stage time)
+    stage_ms = {k: v / max(1, prof["n_timed"][k]) for k, v in prof["ms"].items()}
+    dominant = max(stage_ms, key=stage_ms.get)
+    roof_corr = roofline_correlate(w, precision, prof)
+    roof = roof_corr if dominant == "correlate" else roofline_stage(w, precision, dominant, prof)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
@@ -357,7 +432,8 @@ def own_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16_split": "bf16-split"}.get(precision, "bf16"),
             "data": "synthetic: seeded N(0,1) noise + 8 accelerated Gaussian pulse trains (fdas_synth)",
             "config": config_json(w, precision),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "roofline_correlate": roof_corr, "paths": paths or None,
+            "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(prof["launches"]), "clocks": clk,
             "stages_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
         }
