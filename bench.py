@@ -144,10 +144,19 @@ def _peaks_file():
     return os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def _traffic(kernel: str, workload: str):
+def _traffic(kernel: str, precision: str, workload: str):
+    """Per-launch DRAM bytes from a committed ncu capture, or None when there is none or the
+    kernel's source has changed since it was taken."""
+    import hashlib
     try:
         with open(_peaks_file()) as f:
-            return json.load(f).get(f"{kernel}:{workload}")
+            rec = json.load(f).get(f"{kernel}:{precision}:{workload}")
+        if not rec:
+            return None
+        with open(os.path.join(ROOT, rec["src"]), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest()[:16] != rec["sha"]:
+                return None
+        return rec["bytes"]
     except Exception:
         return None
 
@@ -163,7 +172,7 @@ def roofline_correlate(w, precision: str, prof):
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070 / 1e3
         ach = flops / (ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": _traffic("k3_plane_fp32", w.name), "kernel": "k3_plane_fp32<8192>",
+                "traffic": _traffic("k3_plane_fp32", "fp32", w.name), "kernel": "k3_plane_fp32<8192>",
                 "avg_launch_ms": ms, "flops_per_launch": flops,
                 "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz (no measured FP32 figure)"}
     S = 4096
@@ -177,7 +186,7 @@ def roofline_correlate(w, precision: str, prof):
     kern = "k3_plane_tc_split" if precision == "bf16_split" else "k3_plane_tc"
     plane_b = w.K * w.nb * (4 if precision == "bf16_split" else 2)
     return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": _traffic(kern, w.name), "kernel": kern, "avg_launch_ms": ms, "flops_per_launch": flops,
+            "traffic": _traffic(kern, precision, w.name), "kernel": kern, "avg_launch_ms": ms, "flops_per_launch": flops,
             "peak_note": "of measured: MEASURED_PEAKS bf16_tflops_sustained (cuBLAS bf16 under the power cap)",
             "hbm_GBps_algorithmic": (plane_b + n_seg * S * 4) / (ms / 1e3) / 1e9}
 
@@ -202,7 +211,7 @@ def roofline_stage(w, precision: str, stage: str, prof):
     ach = nbytes / (ms / 1e3) / 1e9
     peak = MEASURED["hbm_gbs"]
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": _traffic(kern, w.name), "kernel": kern, "avg_launch_ms": ms, "bytes_per_launch": nbytes,
+            "traffic": _traffic(kern, precision, w.name), "kernel": kern, "avg_launch_ms": ms, "bytes_per_launch": nbytes,
             "peak_note": "of measured: MEASURED_PEAKS hbm_gbs (copy bandwidth)"}
 
 
