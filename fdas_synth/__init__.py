@@ -137,3 +137,57 @@ def pulse_train_workload(config_index: int = 1, n: int = 1 << 23, tsamp: float =
         x += pulse_train(n, t.r0, t.z0, t.duty, t.snr, t.phase0)
     name = f"pulse_trains_n{n}_z{zmax}_m{taps}_s{seg_len}"
     return Workload(name, n, tsamp, zmax, taps, seg_len, x.astype(np.float32), trains)
+
+
+def harmonic_shares(duty: float, h_max: int = 4096) -> np.ndarray:
+    """Fraction of a Gaussian pulse train's power in each harmonic h = 1..h_max.
+
+    The periodic Gaussian of width w (in cycles, FWHM = duty) has Fourier coefficients
+    c_h ~ exp(-2 pi^2 h^2 w^2); with the mean removed, harmonic h carries c_h^2 / sum_h' c_h'^2
+    of sum_j s_j^2 (Parseval).  Index 0 of the result is harmonic 1."""
+    w = duty / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    h = np.arange(1, h_max + 1, dtype=np.float64)
+    c2 = np.exp(-4.0 * math.pi ** 2 * h * h * w * w)
+    return c2 / c2.sum()
+
+
+@dataclasses.dataclass
+class RefineWorkload:
+    """Candidates seeded near the injected harmonics of a pulse-train series."""
+    series: Workload
+    truths: np.ndarray        # [T, 3]: r, z (start bin, drift in bins) and expected noiseless power
+    seeds: np.ndarray         # [n_cand, 2]: r, z
+    truth_index: np.ndarray   # [n_cand]: row of truths each seed belongs to
+
+
+def refine_workload(config_index: int = 3, n: int = 1 << 23, tsamp: float = 64e-6, n_trains: int = 8,
+                    zmax: int = 84, taps: int = 256, seg_len: int = 8192, n_cand: int = 100_000,
+                    p_min: float = 30.0, series_index: int = 0) -> RefineWorkload:
+    """Differentiation case: a series like the precision case (N = 2^23 at 64 us, 8 pulse trains,
+    z in [-80, 80], SNR 5-30, 5% duty), and n_cand candidates seeded within half a bin in r and in z
+    (uniform offsets) of the trains' harmonics (h r0, h z0).  Harmonics qualify when their
+    expected noiseless power snr^2 * share_h is at least p_min, |h z0| <= zmax and the m-tap window
+    stays inside the spectrum.  The first len(truths) seeds are the nearest integer bins of each
+    truth; the rest pick a truth uniformly at random."""
+    w = pulse_train_workload(config_index, n, tsamp, n_trains, zmax, taps, seg_len, series_index)
+    nb = n // 2
+    rows = []
+    for t in w.trains:
+        share = harmonic_shares(t.duty)
+        for h in range(1, share.size + 1):
+            p = t.snr ** 2 * share[h - 1]
+            if p < p_min:
+                break
+            r, z = h * t.r0, h * t.z0
+            if abs(z) <= zmax and taps <= r < nb - taps:
+                rows.append((r, z, p))
+    truths = np.array(rows, dtype=np.float64).reshape(-1, 3)
+    rng = rng_for(config_index, 1000 + series_index)
+    if truths.shape[0] == 0:
+        return RefineWorkload(w, truths, np.zeros((0, 2)), np.zeros(0, dtype=np.int64))
+    idx = rng.integers(0, truths.shape[0], n_cand)
+    seeds = truths[idx, :2] + rng.uniform(-0.5, 0.5, (n_cand, 2))
+    k = min(n_cand, truths.shape[0])
+    idx[:k] = np.arange(k)
+    seeds[:k] = np.round(truths[:k, :2])
+    return RefineWorkload(w, truths, seeds, idx)

@@ -63,6 +63,8 @@ def _load():
             "orc_peaks_f32": (ctypes.c_int, [P, i64, ctypes.c_int, ctypes.c_int, P, i64, P, P, P, P, P]),
             "orc_peaks_f64": (ctypes.c_int, [P, i64, ctypes.c_int, ctypes.c_int, P, i64, P, P, P, P, P]),
             "orc_interp_power": (None, [P, i64, ctypes.c_int, f64, f64, P, P, P]),
+            "orc_interp_power_at": (None, [P, i64, ctypes.c_int, i64, f64, f64, P, P, P]),
+            "orc_refine_many": (None, [P, i64, ctypes.c_int, i64, P, ctypes.c_int, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -205,13 +207,34 @@ def peaks_f64(plane_f64, zmax: int, max_harm: int, thr, max_out: int = 1 << 20):
     return _peaks(_load().orc_peaks_f64, a, zmax, max_harm, thr, max_out, np.float64)
 
 
-def interp_power(xhat, m: int, r: float, z: float):
-    """(P, dP/dr, dP/dz) of the Fourier-interpolated power at fractional (r, z)."""
+def interp_power(xhat, m: int, r: float, z: float, k0=None):
+    """(P, dP/dr, dP/dz) of the Fourier-interpolated power at fractional (r, z).
+
+    The m-tap window is anchored at bin k0 (default: the nearest bin, floor(r + 1/2))."""
     xhat = np.ascontiguousarray(xhat, dtype=np.complex128)
     v = np.zeros(3, dtype=np.float64)
-    _load().orc_interp_power(_p(xhat), xhat.size, int(m), float(r), float(z),
-                             _p(v[0:]), _p(v[1:]), _p(v[2:]))
+    if k0 is None:
+        _load().orc_interp_power(_p(xhat), xhat.size, int(m), float(r), float(z),
+                                 _p(v[0:]), _p(v[1:]), _p(v[2:]))
+    else:
+        _load().orc_interp_power_at(_p(xhat), xhat.size, int(m), int(k0), float(r), float(z),
+                                    _p(v[0:]), _p(v[1:]), _p(v[2:]))
     return float(v[0]), float(v[1]), float(v[2])
+
+
+def refine(xhat, m: int, rz, steps: int):
+    """Gradient-ascent refinement of seeds rz ([n, 2] of (r, z)), every step in FP64.
+
+    Returns (points [n, 2], P [n], evaluations [n])."""
+    xhat = np.ascontiguousarray(xhat, dtype=np.complex128)
+    rz = np.ascontiguousarray(np.asarray(rz, dtype=np.float64).reshape(-1, 2))
+    n = rz.shape[0]
+    out = np.zeros((n, 2), dtype=np.float64)
+    pw = np.zeros(n, dtype=np.float64)
+    ev = np.zeros(n, dtype=np.int32)
+    if n:
+        _load().orc_refine_many(_p(xhat), xhat.size, int(m), n, _p(rz), int(steps), _p(out), _p(pw), _p(ev))
+    return out, pw, ev
 
 
 def search(x, zmax: int, m: int, max_harm: int, thr, sigma2: float = 0.0, max_out: int = 1 << 20):

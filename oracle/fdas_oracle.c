@@ -454,19 +454,19 @@ int orc_peaks_f64(const double *plane, int64_t nb, int zmax, int max_harm, const
 
 /* ------------------------------------------------------------------------------------ */
 /* Fourier-interpolated power at fractional (r, z) and its gradient (sub-bin candidate    */
-/* refinement of a plane peak).  With k0 = floor(r + 1/2) and the same m-tap window as    */
-/* the plane:                                                                             */
+/* refinement of a plane peak).  With the m-tap window anchored at bin k0 (the same      */
+/* window shape as the plane):                                                            */
 /*   A(r, z) = sum_{k = k0-m/2}^{k0+m/2-1} Xhat_k conj(I(k - r, z)),  P = |A|^2            */
-/* (I unnormalised).  With E = exp(i pi (z u^2 - 2 q u)), q = k - r:                       */
+/* (I unnormalised; taps off the spectrum are zero).  With E = exp(i pi (z u^2 - 2 q u)),  */
+/* q = k - r:                                                                             */
 /*   d/dr I(k - r, z) = int 2 pi i u E du = 2 pi i M_1,   d/dz I = int i pi u^2 E du = i pi M_2 */
 /*   dP/dx = 2 Re(conj(A) dA/dx).                                                         */
-/* The moments come from quadrature.  The window is fixed inside (k0 - 1/2, k0 + 1/2], so */
-/* P is smooth in r there.                                                                */
+/* The moments come from quadrature.  For a fixed k0, P is smooth in (r, z) everywhere;  */
+/* the refinement keeps k0 at its seed bin so the power it climbs has no jumps.          */
 /* ------------------------------------------------------------------------------------ */
-void orc_interp_power(const cplx *xhat, int64_t nb, int m, double r, double z,
-                      double *P, double *dPdr, double *dPdz)
+void orc_interp_power_at(const cplx *xhat, int64_t nb, int m, int64_t k0, double r, double z,
+                         double *P, double *dPdr, double *dPdz)
 {
-    int64_t k0 = (int64_t)floor(r + 0.5);
     cplx A = 0.0, Ar = 0.0, Az = 0.0;
     for (int t = 0; t < m; t++) {
         int64_t k = k0 + (int64_t)(t - m / 2);
@@ -482,4 +482,65 @@ void orc_interp_power(const cplx *xhat, int64_t nb, int m, double r, double z,
     if (P) *P = creal(A) * creal(A) + cimag(A) * cimag(A);
     if (dPdr) *dPdr = 2.0 * creal(conj(A) * Ar);
     if (dPdz) *dPdz = 2.0 * creal(conj(A) * Az);
+}
+
+/* The window centred on the nearest bin, k0 = floor(r + 1/2). */
+void orc_interp_power(const cplx *xhat, int64_t nb, int m, double r, double z,
+                      double *P, double *dPdr, double *dPdz)
+{
+    orc_interp_power_at(xhat, nb, m, (int64_t)floor(r + 0.5), r, z, P, dPdr, dPdz);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Sub-bin refinement of one candidate by preconditioned gradient ascent on P(r, z)       */
+/* (every step in FP64).  The window stays anchored at k0 = floor(r_seed + 1/2).  Each    */
+/* step is d = Hinv grad P / P with Hinv = (1/(2 pi^2)) [[48, -90], [-90, 180]], the       */
+/* inverse of the Hessian of 1 - P/P_peak of an ideal chirp: an offset (dr, dz) leaves    */
+/* the phase error 2 pi (dr u + dz u^2 / 2) over u in [0, 1], whose variance             */
+/* pi^2 (dr^2/3 + dr dz/3 + 4 dz^2/45) is 1 - P/P_peak to second order.  d is scaled to    */
+/* |dr| <= 1/4, |dz| <= 1 and halved at most three times until P does not decrease; the    */
+/* ascent stops when no such step exists.  Returns the number of power evaluations.       */
+/* ------------------------------------------------------------------------------------ */
+int orc_refine(const cplx *xhat, int64_t nb, int m, double r, double z, int steps,
+               double *r_out, double *z_out, double *P_out)
+{
+    int64_t k0 = (int64_t)floor(r + 0.5);
+    double P, gr, gz;
+    orc_interp_power_at(xhat, nb, m, k0, r, z, &P, &gr, &gz);
+    int evals = 1;
+    for (int s = 0; s < steps; s++) {
+        if (!(P > 0.0)) break;
+        double c = 1.0 / (2.0 * PI * PI * P);
+        double dr = (48.0 * gr - 90.0 * gz) * c;
+        double dz = (-90.0 * gr + 180.0 * gz) * c;
+        double sc = fmax(fmax(4.0 * fabs(dr), fabs(dz)), 1.0);
+        dr /= sc;
+        dz /= sc;
+        int ok = 0;
+        double P2 = 0.0, gr2 = 0.0, gz2 = 0.0;
+        for (int h = 0; h < 4; h++) {
+            orc_interp_power_at(xhat, nb, m, k0, r + dr, z + dz, &P2, &gr2, &gz2);
+            evals++;
+            if (P2 >= P) { ok = 1; break; }
+            dr *= 0.5;
+            dz *= 0.5;
+        }
+        if (!ok) break;
+        r += dr; z += dz; P = P2; gr = gr2; gz = gz2;
+    }
+    *r_out = r;
+    *z_out = z;
+    *P_out = P;
+    return evals;
+}
+
+/* orc_refine over n candidates (rz: [n][2] in, out: [n][2]), threaded over candidates. */
+void orc_refine_many(const cplx *xhat, int64_t nb, int m, int64_t n, const double *rz, int steps,
+                     double *out, double *P_out, int32_t *evals)
+{
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; i++) {
+        int e = orc_refine(xhat, nb, m, rz[2 * i], rz[2 * i + 1], steps, &out[2 * i], &out[2 * i + 1], &P_out[i]);
+        if (evals) evals[i] = e;
+    }
 }

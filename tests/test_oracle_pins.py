@@ -324,6 +324,65 @@ def test_interp_power_on_grid_and_gradient(oracle_mod):
         assert abs(gr - fr4) <= 1e-7 * scale + 1e-8
 
 
+def test_interp_power_anchored_window_against_fresnel_sum(oracle_mod):
+    """P with the window anchored at an explicit bin equals |sum_k Xhat_k conj(I(k - r, z))|^2
+    summed over that window with I from the Fresnel closed form (an independent route from the
+    quadrature moments); moving the anchor by one bin drops the lowest tap and adds one above."""
+    n, m = 1 << 14, 32
+    rng = synth.rng_for(60, 1)
+    x = (synth.noise(n, rng) + synth.chirp(n, 0.1, 3000.37, -5.3)).astype(np.float32)
+    xhat, _ = oracle_mod.spectrum(x, sigma2=float(n))
+    r, z = 3000.37, -5.3
+    for k0 in (2999, 3000, 3001):
+        k = np.arange(k0 - m // 2, k0 + m // 2)
+        A = np.sum(xhat[k] * np.conj(oracle_mod.response(k - r, z)))
+        P = oracle_mod.interp_power(xhat, m, r, z, k0)[0]
+        assert abs(P - abs(A) ** 2) <= 1e-11 * abs(A) ** 2
+    # the default anchor is the nearest bin
+    assert oracle_mod.interp_power(xhat, m, r, z) == oracle_mod.interp_power(xhat, m, r, z, 3000)
+    # an anchored window is smooth across the half-integer where the nearest bin changes
+    k0, h = 3000, 1e-3
+    for rr in (3000.5, 3000.9):
+        P0, gr, _ = oracle_mod.interp_power(xhat, m, rr, z, k0)
+        fr = (oracle_mod.interp_power(xhat, m, rr + h, z, k0)[0] - oracle_mod.interp_power(xhat, m, rr - h, z, k0)[0]) / (2 * h)
+        assert abs(gr - fr) <= 1e-5 * max(1.0, abs(P0), abs(fr))
+
+
+def _refine_err(oracle_mod, m, r0, z0, seeds, n=1 << 16, a=0.05):
+    x = synth.chirp(n, a, r0, z0)
+    xhat, _ = oracle_mod.spectrum(x, sigma2=float(n))
+    pts, P, ev = oracle_mod.refine(xhat, m, seeds, 21)
+    out = []
+    for s, p, pp in zip(seeds, pts, P):
+        k0 = math.floor(s[0] + 0.5)
+        k = np.arange(k0 - m // 2, k0 + m // 2)
+        eta = np.sum(np.abs(oracle_mod.response(k - r0, z0)) ** 2)
+        Pseed = oracle_mod.interp_power(xhat, m, s[0], s[1], k0)[0]
+        out.append((p[0] - r0, p[1] - z0, pp / (n * a * a * eta * eta / 2) - 1.0, pp - Pseed))
+    return np.array(out)
+
+
+def test_refine_recovers_noiseless_chirp(oracle_mod):
+    """The ascent ends at the injected (r0, z0) of a noiseless constant-fdot sinusoid, from seeds
+    up to half a bin away (the nearest integer bins and off-grid points), with the closed-form
+    peak power N a^2 eta^2 / 2 (sigma2 = N, eta = window energy of the response at the truth).
+    What remains is the bias of the m-tap window (it falls as 1/m)."""
+    for (r0, z0) in ((8000.3, 6.2), (12000.71, -13.4), (5000.5, 0.4)):
+        seeds = np.array([(round(r0), round(z0)), (r0 + 0.45, z0 - 0.45), (r0 - 0.4, z0 + 0.5)])
+        e = _refine_err(oracle_mod, 256, r0, z0, seeds)
+        assert np.all(np.abs(e[:, 0]) <= 1.5e-3), e
+        assert np.all(np.abs(e[:, 1]) <= 1e-3), e
+        assert np.all(np.abs(e[:, 2]) <= 1e-4), e
+        assert np.all(e[:, 3] >= 0.0)                     # the ascent never lowers P
+        # one maximum, whatever the seed
+        assert np.ptp(e[:, 0]) <= 1e-5 and np.ptp(e[:, 1]) <= 1e-5
+    # the window bias shrinks as the window grows (long sinc tails at z ~ 0)
+    seeds = np.array([(5000.0, 0.0)])
+    e64 = _refine_err(oracle_mod, 64, 5000.5, 0.4, seeds)
+    e256 = _refine_err(oracle_mod, 256, 5000.5, 0.4, seeds)
+    assert abs(e256[0, 0]) < 0.5 * abs(e64[0, 0])
+
+
 # ---------------------------------------------------------------- paper's printed numbers
 def test_template_bf16_conversion_stats_match_paper(oracle_mod):
     """Table template_stats (Sec. 3.3): FP32 -> BF16 template conversion error under Eq.
