@@ -10,6 +10,7 @@
  *        --(overlap-save correlation with K acceleration templates;
  *           Sec. 2.1, Fig. fdas_flow "blue box"; BF16 variant Sec. 3)--> P[K][Nb]   fdas_plane
  *        --(harmonic sum + threshold + local maxima; Sec. 2.1)--> peaks        fdas_peaks
+ *   peaks --(gradient ascent on the interpolated power)--> sub-bin (r, z)  fdas_refine
  *
  * fdas_search runs all three.  Every step runs in this library's CUDA kernels.
  *
@@ -205,6 +206,53 @@ fdas_status fdas_get_templates(fdas_plan_t plan, float *d_out, void *stream);
  * (FDAS_DEV_* bits).  Synchronises the device.  Errors: FDAS_E_INVALID, FDAS_E_CUDA.
  */
 fdas_status fdas_device_status(fdas_plan_t plan, int32_t *bits, int clear);
+
+/* A point of the f-z plane at sub-bin resolution: r is the frequency bin at the start of the
+ * observation (the plane's r axis) and z the drift in bins over the observation (Eq. fdotz). */
+typedef struct {
+    double r;
+    double z;
+} fdas_cand;
+
+/* Largest step count fdas_refine accepts. */
+#define FDAS_REFINE_MAX_STEPS 1000
+
+/*
+ * Fourier-interpolated power between the plane's grid points and its gradient (the f-z plane of
+ * Sec. 2.1 evaluated at fractional (r, z); the derivatives are the adjoint sums of the same
+ * interpolation).  For each point:
+ *   A = sum_{k = k0-m/2}^{k0+m/2-1} Xhat_k conj(I(k - r, z)),  P = |A|^2,
+ * with the unnormalised response I(q, z) = int_0^1 exp(i pi (z u^2 - 2 q u)) du, the plan's m
+ * taps, and Xhat_k = 0 outside [0, Nb).
+ *   d_xhat  Nb interleaved complex floats (a normalised spectrum, as from fdas_spectrum).
+ *   d_pts   n points; d_k0 (nullable) n window anchors, NULL meaning floor(r + 1/2) per point.
+ *   fp64    0: FP32 arithmetic (phases of large argument reduced in FP64); 1: FP64 throughout.
+ *   d_out   n x 3 doubles: P, dP/dr, dP/dz.  A non-finite point, |r| >= 2^52, |z| >= 2^20 or an
+ *           anchor 2^24 or more bins from r gives NaN in all three.
+ * Device pointers 8-byte aligned.  Needs no templates (fdas_make_templates not required).
+ * Errors: FDAS_E_INVALID (NULL or misaligned pointer, n < 0, fp64 not 0 or 1), FDAS_E_CUDA.
+ */
+fdas_status fdas_interp_power(fdas_plan_t plan, const float *d_xhat, const fdas_cand *d_pts,
+                              const int64_t *d_k0, int32_t n, int32_t fp64, double *d_out, void *stream);
+
+/*
+ * Sub-bin candidate refinement: gradient ascent on the interpolated power of fdas_interp_power,
+ * one warp per candidate.  From each seed in d_in, with the window anchored at
+ * k0 = floor(r_seed + 1/2) for the whole ascent: up to `steps` FP32 steps, then one FP64 step, of
+ *   d = (1/(2 pi^2)) [[48, -90], [-90, 180]] grad P / P
+ * (the inverse Hessian of 1 - P/P_peak of an ideal chirp, i.e. a Newton step on a matched
+ * response), scaled to |dr| <= 1/4 and |dz| <= 1 and halved up to three times until P does not
+ * decrease; a candidate stops early when no such step exists.
+ *   d_out    n refined points (may equal d_in).
+ *   d_power  (nullable) n x 3 doubles: FP64 P, dP/dr, dP/dz at the refined point.
+ *   d_evals  (nullable) n int32: power evaluations spent on each candidate.
+ * A seed that fdas_interp_power would reject is copied unchanged with NaN power.
+ * Device pointers 8-byte aligned (d_evals 4).  Needs no templates.
+ * Errors: FDAS_E_INVALID (NULL or misaligned pointer, n < 0, steps outside
+ * 0..FDAS_REFINE_MAX_STEPS), FDAS_E_CUDA.
+ */
+fdas_status fdas_refine(fdas_plan_t plan, const float *d_xhat, const fdas_cand *d_in, int32_t n,
+                        int32_t steps, fdas_cand *d_out, double *d_power, int32_t *d_evals, void *stream);
 
 /* Per-stage device times of profiled calls (CUDA events on the caller's stream). */
 typedef struct {

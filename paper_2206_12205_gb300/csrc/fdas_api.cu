@@ -242,6 +242,35 @@ fdas_status fdas_search(fdas_plan_t plan, const float *d_series, void *d_workspa
     return record(p, e);
 }
 
+fdas_status fdas_interp_power(fdas_plan_t plan, const float *d_xhat, const fdas_cand *d_pts, const int64_t *d_k0,
+                              int32_t n, int32_t fp64, double *d_out, void *stream) {
+    if (!plan || n < 0 || (fp64 != 0 && fp64 != 1)) return FDAS_E_INVALID;
+    if (n == 0) return FDAS_OK;
+    if (!d_xhat || !d_pts || !d_out) return FDAS_E_INVALID;
+    if (!aligned(d_xhat, 8) || !aligned(d_pts, 8) || !aligned(d_out, 8) || (d_k0 && !aligned(d_k0, 8)))
+        return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    p->prof.calls++;
+    const cudaError_t e = fdas::launch_interp(*p, reinterpret_cast<const float2 *>(d_xhat), d_pts, d_k0, n, fp64 != 0,
+                                              d_out, static_cast<cudaStream_t>(stream));
+    return record(p, e);
+}
+
+fdas_status fdas_refine(fdas_plan_t plan, const float *d_xhat, const fdas_cand *d_in, int32_t n, int32_t steps,
+                        fdas_cand *d_out, double *d_power, int32_t *d_evals, void *stream) {
+    if (!plan || n < 0 || steps < 0 || steps > FDAS_REFINE_MAX_STEPS) return FDAS_E_INVALID;
+    if (n == 0) return FDAS_OK;
+    if (!d_xhat || !d_in || !d_out) return FDAS_E_INVALID;
+    if (!aligned(d_xhat, 8) || !aligned(d_in, 8) || !aligned(d_out, 8) || (d_power && !aligned(d_power, 8)) ||
+        (d_evals && !aligned(d_evals, 4)))
+        return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    p->prof.calls++;
+    const cudaError_t e = fdas::launch_refine(*p, reinterpret_cast<const float2 *>(d_xhat), d_in, n, steps, d_out,
+                                              d_power, d_evals, static_cast<cudaStream_t>(stream));
+    return record(p, e);
+}
+
 fdas_status fdas_get_templates(fdas_plan_t plan, float *d_out, void *stream) {
     if (!plan || !d_out) return FDAS_E_INVALID;
     Plan *p = P(plan);

@@ -90,6 +90,9 @@ struct LevelTable {
 
 LevelTable make_levels(const Plan &p);
 
+// n-point Gauss-Legendre nodes xs and weights ws on [-1, 1] (host, FP64).
+void gauss_legendre(int n, double *xs, double *ws);
+
 // ---- launchers (each returns cudaGetLastError() of its launches) ----
 cudaError_t launch_make_templates(Plan &p, cudaStream_t st);
 cudaError_t launch_spectrum(const Plan &p, const float *d_series, char *ws, cudaStream_t st);
@@ -110,5 +113,9 @@ cudaError_t launch_plane_split(const Plan &p, const float2 *d_x, const float *d_
                                cudaStream_t st);
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
                          fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st);
+cudaError_t launch_interp(Plan &p, const float2 *d_x, const fdas_cand *d_pts, const int64_t *d_k0, int n, bool fp64,
+                          double *d_out, cudaStream_t st);
+cudaError_t launch_refine(Plan &p, const float2 *d_x, const fdas_cand *d_in, int n, int steps, fdas_cand *d_out,
+                          double *d_power, int32_t *d_evals, cudaStream_t st);
 
 }  // namespace fdas

@@ -18,18 +18,9 @@
 
 namespace fdas {
 
-namespace {
-
-constexpr int GL_N = 20;
-struct GaussLegendre {
-    double x[GL_N];
-    double w[GL_N];
-};
-
-// Nodes and weights on [-1, 1]: Newton iteration on the Legendre polynomial P_n.
-GaussLegendre gauss_legendre_nodes() {
-    GaussLegendre g;
-    const int n = GL_N;
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton iteration on the Legendre polynomial
+// P_n from the usual cosine start, weights 2 / ((1 - x^2) P_n'(x)^2).
+void gauss_legendre(int n, double *xs, double *ws) {
     for (int i = 0; i < n; i++) {
         double x = std::cos(M_PI * (i + 0.75) / (n + 0.5));
         double dpn = 1.0;
@@ -52,9 +43,22 @@ GaussLegendre gauss_legendre_nodes() {
             b = c;
         }
         dpn = n * (x * b - a) / (x * x - 1.0);
-        g.x[i] = x;
-        g.w[i] = 2.0 / ((1.0 - x * x) * dpn * dpn);
+        xs[i] = x;
+        ws[i] = 2.0 / ((1.0 - x * x) * dpn * dpn);
     }
+}
+
+namespace {
+
+constexpr int GL_N = 20;
+struct GaussLegendre {
+    double x[GL_N];
+    double w[GL_N];
+};
+
+GaussLegendre gauss_legendre_nodes() {
+    GaussLegendre g;
+    gauss_legendre(GL_N, g.x, g.w);
     return g;
 }
 

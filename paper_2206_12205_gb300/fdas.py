@@ -26,11 +26,13 @@ EXPORTED = (
     "fdas_plan", "fdas_plan_get_info", "fdas_make_templates", "fdas_spectrum", "fdas_plane",
     "fdas_peaks", "fdas_search", "fdas_get_templates", "fdas_device_status", "fdas_last_error",
     "fdas_destroy", "fdas_status_string", "fdas_version", "fdas_profile_enable", "fdas_profile_read",
-    "fdas_plane_static",
+    "fdas_plane_static", "fdas_interp_power", "fdas_refine",
 )
+REFINE_MAX_STEPS = 1000
 STATIC_SCRATCH_BYTES = 40 << 20
 STAGES = ("spectrum", "segments", "correlate", "peaks")
 
+CAND_DTYPE = np.dtype([("r", "<f8"), ("z", "<f8")])   # fdas_cand
 PEAK_DTYPE = np.dtype([("series", "<u4"), ("r", "<u4"), ("zi", "<i2"), ("harm", "u1"),
                        ("pad", "u1"), ("power", "<f4")])
 assert PEAK_DTYPE.itemsize == 16
@@ -99,6 +101,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "fdas_profile_enable": (S, [V, ctypes.c_int]),
         "fdas_profile_read": (S, [V, ctypes.POINTER(_Profile), ctypes.c_int]),
         "fdas_plane_static": (S, [V, V, V, V]),
+        "fdas_interp_power": (S, [V, V, V, V, I32, I32, V, V]),
+        "fdas_refine": (S, [V, V, V, I32, I32, V, V, V, V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -277,6 +281,45 @@ def fdas_search(plan: Plan, series, workspace, plane, peaks, npeaks, stream=None
             _dev_ptr(npeaks, "npeaks", torch.int32, 4),
             _stream_ptr(stream))
     _check(load().fdas_search(*args), "fdas_search", plan)
+
+
+def _points(pts, name: str, n=None) -> int:
+    """A float64 tensor of shape (n, 2) holding (r, z) rows, as fdas_cand records."""
+    torch = _torch()
+    if pts.dim() != 2 or pts.shape[1] != 2:
+        raise ValueError(f"{name}: expected shape (n, 2), got {tuple(pts.shape)}")
+    if n is not None and pts.shape[0] != n:
+        raise ValueError(f"{name}: expected {n} rows, got {pts.shape[0]}")
+    return _dev_ptr(pts, name, torch.float64)
+
+
+def fdas_interp_power(plan: Plan, xhat, pts, out, k0=None, fp64: bool = False, stream=None):
+    """Interpolated power and gradient at the (n, 2) points pts into out (n, 3): P, dP/dr, dP/dz."""
+    torch = _torch()
+    n = int(pts.shape[0])
+    args = (plan.handle,
+            _dev_ptr(xhat, "xhat", torch.float32, 8 * plan.info.nb),
+            _points(pts, "pts"),
+            _dev_ptr(k0, "k0", torch.int64, 8 * n) if k0 is not None else None,
+            n, 1 if fp64 else 0,
+            _dev_ptr(out, "out", torch.float64, 24 * n),
+            _stream_ptr(stream))
+    _check(load().fdas_interp_power(*args), "fdas_interp_power", plan)
+
+
+def fdas_refine(plan: Plan, xhat, cands_in, steps: int, cands_out, power=None, evals=None, stream=None):
+    """Gradient-ascent refinement of (n, 2) seeds; power (n, 3) and evals (n,) are optional outputs."""
+    torch = _torch()
+    n = int(cands_in.shape[0])
+    args = (plan.handle,
+            _dev_ptr(xhat, "xhat", torch.float32, 8 * plan.info.nb),
+            _points(cands_in, "cands_in"),
+            n, int(steps),
+            _points(cands_out, "cands_out", n),
+            _dev_ptr(power, "power", torch.float64, 24 * n) if power is not None else None,
+            _dev_ptr(evals, "evals", torch.int32, 4 * n) if evals is not None else None,
+            _stream_ptr(stream))
+    _check(load().fdas_refine(*args), "fdas_refine", plan)
 
 
 def fdas_get_templates(plan: Plan, out, stream=None):

@@ -126,3 +126,30 @@ def test_misaligned_pointers_rejected(lib):
     assert lib.fdas_plane_static(p_ptr, ok, odd, None) == fb.FDAS_E_INVALID
     assert lib.fdas_search(p_ptr, odd, ok, ok, ok, ok, None) == fb.FDAS_E_INVALID
     fd.fdas_destroy(p)
+
+
+def test_refine_entry_points_check_arguments(lib):
+    """fdas_interp_power / fdas_refine validate on the host before any device work."""
+    assert ctypes.sizeof(ctypes.c_double) * 2 == fb.CAND_DTYPE.itemsize == 16
+    p = fd.fdas_plan(fd.make_config(1 << 16, 16, 64, 1024))
+    h = p.handle
+    base = 1 << 20                                # never dereferenced: argument checks come first
+    ok = ctypes.c_void_p(base)
+    odd = ctypes.c_void_p(base + 4)
+    # n = 0 is a no-op even with NULL buffers; negative n, NULL buffers and bad flags are invalid
+    assert lib.fdas_interp_power(h, None, None, None, 0, 0, None, None) == fb.FDAS_OK
+    assert lib.fdas_refine(h, None, None, 0, 20, None, None, None, None) == fb.FDAS_OK
+    assert lib.fdas_interp_power(None, ok, ok, None, 1, 0, ok, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_interp_power(h, ok, ok, None, -1, 0, ok, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_interp_power(h, ok, ok, None, 1, 2, ok, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_interp_power(h, None, ok, None, 1, 0, ok, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_interp_power(h, ok, odd, None, 1, 0, ok, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_interp_power(h, ok, ok, odd, 1, 0, ok, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_refine(None, ok, ok, 1, 20, ok, None, None, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_refine(h, ok, ok, 1, -1, ok, None, None, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_refine(h, ok, ok, 1, fb.REFINE_MAX_STEPS + 1, ok, None, None, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_refine(h, ok, None, 1, 20, ok, None, None, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_refine(h, ok, ok, 1, 20, odd, None, None, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_refine(h, ok, ok, 1, 20, ok, odd, None, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_refine(h, ok, ok, 1, 20, ok, None, ctypes.c_void_p(base + 2), None) == fb.FDAS_E_INVALID
+    fd.fdas_destroy(p)

@@ -1,0 +1,358 @@
+"""GPU parity of sub-bin refinement (K5: fdas_interp_power, fdas_refine and the autograd wrapper)
+against the FP64 oracle, on spectra computed by the oracle and rounded once to complex64 (both
+sides read the same rounded values).
+
+Tolerances, with the floor 2 (the mean noise power) and s = max(P_ref, 2):
+  - FP32 evaluation: |P - P_ref| <= 1e-5 s; |dP/dx - ref| <= 1e-4 (s + |ref|).  Each tap's moments
+    carry about 2e-7 absolute error in FP32 (a few roundings of O(1) terms), the m-term sums add
+    about sqrt(m) of them, and the gradients carry the factors 2 pi and pi;
+  - FP64 evaluation: 1e-10 s for P, 1e-9 (s + |ref|) for the gradients;
+  - gradient vs central finite differences of the oracle's FP64 P (h = 1e-3): 1e-4 of the
+    gradient scale (the O(h^2) truncation, h^2/6 times the third derivative, which is about
+    (2 pi)^3 P); vs the five-point O(h^4) stencil: 1e-7;
+  - refinement: the FP64 power reported at the refined point equals the oracle's P there
+    (1e-10 s); the refined P is within 1e-5 of the oracle ascent's maximum and the points agree
+    to 2e-3 bin in r and 5e-3 in z (the same maximum, to what the FP32 steps resolve);
+  - against the injected truth: noiseless chirps within 2e-3 bin (the 256-tap window's bias); in
+    noise the maximum itself scatters about the truth, by the Cramer-Rao bound for (r, z) with an
+    unknown complex amplitude, Var(r, z) = (1/(pi^2 P)) [[48, -90], [-90, 180]] (P the peak power,
+    noise mean 2), so errors are checked in units of that bound.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import fdas_synth as synth
+import oracle
+import paper_2206_12205_gb300 as fd
+from paper_2206_12205_gb300 import refine as rf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fd.build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def _plan(n, m):
+    # refinement uses only the plan's Nb and m; no templates are needed
+    return fd.fdas_plan(fd.make_config(n, 2, m, max(1024, 2 * m)))
+
+
+def _shared_spectrum(x, sigma2):
+    """Oracle spectrum rounded to complex64: (device float32 view, the same values as complex128)."""
+    xh, _ = oracle.spectrum(x, sigma2=sigma2)
+    c64 = xh.astype(np.complex64)
+    dev = torch.from_numpy(np.ascontiguousarray(c64).view(np.float32)).cuda()
+    return dev, c64.astype(np.complex128)
+
+
+def _pts(rows):
+    return torch.tensor(np.asarray(rows, dtype=np.float64).reshape(-1, 2), dtype=torch.float64, device="cuda")
+
+
+def _interp(plan, xdev, pts, fp64, k0=None):
+    out = torch.empty(pts.shape[0], 3, dtype=torch.float64, device="cuda")
+    fd.fdas_interp_power(plan, xdev, pts, out, k0=k0, fp64=fp64)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _oracle_at(xh, m, rows, k0s=None):
+    ref = []
+    for i, (r, z) in enumerate(rows):
+        ref.append(oracle.interp_power(xh, m, r, z, None if k0s is None else int(k0s[i])))
+    return np.array(ref)
+
+
+def _check(got, ref, fp64, label):
+    s = np.maximum(ref[:, 0], 2.0)
+    tp, tg = (1e-10, 1e-9) if fp64 else (1e-5, 1e-4)
+    ep = np.abs(got[:, 0] - ref[:, 0]) / s
+    eg = np.abs(got[:, 1:] - ref[:, 1:]) / (s[:, None] + np.abs(ref[:, 1:]))
+    print(f"{label} fp64={fp64}: max P err {ep.max():.3e}, max grad err {eg.max():.3e}")
+    assert ep.max() <= tp, (label, ep.max(), int(ep.argmax()))
+    assert eg.max() <= tg, (label, eg.max(), np.unravel_index(eg.argmax(), eg.shape))
+
+
+def _points_around(r0, z0, rng, count, zs):
+    rows = [(r0 + rng.uniform(-0.6, 0.6), z0 + rng.uniform(-1.5, 1.5)) for _ in range(count)]
+    rows += [(r0 + rng.uniform(-0.5, 0.5), z) for z in zs]
+    return rows
+
+
+# ------------------------------------------------------------------ interpolated power
+def test_interp_power_matches_oracle_small_window():
+    """m = 64 taps (the single-chirp case), points on both sides of two chirps, every branch of
+    the moment evaluation: z = 0 exactly, |z| < 1, |z| = 1, moderate and large |z|."""
+    n, m = 1 << 16, 64
+    x = (synth.noise(n, synth.rng_for(70, 0)) + synth.chirp(n, 0.05, 8000.3, 6.2)
+         + synth.chirp(n, 0.08, 20000.6, -11.3))
+    xdev, xh = _shared_spectrum(x.astype(np.float32), float(n))
+    plan = _plan(n, m)
+    rng = np.random.default_rng(3)
+    zs = (0.0, 0.3, -0.7, 1.0, -1.0, 2.5, -16.0, 40.0, -73.3)
+    rows = _points_around(8000.3, 6.2, rng, 12, zs) + _points_around(20000.6, -11.3, rng, 12, zs)
+    ref = _oracle_at(xh, m, rows)
+    pts = _pts(rows)
+    for fp64 in (False, True):
+        _check(_interp(plan, xdev, pts, fp64), ref, fp64, "m64")
+
+
+def test_interp_power_matches_oracle_wide_window():
+    """m = 256 taps (the precision case's window), drifts up to and beyond zmax = 84."""
+    n, m = 1 << 18, 256
+    x = (synth.noise(n, synth.rng_for(70, 1)) + synth.chirp(n, 0.03, 30000.41, 61.7)
+         + synth.chirp(n, 0.03, 50000.13, -83.2))
+    xdev, xh = _shared_spectrum(x.astype(np.float32), float(n))
+    plan = _plan(n, m)
+    rng = np.random.default_rng(4)
+    zs = (0.0, -0.45, 1.0, 84.0, -150.5)
+    rows = _points_around(30000.41, 61.7, rng, 6, zs) + _points_around(50000.13, -83.2, rng, 6, zs)
+    ref = _oracle_at(xh, m, rows)
+    pts = _pts(rows)
+    for fp64 in (False, True):
+        _check(_interp(plan, xdev, pts, fp64), ref, fp64, "m256")
+
+
+def test_interp_power_edges_and_anchors():
+    """Windows cut by either end of the spectrum, windows wholly outside it (P = 0), explicit
+    anchors away from the nearest bin, and rejected points (NaN)."""
+    n, m = 1 << 14, 64
+    nb = n // 2
+    x = synth.noise(n, synth.rng_for(70, 2)) + synth.chirp(n, 0.2, 3.3, 2.0) + synth.chirp(n, 0.2, nb - 9.7, -4.0)
+    xdev, xh = _shared_spectrum(x.astype(np.float32), float(n))
+    plan = _plan(n, m)
+    rows = [(0.2, 2.0), (3.7, 1.5), (-0.4, -3.0), (nb - 1.3, -4.0), (nb - 20.6, -3.0), (nb + 10.2, 0.5),
+            (1000.25, 0.0), (1000.75, -0.25), (2000.5, 7.0), (2000.5, -7.0)]
+    k0s = [0, 4, 0, nb - 1, nb - 21, nb + 10, 997, 1004, 2000, 2001]
+    ref = _oracle_at(xh, m, rows, k0s)
+    pts = _pts(rows)
+    k0d = torch.tensor(k0s, dtype=torch.int64, device="cuda")
+    for fp64 in (False, True):
+        _check(_interp(plan, xdev, pts, fp64, k0d), ref, fp64, "edges")
+    # wholly outside the spectrum: exactly zero
+    out = _interp(plan, xdev, _pts([(-1000.0, 3.0), (nb + 500.0, -2.0)]), False)
+    assert np.all(out == 0.0)
+    # rejected points
+    out = _interp(plan, xdev, _pts([(float("nan"), 1.0), (10.0, float("inf")), (1e17, 0.0), (100.0, 2e6)]), True)
+    assert np.all(np.isnan(out))
+    # n = 0 is a no-op; bad arguments are rejected
+    fd.fdas_interp_power(plan, xdev, _pts([]), torch.empty(0, 3, dtype=torch.float64, device="cuda"))
+    lib = fd.load()
+    assert lib.fdas_interp_power(plan.handle, int(xdev.data_ptr()), int(pts.data_ptr()), None, 1, 2,
+                                 int(pts.data_ptr()), None) == fd.fdas.FDAS_E_INVALID
+    assert lib.fdas_interp_power(plan.handle, int(xdev.data_ptr()), int(pts.data_ptr()) + 4, None, 1, 0,
+                                 int(pts.data_ptr()), None) == fd.fdas.FDAS_E_INVALID
+
+
+def test_gradient_matches_finite_differences_of_oracle():
+    """The adjoint gradient (FP64 evaluation) against central differences, h = 1e-3, of the
+    oracle's FP64 P (the window anchored at the nearest bin of the centre point)."""
+    n, m = 1 << 16, 64
+    x = synth.noise(n, synth.rng_for(70, 3)) + synth.chirp(n, 0.05, 12000.71, -13.4)
+    xdev, xh = _shared_spectrum(x.astype(np.float32), float(n))
+    plan = _plan(n, m)
+    rows = [(12000.9, -13.0), (12000.55, -14.2), (12001.3, -12.1), (12000.2, -13.9), (11999.8, -10.0)]
+    k0s = [math.floor(r + 0.5) for r, _ in rows]
+    got = _interp(plan, xdev, _pts(rows), True, torch.tensor(k0s, dtype=torch.int64, device="cuda"))
+    h = 1e-3
+
+    def P(r, z, k0):
+        return oracle.interp_power(xh, m, r, z, k0)[0]
+
+    for (r, z), k0, g in zip(rows, k0s, got):
+        fr = (P(r + h, z, k0) - P(r - h, z, k0)) / (2 * h)
+        fz = (P(r, z + h, k0) - P(r, z - h, k0)) / (2 * h)
+        scale = max(1.0, abs(g[0]), abs(fr), abs(fz))
+        assert abs(g[1] - fr) <= 1e-4 * scale, (r, z, g[1], fr)
+        assert abs(g[2] - fz) <= 1e-4 * scale, (r, z, g[2], fz)
+        f5r = (8 * (P(r + h, z, k0) - P(r - h, z, k0)) - (P(r + 2 * h, z, k0) - P(r - 2 * h, z, k0))) / (12 * h)
+        f5z = (8 * (P(r, z + h, k0) - P(r, z - h, k0)) - (P(r, z + 2 * h, k0) - P(r, z - 2 * h, k0))) / (12 * h)
+        assert abs(g[1] - f5r) <= 1e-7 * scale, (r, z, g[1], f5r)
+        assert abs(g[2] - f5z) <= 1e-7 * scale, (r, z, g[2], f5z)
+
+
+def test_autograd_wrapper():
+    """InterpolatedPower: backward applies the kernel's gradient; torch's numerical Jacobian of
+    the FP64 forward agrees with it."""
+    n, m = 1 << 16, 64
+    x = synth.noise(n, synth.rng_for(70, 4)) + synth.chirp(n, 0.05, 8000.3, 6.2)
+    xdev, _ = _shared_spectrum(x.astype(np.float32), float(n))
+    plan = _plan(n, m)
+    r = torch.tensor([8000.1, 8000.45, 7999.8], dtype=torch.float64, device="cuda", requires_grad=True)
+    z = torch.tensor([6.0, 5.1, 7.3], dtype=torch.float64, device="cuda", requires_grad=True)
+    P = rf.interp_power(plan, xdev, r, z, fp64=True)
+    (P * torch.tensor([1.0, 2.0, -0.5], dtype=torch.float64, device="cuda")).sum().backward()
+    ref = _interp(plan, xdev, torch.stack([r.detach(), z.detach()], 1).contiguous(), True)
+    w = np.array([1.0, 2.0, -0.5])
+    assert np.allclose(P.detach().cpu().numpy(), ref[:, 0], rtol=0, atol=0)
+    assert np.allclose(r.grad.cpu().numpy(), w * ref[:, 1], rtol=1e-15, atol=0)
+    assert np.allclose(z.grad.cpu().numpy(), w * ref[:, 2], rtol=1e-15, atol=0)
+    r2 = r.detach()[:2].clone().requires_grad_(True)
+    z2 = z.detach()[:2].clone().requires_grad_(True)
+    k0 = torch.tensor([8000, 8000], dtype=torch.int64, device="cuda")
+    assert torch.autograd.gradcheck(lambda a, b: rf.interp_power(plan, xdev, a, b, fp64=True, k0=k0), (r2, z2),
+                                    eps=1e-4, atol=1e-4, rtol=1e-5)
+
+
+# ------------------------------------------------------------------ refinement
+def _chirp_cases(seed, count, n, zlim):
+    rng = np.random.default_rng(seed)
+    return [(4000 + 3000 * i + rng.uniform(0, 1), rng.uniform(-zlim, zlim)) for i in range(count)]
+
+
+def _crb_sigma(P):
+    """Cramer-Rao standard deviations of (r, z) at peak power P (noise mean 2)."""
+    P = np.asarray(P, dtype=np.float64)
+    return np.sqrt(48.0 / (math.pi ** 2 * P)), np.sqrt(180.0 / (math.pi ** 2 * P))
+
+
+def test_refine_matches_oracle_ascent():
+    """Noisy chirps (P ~ 82 in unit noise), seeds at the nearest integer bins of the truth and at
+    uniform offsets within half a bin: the device ascent (20 FP32 steps + 1 FP64 step) against
+    the oracle's (21 FP64 steps), and against the injected truth in Cramer-Rao units."""
+    n, m, a = 1 << 16, 64, 0.05
+    cases = _chirp_cases(11, 8, n, 14.0)
+    x = synth.noise(n, synth.rng_for(70, 5))
+    for r0, z0 in cases:
+        x = x + synth.chirp(n, a, r0, z0)
+    xdev, xh = _shared_spectrum(x.astype(np.float32), float(n))
+    plan = _plan(n, m)
+    rng = np.random.default_rng(12)
+    seeds, truth = [], []
+    for r0, z0 in cases:
+        seeds.append((round(r0), round(z0)))
+        truth.append((r0, z0))
+        for _ in range(2):
+            seeds.append((r0 + rng.uniform(-0.5, 0.5), z0 + rng.uniform(-0.5, 0.5)))
+            truth.append((r0, z0))
+    seeds, truth = np.array(seeds), np.array(truth)
+    pts, power, evals = rf.refine(plan, xdev, _pts(seeds), steps=20)
+    torch.cuda.synchronize()
+    pts, power, evals = pts.cpu().numpy(), power.cpu().numpy(), evals.cpu().numpy()
+    opts, oP, _ = oracle.refine(xh, m, seeds, 21)
+    k0s = np.floor(seeds[:, 0] + 0.5).astype(np.int64)
+    ref = _oracle_at(xh, m, pts, k0s)
+    s = np.maximum(ref[:, 0], 2.0)
+    assert np.max(np.abs(power[:, 0] - ref[:, 0]) / s) <= 1e-10
+    assert np.max(np.abs(power[:, 1:] - ref[:, 1:]) / (s[:, None] + np.abs(ref[:, 1:]))) <= 1e-9
+    # the same maximum as the oracle ascent
+    rel = (power[:, 0] - oP) / oP
+    print("P vs oracle ascent: min", rel.min(), "max", rel.max(), "| point diff r",
+          np.abs(pts[:, 0] - opts[:, 0]).max(), "z", np.abs(pts[:, 1] - opts[:, 1]).max(),
+          "| evals", evals.min(), evals.mean(), evals.max())
+    assert rel.min() >= -1e-5
+    assert np.abs(pts[:, 0] - opts[:, 0]).max() <= 2e-3 and np.abs(pts[:, 1] - opts[:, 1]).max() <= 5e-3
+    # never below the seed
+    pseed = _oracle_at(xh, m, seeds, k0s)[:, 0]
+    assert np.all(power[:, 0] >= pseed)
+    # against the injected truth, in units of the Cramer-Rao bound
+    sr, sz = _crb_sigma(power[:, 0])
+    nr, nz = (pts[:, 0] - truth[:, 0]) / sr, (pts[:, 1] - truth[:, 1]) / sz
+    print("refined - truth in CRB units: rms r", np.sqrt(np.mean(nr ** 2)), "rms z", np.sqrt(np.mean(nz ** 2)),
+          "max", np.abs(nr).max(), np.abs(nz).max())
+    assert np.sqrt(np.mean(nr ** 2)) <= 2.0 and np.sqrt(np.mean(nz ** 2)) <= 2.0
+    assert np.abs(nr).max() <= 4.0 and np.abs(nz).max() <= 4.0
+
+
+def test_refine_recovers_noiseless_truth():
+    """Noiseless chirps, 256-tap window: the device ascent lands on the injected (r0, z0) up to
+    the window's bias (as in the oracle's own pin), from the nearest integer bins and from
+    off-grid seeds within half a bin."""
+    n, m, a = 1 << 16, 256, 0.05
+    cases = ((8000.3, 6.2), (12000.71, -13.4), (20000.5, 0.4), (26000.05, 40.6), (30000.9, -63.1))
+    x = np.zeros(n)
+    for r0, z0 in cases:
+        x = x + synth.chirp(n, a, r0, z0)
+    xdev, _ = _shared_spectrum(x.astype(np.float32), float(n))
+    plan = _plan(n, m)
+    seeds, truth = [], []
+    for r0, z0 in cases:
+        for dr, dz in ((None, None), (0.45, -0.45), (-0.4, 0.5)):
+            seeds.append((round(r0), round(z0)) if dr is None else (r0 + dr, z0 + dz))
+            truth.append((r0, z0))
+    pts, power, _ = rf.refine(plan, xdev, _pts(seeds), steps=20)
+    err = np.abs(pts.cpu().numpy() - np.array(truth))
+    print("noiseless refined - truth: max r", err[:, 0].max(), "max z", err[:, 1].max())
+    assert err[:, 0].max() <= 2e-3 and err[:, 1].max() <= 2e-3
+
+
+def test_refine_edge_cases():
+    n, m = 1 << 14, 64
+    nb = n // 2
+    x = synth.noise(n, synth.rng_for(70, 6)) + synth.chirp(n, 0.2, 2000.4, -3.3) + synth.chirp(n, 0.2, 5.6, 0.0)
+    xdev, xh = _shared_spectrum(x.astype(np.float32), float(n))
+    plan = _plan(n, m)
+    seeds = np.array([(2000.0, -3.0), (6.0, 0.0), (-1000.0, 2.0), (float("nan"), 0.0), (nb + 5000.0, 1.0)])
+    sd = _pts(seeds)
+    pts, power, evals = rf.refine(plan, xdev, sd, steps=20)
+    torch.cuda.synchronize()
+    pts, power, evals = pts.cpu().numpy(), power.cpu().numpy(), evals.cpu().numpy()
+    assert abs(pts[0, 0] - 2000.4) < 0.05 and abs(pts[0, 1] + 3.3) < 0.1
+    # window cut by the spectrum edge; the negative-frequency image 11 bins away pulls the maximum
+    assert abs(pts[1, 0] - 5.6) < 0.2 and abs(pts[1, 1]) < 0.4
+    ref = _oracle_at(xh, m, pts[:2], np.floor(seeds[:2, 0] + 0.5).astype(np.int64))
+    assert np.max(np.abs(power[:2, 0] - ref[:, 0]) / np.maximum(ref[:, 0], 2.0)) <= 1e-10
+    # off the spectrum: P = 0, no step taken, the seed comes back
+    for i in (2, 4):
+        assert np.all(pts[i] == seeds[i]) and np.all(power[i] == 0.0)
+    # rejected seed: copied, NaN power, no evaluations
+    assert math.isnan(pts[3, 0]) and np.all(np.isnan(power[3])) and evals[3] == 0
+    # steps = 0: only the FP64 step
+    pts0, power0, ev0 = rf.refine(plan, xdev, sd[:1], steps=0)
+    assert 1 <= int(ev0.item()) <= 1 + 4 and power0[0, 0].item() > 0
+    # in place
+    inplace = sd[:2].clone()
+    fd.fdas_refine(plan, xdev, inplace, 20, inplace)
+    torch.cuda.synchronize()
+    assert np.allclose(inplace.cpu().numpy(), pts[:2], rtol=0, atol=0)
+    # bad arguments
+    with pytest.raises(fd.FdasError):
+        fd.fdas_refine(plan, xdev, sd, -1, sd)
+    with pytest.raises(fd.FdasError):
+        fd.fdas_refine(plan, xdev, sd, fd.fdas.REFINE_MAX_STEPS + 1, sd)
+    fd.fdas_refine(plan, xdev, _pts([]), 20, _pts([]))
+
+
+def test_refine_full_size_sampled():
+    """The differentiation workload at full size (N = 2^23, m = 256, 100k candidates seeded within
+    half a bin of the injected harmonics), the launch the benchmark times: every candidate ends
+    finite and no lower than its seed (checked with the FP64 evaluation of the seed); sampled
+    candidates' reported power equals the oracle's at the refined point; the refined points sit
+    within the Cramer-Rao scatter of the truths (these harmonics have P ~ 30-60)."""
+    wl = synth.refine_workload()
+    n, m = wl.series.n, wl.series.taps
+    xdev, xh = _shared_spectrum(wl.series.series, 0.0)
+    plan = _plan(n, m)
+    sd = _pts(wl.seeds)
+    pts, power, evals = rf.refine(plan, xdev, sd, steps=20)
+    seedp = torch.empty(sd.shape[0], 3, dtype=torch.float64, device="cuda")
+    fd.fdas_interp_power(plan, xdev, sd, seedp, fp64=True)
+    torch.cuda.synchronize()
+    pts, power, evals, seedp = pts.cpu().numpy(), power.cpu().numpy(), evals.cpu().numpy(), seedp.cpu().numpy()
+    assert np.all(np.isfinite(pts)) and np.all(np.isfinite(power))
+    assert np.all(power[:, 0] >= seedp[:, 0] * (1 - 1e-12))
+    rng = np.random.default_rng(5)
+    pick = rng.choice(pts.shape[0], 8, replace=False)
+    k0s = np.floor(wl.seeds[pick, 0] + 0.5).astype(np.int64)
+    ref = _oracle_at(xh, m, pts[pick], k0s)
+    assert np.max(np.abs(power[pick, 0] - ref[:, 0]) / np.maximum(ref[:, 0], 2.0)) <= 1e-10
+    sr, sz = _crb_sigma(power[:, 0])
+    tr = wl.truths[wl.truth_index, :2]
+    nr, nz = (pts[:, 0] - tr[:, 0]) / sr, (pts[:, 1] - tr[:, 1]) / sz
+    inside = (np.abs(nr) <= 3.0) & (np.abs(nz) <= 3.0)
+    err = np.abs(pts - tr)
+    print("full size: evals mean", evals.mean(), "max", evals.max(), "| |dr| median", np.median(err[:, 0]),
+          "| |dz| median", np.median(err[:, 1]), "| CRB rms r", np.sqrt(np.mean(nr ** 2)), "z",
+          np.sqrt(np.mean(nz ** 2)), "| within 3 sigma", inside.mean())
+    # near the detection threshold (P ~ 30) the maximum-likelihood scatter exceeds the bound
+    # and a few seeds climb a neighbouring noise peak instead
+    assert inside.mean() >= 0.8
