@@ -191,3 +191,9 @@ def refine_workload(config_index: int = 3, n: int = 1 << 23, tsamp: float = 64e-
     idx[:k] = np.arange(k)
     seeds[:k] = np.round(truths[:k, :2])
     return RefineWorkload(w, truths, seeds, idx)
+
+
+def noise_plane(K: int, nb: int, rng: np.random.Generator) -> np.ndarray:
+    """A stand-in f-z plane for peak-search tests: K x nb independent exponential cells of mean 2
+    (the chi^2, 2 dof law of noise-only plane cells), float32.  Callers plant signals on top."""
+    return rng.exponential(2.0, size=(K, nb)).astype(np.float32)

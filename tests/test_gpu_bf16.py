@@ -54,6 +54,13 @@ def _bf16_search(n, zmax, m, **kw):
     return fd.Search(fd.make_config(n, zmax, m, 8192, precision="bf16", **kw), device="cuda")
 
 
+def _shared_spectrum(x):
+    """The oracle's spectrum rounded once to complex64: (device float32 view, same values as complex128)."""
+    xr, _ = oracle.spectrum(x)
+    c64 = np.ascontiguousarray(xr.astype(np.complex64))
+    return torch.from_numpy(c64.view(np.float32)).cuda(), c64.astype(np.complex128)
+
+
 def _plane_f64(s):
     return s.plane_2d().float().cpu().numpy().astype(np.float64)
 
@@ -82,11 +89,10 @@ def match_peaks(ref, got, thr_by_h, tol_pct, margin=1.03):
 def test_bf16_plane_matches_oracle(n, zmax, m):
     x = (synth.noise(n, synth.rng_for(60, n.bit_length())) + synth.chirp(n, 0.25, n / 13.3, zmax * 0.6)).astype(np.float32)
     s = _bf16_search(n, zmax, m)
-    xh = s.spectrum(torch.from_numpy(x).cuda()).clone()
-    s.plane_from_spectrum(xh)
+    xdev, xin = _shared_spectrum(x)
+    s.plane_from_spectrum(xdev)
     torch.cuda.synchronize()
     got = _plane_f64(s)
-    xin = xh.cpu().numpy().view(np.complex64).astype(np.complex128)
     ref = oracle.plane(xin, zmax, m)
     # BF16 operands carry 8 significant bits: a transform's rounding error in amplitude is a
     # few 2^-9 of the largest amplitude in its segment, so a cell's power error is bounded by
@@ -125,16 +131,21 @@ def test_bf16_single_chirp_peaks_paper_criterion():
 
 
 def test_bf16_peaks_bit_exact_given_plane():
+    """The oracle's FP64 plane rounded once to BF16 (round to nearest even), searched by the BF16
+    peak kernel (quick cast on read) and by the oracle's float mode on the widened values."""
     n, zmax, m = 1 << 16, 32, 64
     x = synth.noise(n, synth.rng_for(61, 0))
     for h in range(1, 6):
         x += synth.chirp(n, 0.08 / h, 1234.0 * h, 6.0 * h)
     x = x.astype(np.float32)
+    xr, _ = oracle.spectrum(x)
+    pl_bf = torch.from_numpy(oracle.plane(xr, zmax, m).astype(np.float32)).to(torch.bfloat16)
+    widened = pl_bf.float().numpy()
     thr = (12.0, 18.0, 28.0, 45.0, 70.0)
     s = _bf16_search(n, zmax, m, max_harm=16, thr=thr, max_peaks=1 << 16)
-    s.search(torch.from_numpy(x).cuda())
+    s.plane.copy_(pl_bf.reshape(-1).cuda())
+    s.find_peaks()
     torch.cuda.synchronize()
-    widened = s.plane_2d().float().cpu().numpy()
     want, cnt = oracle.peaks_f32(widened, zmax, 16, thr)
     got = s.peak_list()
     assert int(s.npeaks.item()) == cnt > 0
@@ -150,10 +161,10 @@ def bf16_full():
     w = synth.pulse_train_workload()
     thr = (40.0, 44.0, 51.0, 64.0, 88.0)
     s = _bf16_search(w.n, w.zmax, w.taps, max_harm=16, thr=thr, max_peaks=1 << 16)
-    xdev = torch.from_numpy(w.series).cuda()
-    s.search(xdev)
+    s.search(torch.from_numpy(w.series).cuda())           # end to end: the peak list
+    xdev, xh = _shared_spectrum(w.series)
+    s.plane_from_spectrum(xdev)                            # shared spectrum: the sampled cells
     torch.cuda.synchronize()
-    xh = s.spectrum(xdev).cpu().numpy().view(np.complex64).astype(np.complex128)
     return w, s, xh, thr
 
 
@@ -206,11 +217,11 @@ def test_split_bf16_plane_matches_oracle(n, zmax, m):
     x = (synth.noise(n, synth.rng_for(62, n.bit_length())) + synth.chirp(n, 0.25, n / 13.3, zmax * 0.6)).astype(np.float32)
     s = fd.Search(fd.make_config(n, zmax, m, 8192, precision="bf16_split"), device="cuda")
     assert s.plan.info.plane_elem_bytes == 4
-    xh = s.spectrum(torch.from_numpy(x).cuda()).clone()
-    s.plane_from_spectrum(xh)
+    xdev, xin = _shared_spectrum(x)
+    s.plane_from_spectrum(xdev)
     torch.cuda.synchronize()
     got = s.plane_2d().cpu().numpy().astype(np.float64)
-    ref = oracle.plane(xh.cpu().numpy().view(np.complex64).astype(np.complex128), zmax, m)
+    ref = oracle.plane(xin, zmax, m)
     err = np.abs(got - ref) / np.maximum(ref, 2.0)
     print(f"split-bf16 floor-relative error: max {err.max():.2e} rms {np.sqrt(np.mean(err ** 2)):.2e}")
     assert err.max() <= 5e-4

@@ -140,17 +140,22 @@ def _peaks_equal(got, want):
 
 @pytest.mark.parametrize("max_harm", [1, 2, 4, 8, 16])
 def test_peaks_bit_exact_given_plane(max_harm):
+    """The oracle's FP64 plane of a harmonic-rich accelerated signal, rounded once to float,
+    searched by both sides: bit-exact peak lists."""
     n, zmax, m, S = 1 << 16, 32, 64, 1024
     x = synth.noise(n, synth.rng_for(52, max_harm))
     for h in range(1, 6):                             # a harmonic-rich accelerated signal
         x += synth.chirp(n, 0.08 / h, 1234.0 * h, 6.0 * h)
     x = x.astype(np.float32)
+    xr, _ = oracle.spectrum(x)
+    pl = oracle.plane(xr, zmax, m).astype(np.float32)
     thr = (12.0, 18.0, 28.0, 45.0, 70.0)
     s = _search(n, zmax, m, S, max_harm=max_harm, thr=thr, max_peaks=1 << 16)
-    s.search(_to_dev(x))
+    s.plane.copy_(torch.from_numpy(pl.ravel()))
+    s.find_peaks()
     torch.cuda.synchronize()
     got = s.peak_list()
-    want, cnt = oracle.peaks_f32(s.plane_2d().cpu().numpy(), zmax, max_harm, thr)
+    want, cnt = oracle.peaks_f32(pl, zmax, max_harm, thr)
     assert int(s.npeaks.item()) == cnt > 0
     _peaks_equal(got, want)
     assert fd.fdas_device_status(s.plan) == 0
@@ -199,18 +204,21 @@ FULL_THR = (40.0, 44.0, 51.0, 64.0, 88.0)   # about one noise peak per harmonic 
 
 @pytest.fixture(scope="module")
 def pulse_train_case():
+    """The benchmark series: the oracle's spectrum (FP64, and rounded once to complex64 for the
+    shared-spectrum plane) and a search plan in the benchmark's configuration."""
     w = synth.pulse_train_workload()
     s = _search(w.n, w.zmax, w.taps, w.seg_len, max_harm=16, thr=FULL_THR, max_peaks=1 << 16)
-    s.search(_to_dev(w.series))
-    xh = s.spectrum(_to_dev(w.series))
-    torch.cuda.synchronize()
-    return w, s, xh.cpu().numpy().view(np.complex64).astype(np.complex128)
+    xr, s2 = oracle.spectrum(w.series)
+    xr32 = _xhat_f32(xr)
+    return w, s, xr, s2, xr32
 
 
 def test_full_size_spectrum(pulse_train_case):
-    w, s, xh = pulse_train_case
-    ref, s2 = oracle.spectrum(w.series)
-    assert np.abs(xh - ref).max() <= 2e-6 * np.abs(ref).max() + 2e-5
+    w, s, xr, s2, _ = pulse_train_case
+    xh = s.spectrum(_to_dev(w.series))
+    torch.cuda.synchronize()
+    got = xh.cpu().numpy().view(np.complex64).astype(np.complex128)
+    assert np.abs(got - xr).max() <= 2e-6 * np.abs(xr).max() + 2e-5
     assert abs(s.sigma2.item() - s2) <= 1e-5 * s2
 
 
@@ -218,7 +226,10 @@ def test_full_size_plane_sampled(pulse_train_case):
     """N = 2^23, 85 templates, 256 taps, 8192-bin segments, in the launch configuration the
     benchmark times: sampled cells (random, segment edges, the ragged tail, each train's
     fundamental) against the oracle evaluated cell by cell on the same spectrum."""
-    w, s, xh = pulse_train_case
+    w, s, xr, _, xr32 = pulse_train_case
+    xh = xr32.view(np.complex64).astype(np.complex128)
+    s.plane_from_spectrum(_to_dev(xr32))
+    torch.cuda.synchronize()
     K, nb, L = w.K, w.nb, w.seg_len - w.taps + 1
     rng = np.random.default_rng(7)
     zi = list(rng.integers(0, K, 3000))
@@ -247,13 +258,45 @@ def test_full_size_plane_sampled(pulse_train_case):
     assert _floor_err(got, ref) <= 1e-5
     # the whole-plane noise law: mean power 2 (chi^2, 2 dof) away from injected signals
     assert abs(float(plane.double().mean().item()) - 2.0) < 0.1
+    # end to end from the series (the FP32 long FFT included) against the oracle's FP64 spectrum
+    s.search(_to_dev(w.series))
+    torch.cuda.synchronize()
+    got_e2e = plane.reshape(-1)[idx].cpu().numpy().astype(np.float64)
+    ref_e2e = oracle.plane_cells(xr, w.zmax, w.taps, T, zi, r)
+    e2e = _floor_err(got_e2e, ref_e2e)
+    print(f"full size end to end: floor-relative plane error {e2e:.2e}")
+    assert e2e <= 1e-4
+
+
+def _planted_plane(K, nb, zmax, rng, families):
+    """Exponential noise cells plus `families` harmonic families: fundamental power A at a random
+    (i, r) and A/h at (h r, i_h) (z_{i_h} = h z_i) wherever that cell is on the plane."""
+    pl = synth.noise_plane(K, nb, rng)
+    for f in range(families):
+        # every other family drifts slowly enough (|z| <= 4) and sits low enough in frequency
+        # (r < nb/16) to reach the 16-harmonic level
+        i = int(rng.integers(0, K)) if f % 2 else zmax // 2 + int(rng.integers(-2, 3))
+        r = int(rng.integers(1, nb // 2 if f % 2 else nb // 16))
+        A = float(rng.uniform(25.0, 90.0))
+        z = -zmax + 2 * i
+        for h in range(1, 17):
+            ih = (h * z + zmax) // 2
+            if abs(h * z) > zmax or h * r >= nb:
+                break
+            pl[ih, h * r] += np.float32(A / h)
+    return pl
 
 
 def test_full_size_peaks_bit_exact(pulse_train_case):
-    """16-harmonic peak list of the full-size plane, bit-exact against the oracle's float
-    given-plane mode, and every injected train's fundamental found near its (r0, z0)."""
-    w, s, _ = pulse_train_case
+    """16-harmonic peak search over a full-size plane (85 x 2^22 cells) of exponential noise with
+    planted harmonic families, given to both sides: bit-exact peak lists at every level."""
+    w, s, _, _, _ = pulse_train_case
+    pl = _planted_plane(w.K, w.nb, w.zmax, synth.rng_for(53, 0), 400)
+    s.plane.copy_(torch.from_numpy(pl.ravel()))
+    s.find_peaks()
+    torch.cuda.synchronize()
     got = s.peak_list()
-    want, cnt = oracle.peaks_f32(s.plane_2d().cpu().numpy(), w.zmax, 16, FULL_THR)
+    want, cnt = oracle.peaks_f32(pl, w.zmax, 16, FULL_THR)
     assert int(s.npeaks.item()) == cnt
+    assert len({int(p["h"]) for p in want}) == 5          # every harmonic level has peaks
     _peaks_equal(got, want)
