@@ -210,7 +210,7 @@ def roofline_stage(w, precision: str, stage: str, prof):
             zl = (w.zmax // H) // 2 * 2
             gathers += (zl + 1) * (w.nb // H) * (H // 2)
         nbytes = (w.K * w.nb + gathers) * eb
-        kern = "k4_detect"
+        kern = "k4_level1+k4_levels"
     else:
         nbytes = 6 * 8 * (w.nb)                                 # three passes, complex64 in and out
         kern = "k1_spectrum"

@@ -8,15 +8,20 @@
 // |H z_i| <= zmax and H r < Nb.  Peak: S_H > thr and a 3x3 local maximum (strictly above
 // earlier neighbours in row-major (i, r) order, >= later ones, undefined neighbours ignored).
 //
-// The defined regions nest (level 2H's lies inside level H's), so one pass builds every level
-// in place: a tile of RB rows x CB bins (plus a one-cell halo) is loaded once into shared
-// memory as S_1 = P, peaks of level 1 are detected, then S_2 = S_1 + P(2r, i_2) is formed in
-// place (cells outside level 2's region become -inf), and so on up to max_harm.  The running
-// sum adds the terms in the order h = 1..H, so every S_H is bit-identical to the direct sum.
+// The defined regions nest (level 2H's lies inside level H's), so one pass builds every level:
+// a warp owns one (row i, chunk of CB bins) of the plane, lane l the 16 consecutive bins
+// r0 + 16 l .. r0 + 16 l + 15, and the running sums S_H of those bins stay in registers.  S_1 = P
+// comes from two (BF16) or four (FP32) 16-byte loads; S_2H = S_H + sum_{h = H+1 .. 2H} P(h r, i_h)
+// adds the new harmonics in order, so every S_H is bit-identical to the direct sum.  A harmonic
+// h whose 16 values span few 16-byte vectors (h r for 16 consecutive r covers 15 h + 1 elements)
+// is read with vector loads and the needed elements picked at compile time; larger h with scalar
+// gathers.  A lane tests its 16 values against the threshold through their maximum; only cells
+// above it (a handful per plane) recompute their 3x3 neighbourhood's sums to decide the peak.
 //
 // Output order (H, i, r) without a sort: a "unit" is (level, row, chunk of CB bins), units
 // are numbered in that order, and
-//   pass A (k4_detect) writes each unit's peak count and, when non-zero, its CB-bit mask;
+//   pass A (k4_level1 over the plane, k4_levels over level 2's region) writes each unit's peak
+//     count and, when non-zero, its CB-bit mask;
 //   pass B (k4_scan_blocks, k4_scan_top) turns the counts into exclusive offsets + total;
 //   pass C (k4_emit, one warp per unit, empty units skipped) recomputes S_H at the few
 //   marked cells and writes the records at offset + rank.
@@ -28,13 +33,24 @@ namespace fdas {
 
 namespace {
 
-constexpr int RB = PEAK_ROWS;            // rows per tile (one warp each)
-constexpr int CB = PEAK_CHUNK;           // bins per tile / unit
-constexpr int SW = CB + 2;               // staged cells per row: bins r0-1 .. r0+CB
-constexpr int SOFF = 3;                  // staged cell c sits at S[row][c + SOFF]: the interior
-constexpr int SWP = CB + 8;              // (c = 1 .. CB) starts on a 16-byte boundary; row pitch
+constexpr int CB = PEAK_CHUNK;           // bins per unit (a warp's chunk)
+constexpr int LB = CB / 32;              // bins per lane (16)
 constexpr int WORDS = CB / 32;           // mask words per unit
 constexpr int SCAN_BLOCK = PEAK_SCAN_BLOCK;
+constexpr int DETECT_WARPS = 8;          // warps per k4_level1 / k4_levels block
+#ifndef FDAS_K4_CPW
+#define FDAS_K4_CPW 2                    // chunks per k4_levels warp
+#endif
+constexpr int CPW = FDAS_K4_CPW;
+static_assert((CPW & (CPW - 1)) == 0 && CPW <= 2, "chunks per warp: 1 or 2 (chunks1 >= 2 is a power of two)");
+#ifndef FDAS_K4_L1_MIN_BLOCKS
+#define FDAS_K4_L1_MIN_BLOCKS 2          // resident k4_level1 blocks per SM the registers must allow
+#endif
+#ifndef FDAS_K4_MIN_BLOCKS
+#define FDAS_K4_MIN_BLOCKS 2             // resident k4_levels blocks per SM the registers must allow
+#endif
+
+static_assert(LB == 16, "a lane owns 16 bins: two BF16 or four FP32 16-byte vectors");
 
 __device__ __forceinline__ float ld_plane(const float *p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float ld_plane(const __nv_bfloat16 *p, int64_t i) {
@@ -42,20 +58,77 @@ __device__ __forceinline__ float ld_plane(const __nv_bfloat16 *p, int64_t i) {
     return __uint_as_float(((unsigned)bits) << 16);
 }
 
-// 16-byte vector of plane values widened to float: 4 FP32 or 8 BF16 elements.
+// Plane element formats: elements per 16-byte vector, widening of one vector, and the maximum of
+// a lane's 16 values (BF16 compares packed pairs; widening is exact, so the order is the same).
 template <typename E>
-struct Vec;
+struct Fmt;
 template <>
-struct Vec<float> {
-    static constexpr int N = 4;
+struct Fmt<float> {
+    static constexpr int EPV = 4;
+    struct Raw {
+        float4 v[LB / 4];
+    };
+    __device__ __forceinline__ static void load_raw(const float *p, Raw &r) {
+#pragma unroll
+        for (int k = 0; k < LB / 4; k++) r.v[k] = __ldg(reinterpret_cast<const float4 *>(p) + k);
+    }
+    __device__ __forceinline__ static void widen(const Raw &r, float (&s)[LB]) {
+#pragma unroll
+        for (int k = 0; k < LB / 4; k++) {
+            s[4 * k] = r.v[k].x; s[4 * k + 1] = r.v[k].y; s[4 * k + 2] = r.v[k].z; s[4 * k + 3] = r.v[k].w;
+        }
+    }
+    __device__ __forceinline__ static float max16(const Raw &r) {
+        float m = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < LB / 4; k++) m = fmaxf(fmaxf(m, fmaxf(r.v[k].x, r.v[k].y)), fmaxf(r.v[k].z, r.v[k].w));
+        return m;
+    }
     __device__ __forceinline__ static void load(const float *p, float (&o)[4]) {
         const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
     }
+    __device__ __forceinline__ static float load16(const float *p, float (&s)[LB]) {
+        float m = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < LB / 4; k++) {
+            float v[4];
+            load(p + 4 * k, v);
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                s[4 * k + e] = v[e];
+                m = fmaxf(m, v[e]);
+            }
+        }
+        return m;
+    }
 };
 template <>
-struct Vec<__nv_bfloat16> {
-    static constexpr int N = 8;
+struct Fmt<__nv_bfloat16> {
+    static constexpr int EPV = 8;
+    struct Raw {
+        uint4 v[LB / 8];
+    };
+    __device__ __forceinline__ static void load_raw(const __nv_bfloat16 *p, Raw &r) {
+#pragma unroll
+        for (int k = 0; k < LB / 8; k++) r.v[k] = __ldg(reinterpret_cast<const uint4 *>(p) + k);
+    }
+    __device__ __forceinline__ static void widen(const Raw &r, float (&s)[LB]) {
+        const uint32_t w[8] = {r.v[0].x, r.v[0].y, r.v[0].z, r.v[0].w, r.v[1].x, r.v[1].y, r.v[1].z, r.v[1].w};
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            s[2 * k] = __uint_as_float(w[k] << 16);
+            s[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+        }
+    }
+    // packed BF16 maximum (exact: widening preserves the order)
+    __device__ __forceinline__ static float max16(const Raw &r) {
+        const uint32_t w[8] = {r.v[0].x, r.v[0].y, r.v[0].z, r.v[0].w, r.v[1].x, r.v[1].y, r.v[1].z, r.v[1].w};
+        __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(&w[0]);
+#pragma unroll
+        for (int k = 1; k < 8; k++) m = __hmax2(m, *reinterpret_cast<const __nv_bfloat162 *>(&w[k]));
+        return fmaxf(__low2float(m), __high2float(m));
+    }
     __device__ __forceinline__ static void load(const __nv_bfloat16 *p, float (&o)[8]) {
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -64,6 +137,19 @@ struct Vec<__nv_bfloat16> {
             o[2 * k] = __uint_as_float(w[k] << 16);
             o[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
         }
+    }
+    __device__ __forceinline__ static float load16(const __nv_bfloat16 *p, float (&s)[LB]) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(p + 8));
+        const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(&w[0]);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            m = __hmax2(m, *reinterpret_cast<const __nv_bfloat162 *>(&w[k]));
+            s[2 * k] = __uint_as_float(w[k] << 16);
+            s[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+        }
+        return fmaxf(__low2float(m), __high2float(m));
     }
 };
 
@@ -83,172 +169,229 @@ __device__ __forceinline__ bool row_in_level(int i, int K, int zmax, int H) {
     return i >= 0 && i < K && abs(H * z) <= zmax;
 }
 
-// S_H = S_{H/2} + sum_{h = H/2+1 .. H} P(h r, i_h) for every staged cell inside level H's region
-// (-inf outside).  A thread owns columns tid, tid + 256, tid + 512 of every staged row; the row
-// pointers of each harmonic are formed once per row, and a batch of rows issues all of its
-// loads before the ordered sums, so that about 16 independent loads are in flight per thread.
-template <typename E, int H>
-__device__ __forceinline__ void level_update(float (*S)[SWP], const E *__restrict__ plane, int64_t nb, int zmax,
-                                             int K, int i0, int64_t r0, int64_t rmax) {
-    constexpr int NH = H / 2;
-    constexpr int NC = (SW + RB * 32 - 1) / (RB * 32);            // columns per thread (3)
-    constexpr int RBAT = (16 / (NH * NC)) > 0 ? 16 / (NH * NC) : 1;
-    for (int ri0 = 0; ri0 < RB + 2; ri0 += RBAT) {
-        float v[RBAT][NC][NH];
-        bool ok[RBAT][NC];
+// s[e] += P(h (rl + e), i_h) for the lane's 16 bins, row pointer `row` of i_h.  The elements
+// h rl .. h rl + 15 h lie in NV consecutive 16-byte vectors starting at h rl (16-byte aligned:
+// rl is a multiple of 16); up to 8 vectors (h <= 4) are cheaper than 16 gathers and keep the
+// registers in check (levels 8 and 16, under 2 % of the cells, gather).  The last vector ends at
+// or before h (rl + 16) - 1, inside the row (h rl + 16 h <= nb for H >= h).
+template <typename E, int h>
+__device__ __forceinline__ void add_harmonic(const E *__restrict__ row, int64_t rl, float (&s)[LB]) {
+    constexpr int EPV = Fmt<E>::EPV;
+    constexpr int NV = (15 * h + 1 + EPV - 1) / EPV;
+    if constexpr (NV <= 8) {
+        const E *p = row + (int64_t)h * rl;
 #pragma unroll
-        for (int rb = 0; rb < RBAT; rb++) {
-            const int ri = ri0 + rb;
-            const int i = i0 - 1 + ri;
-            const bool row_ok = ri < RB + 2 && row_in_level(i, K, zmax, H);
-            const int z = -zmax + 2 * i;
-            const E *base[NH];
+        for (int k = 0; k < NV; k++) {
+            float v[EPV];
+            Fmt<E>::load(p + k * EPV, v);
 #pragma unroll
-            for (int q = 0; q < NH; q++)
-                base[q] = plane + (row_ok ? (int64_t)(((NH + 1 + q) * z + zmax) >> 1) * nb : 0);
-#pragma unroll
-            for (int cc = 0; cc < NC; cc++) {
-                const int c = threadIdx.x + cc * RB * 32;
-                const int64_t r = r0 - 1 + c;
-                ok[rb][cc] = row_ok && c < SW && r >= 0 && r <= rmax;
-#pragma unroll
-                for (int q = 0; q < NH; q++)
-                    v[rb][cc][q] = ok[rb][cc] ? ld_plane(base[q], (int64_t)(NH + 1 + q) * r) : 0.0f;
-            }
+            for (int e = 0; e < LB; e++)
+                if ((h * e) / EPV == k) s[e] = __fadd_rn(s[e], v[(h * e) % EPV]);
         }
+    } else {
+        float v[LB];
 #pragma unroll
-        for (int rb = 0; rb < RBAT; rb++) {
-            const int ri = ri0 + rb;
-            if (ri >= RB + 2) break;
+        for (int e = 0; e < LB; e++) v[e] = ld_plane(row, (int64_t)h * (rl + e));
 #pragma unroll
-            for (int cc = 0; cc < NC; cc++) {
-                const int c = threadIdx.x + cc * RB * 32;
-                if (c >= SW) break;
-                float sum = -INFINITY;
-                if (ok[rb][cc]) {
-                    sum = S[ri][c + SOFF];
+        for (int e = 0; e < LB; e++) s[e] = __fadd_rn(s[e], v[e]);
+    }
+}
+
+// S_H from S_{H/2}: the new harmonics h = H/2 + 1 .. H in order.
+template <typename E, int H>
+__device__ __forceinline__ void add_level(const E *__restrict__ plane, int64_t nb, int zmax, int z, int64_t rl,
+                                          float (&s)[LB]) {
 #pragma unroll
-                    for (int q = 0; q < NH; q++) sum = __fadd_rn(sum, v[rb][cc][q]);
-                }
-                S[ri][c + SOFF] = sum;
-            }
+    for (int q = 0; q < H / 2; q++) {
+        const int h = H / 2 + 1 + q;
+        const E *row = plane + (int64_t)((h * z + zmax) >> 1) * nb;
+        switch (h) {   // compile-time after unrolling
+            case 2: add_harmonic<E, 2>(row, rl, s); break;
+            case 3: add_harmonic<E, 3>(row, rl, s); break;
+            case 4: add_harmonic<E, 4>(row, rl, s); break;
+            case 5: add_harmonic<E, 5>(row, rl, s); break;
+            case 6: add_harmonic<E, 6>(row, rl, s); break;
+            case 7: add_harmonic<E, 7>(row, rl, s); break;
+            case 8: add_harmonic<E, 8>(row, rl, s); break;
+            case 9: add_harmonic<E, 9>(row, rl, s); break;
+            case 10: add_harmonic<E, 10>(row, rl, s); break;
+            case 11: add_harmonic<E, 11>(row, rl, s); break;
+            case 12: add_harmonic<E, 12>(row, rl, s); break;
+            case 13: add_harmonic<E, 13>(row, rl, s); break;
+            case 14: add_harmonic<E, 14>(row, rl, s); break;
+            case 15: add_harmonic<E, 15>(row, rl, s); break;
+            default: add_harmonic<E, 16>(row, rl, s); break;
+        }
+        // keep one harmonic's loads in flight at a time (bounds the registers of levels 8, 16)
+        asm volatile("" ::: "memory");
+    }
+}
+
+// The 3x3 rule for a cell of level H holding S_H = v: strictly above the defined neighbours that
+// come earlier in row-major (i, r) order, at least equal to the later ones.
+template <typename E>
+__device__ __noinline__ bool local_max(const E *plane, int64_t nb, int zmax, int K, int H, int64_t rmax, int i, int64_t r, float v) {
+    for (int di = -1; di <= 1; di++) {
+        const int ii = i + di;
+        if (!row_in_level(ii, K, zmax, H)) continue;
+        for (int dr = -1; dr <= 1; dr++) {
+            if (di == 0 && dr == 0) continue;
+            const int64_t rr = r + dr;
+            if (rr < 0 || rr > rmax) continue;
+            const float w = harm_sum(plane, nb, zmax, H, ii, rr);
+            const bool earlier = di < 0 || (di == 0 && dr < 0);
+            if (earlier ? !(v > w) : !(v >= w)) return false;
+        }
+    }
+    return true;
+}
+
+// One level H of one (row, chunk): S_H from S_{H/2} (H > 1), then the unit's count and mask.
+// Returns false when the chunk lies outside level H's region (the regions nest: stop there).
+template <typename E, int H>
+__device__ __forceinline__ bool level_step(const E *__restrict__ plane, int64_t nb, int zmax, int K,
+                                           const LevelDesc &d, int i, int z, int chunk, int64_t rl, float (&s)[LB],
+                                           float vmax, int32_t *__restrict__ unit_count,
+                                           uint32_t *__restrict__ unit_mask) {
+    const int lane = threadIdx.x & 31;
+    if (H > 1) {
+        if (!row_in_level(i, K, zmax, H) || (int64_t)chunk * CB > d.rmax) return false;   // warp-uniform
+        // d.rmax + 1 = Nb / H is a multiple of 16: a lane's bins are all in or all out
+        if (rl <= d.rmax) {
+            add_level<E, H>(plane, nb, zmax, z, rl, s);
+            vmax = s[0];
+#pragma unroll
+            for (int e = 1; e < LB; e++) vmax = fmaxf(vmax, s[e]);
+        } else {
+            vmax = -INFINITY;
+        }
+    }
+    // unit indices fit 32 bits (at most 1023 rows x 2^17 chunks per level, five levels)
+    const int u = (int)d.unit0 + (i - d.i_lo) * (int)d.chunks + chunk;
+    if (__any_sync(0xffffffffu, vmax > d.thr)) {
+        uint32_t pk = 0;
+        if (vmax > d.thr) {
+#pragma unroll
+            for (int e = 0; e < LB; e++)
+                if (s[e] > d.thr && local_max(plane, nb, zmax, K, H, d.rmax, i, rl + e, s[e])) pk |= 1u << e;
+        }
+        int cnt = __popc(pk);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        const uint32_t hi = __shfl_down_sync(0xffffffffu, pk, 1);
+        if (lane == 0) unit_count[u] = cnt;
+        if (cnt > 0 && !(lane & 1)) unit_mask[(int64_t)u * WORDS + (lane >> 1)] = pk | (hi << 16);
+    } else if (lane == 0) {
+        unit_count[u] = 0;
+    }
+    return true;
+}
+
+// Levels 4, 8 and 16 (under 10 % of the cells): out of line, so that their gathers do not set
+// the register budget of the common path (levels 1 and 2).
+template <typename E>
+__device__ __noinline__ void high_levels(const E *__restrict__ plane, int64_t nb, int zmax, int K,
+                                         const LevelTable *lt, int i, int z, int chunk, int64_t rl,
+                                         const float *s_in, int32_t *__restrict__ unit_count,
+                                         uint32_t *__restrict__ unit_mask) {
+    float s[LB];
+#pragma unroll
+    for (int e = 0; e < LB; e++) s[e] = s_in[e];
+    const int n = lt->n_levels;
+    if (!level_step<E, 4>(plane, nb, zmax, K, lt->lev[2], i, z, chunk, rl, s, 0.0f, unit_count, unit_mask)) return;
+    if (n < 4 || !level_step<E, 8>(plane, nb, zmax, K, lt->lev[3], i, z, chunk, rl, s, 0.0f, unit_count, unit_mask))
+        return;
+    if (n > 4) level_step<E, 16>(plane, nb, zmax, K, lt->lev[4], i, z, chunk, rl, s, 0.0f, unit_count, unit_mask);
+}
+
+// Levels 2 .. of one (row, chunk) inside level 2's region; s holds S_1 on entry.
+template <typename E>
+__device__ __forceinline__ void detect_chunk(const E *__restrict__ plane, int64_t nb, int zmax, int K,
+                                             const LevelTable &lt, int i, int z, int chunk, int64_t rl,
+                                             float (&s)[LB], int32_t *__restrict__ unit_count,
+                                             uint32_t *__restrict__ unit_mask) {
+    if (!level_step<E, 2>(plane, nb, zmax, K, lt.lev[1], i, z, chunk, rl, s, 0.0f, unit_count, unit_mask)) return;
+    if (lt.n_levels > 2 && row_in_level(i, K, zmax, 4) && (int64_t)chunk * CB <= lt.lev[2].rmax)
+        high_levels<E>(plane, nb, zmax, K, &lt, i, z, chunk, rl, s, unit_count, unit_mask);
+}
+
+// The level-1 peaks among a lane's 16 bins rl .. rl + 15 of row i (a lane holding a value above
+// the threshold, a handful per plane): re-read, test each against the 3x3 rule, return the mask.
+template <typename E>
+__device__ __noinline__ uint32_t level1_peaks(const E *__restrict__ plane, int64_t nb, int zmax, int K,
+                                              const LevelDesc d, int i, int64_t rl) {
+    uint32_t pk = 0;
+    for (int e = 0; e < LB; e++) {
+        const float v = ld_plane(plane, (int64_t)i * nb + rl + e);
+        if (v > d.thr && local_max(plane, nb, zmax, K, 1, d.rmax, i, rl + e, v)) pk |= 1u << e;
+    }
+    return pk;
+}
+
+// Level 1 over the whole plane: a pure stream.  Grid (ceil(chunks1 / (DETECT_WARPS * CPW1)), K);
+// each warp takes CPW1 consecutive chunks of row blockIdx.y, all loads issued first; a lane tests
+// its 16 values through their maximum (BF16: packed) and widens them only when it holds a
+// candidate.  Few registers, so many warps keep the loads in flight.
+template <typename E>
+__global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_L1_MIN_BLOCKS) k4_level1(const E *__restrict__ plane, int64_t nb, int zmax,
+                                                              int K, LevelDesc d, int chunks1,
+                                                              int32_t *__restrict__ unit_count,
+                                                              uint32_t *__restrict__ unit_mask) {
+    constexpr int CPW1 = Fmt<E>::EPV == 8 ? 4 : 2;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.y;
+    const int c0 = (blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * CPW1;
+    if (c0 >= chunks1) return;                       // warp-uniform
+    const E *row = plane + (int64_t)i * nb;
+    typename Fmt<E>::Raw raw[CPW1];
+#pragma unroll
+    for (int c = 0; c < CPW1; c++)
+        if (c0 + c < chunks1) Fmt<E>::load_raw(row + (int64_t)(c0 + c) * CB + LB * lane, raw[c]);
+#pragma unroll
+    for (int c = 0; c < CPW1; c++) {
+        if (c0 + c >= chunks1) break;
+        const float vmax = Fmt<E>::max16(raw[c]);
+        const int u = (int)d.unit0 + i * (int)d.chunks + c0 + c;
+        if (__any_sync(0xffffffffu, vmax > d.thr)) {
+            const uint32_t pk =
+                vmax > d.thr ? level1_peaks(plane, nb, zmax, K, d, i, (int64_t)(c0 + c) * CB + LB * lane) : 0u;
+            int cnt = __popc(pk);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            const uint32_t hi = __shfl_down_sync(0xffffffffu, pk, 1);
+            if (lane == 0) unit_count[u] = cnt;
+            if (cnt > 0 && !(lane & 1)) unit_mask[(int64_t)u * WORDS + (lane >> 1)] = pk | (hi << 16);
+        } else if (lane == 0) {
+            unit_count[u] = 0;
         }
     }
 }
 
+// Levels 2 .. 16 over level 2's region (rows i_lo .. i_lo + rows - 1 of level 2, chunks up to its
+// rmax): grid (ceil(chunks2 / (DETECT_WARPS * CPW)), rows2); each warp re-reads S_1 of CPW chunks
+// and carries the running sums through the levels in registers.
 template <typename E>
-__global__ void __launch_bounds__(RB * 32, 4) k4_detect(const E *__restrict__ plane, int64_t nb, int zmax, int K,
-                                                     LevelTable lt, int n_rb, int32_t *__restrict__ unit_count,
-                                                     uint32_t *__restrict__ unit_mask) {
-    __shared__ __align__(16) float S[RB + 2][SWP];
-    const int tile = blockIdx.x;
-    const int rb = tile % n_rb;                    // row blocks of one chunk run side by side (halo rows hit L2)
-    const int64_t chunk = tile / n_rb;
-    const int i0 = rb * RB;
-    const int64_t r0 = chunk * CB;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = i0 + warp;
-
-    // level 1: S_1 = P on rows i0-1 .. i0+RB, bins r0-1 .. r0+CB.  The chunk interior
-    // [r0, r0 + CB) is 16-byte aligned (r0 is a multiple of CB, Nb a power of two): vector loads,
-    // all issued before the shared-memory stores; the two halo columns are loaded singly.
-    {
-        constexpr int EPV = Vec<E>::N;
-        constexpr int VPR = CB / EPV;                       // vectors per row
-        constexpr int NV = ((RB + 2) * VPR + RB * 32 - 1) / (RB * 32);
-        float vals[NV][EPV];
+__global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_levels(const E *__restrict__ plane, int64_t nb, int zmax, int K,
+                                                              LevelTable lt, int chunks2,
+                                                              int32_t *__restrict__ unit_count,
+                                                              uint32_t *__restrict__ unit_mask) {
+    const int lane = threadIdx.x & 31;
+    const int i = lt.lev[1].i_lo + blockIdx.y;
+    const int c0 = (blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * CPW;
+    if (c0 >= chunks2) return;                       // warp-uniform
+    const int z = -zmax + 2 * i;
+    const E *row = plane + (int64_t)i * nb;
+    typename Fmt<E>::Raw raw[CPW];
 #pragma unroll
-        for (int k = 0; k < NV; k++) {
-            const int v = threadIdx.x + k * RB * 32;
-            const int ri = v / VPR, q = v % VPR;
-            const int i = i0 - 1 + ri;
-            const int64_t r = r0 + (int64_t)q * EPV;
-            if (ri < RB + 2 && i >= 0 && i < K && r < nb) {
-                Vec<E>::load(plane + (int64_t)i * nb + r, vals[k]);
-            } else {
+    for (int c = 0; c < CPW; c++)
+        if (c0 + c < chunks2) Fmt<E>::load_raw(row + (int64_t)(c0 + c) * CB + LB * lane, raw[c]);
 #pragma unroll
-                for (int e = 0; e < EPV; e++) vals[k][e] = -INFINITY;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < NV; k++) {
-            const int v = threadIdx.x + k * RB * 32;
-            const int ri = v / VPR, q = v % VPR;
-            if (ri < RB + 2) {
-#pragma unroll
-                for (int e = 0; e < EPV; e += 4)
-                    *reinterpret_cast<float4 *>(&S[ri][1 + SOFF + q * EPV + e]) =
-                        make_float4(vals[k][e], vals[k][e + 1], vals[k][e + 2], vals[k][e + 3]);
-            }
-        }
-        if (threadIdx.x < 2 * (RB + 2)) {
-            const int ri = threadIdx.x >> 1;
-            const int c = (threadIdx.x & 1) ? SW - 1 : 0;
-            const int i = i0 - 1 + ri;
-            const int64_t r = r0 - 1 + c;
-            S[ri][c + SOFF] = (i >= 0 && i < K && r >= 0 && r < nb) ? ld_plane(plane + (int64_t)i * nb, r) : -INFINITY;
-        }
-    }
-    __syncthreads();
-
-    for (int l = 0; l < lt.n_levels; l++) {
-        const LevelDesc &d = lt.lev[l];
-        const int H = d.H;
-        if (r0 > d.rmax) break;                                     // regions nest: nothing further
-        const int rlo = max(i0 - 1, d.i_lo), rhi = min(i0 + RB, d.i_lo + d.rows - 1);
-        if (rlo > rhi) break;
-        if (l > 0) {
-            // S_H = S_{H/2} + sum_{h = H/2+1 .. H} P(h r, i_h) inside level H's region, -inf outside
-            __syncthreads();
-            switch (H) {
-                case 2: level_update<E, 2>(S, plane, nb, zmax, K, i0, r0, d.rmax); break;
-                case 4: level_update<E, 4>(S, plane, nb, zmax, K, i0, r0, d.rmax); break;
-                case 8: level_update<E, 8>(S, plane, nb, zmax, K, i0, r0, d.rmax); break;
-                default: level_update<E, 16>(S, plane, nb, zmax, K, i0, r0, d.rmax); break;
-            }
-            __syncthreads();
-        }
-        // detection: warp `warp` owns row i0 + warp; lane handles bins r0 + lane + 32 e
-        if (row_in_level(row, K, zmax, H)) {
-            int cnt = 0;
-            uint32_t words[WORDS];
-            const int cmax = (int)min((int64_t)CB, d.rmax - r0 + 1);   // valid bins in this chunk
-            // fast path: nothing in the row segment above the threshold -> an empty unit
-            float vmax = -INFINITY;
-#pragma unroll
-            for (int e = 0; e < WORDS; e++)
-                if (lane + 32 * e < cmax) vmax = fmaxf(vmax, S[warp + 1][1 + SOFF + lane + 32 * e]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-            if (!(vmax > d.thr)) {
-                if (lane == 0) unit_count[d.unit0 + (int64_t)(row - d.i_lo) * d.chunks + chunk] = 0;
-            } else {
-#pragma unroll
-            for (int e = 0; e < WORDS; e++) {
-                const int c = 1 + SOFF + lane + 32 * e;
-                bool pk = false;
-                if (lane + 32 * e < cmax) {
-                    const float v = S[warp + 1][c];
-                    if (v > d.thr) {
-                        pk = v > S[warp][c - 1] && v > S[warp][c] && v > S[warp][c + 1] && v > S[warp + 1][c - 1] &&
-                             v >= S[warp + 1][c + 1] && v >= S[warp + 2][c - 1] && v >= S[warp + 2][c] &&
-                             v >= S[warp + 2][c + 1];
-                    }
-                }
-                words[e] = __ballot_sync(0xffffffffu, pk);
-                cnt += __popc(words[e]);
-            }
-            const int64_t u = d.unit0 + (int64_t)(row - d.i_lo) * d.chunks + chunk;
-            if (lane == 0) unit_count[u] = cnt;
-            if (cnt > 0 && lane < WORDS) {
-                uint32_t w = 0;
-#pragma unroll
-                for (int e = 0; e < WORDS; e++)
-                    if (e == lane) w = words[e];
-                unit_mask[u * WORDS + lane] = w;
-            }
-            }
-        }
+    for (int c = 0; c < CPW; c++) {
+        if (c0 + c >= chunks2) break;
+        float s[LB];
+        Fmt<E>::widen(raw[c], s);
+        detect_chunk<E>(plane, nb, zmax, K, lt, i, z, c0 + c, (int64_t)(c0 + c) * CB + LB * lane, s, unit_count,
+                        unit_mask);
     }
 }
 
@@ -342,7 +485,8 @@ __device__ __forceinline__ UnitRef unit_of(const LevelTable &lt, int64_t u) {
     return ref;
 }
 
-// One warp per non-empty unit: records at (block offset + in-block offset + rank).
+// Records of the non-empty units at (block offset + in-block offset + rank).  A warp reads 32
+// units' counts at a time (one per lane) and then serves the non-empty ones one by one.
 template <typename E>
 __global__ void __launch_bounds__(256) k4_emit(const E *__restrict__ plane, int64_t nb, int zmax, LevelTable lt,
                                                int64_t n_units, const int32_t *__restrict__ unit_count,
@@ -353,36 +497,42 @@ __global__ void __launch_bounds__(256) k4_emit(const E *__restrict__ plane, int6
     const int lane = threadIdx.x & 31;
     const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = warp_id; u < n_units; u += n_warps) {
-        const int32_t cnt = unit_count[u];
-        if (cnt == 0) continue;                                  // warp-uniform
-        const int64_t base = block_off[u / SCAN_BLOCK] + unit_off[u];
-        const UnitRef ref = unit_of(lt, u);
-        const int H = lt.lev[ref.l].H;
-        const uint32_t w = lane < WORDS ? unit_mask[u * WORDS + lane] : 0u;
-        int incl = __popc(w);
+    for (int64_t u0 = warp_id * 32; u0 < n_units; u0 += n_warps * 32) {
+        const int64_t mine = u0 + lane;
+        const int32_t my_cnt = mine < n_units ? unit_count[mine] : 0;
+        uint32_t busy = __ballot_sync(0xffffffffu, my_cnt != 0);
+        while (busy) {                                           // warp-uniform
+            const int j = __ffs(busy) - 1;
+            busy &= busy - 1;
+            const int64_t u = u0 + j;
+            const int64_t base = block_off[u / SCAN_BLOCK] + unit_off[u];
+            const UnitRef ref = unit_of(lt, u);
+            const int H = lt.lev[ref.l].H;
+            const uint32_t w = lane < WORDS ? unit_mask[u * WORDS + lane] : 0u;
+            int incl = __popc(w);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        int64_t pos = base + incl - __popc(w);
-        uint32_t bits = w;
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            if (pos < max_peaks) {
-                const int64_t r = ref.chunk * CB + lane * 32 + b;
-                fdas_peak pk;
-                pk.series = series;
-                pk.r = (uint32_t)r;
-                pk.zi = (int16_t)ref.row;
-                pk.harm = (uint8_t)H;
-                pk.pad = 0;
-                pk.power = harm_sum(plane, nb, zmax, H, ref.row, r);
-                out[pos] = pk;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            pos++;
+            int64_t pos = base + incl - __popc(w);
+            uint32_t bits = w;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (pos < max_peaks) {
+                    const int64_t r = ref.chunk * CB + lane * 32 + b;
+                    fdas_peak pk;
+                    pk.series = series;
+                    pk.r = (uint32_t)r;
+                    pk.zi = (int16_t)ref.row;
+                    pk.harm = (uint8_t)H;
+                    pk.pad = 0;
+                    pk.power = harm_sum(plane, nb, zmax, H, ref.row, r);
+                    out[pos] = pk;
+                }
+                pos++;
+            }
         }
     }
 }
@@ -395,17 +545,24 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
     int32_t *unit_off = reinterpret_cast<int32_t *>(ws + p.ws_uoff);
     uint32_t *unit_mask = reinterpret_cast<uint32_t *>(ws + p.ws_umask);
     int64_t *block_off = reinterpret_cast<int64_t *>(ws + p.ws_ublock);
-    const int n_rb = (p.K + RB - 1) / RB;
     const int64_t chunks1 = lt.lev[0].chunks;
+    constexpr int CPW1 = Fmt<E>::EPV == 8 ? 4 : 2;
+    const dim3 level1_grid((unsigned)((chunks1 + DETECT_WARPS * CPW1 - 1) / (DETECT_WARPS * CPW1)), (unsigned)p.K);
+    const int64_t chunks2 = lt.n_levels > 1 ? lt.lev[1].chunks : 0;
+    const dim3 levels_grid((unsigned)((chunks2 + DETECT_WARPS * CPW - 1) / (DETECT_WARPS * CPW)),
+                           (unsigned)(lt.n_levels > 1 ? lt.lev[1].rows : 0));
     const int64_t n_units = p.n_units;
     const int64_t n_blocks = (n_units + SCAN_BLOCK - 1) / SCAN_BLOCK;
     p.prof.begin(FDAS_STAGE_PEAKS, st);
-    p.prof.launches += 4;
-    k4_detect<E><<<(unsigned)(n_rb * chunks1), RB * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, n_rb, unit_count,
-                                                                  unit_mask);
+    p.prof.launches += lt.n_levels > 1 ? 5 : 4;
+    k4_level1<E><<<level1_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt.lev[0], (int)chunks1,
+                                                             unit_count, unit_mask);
+    if (lt.n_levels > 1)
+        k4_levels<E><<<levels_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2,
+                                                                 unit_count, unit_mask);
     k4_scan_blocks<<<(unsigned)n_blocks, 1024, 0, st>>>(unit_count, n_units, unit_off, block_off);
     k4_scan_top<<<1, 1024, 0, st>>>(block_off, n_blocks, npeaks, p.cfg.max_peaks, p.d_status);
-    const int64_t emit_blocks = std::min<int64_t>((n_units + 7) / 8, 152 * 16);
+    const int64_t emit_blocks = std::min<int64_t>((n_units + 255) / 256, 152 * 8);
     k4_emit<E><<<(unsigned)emit_blocks, 256, 0, st>>>(plane, p.nb, p.cfg.zmax, lt, n_units, unit_count, unit_off,
                                                        block_off, unit_mask, peaks, p.cfg.max_peaks, series);
     p.prof.end(FDAS_STAGE_PEAKS, st);
