@@ -4,13 +4,16 @@
 //
 // A real series x[N] is read as the complex series z_n = x_{2n} + i x_{2n+1} of length
 // M = N/2 = M1*M2, transformed by a four-step FFT, then split:
-//   pass A (one CTA per column n2):  FFT_M1 over n1 of z[n1*M2 + n2], times W_M^{n2 k1},
-//                                    stored as a contiguous row B[n2*M1 + k1];
-//   pass B (one CTA per row pair):   FFT_M2 over n2 of B[n2*M1 + k1] gives Z[k1 + M1*k2];
-//                                    with Z for rows k1 and M1-k1 both in shared memory,
+//   pass A (one CTA per C1 adjacent columns n2):  FFT_M1 over n1 of z[n1*M2 + n2], times
+//                                    W_M^{n2 k1}, stored transposed as B[k1*M2 + n2];
+//   pass B (one CTA per C2 rows k1 and their partners M1 - k1):  FFT_M2 over n2 of the row
+//                                    B[k1*M2 + n2] gives Z[k1 + M1*k2]; with Z for rows k1 and
+//                                    M1-k1 both in shared memory,
 //                                    X_k = (Z_k + conj Z_{M-k})/2 - (i/2) W_N^k (Z_k - conj Z_{M-k}),
 //                                    k < M, and a per-CTA FP64 partial of sum |X_k|^2;
 //   finalize (one CTA):              fixed-order sum of the partials -> sigma2, scale.
+// The lanes of a warp interleave over the CTA's columns (pass A) or rows (pass B), so every
+// global access of a warp covers whole 32-byte sectors instead of strided single elements.
 // Twiddles W_N^e come from a two-level FP32 table (W_N^e = hi[e >> 13] * lo[e & 8191]).
 #include "block_fft.cuh"
 #include "fdas_internal.cuh"
@@ -23,52 +26,67 @@ __device__ __forceinline__ float2 twN(const float2 *__restrict__ lo, const float
     return cmul(__ldg(hi + (e >> TW_LO_BITS)), __ldg(lo + (e & ((1 << TW_LO_BITS) - 1))));
 }
 
+// FFTs of one CTA: groups per CTA (bounded by 1024 threads and the shared memory) and the
+// padding between the groups' shared-memory regions (16 words: groups interleaved in a warp
+// fall on different banks).
+constexpr int k1_groups(int S) { return S >= 8192 ? 1 : (S >= 4096 ? 2 : 4); }
+constexpr int K1_GPAD = 8;
+#ifndef FDAS_K1A_MIN_BLOCKS
+#define FDAS_K1A_MIN_BLOCKS 1            // resident pass-A blocks per SM the registers must allow
+#endif
+
 template <int M1>
-__global__ void __launch_bounds__(M1 / 32) k1_pass_a(const float2 *__restrict__ z, const float2 *__restrict__ tw,
-                                                     const float2 *__restrict__ lo, const float2 *__restrict__ hi,
-                                                     float2 *__restrict__ B, int M2) {
-    constexpr int T = M1 / 32;
-    extern __shared__ float2 sm[];        // fft_smem_entries(M1) entries
-    const int t = threadIdx.x;
-    const int n2 = blockIdx.x;
+__global__ void __launch_bounds__(k1_groups(M1) * (M1 / 32), FDAS_K1A_MIN_BLOCKS) k1_pass_a(const float2 *__restrict__ z,
+                                                                     const float2 *__restrict__ tw,
+                                                                     const float2 *__restrict__ lo,
+                                                                     const float2 *__restrict__ hi,
+                                                                     float2 *__restrict__ B, int M2) {
+    constexpr int T = M1 / 32, C1 = k1_groups(M1);
+    constexpr int E = fft_smem_entries(M1) + K1_GPAD;
+    extern __shared__ float2 sm[];        // C1 * E entries
+    const int g = threadIdx.x % C1, t = threadIdx.x / C1;
+    const int n2 = blockIdx.x * C1 + g;
     float2 v[32];
 #pragma unroll
     for (int i = 0; i < 32; i++) v[i] = __ldg(z + (int64_t)(t + i * T) * M2 + n2);
-    block_fft<M1>(v, sm, tw, t);
-    float2 *row = B + (int64_t)n2 * M1;
+    block_fft<M1>(v, sm + g * E, tw, t);
 #pragma unroll
     for (int i = 0; i < 32; i++) {
         const int k1 = t + i * T;
         // W_M^{n2 k1} = W_N^{2 n2 k1}
-        row[k1] = cmul(v[i], twN(lo, hi, 2 * (int64_t)n2 * k1));
+        B[(int64_t)k1 * M2 + n2] = cmul(v[i], twN(lo, hi, 2 * (int64_t)n2 * k1));
     }
 }
 
+// Groups 0 .. C2-1 take rows a = p C2 + g; groups C2 .. 2 C2 - 1 their partners M1 - a (row 0,
+// its own partner, lends its partner slot to row M1/2, the other self-partnered row).
 template <int M2>
-__global__ void __launch_bounds__(2 * (M2 / 32)) k1_pass_b(const float2 *__restrict__ B, const float2 *__restrict__ tw,
-                                                           const float2 *__restrict__ lo, const float2 *__restrict__ hi,
-                                                           float2 *__restrict__ X, double *__restrict__ partial, int M1) {
-    constexpr int T = M2 / 32;
-    constexpr int E = fft_smem_entries(M2);
-    extern __shared__ float2 smb[];       // 2 * E entries
-    __shared__ double red[2 * T];
-    const int half = threadIdx.x / T, t = threadIdx.x - half * T;
-    const int p = blockIdx.x;             // row pair
-    const int rowA = p, rowB = (p == 0) ? M1 / 2 : M1 - p;
-    const int row = half ? rowB : rowA;
-    float2 *sm = smb + half * E;
+__global__ void __launch_bounds__(2 * k1_groups(M2) * (M2 / 32)) k1_pass_b(const float2 *__restrict__ B,
+                                                                         const float2 *__restrict__ tw,
+                                                                         const float2 *__restrict__ lo,
+                                                                         const float2 *__restrict__ hi,
+                                                                         float2 *__restrict__ X,
+                                                                         double *__restrict__ partial, int M1) {
+    constexpr int T = M2 / 32, C2 = k1_groups(M2), G = 2 * C2;
+    constexpr int E = fft_smem_entries(M2) + K1_GPAD;
+    extern __shared__ float2 smb[];       // G * E entries
+    __shared__ double red[G * T];
+    const int g = threadIdx.x % G, t = threadIdx.x / G;
+    const int a = blockIdx.x * C2 + (g % C2);
+    const int row = g < C2 ? a : (a == 0 ? M1 / 2 : M1 - a);
+    float2 *sm = smb + g * E;
     float2 v[32];
 #pragma unroll
-    for (int i = 0; i < 32; i++) v[i] = __ldg(B + (int64_t)(t + i * T) * M1 + row);
+    for (int i = 0; i < 32; i++) v[i] = __ldg(B + (int64_t)row * M2 + t + i * T);
     block_fft<M2>(v, sm, tw, t);
     // the last FFT stage works in registers and the previous exchange ended with a barrier
 #pragma unroll
     for (int i = 0; i < 32; i++) sm[fft_pad(t + i * T)] = v[i];
     __syncthreads();
-    // partner of k = row + M1 k2 is M - k = pr + M1 k2' (row 0 pairs with itself)
-    const int pr = (row == 0) ? 0 : M1 - row;
-    const float2 *smp = smb + ((pr == rowA) ? 0 : E);
-    const int64_t M = (int64_t)M1 * M2;
+    // partner of k = row + M1 k2 is M - k = pr + M1 k2' (rows 0 and M1/2 pair with themselves)
+    const bool self = (row == 0) || (row == M1 / 2);
+    const int gp = self ? g : (g < C2 ? g + C2 : g - C2);
+    const float2 *smp = smb + gp * E;
     double acc = 0.0;
 #pragma unroll
     for (int i = 0; i < 32; i++) {
@@ -86,14 +104,13 @@ __global__ void __launch_bounds__(2 * (M2 / 32)) k1_pass_b(const float2 *__restr
         X[k] = xk;
         acc += (double)xk.x * xk.x + (double)xk.y * xk.y;
     }
-    (void)M;
     red[threadIdx.x] = acc;
     __syncthreads();
-    for (int s = T; s > 0; s >>= 1) {
+    for (int s = G * T / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[p] = red[0];
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
 // sigma2 = (sum of partials, fixed order) / (Nb - 1) unless fixed; scale = sqrt(2 / sigma2).
@@ -126,21 +143,23 @@ __global__ void k1_apply_scale(const float2 *__restrict__ X, const float *__rest
 
 template <int M1>
 cudaError_t run_pass_a(const Plan &p, const float2 *z, float2 *B, cudaStream_t st) {
-    const size_t smem = sizeof(float2) * fft_smem_entries(M1);
+    constexpr int C1 = k1_groups(M1);
+    const size_t smem = sizeof(float2) * C1 * (fft_smem_entries(M1) + K1_GPAD);
     auto kern = k1_pass_a<M1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<p.M2, M1 / 32, smem, st>>>(z, p.d_tw, p.d_twn_lo, p.d_twn_hi, B, p.M2);
+    kern<<<p.M2 / C1, C1 * (M1 / 32), smem, st>>>(z, p.d_tw, p.d_twn_lo, p.d_twn_hi, B, p.M2);
     return cudaGetLastError();
 }
 
 template <int M2>
 cudaError_t run_pass_b(const Plan &p, const float2 *B, float2 *X, double *partial, cudaStream_t st) {
-    const size_t smem = 2 * sizeof(float2) * fft_smem_entries(M2);
+    constexpr int C2 = k1_groups(M2);
+    const size_t smem = 2 * C2 * sizeof(float2) * (fft_smem_entries(M2) + K1_GPAD);
     auto kern = k1_pass_b<M2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<p.M1 / 2, 2 * (M2 / 32), smem, st>>>(B, p.d_tw, p.d_twn_lo, p.d_twn_hi, X, partial, p.M1);
+    kern<<<p.M1 / (2 * C2), 2 * C2 * (M2 / 32), smem, st>>>(B, p.d_tw, p.d_twn_lo, p.d_twn_hi, X, partial, p.M1);
     return cudaGetLastError();
 }
 
@@ -181,7 +200,7 @@ cudaError_t launch_spectrum(const Plan &p, const float *d_series, char *ws, cuda
         case 8192: e = run_pass_b<8192>(p, B, X, partial, st); break;
     }
     if (e != cudaSuccess) return e;
-    k1_finalize<<<1, 256, 0, st>>>(partial, p.M1 / 2, p.nb, p.cfg.sigma2, sigma2, scale);
+    k1_finalize<<<1, 256, 0, st>>>(partial, p.M1 / (2 * k1_groups(p.M2)), p.nb, p.cfg.sigma2, sigma2, scale);
     p.prof.end(FDAS_STAGE_SPECTRUM, st);
     return cudaGetLastError();
 }
