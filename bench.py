@@ -13,7 +13,9 @@ accelerated pulse trains, 85 templates (zmax 84), 256 taps, 8192-bin segments.
 Beside the plane metric, the line carries "refine": sub-bin refinement of 100k candidates seeded
 within half a bin of the injected harmonics of a series like the one above (20 FP32 gradient
 steps and a final FP64 step per candidate), in candidates/s, with the oracle's own ascent timed
-on a sample of the same candidates.
+on a sample of the same candidates; and "batch": 256 dispersion-trial series of uneven length
+(2^21 .. 2^23) and zmax (20, 50, 84) searched with 16-harmonic sums as one graph-launched BF16
+batch, in cells/s, beside the same series searched one by one on the FP32 path.
 
 Prints one JSON line (rank 0).  Multi-GPU: one process per GPU (torchrun), each searching
 its own series (dispersion trials are independent: weak scaling, no data-path collective);
@@ -68,6 +70,7 @@ def parse_args():
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision comparison runs")
     ap.add_argument("--quick", action="store_true", help="no clocks, e2e or CPU baseline (profiling runs)")
     ap.add_argument("--no-refine", action="store_true", help="skip the candidate-refinement measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the many-series batch measurement")
     ap.add_argument("--n-log2", type=int, default=23,
                     help="series length 2^n (23 = the benchmark workload; smaller only for profiler captures)")
     return ap.parse_args()
@@ -388,6 +391,83 @@ def refine_bench(dev, stream, reps: int = 10, warmup: int = 3, cpu_sample: int =
     return res
 
 
+# ------------------------------------------------------------------------------ batch of series
+BATCH_SERIES = 256
+
+
+def batch_bench(dev, stream, reps: int = 5, warmup: int = 2, loop_reps: int = 2):
+    """The batching workload: one fdas_batch_search (a captured graph) over all series, BF16,
+    vs an FP32 per-series loop of fdas_search calls (one plan per distinct series shape).  The
+    packed series (about 4.8 GB) stay on the device; each pass streams far more than L2."""
+    import numpy as np
+    import torch
+
+    import fdas_synth as synth
+    import paper_2206_12205_gb300 as fd
+    from paper_2206_12205_gb300 import batch as fbat
+
+    t0 = time.perf_counter()
+    wl = synth.batch_workload(n_series=BATCH_SERIES, workers=min(16, os.cpu_count() or 1))
+    t_gen = time.perf_counter() - t0
+    packed = torch.from_numpy(wl.packed).to(dev)
+    cells = wl.total_cells
+
+    def cfg(w, prec):
+        return fd.make_config(w.n, w.zmax, w.taps, w.seg_len, precision=prec, max_harm=MAX_HARM, thr=THRESHOLDS,
+                              max_peaks=4096)
+
+    bs = fbat.BatchSearch([cfg(w, "bf16") for w in wl.series], device=dev, stream=stream)
+    for _ in range(warmup):
+        bs.search(packed, stream)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bs.search(packed, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    ms_batch = statistics.median(ms)
+    npk = int(bs.npeaks.sum().item())
+    assert fd.fdas_batch_device_status(bs.batch) == 0
+    del bs
+
+    # FP32 per-series loop: one Search per distinct shape, fdas_search per series
+    searches = {}
+    for w in wl.series:
+        key = (w.n, w.zmax, w.taps)
+        if key not in searches:
+            searches[key] = fd.Search(cfg(w, "fp32"), device=dev, stream=stream)
+    views = [packed[int(o): int(o) + w.n] for o, w in zip(wl.offsets, wl.series)]
+    for w, x in zip(wl.series, views):
+        searches[(w.n, w.zmax, w.taps)].search(x, stream)
+    torch.cuda.synchronize()
+    ms_loop = []
+    for _ in range(loop_reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for w, x in zip(wl.series, views):
+            searches[(w.n, w.zmax, w.taps)].search(x, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_loop.append(a.elapsed_time(b))
+    ms_fp32 = statistics.median(ms_loop)
+    del searches, packed
+    shapes = sorted({(w.n, w.zmax) for w in wl.series})
+    return {
+        "metric": "f-z plane cells/s over a batch of series (BF16, one graph launch per batch)",
+        "value": cells / (ms_batch / 1e3), "unit": "cells/s", "series": BATCH_SERIES, "cells": cells,
+        "ms_per_batch": ms_batch, "peaks_found": npk, "gpu_launches_per_batch": 10 * BATCH_SERIES,
+        "fp32_loop": {"value": cells / (ms_fp32 / 1e3), "unit": "cells/s", "ms_per_batch": ms_fp32,
+                      "how": "fdas_search per series from Python, FP32 path, one plan per series shape"},
+        "speedup_vs_fp32_loop": ms_fp32 / ms_batch,
+        "workload": (f"{BATCH_SERIES} series, N in {{2^21, 2^22, 2^23}}, zmax in {{20, 50, 84}} (taps 64/128/256), "
+                     f"0-2 pulse trains each, {len(shapes)} distinct shapes; synthesised in {t_gen:.1f} s"),
+        "l2": "each batch streams about 4.8 GB of series and 33 G cells of planes through HBM (L2 is 129 MB)",
+    }
+
+
 # ------------------------------------------------------------------------------ own arm
 def own_arm(args):
     import numpy as np
@@ -517,6 +597,9 @@ def own_arm(args):
     refine = None
     if rank == 0 and world == 1 and not args.no_refine and not args.quick:
         refine = refine_bench(dev, stream, cpu=not args.no_cpu_baseline)
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch and not args.quick:
+        batch = batch_bench(dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
@@ -533,7 +616,7 @@ def own_arm(args):
             "data": "synthetic: seeded N(0,1) noise + 8 accelerated Gaussian pulse trains (fdas_synth)",
             "config": config_json(w, precision),
             "roofline": roof, "roofline_correlate": roof_corr, "paths": paths or None,
-            "cpu_baseline": cpu, "e2e": e2e, "refine": refine,
+            "cpu_baseline": cpu, "e2e": e2e, "refine": refine, "batch": batch,
             "gpu_launches": int(prof["launches"]), "clocks": clk,
             "stages_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
         }

@@ -197,3 +197,113 @@ def noise_plane(K: int, nb: int, rng: np.random.Generator) -> np.ndarray:
     """A stand-in f-z plane for peak-search tests: K x nb independent exponential cells of mean 2
     (the chi^2, 2 dof law of noise-only plane cells), float32.  Callers plant signals on top."""
     return rng.exponential(2.0, size=(K, nb)).astype(np.float32)
+
+
+BATCH_N = (1 << 21, 1 << 22, 1 << 23)
+BATCH_ZMAX = (20, 50, 84)
+
+
+def taps_for_zmax(zmax: int) -> int:
+    """Smallest power-of-two tap count with m/2 >= zmax + 12 (the response of the largest drift
+    plus its tails fits the window)."""
+    m = 2
+    while m // 2 < zmax + 12:
+        m *= 2
+    return m
+
+
+@dataclasses.dataclass
+class BatchWorkload:
+    """Many dispersion-trial series of uneven length and zmax, packed back to back."""
+    series: list              # Workload per series (series arrays not kept: see `packed`)
+    packed: np.ndarray        # float32, all series concatenated
+    offsets: np.ndarray       # int64 start of each series in `packed`
+
+    @property
+    def total_cells(self) -> int:
+        return int(sum(w.K * w.nb for w in self.series))
+
+
+def _batch_shapes(config_index, n_series, n_choices, zmax_choices):
+    shapes = []
+    for s in range(n_series):
+        rng = rng_for(config_index, s)
+        n = int(rng.choice(np.array(n_choices)))
+        zmax = int(rng.choice(np.array(zmax_choices)))
+        shapes.append((n, zmax))
+    return shapes
+
+
+def _batch_series(config_index, s, n_choices, zmax_choices, tsamp, max_trains, duty, snr, out):
+    """Series s of a batch into `out` (float32, its length); returns its trains."""
+    rng = rng_for(config_index, s)
+    n = int(rng.choice(np.array(n_choices)))                 # the shape draws of _batch_shapes
+    zmax = int(rng.choice(np.array(zmax_choices)))
+    assert out.shape[0] == n
+    out[:] = rng.standard_normal(n, dtype=np.float32)
+    k = int(rng.integers(0, max_trains + 1))
+    trains = draw_trains(rng, k, n, tsamp, zlim=0.95 * zmax, duty=duty, snr=snr)
+    for t in trains:
+        out += pulse_train(n, t.r0, t.z0, t.duty, t.snr, t.phase0).astype(np.float32)
+    return trains
+
+
+def _batch_worker(args):
+    from multiprocessing import shared_memory
+    shm_name, total, jobs = args
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        packed = np.ndarray((total,), dtype=np.float32, buffer=shm.buf)
+        res = []
+        for (config_index, s, nc, zc, tsamp, max_trains, duty, snr, off, n) in jobs:
+            res.append((s, _batch_series(config_index, s, nc, zc, tsamp, max_trains, duty, snr,
+                                         packed[off:off + n])))
+        del packed
+        return res
+    finally:
+        shm.close()
+
+
+def batch_workload(config_index: int = 2, n_series: int = 256, tsamp: float = 64e-6, n_choices=BATCH_N,
+                   zmax_choices=BATCH_ZMAX, max_trains: int = 2, duty: float = 0.05, snr=(5.0, 30.0),
+                   seg_len: int = 8192, workers: int = 1) -> BatchWorkload:
+    """Batching case: n_series series, each with N drawn from {2^21, 2^22, 2^23}, zmax from
+    {20, 50, 84} (K = zmax + 1, taps from taps_for_zmax), 0 .. max_trains injected pulse trains
+    (periods 1-20 ms, z uniform within 95% of the series' zmax, 5% duty, SNR 5-30), unit
+    Gaussian noise, float32.  Series s draws from the generator seeded (config_index, s), so the
+    result does not depend on `workers` (processes started with spawn, filling shared memory)."""
+    shapes = _batch_shapes(config_index, n_series, n_choices, zmax_choices)
+    offsets = np.zeros(n_series, dtype=np.int64)
+    o = 0
+    for s, (n, _) in enumerate(shapes):
+        offsets[s] = o
+        o += n
+    total = o
+    jobs = [(config_index, s, tuple(n_choices), tuple(zmax_choices), tsamp, max_trains, duty, snr, int(offsets[s]), n)
+            for s, (n, zmax) in enumerate(shapes)]
+    trains = {}
+    if workers <= 1:
+        packed = np.empty(total, dtype=np.float32)
+        for j in jobs:
+            trains[j[1]] = _batch_series(*j[:8], packed[j[8]:j[8] + j[9]])
+    else:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        from multiprocessing import shared_memory
+        shm = shared_memory.SharedMemory(create=True, size=4 * total)
+        try:
+            chunks = [(shm.name, total, jobs[w::workers]) for w in range(workers)]
+            with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+                for res in ex.map(_batch_worker, chunks):
+                    for s, tr in res:
+                        trains[s] = tr
+            packed = np.ndarray((total,), dtype=np.float32, buffer=shm.buf).copy()
+        finally:
+            shm.close()
+            shm.unlink()
+    meta = []
+    for s, (n, zmax) in enumerate(shapes):
+        m = taps_for_zmax(zmax)
+        meta.append(Workload(f"batch{config_index}_s{s}_n{n}_z{zmax}_m{m}", n, tsamp, zmax, m, seg_len,
+                             np.empty(0, dtype=np.float32), trains[s]))
+    return BatchWorkload(meta, packed, offsets)

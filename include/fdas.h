@@ -254,6 +254,69 @@ fdas_status fdas_interp_power(fdas_plan_t plan, const float *d_xhat, const fdas_
 fdas_status fdas_refine(fdas_plan_t plan, const float *d_xhat, const fdas_cand *d_in, int32_t n,
                         int32_t steps, fdas_cand *d_out, double *d_power, int32_t *d_evals, void *stream);
 
+/*
+ * Batched search over many series: dispersion-measure trials of uneven length and zmax, one
+ * configuration each (the paper searches every trial of a dedispersed observation; Sec. 2.1).
+ * Series with the same (n_samples, zmax, taps, seg_len, precision) share one template bank.
+ * All series run back to back in one CUDA graph (captured on a library-owned stream the first
+ * time a set of buffers is seen, relaunched on the caller's stream afterwards), reusing one
+ * workspace and one plane buffer sized for the largest series, so device memory does not grow
+ * with the number of series.
+ */
+typedef struct fdas_batch_s *fdas_batch_t;
+
+/*
+ * Validate and plan n_series configurations (host only).  *workspace_bytes (nullable)
+ * receives the scratch fdas_batch_search needs.  Errors: as fdas_plan for any series;
+ * FDAS_E_INVALID for n_series <= 0 or NULL pointers.
+ */
+fdas_status fdas_batch_plan(const fdas_config *cfgs, int32_t n_series, fdas_batch_t *batch,
+                            size_t *workspace_bytes);
+
+/*
+ * Autotune (optional, before fdas_batch_make_templates; allocates and runs on the current
+ * device): for each FP32 group, time the segment lengths S = 1024 .. 8192 (S >= 2 taps) and
+ * 1 .. 16 templates per correlation CTA on a zero spectrum, keep the fastest and re-plan the
+ * group's series with it (the plane does not depend on S).  Choices are read from and written
+ * to the JSON file cache_path (nullable: no cache), keyed by the device and the group shape.
+ * The workspace size may change: read it again with fdas_batch_get_info.
+ * Errors: FDAS_E_STATE after templates exist; FDAS_E_INVALID when the cache cannot be written;
+ * FDAS_E_NOMEM, FDAS_E_CUDA.
+ */
+fdas_status fdas_batch_autotune(fdas_batch_t batch, const char *cache_path, void *stream);
+
+/* Build the template banks (one per group) on the current device.  Synchronises the stream. */
+fdas_status fdas_batch_make_templates(fdas_batch_t batch, void *stream);
+
+/*
+ * Search every series.  d_series: the series packed back to back (series i starts at element
+ * sample_offset(i) = sum of the earlier n_samples, 8-byte aligned).  d_workspace: the batch's
+ * workspace_bytes (256-byte aligned).  d_peaks: one region of cfgs[i].max_peaks records per
+ * series, region i at record peak_offset(i) = sum of the earlier max_peaks, each record's
+ * series field = i; d_npeaks: n_series true counts (overflow as in fdas_peaks).
+ * Errors: FDAS_E_INVALID, FDAS_E_STATE (no templates), FDAS_E_CUDA.
+ */
+fdas_status fdas_batch_search(fdas_batch_t batch, const float *d_series, void *d_workspace,
+                              fdas_peak *d_peaks, int32_t *d_npeaks, void *stream);
+
+/* Totals of a batch (each pointer nullable). */
+fdas_status fdas_batch_get_info(fdas_batch_t batch, int32_t *n_series, size_t *workspace_bytes,
+                                int64_t *total_samples, int64_t *total_peaks, int64_t *total_cells);
+
+/* One series of a batch: its plan sizes, configuration (seg_len as tuned), offsets and group. */
+fdas_status fdas_batch_series_info(fdas_batch_t batch, int32_t series, fdas_plan_info *info,
+                                   fdas_config *cfg, int64_t *sample_offset, int64_t *peak_offset,
+                                   int32_t *group);
+
+/* OR of every series' sticky device status word (synchronises; clears when clear != 0). */
+fdas_status fdas_batch_device_status(fdas_batch_t batch, int32_t *bits, int clear);
+
+/* Text of the batch's last error ("" if none). */
+const char *fdas_batch_last_error(fdas_batch_t batch);
+
+/* Free a batch, its plans and template banks (NULL is ignored).  Synchronises the device. */
+void fdas_batch_destroy(fdas_batch_t batch);
+
 /* Per-stage device times of profiled calls (CUDA events on the caller's stream). */
 typedef struct {
     int64_t calls;          /* entry-point calls that launched work since the last reset        */

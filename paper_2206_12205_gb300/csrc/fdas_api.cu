@@ -42,13 +42,20 @@ bool args_aligned(const void *series, const void *xhat, const void *ws, const vo
 
 }  // namespace
 
+namespace fdas {
+cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale, char *ws, void *d_plane,
+                             cudaStream_t st) {
+    switch (p.cfg.precision) {
+        case FDAS_BF16: return launch_plane_bf16(p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
+        case FDAS_BF16_SPLIT: return launch_plane_split(p, x, scale, ws, static_cast<float *>(d_plane), st);
+        default: return launch_plane_fp32(p, x, scale, ws, static_cast<float *>(d_plane), st);
+    }
+}
+}  // namespace fdas
+
 namespace {
 cudaError_t launch_plane_any(Plan *p, const float2 *x, const float *scale, char *ws, void *d_plane, cudaStream_t st) {
-    switch (p->cfg.precision) {
-        case FDAS_BF16: return fdas::launch_plane_bf16(*p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
-        case FDAS_BF16_SPLIT: return fdas::launch_plane_split(*p, x, scale, ws, static_cast<float *>(d_plane), st);
-        default: return fdas::launch_plane_fp32(*p, x, scale, ws, static_cast<float *>(d_plane), st);
-    }
+    return fdas::launch_plane_any(*p, x, scale, ws, d_plane, st);
 }
 }  // namespace
 
@@ -346,7 +353,10 @@ const char *fdas_last_error(fdas_plan_t plan) {
 void fdas_destroy(fdas_plan_t plan) {
     if (!plan) return;
     Plan *p = P(plan);
-    if (p->device >= 0) {
+    if (p->device >= 0 && p->borrowed) {
+        cudaDeviceSynchronize();
+        cudaFree(p->d_status);
+    } else if (p->device >= 0) {
         cudaDeviceSynchronize();
         cudaFree(p->d_tw);
         cudaFree(p->d_twn_lo);

@@ -64,6 +64,10 @@ struct Plan {
     float2 *d_tcTw;        // W_4096^{n2 k1}, [k1][n2] (32 KB)
     int32_t *d_status;     // sticky device status word
     bool templates_ready;
+    bool borrowed;         // template bank and tables belong to another plan (a batch's group leader)
+    // launch parameters chosen by the batch autotuner (0: built-in heuristic)
+    int tune_zb;           // FP32 path: templates per correlation CTA
+    int tune_cta_per_sm;   // split-BF16 path: persistent CTAs per SM
     std::string last_error;
     mutable Profiler prof;
 };
@@ -111,6 +115,9 @@ cudaError_t launch_segments_fp32(const Plan &p, const float2 *d_x, const float *
                                  cudaStream_t st);
 cudaError_t launch_plane_split(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
                                cudaStream_t st);
+// The plane of the plan's precision from a spectrum (x: Nb complex; scale: device factor or NULL).
+cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale, char *ws, void *d_plane,
+                             cudaStream_t st);
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
                          fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st);
 cudaError_t launch_interp(Plan &p, const float2 *d_x, const fdas_cand *d_pts, const int64_t *d_k0, int n, bool fp64,

@@ -90,6 +90,7 @@ cudaError_t run_plane(const Plan &p, const float2 *d_x, const float *d_scale, fl
     if (e != cudaSuccess) return e;
     // templates per CTA: enough CTAs to fill the GPU several times over
     int zb = (int)std::max<int64_t>(1, std::min<int64_t>(16, (p.n_seg * p.K) / (152 * 8)));
+    if (p.tune_zb > 0) zb = std::min(p.tune_zb, p.K);
     dim3 grid((unsigned)p.n_seg, (unsigned)((p.K + zb - 1) / zb));
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_fp32<S><<<grid, S / 32, smem, st>>>(Y, p.d_G, p.d_tw, plane, p.K, zb, p.nb, p.L);

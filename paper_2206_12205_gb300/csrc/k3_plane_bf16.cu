@@ -625,7 +625,7 @@ cudaError_t launch_plane_split(const Plan &p, const float2 *d_x, const float *d_
     const int64_t n_items = p.n_seg * n_groups;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
-    const int64_t ctas = std::min<int64_t>(n_items, (int64_t)sms);
+    const int64_t ctas = std::min<int64_t>(n_items, (int64_t)sms * (p.tune_cta_per_sm > 0 ? p.tune_cta_per_sm : 1));
     const int64_t per = (n_items + ctas - 1) / ctas;
     const int64_t grid = (n_items + per - 1) / per;
     const uint4 *F = reinterpret_cast<const uint4 *>(p.d_tcF);

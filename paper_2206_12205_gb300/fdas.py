@@ -27,6 +27,9 @@ EXPORTED = (
     "fdas_peaks", "fdas_search", "fdas_get_templates", "fdas_device_status", "fdas_last_error",
     "fdas_destroy", "fdas_status_string", "fdas_version", "fdas_profile_enable", "fdas_profile_read",
     "fdas_plane_static", "fdas_interp_power", "fdas_refine",
+    "fdas_batch_plan", "fdas_batch_autotune", "fdas_batch_make_templates", "fdas_batch_search",
+    "fdas_batch_get_info", "fdas_batch_series_info", "fdas_batch_device_status", "fdas_batch_last_error",
+    "fdas_batch_destroy",
 )
 REFINE_MAX_STEPS = 1000
 STATIC_SCRATCH_BYTES = 40 << 20
@@ -103,6 +106,17 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "fdas_plane_static": (S, [V, V, V, V]),
         "fdas_interp_power": (S, [V, V, V, V, I32, I32, V, V]),
         "fdas_refine": (S, [V, V, V, I32, I32, V, V, V, V]),
+        "fdas_batch_plan": (S, [ctypes.POINTER(_Config), I32, ctypes.POINTER(V), ctypes.POINTER(SZ)]),
+        "fdas_batch_autotune": (S, [V, ctypes.c_char_p, V]),
+        "fdas_batch_make_templates": (S, [V, V]),
+        "fdas_batch_search": (S, [V, V, V, V, V, V]),
+        "fdas_batch_get_info": (S, [V, ctypes.POINTER(I32), ctypes.POINTER(SZ), ctypes.POINTER(I64),
+                                    ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "fdas_batch_series_info": (S, [V, I32, ctypes.POINTER(_Info), ctypes.POINTER(_Config), ctypes.POINTER(I64),
+                                       ctypes.POINTER(I64), ctypes.POINTER(I32)]),
+        "fdas_batch_device_status": (S, [V, ctypes.POINTER(I32), ctypes.c_int]),
+        "fdas_batch_last_error": (ctypes.c_char_p, [V]),
+        "fdas_batch_destroy": (None, [V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -204,13 +218,24 @@ def make_config(n_samples: int, zmax: int, taps: int, seg_len: int, precision="f
 
 
 # ----------------------------------------------------------------------------- entry points
-def fdas_plan(cfg: dict) -> Plan:
-    lib = load()
-    c = _Config()
+def _to_config(cfg: dict, c: "_Config"):
     for k in ("n_samples", "zmax", "taps", "seg_len", "precision", "max_harm", "max_peaks", "sigma2"):
         setattr(c, k, cfg[k])
     for i, v in enumerate(cfg["thr"]):
         c.thr[i] = v
+
+
+def _from_config(c: "_Config") -> dict:
+    d = {k: getattr(c, k) for k in ("n_samples", "zmax", "taps", "seg_len", "precision", "max_harm", "max_peaks",
+                                     "sigma2")}
+    d["thr"] = [float(c.thr[i]) for i in range(5)]
+    return d
+
+
+def fdas_plan(cfg: dict) -> Plan:
+    lib = load()
+    c = _Config()
+    _to_config(cfg, c)
     h = ctypes.c_void_p()
     ws = ctypes.c_size_t()
     _check(lib.fdas_plan(ctypes.byref(c), ctypes.byref(h), ctypes.byref(ws)), "fdas_plan")
@@ -352,6 +377,101 @@ def fdas_destroy(plan: Plan):
     if plan.handle:
         load().fdas_destroy(plan.handle)
         plan.handle = None
+
+
+# ----------------------------------------------------------------------------- batches
+def _check_batch(status: int, where: str, batch=None):
+    if status != FDAS_OK:
+        detail = ""
+        if batch is not None and batch.handle:
+            detail = (load().fdas_batch_last_error(batch.handle) or b"").decode()
+        raise FdasError(status, where, detail)
+
+
+@dataclasses.dataclass
+class BatchSeries:
+    info: PlanInfo
+    cfg: dict
+    sample_offset: int
+    peak_offset: int
+    group: int
+
+
+class Batch:
+    """Owns an fdas_batch_t.  Create with fdas_batch_plan(); freed by fdas_batch_destroy() or GC."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        self.refresh()
+
+    def refresh(self):
+        lib = load()
+        n, ws = ctypes.c_int32(), ctypes.c_size_t()
+        ts, tp, tc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check_batch(lib.fdas_batch_get_info(self.handle, ctypes.byref(n), ctypes.byref(ws), ctypes.byref(ts),
+                                             ctypes.byref(tp), ctypes.byref(tc)), "fdas_batch_get_info", self)
+        self.n_series, self.workspace_bytes = int(n.value), int(ws.value)
+        self.total_samples, self.total_peaks, self.total_cells = int(ts.value), int(tp.value), int(tc.value)
+        self.series = []
+        for i in range(self.n_series):
+            inf, c = _Info(), _Config()
+            so, po, g = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+            _check_batch(lib.fdas_batch_series_info(self.handle, i, ctypes.byref(inf), ctypes.byref(c), ctypes.byref(so),
+                                                    ctypes.byref(po), ctypes.byref(g)), "fdas_batch_series_info", self)
+            self.series.append(BatchSeries(PlanInfo(inf.nb, inf.K, inf.seg_valid, inf.n_seg, inf.plane_elem_bytes,
+                                                    inf.plane_bytes, inf.workspace_bytes, inf.cells),
+                                           _from_config(c), int(so.value), int(po.value), int(g.value)))
+
+    def __del__(self):
+        try:
+            fdas_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def fdas_batch_plan(cfgs: Sequence[dict]) -> Batch:
+    arr = (_Config * len(cfgs))()
+    for i, cfg in enumerate(cfgs):
+        _to_config(cfg, arr[i])
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    _check_batch(load().fdas_batch_plan(arr, len(cfgs), ctypes.byref(h), ctypes.byref(ws)), "fdas_batch_plan")
+    return Batch(h.value)
+
+
+def fdas_batch_autotune(batch: Batch, cache_path: Optional[str] = None, stream=None):
+    path = cache_path.encode() if cache_path else None
+    _check_batch(load().fdas_batch_autotune(batch.handle, path, _stream_ptr(stream)), "fdas_batch_autotune", batch)
+    batch.refresh()
+
+
+def fdas_batch_make_templates(batch: Batch, stream=None):
+    _check_batch(load().fdas_batch_make_templates(batch.handle, _stream_ptr(stream)), "fdas_batch_make_templates",
+                 batch)
+
+
+def fdas_batch_search(batch: Batch, series, workspace, peaks, npeaks, stream=None):
+    torch = _torch()
+    args = (batch.handle,
+            _dev_ptr(series, "series", torch.float32, 4 * batch.total_samples),
+            _dev_ptr(workspace, "workspace", None, batch.workspace_bytes),
+            _dev_ptr(peaks, "peaks", torch.uint8, 16 * batch.total_peaks) if batch.total_peaks > 0 else None,
+            _dev_ptr(npeaks, "npeaks", torch.int32, 4 * batch.n_series),
+            _stream_ptr(stream))
+    _check_batch(load().fdas_batch_search(*args), "fdas_batch_search", batch)
+
+
+def fdas_batch_device_status(batch: Batch, clear: bool = True) -> int:
+    bits = ctypes.c_int32(0)
+    _check_batch(load().fdas_batch_device_status(batch.handle, ctypes.byref(bits), 1 if clear else 0),
+                 "fdas_batch_device_status", batch)
+    return int(bits.value)
+
+
+def fdas_batch_destroy(batch: Batch):
+    if batch.handle:
+        load().fdas_batch_destroy(batch.handle)
+        batch.handle = None
 
 
 # ----------------------------------------------------------------------------- conveniences
