@@ -64,7 +64,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("own", "reference"), default="own")
-    ap.add_argument("--precision", choices=("auto", "fp32", "bf16", "bf16_split"), default="auto")
+    ap.add_argument("--precision", choices=("auto", "fp32", "bf16", "bf16_split", "fp16_scaled"), default="auto")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision comparison runs")
@@ -193,7 +193,7 @@ def roofline_correlate(w, precision: str, prof):
     peak = MEASURED["bf16_tflops_sustained"]
     ach = flops / (ms / 1e3) / 1e12
     kern = "k3_plane_tc_split" if precision == "bf16_split" else "k3_plane_tc"
-    plane_b = w.K * w.nb * (4 if precision == "bf16_split" else 2)
+    plane_b = w.K * w.nb * (2 if precision == "bf16" else 4)
     return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": _traffic(kern, precision, w.name), "kernel": kern, "avg_launch_ms": ms, "flops_per_launch": flops,
             "peak_note": "of measured: MEASURED_PEAKS bf16_tflops_sustained (cuBLAS bf16 under the power cap)",
@@ -574,7 +574,7 @@ def own_arm(args):
     # ---- the other precisions on the same GPU and workload (the metric's comparison)
     paths = {}
     if not args.quick and not args.no_compare:
-        for prec in ("fp32", "bf16", "bf16_split"):
+        for prec in ("fp32", "bf16", "bf16_split", "fp16_scaled"):
             if prec == precision:
                 continue
             cmp_steps = max(3, min(args.steps, 100))
@@ -612,7 +612,7 @@ def own_arm(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16_split": "bf16-split"}.get(precision, "bf16"),
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16_split": "bf16-split", "fp16_scaled": "f16-scaled"}.get(precision, "bf16"),
             "data": "synthetic: seeded N(0,1) noise + 8 accelerated Gaussian pulse trains (fdas_synth)",
             "config": config_json(w, precision),
             "roofline": roof, "roofline_correlate": roof_corr, "paths": paths or None,

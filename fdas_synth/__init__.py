@@ -307,3 +307,22 @@ def batch_workload(config_index: int = 2, n_series: int = 256, tsamp: float = 64
         meta.append(Workload(f"batch{config_index}_s{s}_n{n}_z{zmax}_m{m}", n, tsamp, zmax, m, seg_len,
                              np.empty(0, dtype=np.float32), trains[s]))
     return BatchWorkload(meta, packed, offsets)
+
+
+def sensitivity_workload(config_index: int = 4, series_index: int = 0, n: int = 1 << 23, tsamp: float = 64e-6,
+                         period=(1e-3, 20e-3), accel=(-200.0, 200.0), duty=(0.02, 0.10), snr=(3.0, 40.0),
+                         zmax: int = 84, taps: int = 256, seg_len: int = 8192) -> Workload:
+    """Sensitivity case: one binary pulsar per series (period log-uniform 1-20 ms, line-of-sight
+    acceleration uniform in +-200 m/s^2, so z = a f T^2 / c can exceed zmax; duty cycle 2-10 %;
+    SNR 3-40) in unit Gaussian noise, N = 2^23 at 64 us, 85 templates.  The one train's r0 is its
+    fundamental frequency in bins, f = r0 / T."""
+    rng = rng_for(config_index, series_index)
+    tobs = n * tsamp
+    p = math.exp(rng.uniform(math.log(period[0]), math.log(period[1])))
+    f = 1.0 / p
+    z = accel_to_z(float(rng.uniform(accel[0], accel[1])), f, tobs)
+    d = float(rng.uniform(duty[0], duty[1]))
+    t = Train(p, tobs / p, z, d, float(rng.uniform(snr[0], snr[1])), float(rng.uniform(0.0, 1.0)))
+    x = rng.standard_normal(n, dtype=np.float32)
+    x += pulse_train(n, t.r0, t.z0, t.duty, t.snr, t.phase0).astype(np.float32)
+    return Workload(f"sensitivity{config_index}_s{series_index}_n{n}", n, tsamp, zmax, taps, seg_len, x, [t])

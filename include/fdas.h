@@ -25,7 +25,7 @@
  *   - Plane: P[i][r] = | sum_q Xhat[r+q] conj(T_i(q)) |^2, r = 0..Nb-1, row-major [K][Nb]
  *     (r contiguous); Xhat is zero outside [0, Nb).  Element type is bfloat16 (the upper
  *     16 bits of the float) for FDAS_BF16 and float otherwise.
- *   - The tensor-core precisions (FDAS_BF16, FDAS_BF16_SPLIT) run their overlap-save with
+ *   - The tensor-core precisions (FDAS_BF16, FDAS_BF16_SPLIT, FDAS_FP16_SCALED) run their overlap-save with
  *     4096-bin segments whatever seg_len says (the plane does not depend on it) and accept
  *     at most 2048 taps.
  *   - All device pointers are CUDA device addresses on the current device; the caller
@@ -63,8 +63,13 @@ typedef enum {
     FDAS_FP32 = 0,           /* FP32 plane, FP32 CUDA-core FFTs                           */
     FDAS_BF16 = 1,           /* BF16 spectrum/templates, tensor-core DFT stages with FP32
                                 accumulation, BF16 plane (Sec. 3)                          */
-    FDAS_BF16_SPLIT = 2      /* compensated hi+lo BF16 operands (three products per MMA step,
+    FDAS_BF16_SPLIT = 2,     /* compensated hi+lo BF16 operands (three products per MMA step,
                                 about 16 significant bits), FP32 plane                      */
+    FDAS_FP16_SCALED = 3     /* ablation of Sec. 3.2 (FP16 rejected there for its range): FP16
+                                operands on the tensor cores with a power-of-two scale per
+                                segment (largest component in [0.5, 1)) and the template bank
+                                scaled by the segment length, so no operand overflows and small
+                                ones stay normal; FP32 accumulation; FP32 plane               */
 } fdas_precision;
 
 /* Device status bits (fdas_device_status). */
@@ -195,6 +200,22 @@ fdas_status fdas_search(fdas_plan_t plan, const float *d_series, void *d_workspa
                         void *d_plane, fdas_peak *d_peaks, int32_t *d_npeaks, void *stream);
 
 /*
+ * Band maxima of a plane (the paper's harmonic-band analysis, Sec. 4.3, Table harm_bounds: with
+ * the fundamental f known, band n spans frequencies [(n+0.5) f, (n+1.5) f], the fundamental's
+ * [0, 1.5 f], and the highest cell of band n is taken as harmonic n).  Band b covers bins
+ * [h_lo[b], h_hi[b]] of every template row (host arrays, clipped to [0, Nb)); d_value[b],
+ * d_r[b], d_zi[b] receive the largest value in it and the first cell holding it in row-major
+ * (zi, r) order, or -1 in all three for a band with no cell.  d_plane: the plan's plane type.
+ * d_scratch: 24 * n_bands bytes, 8-byte aligned (the host bounds are copied into it).
+ * Errors: FDAS_E_INVALID (NULL or misaligned pointer, n_bands < 0, lo > hi);
+ * FDAS_E_UNSUPPORTED when K * Nb >= 2^32; FDAS_E_CUDA.
+ */
+fdas_status fdas_band_max(fdas_plan_t plan, const void *d_plane, const int64_t *h_lo,
+                          const int64_t *h_hi, int32_t n_bands, void *d_scratch, float *d_value,
+                          int64_t *d_r, int32_t *d_zi, void *stream);
+
+/*
+ * Copy the frequency-domain template bank G[K][S]/*
  * Copy the frequency-domain template bank G[K][S] (interleaved complex float, FP32) to the
  * device buffer d_out (K*S*8 bytes).  For verification.
  * Errors: FDAS_E_INVALID, FDAS_E_STATE, FDAS_E_CUDA.

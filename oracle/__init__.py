@@ -237,6 +237,24 @@ def refine(xhat, m: int, rz, steps: int):
     return out, pw, ev
 
 
+def band_max(plane, lo, hi):
+    """Band maxima (Sec. 4.3, Table harm_bounds): for each band [lo, hi] of bins (clipped to the
+    plane), the largest cell over all template rows and its first position in row-major
+    (zi, r) order.  Returns (value, r, zi) arrays; an empty band gives -1 in all three."""
+    plane = np.asarray(plane)
+    nb = plane.shape[1]
+    v, rr, zz = [], [], []
+    for l, h in zip(lo, hi):
+        l, h = max(0, int(l)), min(nb - 1, int(h))
+        if h < l:
+            v.append(-1.0); rr.append(-1); zz.append(-1)
+            continue
+        sub = plane[:, l:h + 1]
+        zi, r = np.unravel_index(int(np.argmax(sub)), sub.shape)   # argmax: first maximum, row-major
+        v.append(float(sub[zi, r])); rr.append(l + int(r)); zz.append(int(zi))
+    return np.array(v), np.array(rr, dtype=np.int64), np.array(zz, dtype=np.int32)
+
+
 def search(x, zmax: int, m: int, max_harm: int, thr, sigma2: float = 0.0, max_out: int = 1 << 20):
     """The whole oracle path on one series: spectrum, templates, plane, peaks (FP64)."""
     xhat, s2 = spectrum(x, sigma2)

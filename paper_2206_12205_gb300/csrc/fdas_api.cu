@@ -48,6 +48,7 @@ cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale,
     switch (p.cfg.precision) {
         case FDAS_BF16: return launch_plane_bf16(p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
         case FDAS_BF16_SPLIT: return launch_plane_split(p, x, scale, ws, static_cast<float *>(d_plane), st);
+        case FDAS_FP16_SCALED: return launch_plane_f16(p, x, scale, ws, static_cast<float *>(d_plane), st);
         default: return launch_plane_fp32(p, x, scale, ws, static_cast<float *>(d_plane), st);
     }
 }
@@ -92,7 +93,8 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     if (!(c.sigma2 >= 0.0)) return FDAS_E_INVALID;   // also rejects NaN
     for (int l = 0; l < 5; l++)
         if (c.thr[l] != c.thr[l]) return FDAS_E_INVALID;
-    if (c.precision != FDAS_FP32 && c.precision != FDAS_BF16 && c.precision != FDAS_BF16_SPLIT)
+    if (c.precision != FDAS_FP32 && c.precision != FDAS_BF16 && c.precision != FDAS_BF16_SPLIT &&
+        c.precision != FDAS_FP16_SCALED)
         return FDAS_E_INVALID;
     if (c.precision != FDAS_FP32 && c.taps > fdas::TC_MAX_TAPS) return FDAS_E_UNSUPPORTED;
 
@@ -127,6 +129,7 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     p->ws_part = off;  off = align_up(off + sizeof(double) * (size_t)p->n_part);
     p->ws_scale = off; off = align_up(off + 16);
     p->ws_y = off;     off = align_up(off + sizeof(float2) * (size_t)p->n_seg * p->S);
+    p->ws_segscale = off; off = align_up(off + sizeof(float) * (size_t)p->n_seg);
     const size_t n_scan_blocks = (size_t)((p->n_units + fdas::PEAK_SCAN_BLOCK - 1) / fdas::PEAK_SCAN_BLOCK);
     p->ws_ucount = off; off = align_up(off + sizeof(int32_t) * (size_t)p->n_units);
     p->ws_uoff = off;   off = align_up(off + sizeof(int32_t) * (size_t)p->n_units);
@@ -172,6 +175,10 @@ fdas_status fdas_make_templates(fdas_plan_t plan, void *stream) {
     if (uses_tensor_path(p)) {
         alloc((void **)&p->d_Gbf, sizeof(__nv_bfloat162) * nbank);
         if (p->cfg.precision == FDAS_BF16_SPLIT) alloc((void **)&p->d_Gbf_lo, sizeof(__nv_bfloat162) * nbank);
+        if (p->cfg.precision == FDAS_FP16_SCALED) {
+            alloc((void **)&p->d_Gh, sizeof(__half2) * nbank);
+            alloc((void **)&p->d_tcFh, 2 * 128 * 128);
+        }
         alloc((void **)&p->d_tcF, 2 * 2 * 128 * 128);
         alloc((void **)&p->d_tcTw, sizeof(float2) * 64 * 64);
     }
@@ -278,6 +285,37 @@ fdas_status fdas_refine(fdas_plan_t plan, const float *d_xhat, const fdas_cand *
     return record(p, e);
 }
 
+fdas_status fdas_band_max(fdas_plan_t plan, const void *d_plane, const int64_t *h_lo, const int64_t *h_hi,
+                          int32_t n_bands, void *d_scratch, float *d_value, int64_t *d_r, int32_t *d_zi, void *stream) {
+    if (!plan || n_bands < 0) return FDAS_E_INVALID;
+    if (n_bands == 0) return FDAS_OK;
+    if (!d_plane || !h_lo || !h_hi || !d_scratch || !d_value || !d_r || !d_zi) return FDAS_E_INVALID;
+    if (!aligned(d_plane, 16) || !aligned(d_scratch, 8) || !aligned(d_value, 4) || !aligned(d_r, 8) ||
+        !aligned(d_zi, 4))
+        return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    if ((uint64_t)p->K * (uint64_t)p->nb >= (1ull << 32)) {
+        p->last_error = "band maxima index cells with 32 bits: K * Nb must stay below 2^32";
+        return FDAS_E_UNSUPPORTED;
+    }
+    int64_t max_width = 0;
+    for (int b = 0; b < n_bands; b++) {
+        if (h_lo[b] > h_hi[b]) return FDAS_E_INVALID;
+        max_width = std::max(max_width, std::min<int64_t>(h_hi[b], p->nb - 1) - std::max<int64_t>(h_lo[b], 0) + 1);
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long *slot = static_cast<unsigned long long *>(d_scratch);
+    int64_t *lo = reinterpret_cast<int64_t *>(slot + n_bands);
+    int64_t *hi = lo + n_bands;
+    p->prof.calls++;
+    cudaError_t e = cudaMemcpyAsync(lo, h_lo, sizeof(int64_t) * n_bands, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hi, h_hi, sizeof(int64_t) * n_bands, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = fdas::launch_band_max(*p, d_plane, plane_is_bf16(p), lo, hi, n_bands, max_width, slot, d_value, d_r, d_zi,
+                                  st);
+    return record(p, e);
+}
+
 fdas_status fdas_get_templates(fdas_plan_t plan, float *d_out, void *stream) {
     if (!plan || !d_out) return FDAS_E_INVALID;
     Plan *p = P(plan);
@@ -364,6 +402,8 @@ void fdas_destroy(fdas_plan_t plan) {
         cudaFree(p->d_G);
         cudaFree(p->d_Gbf);
         cudaFree(p->d_Gbf_lo);
+        cudaFree(p->d_Gh);
+        cudaFree(p->d_tcFh);
         cudaFree(p->d_tcF);
         cudaFree(p->d_tcTw);
         cudaFree(p->d_status);

@@ -331,6 +331,8 @@ fdas_status fdas_batch_make_templates(fdas_batch_t b, void *stream) {
         p->d_Gbf_lo = l->d_Gbf_lo;
         p->d_tcF = l->d_tcF;
         p->d_tcTw = l->d_tcTw;
+        p->d_Gh = l->d_Gh;
+        p->d_tcFh = l->d_tcFh;
         p->borrowed = true;
         e = cudaMalloc((void **)&p->d_status, sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 #include <string>
 
@@ -50,7 +51,7 @@ struct Plan {
     int n_levels;
     int64_t n_units;
     // workspace layout (byte offsets inside the caller's workspace)
-    size_t ws_x, ws_tmp, ws_part, ws_scale, ws_y, ws_ucount, ws_uoff, ws_umask, ws_ublock, ws_bytes;
+    size_t ws_x, ws_tmp, ws_part, ws_scale, ws_y, ws_segscale, ws_ucount, ws_uoff, ws_umask, ws_ublock, ws_bytes;
     int n_part;
     // plan-owned device memory
     int device;
@@ -61,6 +62,8 @@ struct Plan {
     __nv_bfloat162 *d_Gbf; // [K][S] BF16 template bank (hi), BF16 precisions
     __nv_bfloat162 *d_Gbf_lo; // [K][S] BF16 residual (lo), split precision
     void *d_tcF;           // real-ified radix-64 DFT matrix, BF16 K-major operand images: hi, then lo (2 x 32 KB)
+    __half2 *d_Gh;         // [K][S] FP16 template bank times S, FP16-scaled precision
+    void *d_tcFh;          // the DFT matrix as an FP16 K-major operand image (32 KB)
     float2 *d_tcTw;        // W_4096^{n2 k1}, [k1][n2] (32 KB)
     int32_t *d_status;     // sticky device status word
     bool templates_ready;
@@ -115,11 +118,16 @@ cudaError_t launch_segments_fp32(const Plan &p, const float2 *d_x, const float *
                                  cudaStream_t st);
 cudaError_t launch_plane_split(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
                                cudaStream_t st);
+cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
+                             cudaStream_t st);
 // The plane of the plan's precision from a spectrum (x: Nb complex; scale: device factor or NULL).
 cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale, char *ws, void *d_plane,
                              cudaStream_t st);
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
                          fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st);
+cudaError_t launch_band_max(const Plan &p, const void *d_plane, bool bf16, const int64_t *d_lo, const int64_t *d_hi,
+                            int n_bands, int64_t max_width, unsigned long long *d_slot, float *d_value,
+                            int64_t *d_r, int32_t *d_zi, cudaStream_t st);
 cudaError_t launch_interp(Plan &p, const float2 *d_x, const fdas_cand *d_pts, const int64_t *d_k0, int n, bool fp64,
                           double *d_out, cudaStream_t st);
 cudaError_t launch_refine(Plan &p, const float2 *d_x, const fdas_cand *d_in, int n, int steps, fdas_cand *d_out,

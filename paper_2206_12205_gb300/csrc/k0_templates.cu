@@ -110,7 +110,8 @@ __global__ void k0_normalise(double2 *__restrict__ taps, int m, double *__restri
 // G_i(k) = (1/S) sum_d T_i(d - m/2) W_S^{d k}: direct FP64 DFT, rounded once to each format.
 __global__ void k0_dft(const double2 *__restrict__ taps, int m, int S, const double2 *__restrict__ wS,
                        float2 *__restrict__ G, __nv_bfloat162 *__restrict__ Ghi,
-                       __nv_bfloat162 *__restrict__ Glo) {
+                       __nv_bfloat162 *__restrict__ Glo,
+                       __half2 *__restrict__ Gh) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (k >= S) return;
@@ -126,6 +127,8 @@ __global__ void k0_dft(const double2 *__restrict__ taps, int m, int S, const dou
     im /= (double)S;
     const float fr = (float)re, fi = (float)im;
     G[(size_t)i * S + k] = make_float2(fr, fi);
+    // FP16 bank of the scaled precision: S G (|S G| <= sqrt(m) for unit-norm taps), rounded once
+    if (Gh) Gh[(size_t)i * S + k] = __floats2half2_rn((float)(re * S), (float)(im * S));
     if (Ghi) {
         // hi = BF16 rounding of the FP32 value (the paper's conversion); lo = BF16 of the
         // FP64 remainder, so hi + lo carries about 16 significant bits.
@@ -203,7 +206,7 @@ cudaError_t launch_make_templates(Plan &p, cudaStream_t st) {
         k0_taps<<<(n + 127) / 128, 128, 0, st>>>(d_taps, K, m, p.cfg.zmax, gl);
         k0_normalise<<<K, 256, 0, st>>>(d_taps, m, d_eta);
         dim3 grid((S + 255) / 256, K);
-        k0_dft<<<grid, 256, 0, st>>>(d_taps, m, S, d_wS, p.d_G, p.d_Gbf, p.d_Gbf_lo);
+        k0_dft<<<grid, 256, 0, st>>>(d_taps, m, S, d_wS, p.d_G, p.d_Gbf, p.d_Gbf_lo, p.d_Gh);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }

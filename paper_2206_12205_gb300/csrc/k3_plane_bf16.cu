@@ -42,6 +42,30 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
+// Operand formats of the tensor stages: BF16 (the paper's Sec. 3 variant, BF16 plane) or FP16 with
+// per-segment scaling (the Sec. 3.2 ablation, FP32 plane times the segment's unscale factor).
+struct OpsBF16 {
+    using V = __nv_bfloat162;
+    using Out = __nv_bfloat16;
+    static constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_N);
+    __device__ __forceinline__ static V high2(V a) { return __high2bfloat162(a); }
+    __device__ __forceinline__ static V low2(V a) { return __low2bfloat162(a); }
+    __device__ __forceinline__ static uint32_t pack(float lo, float hi) { return pack_bf16x2(lo, hi); }
+    __device__ __forceinline__ static Out out(float pw, float) { return __float2bfloat16_rn(pw); }
+};
+struct OpsF16 {
+    using V = __half2;
+    using Out = float;
+    static constexpr uint32_t idesc = tc::idesc_f16_f32(TC_M, TC_N);
+    __device__ __forceinline__ static V high2(V a) { return __high2half2(a); }
+    __device__ __forceinline__ static V low2(V a) { return __low2half2(a); }
+    __device__ __forceinline__ static uint32_t pack(float lo, float hi) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    __device__ __forceinline__ static Out out(float pw, float unscale) { return pw * unscale; }
+};
+
 // Segment FFTs (FP32 CUDA-core block FFT), stored as BF16 pairs for the tensor stages.
 __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_bf16(const float2 *__restrict__ X,
                                                                    const float *__restrict__ scale_ptr,
@@ -66,6 +90,52 @@ __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_bf16(const float2 
     __nv_bfloat162 *out = Y + j * S;
 #pragma unroll
     for (int i = 0; i < 32; i++) out[t + i * T] = __floats2bfloat162_rn(v[i].x, v[i].y);
+}
+
+// Segment FFTs for the FP16 stages: the segment's largest component |re| or |im| is brought into
+// [0.5, 1) by a power of two s_j (exact), the values stored as FP16 pairs, and the plane's factor
+// 1 / (s_j gscale)^2 (gscale: the template bank's scale) kept per segment.
+__global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_f16(const float2 *__restrict__ X,
+                                                                  const float *__restrict__ scale_ptr,
+                                                                  const float2 *__restrict__ tw,
+                                                                  __half2 *__restrict__ Y, float *__restrict__ unscale,
+                                                                  float gscale, int64_t nb, int L, int half_m) {
+    constexpr int S = TC_S_BF16, T = S / 32;
+    extern __shared__ float2 sm[];
+    __shared__ float wmax[T / 32];
+    const int t = threadIdx.x;
+    const int64_t j = blockIdx.x;
+    const float scale = scale_ptr ? __ldg(scale_ptr) : 1.0f;
+    const int64_t base = j * L - half_m;
+    float2 v[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const int64_t k = base + t + i * T;
+        float2 x = make_float2(0.f, 0.f);
+        if (k >= 0 && k < nb) x = __ldg(X + k);
+        v[i] = make_float2(x.x * scale, x.y * scale);
+    }
+    block_fft<S>(v, sm, tw, t);
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; i++) mx = fmaxf(mx, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((t & 31) == 0) wmax[t >> 5] = mx;
+    __syncthreads();
+    mx = wmax[0];
+#pragma unroll
+    for (int w = 1; w < T / 32; w++) mx = fmaxf(mx, wmax[w]);
+    int ex = 0;
+    if (mx > 0.f) frexpf(mx, &ex);                  // mx = f 2^ex, f in [0.5, 1)
+    const float sj = ldexpf(1.0f, -ex);
+    __half2 *out = Y + j * S;
+#pragma unroll
+    for (int i = 0; i < 32; i++) out[t + i * T] = __floats2half2_rn(v[i].x * sj, v[i].y * sj);
+    if (t == 0) {
+        const float g = sj * gscale;
+        unscale[j] = 1.0f / (g * g);
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -129,13 +199,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
-__global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat162 *__restrict__ Y,
-                                                             const __nv_bfloat162 *__restrict__ G,
+template <class Ops>
+__global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const typename Ops::V *__restrict__ Y,
+                                                             const typename Ops::V *__restrict__ G,
                                                              const uint4 *__restrict__ Fimg,
                                                              const float2 *__restrict__ tw,
-                                                             __nv_bfloat16 *__restrict__ plane, int K, int64_t nb,
+                                                             typename Ops::Out *__restrict__ plane, int K, int64_t nb,
                                                              int L, int64_t n_items, int n_groups,
-                                                             int64_t items_per_cta, int32_t *__restrict__ status) {
+                                                             int64_t items_per_cta, const float *__restrict__ unscale,
+                                                             int32_t *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     WsBars *bars = reinterpret_cast<WsBars *>(smem + OFF_BAR);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + OFF_BAR + sizeof(WsBars));
@@ -174,7 +246,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
     if (warp == 0) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0 && n_my > 0) {
-            const uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_N);
+            const uint32_t idesc = Ops::idesc;
             const uint32_t bF = tc::smem_u32(smem + OFF_F);
             auto issue = [&](uint32_t dcol, uint32_t asm_, uint32_t albo, uint32_t asbo) {
 #pragma unroll
@@ -245,11 +317,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         // conj(y) g = (yr, yr) (gr, gi) + (yi, yi) (gi, -gr), in packed BF16 arithmetic
-                        const __nv_bfloat162 y = *reinterpret_cast<const __nv_bfloat162 *>(&ys[e]);
-                        const __nv_bfloat162 g = *reinterpret_cast<const __nv_bfloat162 *>(&gs[e]);
-                        __nv_bfloat162 gb = __lowhigh2highlow(g);
+                        using V = typename Ops::V;
+                        const V y = *reinterpret_cast<const V *>(&ys[e]);
+                        const V g = *reinterpret_cast<const V *>(&gs[e]);
+                        V gb = __lowhigh2highlow(g);
                         *reinterpret_cast<uint32_t *>(&gb) ^= 0x80000000u;
-                        const __nv_bfloat162 x = __hfma2(__high2bfloat162(y), gb, __hmul2(__low2bfloat162(y), g));
+                        const V x = __hfma2(Ops::high2(y), gb, __hmul2(Ops::low2(y), g));
                         w[e][q] = *reinterpret_cast<const uint32_t *>(&x);
                     }
                 }
@@ -300,7 +373,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
                                 const int q = 2 * q2 + u;
                                 const float re = __uint_as_float(rr[hh][2 * q]), im = __uint_as_float(rr[hh][2 * q + 1]);
                                 const float tx = u ? t2.z : t2.x, ty = u ? t2.w : t2.y;
-                                const uint32_t wv = pack_bf16x2(re * tx - im * ty, re * ty + im * tx);
+                                const uint32_t wv = Ops::pack(re * tx - im * ty, re * ty + im * tx);
                                 const int row = zl * TC_R + k1_0 + q;
                                 *reinterpret_cast<uint32_t *>(a2 + tc::kmajor_offset_strided(A2_SBO, A2_LBO, row, 2 * idx)) = wv;
                             }
@@ -317,7 +390,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
                 const int64_t j = it / n_groups;
                 const int z = (int)(it % n_groups) * TC_G + zl;
                 const int64_t r0 = j * L;
-                __nv_bfloat16 *prow = plane + (int64_t)(z < K ? z : 0) * nb + r0 + idx;
+                const float us = unscale ? __ldg(unscale + j) : 1.0f;
+                typename Ops::Out *prow = plane + (int64_t)(z < K ? z : 0) * nb + r0 + idx;
 #pragma unroll 1
                 for (int ch2 = 0; ch2 < 4; ch2 += 2) {
                     uint32_t rr[2][16];
@@ -332,7 +406,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const __nv_bfloat16
                             const int t = idx + 64 * (k2_0 + q);
                             if (z < K && t < L && r0 + t < nb) {
                                 const float re = __uint_as_float(rr[hh][2 * q]), im = __uint_as_float(rr[hh][2 * q + 1]);
-                                prow[64 * (k2_0 + q)] = __float2bfloat16_rn(re * re + im * im);
+                                prow[64 * (k2_0 + q)] = Ops::out(re * re + im * im, us);
                             }
                         }
                     }
@@ -540,7 +614,7 @@ uint16_t host_bf16(float f) {
 // Host tables of the tensor path: F'[(k,p),(n,s)] (W_64^{kn} real-ified, re/im interleaved) as a
 // K-major BF16 operand image, and the four-step twiddles W_4096^{n2 k1}; FP64 then rounded.
 cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st) {
-    std::vector<uint16_t> img(TC_M * TC_K, 0), img_lo(TC_M * TC_K, 0);
+    std::vector<uint16_t> img(TC_M * TC_K, 0), img_lo(TC_M * TC_K, 0), img_h(TC_M * TC_K, 0);
     for (int k = 0; k < TC_R; k++)
         for (int n = 0; n < TC_R; n++) {
             const int e = (k * n) % TC_R;
@@ -557,6 +631,8 @@ cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st) {
                     float hf;
                     std::memcpy(&hf, &hb, 4);
                     img_lo[o] = host_bf16((float)(vd[pr][sg] - (double)hf));
+                    const __half h = __float2half_rn(v[pr][sg]);
+                    std::memcpy(&img_h[o], &h, 2);
                 }
         }
     std::vector<float2> tw(TC_R * TC_R);
@@ -573,6 +649,8 @@ cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st) {
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p.d_tcTw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && p.d_tcFh)
+        e = cudaMemcpyAsync(p.d_tcFh, img_h.data(), img_h.size() * 2, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
 }
@@ -584,7 +662,7 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
     const size_t smem2 = sizeof(float2) * fft_smem_entries(TC_S_BF16);
     cudaError_t e = cudaFuncSetAttribute(k2_segments_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k3_plane_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM);
+    e = cudaFuncSetAttribute(k3_plane_tc<OpsBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM);
     if (e != cudaSuccess) return e;
     p.prof.begin(FDAS_STAGE_SEGMENTS, st);
     k2_segments_bf16<<<(unsigned)p.n_seg, TC_S_BF16 / 32, smem2, st>>>(d_x, d_scale, p.d_tw, Y, p.nb, p.L, p.m / 2);
@@ -599,9 +677,42 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
     const int64_t per = (n_items + ctas - 1) / ctas;
     const int64_t grid = (n_items + per - 1) / per;
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
-    k3_plane_tc<<<(unsigned)grid, WS_THREADS, WS_SMEM, st>>>(Y, p.d_Gbf, reinterpret_cast<const uint4 *>(p.d_tcF),
-                                                               p.d_tcTw, d_plane, p.K, p.nb, p.L, n_items, n_groups,
-                                                               per, p.d_status);
+    k3_plane_tc<OpsBF16><<<(unsigned)grid, WS_THREADS, WS_SMEM, st>>>(
+        Y, p.d_Gbf, reinterpret_cast<const uint4 *>(p.d_tcF), p.d_tcTw, d_plane, p.K, p.nb, p.L, n_items, n_groups,
+        per, nullptr, p.d_status);
+    p.prof.end(FDAS_STAGE_CORRELATE, st);
+    p.prof.launches += 2;
+    return cudaGetLastError();
+}
+
+// FP16-scaled ablation: scaled FP16 segment spectra, the FP16 bank (S G) and DFT image, FP32 plane.
+cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
+                             cudaStream_t st) {
+    if (p.S != TC_S_BF16 || !p.d_Gh || !p.d_tcFh) return cudaErrorInvalidValue;
+    __half2 *Y = reinterpret_cast<__half2 *>(ws + p.ws_y);
+    float *unscale = reinterpret_cast<float *>(ws + p.ws_segscale);
+    const size_t smem2 = sizeof(float2) * fft_smem_entries(TC_S_BF16);
+    cudaError_t e = cudaFuncSetAttribute(k2_segments_f16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k3_plane_tc<OpsF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM);
+    if (e != cudaSuccess) return e;
+    p.prof.begin(FDAS_STAGE_SEGMENTS, st);
+    k2_segments_f16<<<(unsigned)p.n_seg, TC_S_BF16 / 32, smem2, st>>>(d_x, d_scale, p.d_tw, Y, unscale,
+                                                                     (float)TC_S_BF16, p.nb, p.L, p.m / 2);
+    p.prof.end(FDAS_STAGE_SEGMENTS, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int n_groups = (p.K + TC_G - 1) / TC_G;
+    const int64_t n_items = p.n_seg * n_groups;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
+    const int64_t ctas = std::min<int64_t>(n_items, (int64_t)sms);
+    const int64_t per = (n_items + ctas - 1) / ctas;
+    const int64_t grid = (n_items + per - 1) / per;
+    p.prof.begin(FDAS_STAGE_CORRELATE, st);
+    k3_plane_tc<OpsF16><<<(unsigned)grid, WS_THREADS, WS_SMEM, st>>>(
+        Y, p.d_Gh, reinterpret_cast<const uint4 *>(p.d_tcFh), p.d_tcTw, d_plane, p.K, p.nb, p.L, n_items, n_groups,
+        per, unscale, p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 2;
     return cudaGetLastError();

@@ -17,9 +17,9 @@ import numpy as np
 from . import build as _build
 
 FDAS_OK, FDAS_E_INVALID, FDAS_E_UNSUPPORTED, FDAS_E_NOMEM, FDAS_E_CUDA, FDAS_E_OVERFLOW, FDAS_E_TIMEOUT, FDAS_E_STATE = range(8)
-FDAS_FP32, FDAS_BF16, FDAS_BF16_SPLIT = 0, 1, 2
+FDAS_FP32, FDAS_BF16, FDAS_BF16_SPLIT, FDAS_FP16_SCALED = 0, 1, 2, 3
 FDAS_DEV_PEAK_OVERFLOW, FDAS_DEV_TIMEOUT = 0x1, 0x2
-PRECISIONS = {"fp32": FDAS_FP32, "bf16": FDAS_BF16, "bf16_split": FDAS_BF16_SPLIT}
+PRECISIONS = {"fp32": FDAS_FP32, "bf16": FDAS_BF16, "bf16_split": FDAS_BF16_SPLIT, "fp16_scaled": FDAS_FP16_SCALED}
 
 # every symbol include/fdas.h declares
 EXPORTED = (
@@ -29,7 +29,7 @@ EXPORTED = (
     "fdas_plane_static", "fdas_interp_power", "fdas_refine",
     "fdas_batch_plan", "fdas_batch_autotune", "fdas_batch_make_templates", "fdas_batch_search",
     "fdas_batch_get_info", "fdas_batch_series_info", "fdas_batch_device_status", "fdas_batch_last_error",
-    "fdas_batch_destroy",
+    "fdas_batch_destroy", "fdas_band_max",
 )
 REFINE_MAX_STEPS = 1000
 STATIC_SCRATCH_BYTES = 40 << 20
@@ -117,6 +117,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "fdas_batch_device_status": (S, [V, ctypes.POINTER(I32), ctypes.c_int]),
         "fdas_batch_last_error": (ctypes.c_char_p, [V]),
         "fdas_batch_destroy": (None, [V]),
+        "fdas_band_max": (S, [V, V, V, V, I32, V, V, V, V, V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -345,6 +346,29 @@ def fdas_refine(plan: Plan, xhat, cands_in, steps: int, cands_out, power=None, e
             _dev_ptr(evals, "evals", torch.int32, 4 * n) if evals is not None else None,
             _stream_ptr(stream))
     _check(load().fdas_refine(*args), "fdas_refine", plan)
+
+
+def fdas_band_max(plan: Plan, plane, lo: Sequence[int], hi: Sequence[int], stream=None):
+    """Band maxima of a plane: (value float32[n], r int64[n], zi int32[n]) device tensors."""
+    torch = _torch()
+    n = len(lo)
+    dev = plane.device
+    value = torch.empty(n, dtype=torch.float32, device=dev)
+    r = torch.empty(n, dtype=torch.int64, device=dev)
+    zi = torch.empty(n, dtype=torch.int32, device=dev)
+    scratch = torch.empty(max(1, 3 * n), dtype=torch.int64, device=dev)
+    hlo = np.ascontiguousarray(np.asarray(lo, dtype=np.int64))
+    hhi = np.ascontiguousarray(np.asarray(hi, dtype=np.int64))
+    if hlo.shape != hhi.shape:
+        raise ValueError("lo and hi must have the same length")
+    args = (plan.handle,
+            _dev_ptr(plane, "plane", plan.plane_dtype(), plan.info.plane_bytes),
+            hlo.ctypes.data, hhi.ctypes.data, n,
+            _dev_ptr(scratch, "scratch", torch.int64),
+            _dev_ptr(value, "value", torch.float32), _dev_ptr(r, "r", torch.int64), _dev_ptr(zi, "zi", torch.int32),
+            _stream_ptr(stream))
+    _check(load().fdas_band_max(*args), "fdas_band_max", plan)   # pageable bounds are staged before it returns
+    return value, r, zi
 
 
 def fdas_get_templates(plan: Plan, out, stream=None):

@@ -433,3 +433,24 @@ def test_pins_catch_planted_mistakes(oracle_mod):
     assert not peak_ok(xhat, np.roll(T, 1, axis=1))            # tap index shifted by one
     assert not peak_ok(xhat, T[::-1])                          # z axis reversed
     assert not peak_ok(xhat, T[:, ::-1])                       # taps reversed
+
+
+# ---------------------------------------------------------------- band maxima (harmonic-band analysis)
+def test_band_max_against_brute_force(oracle_mod):
+    """Band maxima vs an explicit loop over rows then bins (the first of equal maxima wins)."""
+    rng = np.random.default_rng(12)
+    pl = rng.integers(0, 6, size=(5, 40)).astype(np.float32)        # many ties
+    lo = [0, 3, 17, 39, 35, 50, -4]
+    hi = [39, 9, 17, 39, 60, 70, 2]
+    v, r, zi = oracle_mod.band_max(pl, lo, hi)
+    for b, (l, h) in enumerate(zip(lo, hi)):
+        l, h = max(0, l), min(39, h)
+        if h < l:
+            assert (v[b], r[b], zi[b]) == (-1.0, -1, -1)
+            continue
+        best = (-1.0, -1, -1)
+        for i in range(pl.shape[0]):
+            for k in range(l, h + 1):
+                if pl[i, k] > best[0]:
+                    best = (float(pl[i, k]), k, i)
+        assert (v[b], r[b], zi[b]) == best
