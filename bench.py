@@ -71,6 +71,9 @@ def parse_args():
     ap.add_argument("--quick", action="store_true", help="no clocks, e2e or CPU baseline (profiling runs)")
     ap.add_argument("--no-refine", action="store_true", help="skip the candidate-refinement measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the many-series batch measurement")
+    ap.add_argument("--no-sensitivity", action="store_true", help="skip the precision sensitivity sweep")
+    ap.add_argument("--sensitivity-series", type=int, default=32,
+                    help="series of the sensitivity sweep (the full sweep is 2000)")
     ap.add_argument("--n-log2", type=int, default=23,
                     help="series length 2^n (23 = the benchmark workload; smaller only for profiler captures)")
     return ap.parse_args()
@@ -468,6 +471,75 @@ def batch_bench(dev, stream, reps: int = 5, warmup: int = 2, loop_reps: int = 2)
     }
 
 
+# ------------------------------------------------------------------------------ sensitivity sweep
+SENS_FORMS = ("fp32", "bf16", "bf16_split", "fp16_scaled")
+SENS_BANDS = 8
+
+
+def sensitivity_bench(dev, stream, n_series: int):
+    """The sensitivity workload (one binary pulsar per series, N = 2^23) in every precision form:
+    band peaks of the fundamental and harmonics (Table harm_bounds) compared with FP32's, the
+    noise canopy from noise-only planes, and each form's search throughput."""
+    import numpy as np
+    import torch
+
+    import fdas_synth as synth
+    import paper_2206_12205_gb300 as fd
+    from paper_2206_12205_gb300 import sensitivity as se
+
+    base = synth.sensitivity_workload(series_index=0)
+    cfgs = {f: fd.make_config(base.n, base.zmax, base.taps, base.seg_len, precision=f, max_harm=MAX_HARM,
+                              thr=THRESHOLDS, max_peaks=MAX_PEAKS) for f in SENS_FORMS}
+    searches = {f: fd.Search(c, device=dev, stream=stream) for f, c in cfgs.items()}
+    rows = {f: [] for f in SENS_FORMS[1:]}
+    ms = {f: [] for f in SENS_FORMS}
+    widths = []
+    t0 = time.perf_counter()
+    for sidx in range(n_series):
+        w = base if sidx == 0 else synth.sensitivity_workload(series_index=sidx)
+        f_bins = w.trains[0].r0
+        widths.append(1.5 * f_bins)
+        lo, hi = se.harmonic_bands(f_bins, SENS_BANDS, w.nb)
+        x = torch.from_numpy(w.series).to(dev)
+        peaks = {}
+        for f in SENS_FORMS:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            searches[f].search(x, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms[f].append(a.elapsed_time(b))
+            peaks[f] = se.band_peaks(searches[f].plan, searches[f].plane_2d(), lo, hi)
+        for f in SENS_FORMS[1:]:
+            rows[f].append(se.compare(peaks["fp32"], peaks[f]))
+    t_sweep = time.perf_counter() - t0
+    # noise canopy: noise-only FP32 planes, bands as wide as 1.5 f of each series' pulsar
+    rng = np.random.default_rng(7)
+    lo_c, hi_c = [], []
+    for k in range(2):
+        xn = torch.from_numpy(synth.noise(base.n, synth.rng_for(4, 10_000 + k)).astype(np.float32)).to(dev)
+        searches["fp32"].search(xn, stream)
+        torch.cuda.synchronize()
+        a_, b_ = se.noise_canopy(searches["fp32"].plan, searches["fp32"].plane_2d(), widths, rng)
+        lo_c.append(a_)
+        hi_c.append(b_)
+    canopy = (float(min(lo_c)), float(max(hi_c)))
+    cells = base.K * base.nb
+    out = {
+        "workload": (f"{n_series} of the 2000 sensitivity series (N = 2^23, one pulsar each: P 1-20 ms, "
+                     f"+-200 m/s^2, duty 2-10 %, SNR 3-40), bands 0..{SENS_BANDS - 1}; host time {t_sweep:.1f} s"),
+        "noise_canopy_snr": {"min": canopy[0], "max": canopy[1]},
+        "forms": {},
+    }
+    for f in SENS_FORMS:
+        rec = {"cells_per_s": cells / (statistics.median(ms[f]) / 1e3), "ms_per_series": statistics.median(ms[f])}
+        if f != "fp32":
+            rec.update(se.summarise(rows[f], canopy_hi_snr=canopy[1]))
+        out["forms"][f] = rec
+    del searches
+    return out
+
+
 # ------------------------------------------------------------------------------ own arm
 def own_arm(args):
     import numpy as np
@@ -600,6 +672,9 @@ def own_arm(args):
     batch = None
     if rank == 0 and world == 1 and not args.no_batch and not args.quick:
         batch = batch_bench(dev, stream)
+    sensitivity = None
+    if rank == 0 and world == 1 and not args.no_sensitivity and not args.quick:
+        sensitivity = sensitivity_bench(dev, stream, args.sensitivity_series)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
@@ -616,7 +691,7 @@ def own_arm(args):
             "data": "synthetic: seeded N(0,1) noise + 8 accelerated Gaussian pulse trains (fdas_synth)",
             "config": config_json(w, precision),
             "roofline": roof, "roofline_correlate": roof_corr, "paths": paths or None,
-            "cpu_baseline": cpu, "e2e": e2e, "refine": refine, "batch": batch,
+            "cpu_baseline": cpu, "e2e": e2e, "refine": refine, "batch": batch, "sensitivity": sensitivity,
             "gpu_launches": int(prof["launches"]), "clocks": clk,
             "stages_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
         }

@@ -98,3 +98,42 @@ def test_noise_histograms_agree_between_precisions(noise_planes):
         print(f"{prec}: two-sample KS D {d:.5f}, max relative bin-count difference {rel.max():.4f} over {big.sum()} bins")
         assert d < 0.005
         assert rel.max() < (0.05 if prec == "bf16" else 0.01)
+
+
+def test_sweep_small_series_against_fp64_oracle():
+    """The sweep on small sensitivity series (N = 2^16, one binary pulsar each, SNR 3-40): band
+    peaks (Table harm_bounds) of the FP32 plane against those of the oracle's FP64 plane computed
+    from the same series (the paper finds no drift and <= 0.0098 % power differences between
+    single and double precision), and of the BF16 / split / FP16 planes against FP32 (the
+    paper's criterion: same bin or adjacent z bin, powers within 3 %) above the noise canopy."""
+    from paper_2206_12205_gb300 import sensitivity as se
+    n, zmax, m = 1 << 16, 16, 64
+    forms = ("fp32", "bf16", "bf16_split", "fp16_scaled")
+    rows = {f: [] for f in forms[1:]}
+    fp64_rows = []
+    for sidx in range(6):
+        w = synth.sensitivity_workload(config_index=92, series_index=sidx, n=n, zmax=zmax, taps=m, seg_len=1024)
+        f_bins = w.trains[0].r0
+        lo, hi = se.harmonic_bands(f_bins, 6, n // 2)
+        x = torch.from_numpy(w.series).cuda()
+        peaks = {}
+        for form in forms:
+            s = fd.Search(fd.make_config(n, zmax, m, 1024, precision=form))
+            s.search(x)
+            torch.cuda.synchronize()
+            peaks[form] = se.band_peaks(s.plan, s.plane_2d(), lo, hi)
+        for form in forms[1:]:
+            rows[form].append(se.compare(peaks["fp32"], peaks[form]))
+        ref = oracle.search(w.series, zmax, m, 1, (1e9,))["plane"]
+        v, r, zi = oracle.band_max(ref, lo, hi)
+        fp64 = {"power": v, "r": r, "zi": zi, "std": float(ref.std())}
+        fp64_rows.append(se.compare(fp64, peaks["fp32"]))
+    s64 = se.summarise(fp64_rows)
+    print("fp32 vs fp64:", s64)
+    assert s64["no_drift_fraction"] >= 0.95 and s64["perc_diff_max_abs"] <= 0.01
+    for form, rr in rows.items():
+        sm = se.summarise(rr, canopy_hi_snr=8.0)
+        print(form, "vs fp32:", sm)
+        if "above_canopy_bands" in sm:
+            assert sm["above_canopy_recovered_fraction"] >= 0.9
+            assert sm["above_canopy_perc_diff_max_abs"] <= 3.0
