@@ -173,13 +173,12 @@ fdas_status fdas_make_templates(fdas_plan_t plan, void *stream) {
     alloc((void **)&p->d_twn_hi, sizeof(float2) * (size_t)nhi);
     alloc((void **)&p->d_G, sizeof(float2) * nbank);
     if (uses_tensor_path(p)) {
-        alloc((void **)&p->d_Gbf, sizeof(__nv_bfloat162) * nbank);
-        if (p->cfg.precision == FDAS_BF16_SPLIT) alloc((void **)&p->d_Gbf_lo, sizeof(__nv_bfloat162) * nbank);
+        if (p->cfg.precision == FDAS_BF16) alloc((void **)&p->d_Gbf, sizeof(__nv_bfloat162) * nbank);
         if (p->cfg.precision == FDAS_FP16_SCALED) {
             alloc((void **)&p->d_Gh, sizeof(__half2) * nbank);
-            alloc((void **)&p->d_tcFh, 2 * 128 * 128);
+            alloc((void **)&p->d_tcFh, 2 * 2 * 128 * 128);
         }
-        alloc((void **)&p->d_tcF, 2 * 2 * 128 * 128);
+        alloc((void **)&p->d_tcF, 4 * 2 * 128 * 128);
         alloc((void **)&p->d_tcTw, sizeof(float2) * 64 * 64);
     }
     alloc((void **)&p->d_status, sizeof(int32_t));
@@ -401,7 +400,6 @@ void fdas_destroy(fdas_plan_t plan) {
         cudaFree(p->d_twn_hi);
         cudaFree(p->d_G);
         cudaFree(p->d_Gbf);
-        cudaFree(p->d_Gbf_lo);
         cudaFree(p->d_Gh);
         cudaFree(p->d_tcFh);
         cudaFree(p->d_tcF);

@@ -328,7 +328,6 @@ fdas_status fdas_batch_make_templates(fdas_batch_t b, void *stream) {
         p->d_twn_hi = l->d_twn_hi;
         p->d_G = l->d_G;
         p->d_Gbf = l->d_Gbf;
-        p->d_Gbf_lo = l->d_Gbf_lo;
         p->d_tcF = l->d_tcF;
         p->d_tcTw = l->d_tcTw;
         p->d_Gh = l->d_Gh;

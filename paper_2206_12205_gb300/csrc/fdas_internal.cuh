@@ -18,6 +18,16 @@ constexpr int TW_MAX = 8192;
 constexpr int TW_LO_BITS = 13;
 // Segment length of the BF16 tensor-core path (64 x 64 four-step DFT) and its largest tap count.
 constexpr int TC_S_BF16 = 4096;
+
+// Stage-1 operand order of the tensor path (segment spectra and template banks, S = 64 x 64): per
+// segment 16 chunks x 64 columns n2 of four 16-bit pairs; chunk ch of column n2 holds, with
+// b = (ch & 1) + 8 (ch >> 1), (Re x[b], Re x[b+2]), (Im x[b], Im x[b+2]), (Re x[b+4], Re x[b+6]),
+// (Im x[b+4], Im x[b+6]) of x[n1] = x[64 n1 + n2].  Position, in 16-bit elements, of
+// Re x[64 n1 + n2]; Im x follows 2 elements later.
+__host__ __device__ constexpr uint32_t tc_s1_pos(int n1, int n2) {
+    return (((2u * (uint32_t)(n1 >> 3) + (uint32_t)(n1 & 1)) * 64u + (uint32_t)n2) * 4u +
+            2u * (uint32_t)((n1 >> 2) & 1)) * 2u + (uint32_t)((n1 >> 1) & 1);
+}
 constexpr int TC_MAX_TAPS = 2048;
 
 // Per-stage CUDA-event timing (fdas_profile_enable / fdas_profile_read).
@@ -59,11 +69,10 @@ struct Plan {
     float2 *d_twn_lo;      // W_N^j, j < 2^TW_LO_BITS
     float2 *d_twn_hi;      // W_N^(j << TW_LO_BITS), j < max(1, N >> TW_LO_BITS)
     float2 *d_G;           // [K][S] FP32 template bank
-    __nv_bfloat162 *d_Gbf; // [K][S] BF16 template bank (hi), BF16 precisions
-    __nv_bfloat162 *d_Gbf_lo; // [K][S] BF16 residual (lo), split precision
-    void *d_tcF;           // real-ified radix-64 DFT matrix, BF16 K-major operand images: hi, then lo (2 x 32 KB)
-    __half2 *d_Gh;         // [K][S] FP16 template bank times S, FP16-scaled precision
-    void *d_tcFh;          // the DFT matrix as an FP16 K-major operand image (32 KB)
+    __nv_bfloat162 *d_Gbf; // [K][S] BF16 template bank, stage-1 operand order (tensor path)
+    void *d_tcF;           // BF16 K-major DFT operand images: split hi, split lo, F1, F2 (4 x 32 KB)
+    __half2 *d_Gh;         // [K][S] FP16 template bank times S, stage-1 operand order
+    void *d_tcFh;          // FP16 K-major DFT operand images F1, F2 (2 x 32 KB)
     float2 *d_tcTw;        // W_4096^{n2 k1}, [k1][n2] (32 KB)
     int32_t *d_status;     // sticky device status word
     bool templates_ready;

@@ -108,10 +108,9 @@ __global__ void k0_normalise(double2 *__restrict__ taps, int m, double *__restri
 }
 
 // G_i(k) = (1/S) sum_d T_i(d - m/2) W_S^{d k}: direct FP64 DFT, rounded once to each format.
+// The 16-bit banks of the tensor path (S = 4096) are stored in its stage-1 operand order.
 __global__ void k0_dft(const double2 *__restrict__ taps, int m, int S, const double2 *__restrict__ wS,
-                       float2 *__restrict__ G, __nv_bfloat162 *__restrict__ Ghi,
-                       __nv_bfloat162 *__restrict__ Glo,
-                       __half2 *__restrict__ Gh) {
+                       float2 *__restrict__ G, __nv_bfloat16 *__restrict__ Gbf, __half *__restrict__ Gh) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (k >= S) return;
@@ -127,19 +126,16 @@ __global__ void k0_dft(const double2 *__restrict__ taps, int m, int S, const dou
     im /= (double)S;
     const float fr = (float)re, fi = (float)im;
     G[(size_t)i * S + k] = make_float2(fr, fi);
+    const size_t pos = (size_t)i * 2 * S + tc_s1_pos(k >> 6, k & 63);
     // FP16 bank of the scaled precision: S G (|S G| <= sqrt(m) for unit-norm taps), rounded once
-    if (Gh) Gh[(size_t)i * S + k] = __floats2half2_rn((float)(re * S), (float)(im * S));
-    if (Ghi) {
-        // hi = BF16 rounding of the FP32 value (the paper's conversion); lo = BF16 of the
-        // FP64 remainder, so hi + lo carries about 16 significant bits.
-        const __nv_bfloat16 hr = __float2bfloat16_rn(fr), hi_i = __float2bfloat16_rn(fi);
-        Ghi[(size_t)i * S + k] = __halves2bfloat162(hr, hi_i);
-        if (Glo) {
-            const double rr = re - (double)__bfloat162float(hr);
-            const double ri = im - (double)__bfloat162float(hi_i);
-            Glo[(size_t)i * S + k] = __halves2bfloat162(__float2bfloat16_rn((float)rr),
-                                                        __float2bfloat16_rn((float)ri));
-        }
+    if (Gh) {
+        Gh[pos] = __float2half_rn((float)(re * S));
+        Gh[pos + 2] = __float2half_rn((float)(im * S));
+    }
+    // BF16 bank: the BF16 rounding of the FP32 value (the paper's conversion)
+    if (Gbf) {
+        Gbf[pos] = __float2bfloat16_rn(fr);
+        Gbf[pos + 2] = __float2bfloat16_rn(fi);
     }
 }
 
@@ -206,7 +202,10 @@ cudaError_t launch_make_templates(Plan &p, cudaStream_t st) {
         k0_taps<<<(n + 127) / 128, 128, 0, st>>>(d_taps, K, m, p.cfg.zmax, gl);
         k0_normalise<<<K, 256, 0, st>>>(d_taps, m, d_eta);
         dim3 grid((S + 255) / 256, K);
-        k0_dft<<<grid, 256, 0, st>>>(d_taps, m, S, d_wS, p.d_G, p.d_Gbf, p.d_Gbf_lo, p.d_Gh);
+        const bool tc = S == TC_S_BF16;
+        k0_dft<<<grid, 256, 0, st>>>(d_taps, m, S, d_wS, p.d_G,
+                                     tc ? reinterpret_cast<__nv_bfloat16 *>(p.d_Gbf) : nullptr,
+                                     tc ? reinterpret_cast<__half *>(p.d_Gh) : nullptr);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }

@@ -7,14 +7,14 @@
 // With x = conj(Yhat_j) * G_z (length S, n = 64 n1 + n2) the plane row segment is
 // |X|^2 with the four-step DFT
 //     X[k1 + 64 k2] = sum_{n2} W_64^{n2 k2} W_S^{n2 k1} sum_{n1} W_64^{n1 k1} x[64 n1 + n2],
-// computed for two templates at a time as two real GEMMs of 128 x 128 x 128 (below), where F'
-// is the radix-64 DFT real-ified with re/im interleaved (row 2k+p, column 2n+s).
+// computed for two templates at a time as two real GEMMs of 128 x 128 x 128 (below) against
+// real-ified radix-64 DFT matrices F1 and F2 (each complex entry w as the 2 x 2 block
+// [[Re w, -Im w], [Im w, Re w]], rows and columns permuted as described below).
 //
 // One persistent, warp-specialised CTA per SM walks a contiguous range of (segment, template
-// pair) items with producer, MMA and two epilogue roles overlapped through double-buffered
-// shared-memory tiles and TMEM accumulators (layout below the helpers).  Every mbarrier wait
-// is bounded; a timeout sets FDAS_DEV_TIMEOUT, all roles stop, the issued MMAs drain and the
-// TMEM is released.
+// pair) items with producer, MMA and two epilogue roles overlapped through TMEM and shared-memory
+// buffers (layout below the helpers).  Every mbarrier wait is bounded; a timeout sets
+// FDAS_DEV_TIMEOUT, all roles stop, the issued MMAs drain and the TMEM is released.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -32,13 +32,28 @@ constexpr int TC_G = 2;                          // templates per item
 constexpr int TC_N = TC_G * TC_R;                // GEMM N (columns)
 constexpr int TC_M = 2 * TC_R;                   // GEMM M (real-ified rows)
 constexpr int TC_K = 2 * TC_R;                   // GEMM K
-constexpr uint32_t TILE_BYTES = TC_M * TC_K * 2;  // 32 KB: F' and every B tile are 128 x 128 BF16
+constexpr uint32_t TILE_BYTES = TC_M * TC_K * 2;  // 32 KB: every 128 x 128 16-bit operand tile
 constexpr long long WAIT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
 
 static_assert(TC_S_BF16 == TC_R * TC_R, "segment length must be 64 x 64");
 
+// Stage-1 operand order (tc_s1_pos): products of its 16-bit pairs are again such pairs, so the
+// producer forms conj(Yhat) G with packed arithmetic and no rearrangement and stores the 64 pairs
+// of a row as the row's 64 TMEM columns (stage-1 K index 2 c + h = half h of column c).  It is
+// also the order in which the segment FFT holds its outputs (thread t: n2 = t mod 64,
+// n1 = t / 64 + 2 i).
+// The inverse on the K axis: stage-1 K index kk -> (n1, s), s = 0 real part, 1 imaginary part.
+__host__ __device__ constexpr int s1_n1(int kk) {
+    return ((kk >> 3) & 1) + 8 * (kk >> 4) + 4 * ((kk >> 2) & 1) + 2 * (kk & 1);
+}
+__host__ __device__ constexpr int s1_s(int kk) { return (kk >> 1) & 1; }
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
@@ -48,8 +63,6 @@ struct OpsBF16 {
     using V = __nv_bfloat162;
     using Out = __nv_bfloat16;
     static constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_N);
-    __device__ __forceinline__ static V high2(V a) { return __high2bfloat162(a); }
-    __device__ __forceinline__ static V low2(V a) { return __low2bfloat162(a); }
     __device__ __forceinline__ static uint32_t pack(float lo, float hi) { return pack_bf16x2(lo, hi); }
     __device__ __forceinline__ static Out out(float pw, float) { return __float2bfloat16_rn(pw); }
 };
@@ -57,20 +70,15 @@ struct OpsF16 {
     using V = __half2;
     using Out = float;
     static constexpr uint32_t idesc = tc::idesc_f16_f32(TC_M, TC_N);
-    __device__ __forceinline__ static V high2(V a) { return __high2half2(a); }
-    __device__ __forceinline__ static V low2(V a) { return __low2half2(a); }
-    __device__ __forceinline__ static uint32_t pack(float lo, float hi) {
-        const __half2 h = __floats2half2_rn(lo, hi);
-        return *reinterpret_cast<const uint32_t *>(&h);
-    }
+    __device__ __forceinline__ static uint32_t pack(float lo, float hi) { return pack_f16x2(lo, hi); }
     __device__ __forceinline__ static Out out(float pw, float unscale) { return pw * unscale; }
 };
 
-// Segment FFTs (FP32 CUDA-core block FFT), stored as BF16 pairs for the tensor stages.
+// Segment FFTs (FP32 CUDA-core block FFT), stored as BF16 pairs in the stage-1 order.
 __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_bf16(const float2 *__restrict__ X,
                                                                    const float *__restrict__ scale_ptr,
                                                                    const float2 *__restrict__ tw,
-                                                                   __nv_bfloat162 *__restrict__ Y, int64_t nb, int L,
+                                                                   uint4 *__restrict__ Y, int64_t nb, int L,
                                                                    int half_m) {
     constexpr int S = TC_S_BF16, T = S / 32;
     extern __shared__ float2 sm[];
@@ -87,18 +95,22 @@ __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_bf16(const float2 
         v[i] = make_float2(x.x * scale, x.y * scale);
     }
     block_fft<S>(v, sm, tw, t);
-    __nv_bfloat162 *out = Y + j * S;
+    // v[i] = X[t + 128 i]: n2 = t mod 64, n1 = t / 64 + 2 i; chunk 2 c + t / 64 takes v[4c .. 4c+3]
+    uint4 *out = Y + j * (S / 4) + (t & 63);
 #pragma unroll
-    for (int i = 0; i < 32; i++) out[t + i * T] = __floats2bfloat162_rn(v[i].x, v[i].y);
+    for (int c = 0; c < 8; c++)
+        out[(2 * c + (t >> 6)) * 64] =
+            make_uint4(pack_bf16x2(v[4 * c].x, v[4 * c + 1].x), pack_bf16x2(v[4 * c].y, v[4 * c + 1].y),
+                       pack_bf16x2(v[4 * c + 2].x, v[4 * c + 3].x), pack_bf16x2(v[4 * c + 2].y, v[4 * c + 3].y));
 }
 
 // Segment FFTs for the FP16 stages: the segment's largest component |re| or |im| is brought into
-// [0.5, 1) by a power of two s_j (exact), the values stored as FP16 pairs, and the plane's factor
-// 1 / (s_j gscale)^2 (gscale: the template bank's scale) kept per segment.
+// [0.5, 1) by a power of two s_j (exact), the values stored as FP16 pairs in the stage-1 order,
+// and the plane's factor 1 / (s_j gscale)^2 (gscale: the template bank's scale) kept per segment.
 __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_f16(const float2 *__restrict__ X,
                                                                   const float *__restrict__ scale_ptr,
                                                                   const float2 *__restrict__ tw,
-                                                                  __half2 *__restrict__ Y, float *__restrict__ unscale,
+                                                                  uint4 *__restrict__ Y, float *__restrict__ unscale,
                                                                   float gscale, int64_t nb, int L, int half_m) {
     constexpr int S = TC_S_BF16, T = S / 32;
     extern __shared__ float2 sm[];
@@ -129,9 +141,12 @@ __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_f16(const float2 *
     int ex = 0;
     if (mx > 0.f) frexpf(mx, &ex);                  // mx = f 2^ex, f in [0.5, 1)
     const float sj = ldexpf(1.0f, -ex);
-    __half2 *out = Y + j * S;
+    uint4 *out = Y + j * (S / 4) + (t & 63);
 #pragma unroll
-    for (int i = 0; i < 32; i++) out[t + i * T] = __floats2half2_rn(v[i].x * sj, v[i].y * sj);
+    for (int c = 0; c < 8; c++)
+        out[(2 * c + (t >> 6)) * 64] = make_uint4(
+            pack_f16x2(v[4 * c].x * sj, v[4 * c + 1].x * sj), pack_f16x2(v[4 * c].y * sj, v[4 * c + 1].y * sj),
+            pack_f16x2(v[4 * c + 2].x * sj, v[4 * c + 3].x * sj), pack_f16x2(v[4 * c + 2].y * sj, v[4 * c + 3].y * sj));
     if (t == 0) {
         const float g = sj * gscale;
         unscale[j] = 1.0f / (g * g);
@@ -139,48 +154,52 @@ __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_f16(const float2 *
 }
 
 // ---------------------------------------------------------------------------------------
-// Warp-specialised persistent kernel, one CTA per SM, 25 warps.  Both GEMMs run transposed,
-// data as the A operand (M = 128 rows = two templates x 64) and F' as the B operand:
-//   stage 1  D1t[(z,n2), (k1,p)] = B1[(z,n2), (n1,s)] . F'^T        (B1 = x, from the producer)
-//   stage 2  D2t[(z,k1), (k2,p)] = A2[(z,k1), (n2,s)] . F'^T        (A2 = twiddled D1t, transposed)
-// so a thread's TMEM row holds the real and imaginary parts of its values side by side.
-//   warp 0       TMEM allocation; lane 0 issues the MMAs (stage 1 of item i+1 before stage 2 of i)
-//   warps 1-8    producer:   B1[slot] = conj(Yhat_j) * G_z, one 4 x 4 (n1, n2) block per thread
-//                with all of its 16-byte loads in flight at once
-//   warps 9-16   epilogue 1: D1t[slot] -> W_S^{n2 k1} -> A2[slot] (warps 9-12 and 13-16 take the
-//                two halves of k1)
-//   warps 17-24  epilogue 2: D2t[slot] -> |.|^2 -> BF16 plane (halves of k2)
-// Two slots of B1, A2 (shared memory) and D1t, D2t (TMEM, 4 x 128 of the 512 columns).
-// Hand-offs are mbarriers, one per slot:
-//   b1_full  (256 producer arrivals)   s1_done (MMA commit: D1t ready, B1 free)
-//   b2_full  (256 epilogue-1 arrivals: A2 ready, D1t drained)
-//   s2_done  (MMA commit: D2t ready, A2 free)   d2_free (256 epilogue-2 arrivals: D2t drained)
+// Warp-specialised persistent kernel, one CTA per SM, 28 warps.  Both GEMMs run transposed,
+// data as the A operand (M = 128 rows = two templates x 64) and a DFT matrix as B:
+//   stage 1  D1[(z,n2), (p,k1)] = A1[(z,n2), K1] . F1^T          A1 = x, in TMEM (K1: stage-1 order)
+//   stage 2  D2[(z,k1), (p,k2)] = A2[(z,k1), (s,n2)] . F2^T      A2 = W_S^{n2 k1} D1, shared memory
+// Accumulator columns are ordered (p, k): the 64 real parts, then the 64 imaginary parts, so a
+// thread's TMEM row yields 8 consecutive real (or imaginary) parts per 8 columns.  A2 is stored
+// MN-major: the 8 consecutive k1 of one (z, n2, s) are one 16-byte row of a core matrix, which is
+// what an epilogue-1 thread (one n2, consecutive k1) writes in one store; the tensor core reads the
+// transposed operand from it.
+//   warp 0       TMEM allocation; lane 0 issues the MMAs (stage 1 of item i+1 before stage 2 of i);
+//                warps 1-3 idle (they complete warpgroup 0 for the register hand-over)
+//   warps 4-11   producer:   A1[slot] row (z, n2), half of its 64 columns, = conj(Yhat_j) G_z in packed
+//                16-bit arithmetic, written with tcgen05.st
+//   warps 12-19  epilogue 1: D1[slot] -> W_S^{n2 k1} (FP32, packed pairs) -> A2[slot]; warps 12-15 and
+//                16-19 take the two halves of k1
+//   warps 20-27  epilogue 2: D2 -> |.|^2 -> plane (halves of k2)
+// TMEM (512 columns): D1 slots at columns 0 and 128, D2 at 256, A1 slots (64 columns) at 384, 448.
+// Shared memory: F1, F2 (32 KB each) and two A2 slots (32 KB each).  Hand-offs are mbarriers:
+//   a1_full[s]  (256 producer arrivals)     s1_done[s] (MMA commit: D1 ready, A1 free)
+//   b2_full[s]  (256 epilogue-1 arrivals: A2 ready, D1 drained)
+//   s2_done[s]  (MMA commit: D2 ready, A2 free)       d2_free (256 epilogue-2 arrivals: D2 drained)
 // The k-th use of a slot waits for phase parity k & 1; every wait is bounded and also gives
-// up when another role has aborted.
-constexpr int WS_PRODUCERS = 256;                            // warps 1-8
-constexpr int WS_E1 = 1 + WS_PRODUCERS / 32;                 // first epilogue-1 warp (9)
-constexpr int WS_E2 = WS_E1 + 8;                             // first epilogue-2 warp (17)
-constexpr int WS_THREADS = (WS_E2 + 8) * 32;                 // 25 warps
-// B1 tiles (stage-1 A operand): core matrices 144 B apart along M, 16 x 144 B along K
-constexpr uint32_t B_SBO = 144, B_LBO = 16 * B_SBO;
-constexpr uint32_t B_TILE = 16 * B_LBO;                      // 36 KB
-// A2 tiles (stage-2 A operand): 128 B along M, 2064 B (16 mod 128) along K
-constexpr uint32_t A2_SBO = 128, A2_LBO = 16 * 128 + 16;
-constexpr uint32_t A2_TILE = 16 * A2_LBO;                    // 32.25 KB
-constexpr uint32_t F_LBO = TC_M * 16, F_SBO = 128;           // F': dense
-constexpr uint32_t OFF_F = 0;
-constexpr uint32_t OFF_B1 = OFF_F + TILE_BYTES;              // 2 slots
-constexpr uint32_t OFF_A2 = OFF_B1 + 2 * B_TILE;             // 2 slots
-// twiddles W_S^{n2 k1}, one row per n2 padded to 66 entries (528 B = 16 mod 128) so that the
-// 16-byte row reads of a warp's 32 different rows spread over all banks
-constexpr int TW_LD = TC_R + 2;
-constexpr uint32_t OFF_TW = OFF_A2 + 2 * A2_TILE;
-constexpr uint32_t OFF_BAR = OFF_TW + TC_R * TW_LD * 8;
-constexpr uint32_t WS_SMEM = OFF_BAR + 16 * 8 + 32;
+// up when another role has aborted.  The twiddle W_S^{n2 k1} with k1 = k0 + q (k0 a multiple of
+// 8) is applied as W_S^{n2 q} (per-thread pairs held in registers) then W_S^{n2 k0}.
+constexpr int WS_P0 = 4;                                     // first producer warp
+constexpr int WS_PRODUCERS = 256;                            // warps 4-11
+constexpr int WS_E1 = WS_P0 + WS_PRODUCERS / 32;             // first epilogue-1 warp (12)
+constexpr int WS_E2 = WS_E1 + 8;                             // first epilogue-2 warp (20)
+constexpr int WS_THREADS = (WS_E2 + 8) * 32;                 // 28 warps = 7 warpgroups
+// Registers: 72 a thread at launch (7 warps on each SM sub-partition).  Warpgroup 0 (the MMA
+// warp and three idle warps) gives 32 back; the producers and epilogue 1 take 8 more:
+// 128 x 40 + 256 x 80 + 256 x 80 + 256 x 72 = 896 x 72.
+constexpr int REG_LAUNCH = 72, REG_MMA = 40, REG_WIDE = 80;
+static_assert(128 * REG_MMA + 512 * REG_WIDE + 256 * REG_LAUNCH == WS_THREADS * REG_LAUNCH,
+              "register split must add up to the launch allocation");
+constexpr uint32_t A2_CM = 128, A2_CK = (TC_M / 8) * 128;    // A2 MN-major: core matrices along M, K
+constexpr uint32_t F_LBO = TC_M * 16, F_SBO = 128;           // F1, F2: dense K-major
+constexpr uint32_t OFF_F1 = 0, OFF_F2 = TILE_BYTES;
+constexpr uint32_t OFF_A2 = 2 * TILE_BYTES;                  // 2 slots
+constexpr uint32_t OFF_BAR = OFF_A2 + 2 * TILE_BYTES;
+constexpr uint32_t WS_SMEM = OFF_BAR + 256;
 constexpr uint32_t WS_TMEM_COLS = 512;
+constexpr uint32_t COL_D1 = 0, COL_D2 = 2 * TC_N, COL_A1 = 3 * TC_N;
 
 struct WsBars {
-    uint64_t b1_full[2], s1_done[2], b2_full[2], s2_done[2], d2_free[2], drain;
+    uint64_t a1_full[2], s1_done[2], b2_full[2], s2_done[2], d2_free, drain;
 };
 
 __device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
@@ -199,20 +218,23 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
+__device__ __forceinline__ float2 u2f2(uint32_t a, uint32_t b) {
+    return make_float2(__uint_as_float(a), __uint_as_float(b));
+}
+
 template <class Ops>
-__global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const typename Ops::V *__restrict__ Y,
-                                                             const typename Ops::V *__restrict__ G,
+__global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__restrict__ Y, const uint4 *__restrict__ G,
                                                              const uint4 *__restrict__ Fimg,
                                                              const float2 *__restrict__ tw,
                                                              typename Ops::Out *__restrict__ plane, int K, int64_t nb,
                                                              int L, int64_t n_items, int n_groups,
                                                              int64_t items_per_cta, const float *__restrict__ unscale,
                                                              int32_t *__restrict__ status) {
+    using V = typename Ops::V;
     extern __shared__ __align__(1024) unsigned char smem[];
     WsBars *bars = reinterpret_cast<WsBars *>(smem + OFF_BAR);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + OFF_BAR + sizeof(WsBars));
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + OFF_BAR + sizeof(WsBars) + 8);
-    float2 *sTw = reinterpret_cast<float2 *>(smem + OFF_TW);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
@@ -221,18 +243,17 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const typename Ops:
     }
     if (tid == 0) {
         for (int s = 0; s < 2; s++) {
-            tc::mbar_init(&bars->b1_full[s], WS_PRODUCERS);
+            tc::mbar_init(&bars->a1_full[s], WS_PRODUCERS);
             tc::mbar_init(&bars->s1_done[s], 1);
             tc::mbar_init(&bars->b2_full[s], 256);
             tc::mbar_init(&bars->s2_done[s], 1);
-            tc::mbar_init(&bars->d2_free[s], 256);
         }
+        tc::mbar_init(&bars->d2_free, 256);
         tc::mbar_init(&bars->drain, 1);
         *abort_flag = 0;
     }
-    for (int i = tid; i < (int)(TILE_BYTES / 16); i += WS_THREADS)
-        reinterpret_cast<uint4 *>(smem + OFF_F)[i] = __ldg(Fimg + i);
-    for (int i = tid; i < TC_S_BF16; i += WS_THREADS) sTw[(i / TC_R) * TW_LD + (i % TC_R)] = __ldg(tw + i);
+    for (int i = tid; i < (int)(2 * TILE_BYTES / 16); i += WS_THREADS)
+        reinterpret_cast<uint4 *>(smem + OFF_F1)[i] = __ldg(Fimg + i);
     tc::fence_proxy_async_smem();
     tc::fence_before_thread_sync();
     __syncthreads();
@@ -242,41 +263,51 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const typename Ops:
     const int64_t it0 = (int64_t)blockIdx.x * items_per_cta;
     const int64_t it1 = min(n_items, it0 + items_per_cta);
     const int64_t n_my = it1 - it0;
+    const int quad = warp & 3;                          // TMEM lane quadrant this warp may access
+    const int lrow = 32 * quad + lane;                  // TMEM lane = GEMM row
+    const int zl = lrow >> 6, idx = lrow & 63;          // (template in the pair, n2 or k1)
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
 
-    if (warp == 0) {
+    if (warp < WS_P0) {
         // ---------------------------------------------------------------- MMA issuer
-        if (lane == 0 && n_my > 0) {
-            const uint32_t idesc = Ops::idesc;
-            const uint32_t bF = tc::smem_u32(smem + OFF_F);
-            auto issue = [&](uint32_t dcol, uint32_t asm_, uint32_t albo, uint32_t asbo) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_MMA));
+        if (warp == 0 && lane == 0 && n_my > 0) {
+            const uint32_t id1 = Ops::idesc, id2 = Ops::idesc | (1u << 15);      // stage 2: A MN-major
+            const uint32_t bF1 = tc::smem_u32(smem + OFF_F1), bF2 = tc::smem_u32(smem + OFF_F2);
+            auto stage1 = [&](int sl) {
 #pragma unroll
                 for (int s = 0; s < TC_K / 16; s++)
-                    tc::mma_bf16(tbase + dcol, tc::smem_desc(asm_ + s * 2 * albo, albo, asbo),
-                                 tc::smem_desc(bF + s * 2 * F_LBO, F_LBO, F_SBO), idesc, s > 0 ? 1u : 0u);
+                    tc::mma_tmem_a(tbase + COL_D1 + sl * TC_N, tbase + COL_A1 + sl * (TC_K / 2) + 8 * s,
+                                   tc::smem_desc(bF1 + s * 2 * F_LBO, F_LBO, F_SBO), id1, s > 0 ? 1u : 0u);
+                tc::mma_commit(&bars->s1_done[sl]);
             };
-            bool ok = ws_wait(&bars->b1_full[0], 0, abort_flag);
+            auto stage2 = [&](int sl) {
+                const uint32_t a = tc::smem_u32(smem + OFF_A2 + sl * TILE_BYTES);
+#pragma unroll
+                for (int s = 0; s < TC_K / 16; s++)
+                    tc::mma_bf16(tbase + COL_D2, tc::smem_desc(a + s * 2 * A2_CK, A2_CK, A2_CM),
+                                 tc::smem_desc(bF2 + s * 2 * F_LBO, F_LBO, F_SBO), id2, s > 0 ? 1u : 0u);
+                tc::mma_commit(&bars->s2_done[sl]);
+            };
+            bool ok = ws_wait(&bars->a1_full[0], 0, abort_flag);
             if (ok) {
                 tc::fence_after_thread_sync();
-                issue(0, tc::smem_u32(smem + OFF_B1), B_LBO, B_SBO);
-                tc::mma_commit(&bars->s1_done[0]);
+                stage1(0);
             }
             for (int64_t k = 0; k < n_my && ok; k++) {
                 const int sl = (int)(k & 1);
-                const uint32_t par = (uint32_t)((k >> 1) & 1);
                 if (k + 1 < n_my) {                                    // stage 1 of the next item
                     const int sn = (int)((k + 1) & 1);
-                    ok = ws_wait(&bars->b1_full[sn], (uint32_t)(((k + 1) >> 1) & 1), abort_flag);
+                    ok = ws_wait(&bars->a1_full[sn], (uint32_t)(((k + 1) >> 1) & 1), abort_flag);
                     if (!ok) break;
                     tc::fence_after_thread_sync();
-                    issue(sn * TC_N, tc::smem_u32(smem + OFF_B1 + sn * B_TILE), B_LBO, B_SBO);
-                    tc::mma_commit(&bars->s1_done[sn]);
+                    stage1(sn);
                 }
-                ok = ws_wait(&bars->b2_full[sl], par, abort_flag);     // A2 ready, D1t drained
-                if (ok && k >= 2) ok = ws_wait(&bars->d2_free[sl], par ^ 1u, abort_flag);
+                ok = ws_wait(&bars->b2_full[sl], (uint32_t)((k >> 1) & 1), abort_flag);   // A2 ready
+                if (ok && k >= 1) ok = ws_wait(&bars->d2_free, (uint32_t)((k - 1) & 1), abort_flag);
                 if (!ok) break;
                 tc::fence_after_thread_sync();
-                issue((2 + sl) * TC_N, tc::smem_u32(smem + OFF_A2 + sl * A2_TILE), A2_LBO, A2_SBO);
-                tc::mma_commit(&bars->s2_done[sl]);
+                stage2(sl);
             }
             // drain: every MMA issued above has completed before TMEM can be released
             tc::mma_commit(&bars->drain);
@@ -285,134 +316,163 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const typename Ops:
         __syncwarp();
     } else if (warp < WS_E1) {
         // ---------------------------------------------------------------- producer
-        // thread -> block (n1 = 4 n1q .. 4 n1q + 3, n2 = 4 n2q .. 4 n2q + 3) of both templates
-        const int pt = tid - 32;
-        const int n2q = pt & 15, n1q = pt >> 4;
+        // thread -> A1 row (zl, n2 = idx), columns 32 hp .. 32 hp + 31 (chunks 8 hp .. 8 hp + 7)
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_WIDE));
+        const int hp = (warp - WS_P0) >> 2;
+        const uint4 *Yj = Y + (it0 / n_groups) * (TC_S_BF16 / 4) + 8 * hp * TC_R + idx;
+        int grp = (int)(it0 % n_groups);               // template pair of the current item
         for (int64_t k = 0; k < n_my; k++) {
-            const int64_t it = it0 + k;
-            const int64_t j = it / n_groups;
-            const int z0 = (int)(it % n_groups) * TC_G;
+            const int z = grp * TC_G + zl;
             const int sl = (int)(k & 1);
-            const uint4 *Yj = reinterpret_cast<const uint4 *>(Y + j * TC_S_BF16);
-            uint4 yv[4], gv[TC_G][4];
+            const uint4 *Gz = G + (z < K ? z : 0) * (TC_S_BF16 / 4) + 8 * hp * TC_R + idx;
+            uint4 yv[8], gv[8];
 #pragma unroll
-            for (int q = 0; q < 4; q++) yv[q] = __ldg(Yj + (64 * (4 * n1q + q) + 4 * n2q) / 4);
-#pragma unroll
-            for (int zl = 0; zl < TC_G; zl++) {
-                const int z = z0 + zl;
-                const uint4 *Gz = reinterpret_cast<const uint4 *>(G + (int64_t)(z < K ? z : 0) * TC_S_BF16);
-#pragma unroll
-                for (int q = 0; q < 4; q++)
-                    gv[zl][q] = z < K ? __ldg(Gz + (64 * (4 * n1q + q) + 4 * n2q) / 4) : make_uint4(0, 0, 0, 0);
+            for (int c = 0; c < 8; c++) {
+                yv[c] = __ldg(Yj + c * TC_R);
+                gv[c] = z < K ? __ldg(Gz + c * TC_R) : make_uint4(0, 0, 0, 0);
             }
             if (k >= 2 && !ws_wait(&bars->s1_done[sl], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
-            unsigned char *b1 = smem + OFF_B1 + sl * B_TILE;
+            tc::fence_after_thread_sync();
+            // conj(y) g: Re = yr gr + yi gi, Im = yr gi - yi gr, two n1 per packed pair; written in
+            // place over the spectrum words and stored as two 16-column halves
 #pragma unroll
-            for (int zl = 0; zl < TC_G; zl++) {
-                uint32_t w[4][4];                                  // [n2 offset e][n1 offset q]
+            for (int hh = 0; hh < 2; hh++) {
+                uint32_t w[16];
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const uint32_t ys[4] = {yv[q].x, yv[q].y, yv[q].z, yv[q].w};
-                    const uint32_t gs[4] = {gv[zl][q].x, gv[zl][q].y, gv[zl][q].z, gv[zl][q].w};
+                for (int c = 0; c < 4; c++) {
+                    const uint4 yq = yv[4 * hh + c], gq = gv[4 * hh + c];
+                    const uint32_t ys[4] = {yq.x, yq.y, yq.z, yq.w};
+                    const uint32_t gs[4] = {gq.x, gq.y, gq.z, gq.w};
 #pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        // conj(y) g = (yr, yr) (gr, gi) + (yi, yi) (gi, -gr), in packed BF16 arithmetic
-                        using V = typename Ops::V;
-                        const V y = *reinterpret_cast<const V *>(&ys[e]);
-                        const V g = *reinterpret_cast<const V *>(&gs[e]);
-                        V gb = __lowhigh2highlow(g);
-                        *reinterpret_cast<uint32_t *>(&gb) ^= 0x80000000u;
-                        const V x = __hfma2(Ops::high2(y), gb, __hmul2(Ops::low2(y), g));
-                        w[e][q] = *reinterpret_cast<const uint32_t *>(&x);
+                    for (int e = 0; e < 4; e += 2) {
+                        const V yr = *reinterpret_cast<const V *>(&ys[e]), yi = *reinterpret_cast<const V *>(&ys[e + 1]);
+                        const V gr = *reinterpret_cast<const V *>(&gs[e]), gi = *reinterpret_cast<const V *>(&gs[e + 1]);
+                        const V re = __hfma2(yi, gi, __hmul2(yr, gr));
+                        const V im = __hfma2(__hneg2(yi), gr, __hmul2(yr, gi));
+                        w[4 * c + e] = *reinterpret_cast<const uint32_t *>(&re);
+                        w[4 * c + e + 1] = *reinterpret_cast<const uint32_t *>(&im);
                     }
                 }
+                tc::tmem_st16(tbase + lane_base + COL_A1 + sl * (TC_K / 2) + 32 * hp + 16 * hh, w);
+            }
+            tc::tmem_st_wait();
+            tc::fence_before_thread_sync();
+            mbar_arrive(&bars->a1_full[sl]);
+            if (++grp == n_groups) {
+                grp = 0;
+                Yj += TC_S_BF16 / 4;
+            }
+        }
+    } else if (warp < WS_E2) {
+        // ---------------------------------------------------------------- epilogue 1
+        // thread -> D1 row (zl, n2 = idx), k1 in [32 h, 32 h + 32)
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_WIDE));
+        const int h = (warp - WS_E1) >> 2;
+        float2 wx[4], wy[4], nwy[4];                    // W_S^{n2 q}, q = 2 i, 2 i + 1
 #pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const int c = zl * TC_R + 4 * n2q + e;
-                    *reinterpret_cast<uint4 *>(b1 + tc::kmajor_offset_strided(B_SBO, B_LBO, c, 8 * n1q)) =
-                        make_uint4(w[e][0], w[e][1], w[e][2], w[e][3]);
+        for (int i = 0; i < 4; i++) {
+            const float2 t0 = __ldg(tw + (2 * i) * TC_R + idx), t1 = __ldg(tw + (2 * i + 1) * TC_R + idx);
+            wx[i] = make_float2(t0.x, t1.x);
+            wy[i] = make_float2(t0.y, t1.y);
+            nwy[i] = make_float2(-t0.y, -t1.y);
+        }
+        float bx[4], by[4];                             // W_S^{n2 k0}, k0 = 32 h + 8 g
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+            const float2 b = __ldg(tw + (32 * h + 8 * g) * TC_R + idx);
+            bx[g] = b.x;
+            by[g] = b.y;
+        }
+        // A2 byte offset of (m = 64 zl + 32 h, k = n2); k = 64 + n2 (imaginary part) is 8 A2_CK further
+        const uint32_t a2_row = (uint32_t)(8 * zl + 4 * h) * A2_CM + (uint32_t)(idx >> 3) * A2_CK + (idx & 7) * 16;
+        for (int64_t k = 0; k < n_my; k++) {
+            const int sl = (int)(k & 1);
+            if (!ws_wait(&bars->s1_done[sl], (uint32_t)((k >> 1) & 1), abort_flag)) break;
+            if (k >= 2 && !ws_wait(&bars->s2_done[sl], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+            tc::fence_after_thread_sync();
+            unsigned char *a2 = smem + OFF_A2 + sl * TILE_BYTES + a2_row;
+#pragma unroll
+            for (int gg = 0; gg < 2; gg++) {
+                uint32_t rr[16], ri[16];
+                tc::tmem_ld16(tbase + lane_base + COL_D1 + sl * TC_N + 32 * h + 16 * gg, rr);
+                tc::tmem_ld16(tbase + lane_base + COL_D1 + sl * TC_N + TC_R + 32 * h + 16 * gg, ri);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int g2 = 0; g2 < 2; g2++) {
+                    const int g = 2 * gg + g2;
+                    const float2 BX = make_float2(bx[g], bx[g]), BY = make_float2(by[g], by[g]);
+                    const float2 NBY = make_float2(-by[g], -by[g]);
+                    uint32_t ore[4], oim[4];
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const float2 dr = u2f2(rr[8 * g2 + 2 * i], rr[8 * g2 + 2 * i + 1]);
+                        const float2 di = u2f2(ri[8 * g2 + 2 * i], ri[8 * g2 + 2 * i + 1]);
+                        const float2 er = __ffma2_rn(dr, wx[i], __fmul2_rn(di, nwy[i]));
+                        const float2 ei = __ffma2_rn(dr, wy[i], __fmul2_rn(di, wx[i]));
+                        const float2 yr = __ffma2_rn(er, BX, __fmul2_rn(ei, NBY));
+                        const float2 yi = __ffma2_rn(er, BY, __fmul2_rn(ei, BX));
+                        ore[i] = Ops::pack(yr.x, yr.y);
+                        oim[i] = Ops::pack(yi.x, yi.y);
+                    }
+                    *reinterpret_cast<uint4 *>(a2 + g * A2_CM) = make_uint4(ore[0], ore[1], ore[2], ore[3]);
+                    *reinterpret_cast<uint4 *>(a2 + g * A2_CM + 8 * A2_CK) = make_uint4(oim[0], oim[1], oim[2], oim[3]);
                 }
             }
+            tc::fence_before_thread_sync();
             tc::fence_proxy_async_smem();
-            mbar_arrive(&bars->b1_full[sl]);
+            mbar_arrive(&bars->b2_full[sl]);
         }
     } else {
-        // ---------------------------------------------------------------- epilogues
-        const bool epi1 = warp < WS_E2;
-        const int quad = warp & 3;                      // TMEM lane quadrant this warp may access
-        const int half = ((warp - (epi1 ? WS_E1 : WS_E2)) >> 2) & 1;   // which 64 of the 128 columns
-        const int lrow = 32 * quad + lane;              // TMEM lane = GEMM row = (zl, n2) or (zl, k1)
-        const int zl = lrow >> 6, idx = lrow & 63;
-        const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+        // ---------------------------------------------------------------- epilogue 2
+        // thread -> D2 row (zl, k1 = idx), k2 in [32 h, 32 h + 32)
+        const int h = (warp - WS_E2) >> 2;
+        const int kl = L / TC_R;                        // k2 < L / 64  <=>  bin t = k1 + 64 k2 < L
+        int64_t j = it0 / n_groups;
+        int grp = (int)(it0 % n_groups);
         for (int64_t k = 0; k < n_my; k++) {
-            const int64_t it = it0 + k;
             const int sl = (int)(k & 1);
-            const uint32_t par = (uint32_t)((k >> 1) & 1);
-            if (epi1) {
-                // idx = n2; columns (k1, p) for k1 in [32 half, 32 half + 32)
-                if (!ws_wait(&bars->s1_done[sl], par, abort_flag)) break;
-                if (k >= 2 && !ws_wait(&bars->s2_done[sl], par ^ 1u, abort_flag)) break;   // A2[sl] free
-                tc::fence_after_thread_sync();
-                unsigned char *a2 = smem + OFF_A2 + sl * A2_TILE;
-                const float2 *twr = sTw + idx * TW_LD;                      // W_S^{n2 k1}, row n2
-#pragma unroll 1
-                for (int ch2 = 0; ch2 < 4; ch2 += 2) {
-                    uint32_t rr[2][16];
-                    tc::tmem_ld16(tbase + lane_base + sl * TC_N + 64 * half + 16 * ch2, rr[0]);
-                    tc::tmem_ld16(tbase + lane_base + sl * TC_N + 64 * half + 16 * ch2 + 16, rr[1]);
-                    tc::tmem_ld_wait();
+            if (!ws_wait(&bars->s2_done[sl], (uint32_t)((k >> 1) & 1), abort_flag)) break;
+            tc::fence_after_thread_sync();
+            const int z = grp * TC_G + zl;
+            const int64_t r0 = j * L;
+            const float us = unscale ? __ldg(unscale + j) : 1.0f;
+            if (++grp == n_groups) {                    // the next item
+                grp = 0;
+                j++;
+            }
+            // stored k2 (this thread): k2 < kmax, from t < L, r0 + t < nb and z < K
+            const int64_t rest = nb - r0 - idx;
+            const int64_t kr = (rest + TC_R - 1) / TC_R;
+            int kmax = rest <= 0 ? 0 : (kr < (int64_t)kl ? (int)kr : kl);
+            if (z >= K) kmax = 0;
+            kmax -= 32 * h;
+            float pw[32];
 #pragma unroll
-                    for (int hh = 0; hh < 2; hh++) {
-                        const int k1_0 = 32 * half + 8 * (ch2 + hh);
-                        const float4 *tp = reinterpret_cast<const float4 *>(twr + k1_0);
-#pragma unroll
-                        for (int q2 = 0; q2 < 4; q2++) {
-                            const float4 t2 = tp[q2];
-#pragma unroll
-                            for (int u = 0; u < 2; u++) {
-                                const int q = 2 * q2 + u;
-                                const float re = __uint_as_float(rr[hh][2 * q]), im = __uint_as_float(rr[hh][2 * q + 1]);
-                                const float tx = u ? t2.z : t2.x, ty = u ? t2.w : t2.y;
-                                const uint32_t wv = Ops::pack(re * tx - im * ty, re * ty + im * tx);
-                                const int row = zl * TC_R + k1_0 + q;
-                                *reinterpret_cast<uint32_t *>(a2 + tc::kmajor_offset_strided(A2_SBO, A2_LBO, row, 2 * idx)) = wv;
-                            }
-                        }
-                    }
+            for (int gg = 0; gg < 2; gg++) {
+                uint32_t rr[16], ri[16];
+                tc::tmem_ld16(tbase + lane_base + COL_D2 + 32 * h + 16 * gg, rr);
+                tc::tmem_ld16(tbase + lane_base + COL_D2 + TC_R + 32 * h + 16 * gg, ri);
+                tc::tmem_ld_wait();
+                if (gg == 1) {                                           // D2 drained
+                    tc::fence_before_thread_sync();
+                    mbar_arrive(&bars->d2_free);
                 }
-                tc::fence_before_thread_sync();
-                tc::fence_proxy_async_smem();
-                mbar_arrive(&bars->b2_full[sl]);
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    const float2 re = u2f2(rr[2 * i], rr[2 * i + 1]), im = u2f2(ri[2 * i], ri[2 * i + 1]);
+                    const float2 p = __ffma2_rn(re, re, __fmul2_rn(im, im));
+                    pw[16 * gg + 2 * i] = p.x;
+                    pw[16 * gg + 2 * i + 1] = p.y;
+                }
+            }
+            typename Ops::Out *prow = plane + (int64_t)(z < K ? z : 0) * nb + r0 + idx + 64 * 32 * h;
+            if (kmax >= 32) {
+#pragma unroll
+                for (int i = 0; i < 32; i++) prow[64 * i] = Ops::out(pw[i], us);
             } else {
-                // idx = k1; columns (k2, p) for k2 in [32 half, 32 half + 32)
-                if (!ws_wait(&bars->s2_done[sl], par, abort_flag)) break;
-                tc::fence_after_thread_sync();
-                const int64_t j = it / n_groups;
-                const int z = (int)(it % n_groups) * TC_G + zl;
-                const int64_t r0 = j * L;
-                const float us = unscale ? __ldg(unscale + j) : 1.0f;
-                typename Ops::Out *prow = plane + (int64_t)(z < K ? z : 0) * nb + r0 + idx;
-#pragma unroll 1
-                for (int ch2 = 0; ch2 < 4; ch2 += 2) {
-                    uint32_t rr[2][16];
-                    tc::tmem_ld16(tbase + lane_base + (2 + sl) * TC_N + 64 * half + 16 * ch2, rr[0]);
-                    tc::tmem_ld16(tbase + lane_base + (2 + sl) * TC_N + 64 * half + 16 * ch2 + 16, rr[1]);
-                    tc::tmem_ld_wait();
 #pragma unroll
-                    for (int hh = 0; hh < 2; hh++) {
-                        const int k2_0 = 32 * half + 8 * (ch2 + hh);
-#pragma unroll
-                        for (int q = 0; q < 8; q++) {
-                            const int t = idx + 64 * (k2_0 + q);
-                            if (z < K && t < L && r0 + t < nb) {
-                                const float re = __uint_as_float(rr[hh][2 * q]), im = __uint_as_float(rr[hh][2 * q + 1]);
-                                prow[64 * (k2_0 + q)] = Ops::out(re * re + im * im, us);
-                            }
-                        }
-                    }
-                }
-                tc::fence_before_thread_sync();
-                mbar_arrive(&bars->d2_free[sl]);
+                for (int i = 0; i < 32; i++)
+                    if (i < kmax) prow[64 * i] = Ops::out(pw[i], us);
             }
         }
     }
@@ -432,6 +492,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const typename Ops:
 // dropped): three MMAs per K step, FP32 accumulation in TMEM.  Inputs are the FP32 segment
 // spectra and the FP32 templates; the plane is stored in FP32.  Same transposed two-stage
 // DFT as above, one item at a time per CTA (synchronous), 8 warps.
+// B1 tiles (stage-1 A operand, K-major): core matrices 144 B apart along M, 16 x 144 B along K
+constexpr uint32_t B_SBO = 144, B_LBO = 16 * B_SBO;
+constexpr uint32_t B_TILE = 16 * B_LBO;                      // 36 KB
+// A2 tiles (stage-2 A operand, K-major): 128 B along M, 2064 B (16 mod 128) along K
+constexpr uint32_t A2_SBO = 128, A2_LBO = 16 * 128 + 16;
+constexpr uint32_t A2_TILE = 16 * A2_LBO;                    // 32.25 KB
 constexpr int SP_THREADS = 256;
 constexpr uint32_t SP_OFF_FHI = 0;
 constexpr uint32_t SP_OFF_FLO = TILE_BYTES;
@@ -611,30 +677,50 @@ uint16_t host_bf16(float f) {
 }
 }  // namespace
 
-// Host tables of the tensor path: F'[(k,p),(n,s)] (W_64^{kn} real-ified, re/im interleaved) as a
-// K-major BF16 operand image, and the four-step twiddles W_4096^{n2 k1}; FP64 then rounded.
+// Host tables of the tensor path, FP64 then rounded once:
+//  - the split variant's F'[(k,p),(n,s)] (real-ified W_64^{kn}, re/im interleaved), K-major BF16
+//    images hi and lo;
+//  - F1 (stage 1: rows (p, k1), K in the stage-1 order) and F2 (stage 2: rows (p, k2), K = (s, n2)),
+//    K-major, in BF16 and in FP16;
+//  - the four-step twiddles W_4096^{n2 k1}, [k1][n2].
+// Entry (p, s) of the real-ified W_64^{kn}: [[Re w, -Im w], [Im w, Re w]].
+static double dft64_real(int k, int n, int p, int s) {
+    const int e = (k * n) % TC_R;
+    double f = 2.0 * e / TC_R;
+    if (f > 1.0) f -= 2.0;
+    const double wr = std::cos(M_PI * f), wi = -std::sin(M_PI * f);
+    return p == 0 ? (s == 0 ? wr : -wi) : (s == 0 ? wi : wr);
+}
+
 cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st) {
-    std::vector<uint16_t> img(TC_M * TC_K, 0), img_lo(TC_M * TC_K, 0), img_h(TC_M * TC_K, 0);
+    const size_t T = (size_t)TC_M * TC_K;
+    std::vector<uint16_t> img(4 * T, 0), img_h(2 * T, 0);
+    auto put = [&](size_t tile, int row, int k, double v) {
+        const uint32_t o = tc::kmajor_offset(TC_M, row, k) / 2;
+        img[tile * T + o] = host_bf16((float)v);
+        if (tile >= 2) {
+            const __half h = __float2half_rn((float)v);
+            std::memcpy(&img_h[(tile - 2) * T + o], &h, 2);
+        }
+    };
     for (int k = 0; k < TC_R; k++)
-        for (int n = 0; n < TC_R; n++) {
-            const int e = (k * n) % TC_R;
-            double f = 2.0 * e / TC_R;
-            if (f > 1.0) f -= 2.0;
-            const double wr = std::cos(M_PI * f), wi = -std::sin(M_PI * f);
-            const float v[2][2] = {{(float)wr, (float)-wi}, {(float)wi, (float)wr}};
-            const double vd[2][2] = {{wr, -wi}, {wi, wr}};
+        for (int n = 0; n < TC_R; n++)
             for (int pr = 0; pr < 2; pr++)
                 for (int sg = 0; sg < 2; sg++) {
+                    const double v = dft64_real(k, n, pr, sg);
                     const uint32_t o = tc::kmajor_offset(TC_M, 2 * k + pr, 2 * n + sg) / 2;
-                    img[o] = host_bf16(v[pr][sg]);
+                    img[o] = host_bf16((float)v);
                     uint32_t hb = (uint32_t)img[o] << 16;
                     float hf;
                     std::memcpy(&hf, &hb, 4);
-                    img_lo[o] = host_bf16((float)(vd[pr][sg] - (double)hf));
-                    const __half h = __float2half_rn(v[pr][sg]);
-                    std::memcpy(&img_h[o], &h, 2);
+                    img[T + o] = host_bf16((float)(v - (double)hf));
                 }
-        }
+    for (int pr = 0; pr < 2; pr++)
+        for (int k = 0; k < TC_R; k++)
+            for (int kk = 0; kk < TC_K; kk++) {
+                put(2, TC_R * pr + k, kk, dft64_real(k, s1_n1(kk), pr, s1_s(kk)));     // F1
+                put(3, TC_R * pr + k, kk, dft64_real(k, kk & 63, pr, kk >> 6));         // F2
+            }
     std::vector<float2> tw(TC_R * TC_R);
     for (int k1 = 0; k1 < TC_R; k1++)
         for (int n2 = 0; n2 < TC_R; n2++) {
@@ -645,9 +731,6 @@ cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st) {
         }
     cudaError_t e = cudaMemcpyAsync(p.d_tcF, img.data(), img.size() * 2, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(static_cast<char *>(p.d_tcF) + img.size() * 2, img_lo.data(), img_lo.size() * 2,
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
         e = cudaMemcpyAsync(p.d_tcTw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && p.d_tcFh)
         e = cudaMemcpyAsync(p.d_tcFh, img_h.data(), img_h.size() * 2, cudaMemcpyHostToDevice, st);
@@ -655,14 +738,26 @@ cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st) {
     return e;
 }
 
+// The register hand-over inside k3_plane_tc (setmaxnreg) assumes the launch allocation the kernel
+// was compiled for; a different one could leave the increasing warps waiting, so it is checked
+// before every launch.
+template <class Ops>
+static cudaError_t prepare_plane_tc() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k3_plane_tc<Ops>);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs != REG_LAUNCH) return cudaErrorInvalidDeviceFunction;
+    return cudaFuncSetAttribute(k3_plane_tc<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM);
+}
+
 cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
                               __nv_bfloat16 *d_plane, cudaStream_t st) {
     if (p.S != TC_S_BF16) return cudaErrorInvalidValue;
-    __nv_bfloat162 *Y = reinterpret_cast<__nv_bfloat162 *>(ws + p.ws_y);
+    uint4 *Y = reinterpret_cast<uint4 *>(ws + p.ws_y);
     const size_t smem2 = sizeof(float2) * fft_smem_entries(TC_S_BF16);
     cudaError_t e = cudaFuncSetAttribute(k2_segments_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k3_plane_tc<OpsBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM);
+    e = prepare_plane_tc<OpsBF16>();
     if (e != cudaSuccess) return e;
     p.prof.begin(FDAS_STAGE_SEGMENTS, st);
     k2_segments_bf16<<<(unsigned)p.n_seg, TC_S_BF16 / 32, smem2, st>>>(d_x, d_scale, p.d_tw, Y, p.nb, p.L, p.m / 2);
@@ -678,8 +773,8 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
     const int64_t grid = (n_items + per - 1) / per;
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_tc<OpsBF16><<<(unsigned)grid, WS_THREADS, WS_SMEM, st>>>(
-        Y, p.d_Gbf, reinterpret_cast<const uint4 *>(p.d_tcF), p.d_tcTw, d_plane, p.K, p.nb, p.L, n_items, n_groups,
-        per, nullptr, p.d_status);
+        Y, reinterpret_cast<const uint4 *>(p.d_Gbf), reinterpret_cast<const uint4 *>(p.d_tcF) + 2 * TILE_BYTES / 16,
+        p.d_tcTw, d_plane, p.K, p.nb, p.L, n_items, n_groups, per, nullptr, p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 2;
     return cudaGetLastError();
@@ -689,12 +784,12 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
 cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
                              cudaStream_t st) {
     if (p.S != TC_S_BF16 || !p.d_Gh || !p.d_tcFh) return cudaErrorInvalidValue;
-    __half2 *Y = reinterpret_cast<__half2 *>(ws + p.ws_y);
+    uint4 *Y = reinterpret_cast<uint4 *>(ws + p.ws_y);
     float *unscale = reinterpret_cast<float *>(ws + p.ws_segscale);
     const size_t smem2 = sizeof(float2) * fft_smem_entries(TC_S_BF16);
     cudaError_t e = cudaFuncSetAttribute(k2_segments_f16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k3_plane_tc<OpsF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM);
+    e = prepare_plane_tc<OpsF16>();
     if (e != cudaSuccess) return e;
     p.prof.begin(FDAS_STAGE_SEGMENTS, st);
     k2_segments_f16<<<(unsigned)p.n_seg, TC_S_BF16 / 32, smem2, st>>>(d_x, d_scale, p.d_tw, Y, unscale,
@@ -711,8 +806,8 @@ cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_sc
     const int64_t grid = (n_items + per - 1) / per;
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_tc<OpsF16><<<(unsigned)grid, WS_THREADS, WS_SMEM, st>>>(
-        Y, p.d_Gh, reinterpret_cast<const uint4 *>(p.d_tcFh), p.d_tcTw, d_plane, p.K, p.nb, p.L, n_items, n_groups,
-        per, unscale, p.d_status);
+        Y, reinterpret_cast<const uint4 *>(p.d_Gh), reinterpret_cast<const uint4 *>(p.d_tcFh), p.d_tcTw, d_plane,
+        p.K, p.nb, p.L, n_items, n_groups, per, unscale, p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 2;
     return cudaGetLastError();

@@ -2,11 +2,17 @@
 // GPUs (GB300 = sm_103a): TMEM allocation, shared-memory matrix descriptors, BF16 MMA with
 // FP32 accumulation into TMEM, completion through an mbarrier, and TMEM loads.
 //
-// Operand layout used throughout: "K-major, no swizzle".  A row-major R x K tile (R = M for A,
+// Operand layouts.  "K-major, no swizzle" (the default):  A row-major R x K tile (R = M for A,
 // N for B) is stored as 8x8 core matrices (8 rows x 16 bytes, rows 16 bytes apart); the core
 // matrix holding (row, k) starts at ((k / 8) * (R / 8) + row / 8) * 128 bytes, so core
 // matrices adjacent along R are 128 bytes apart (stride byte offset) and along K R * 16 bytes
 // apart (leading byte offset).  One MMA consumes K = 16 (two core matrices along K).
+// "MN-major, no swizzle" (A only, instruction-descriptor bit 15): a core matrix holds 8 K-rows of
+// 8 consecutive M elements (16 bytes each); element (m, k) of an M-row tile sits at
+// (m / 8) * CM + (k / 8) * CK + (k % 8) * 16 + (m % 8) * 2, and the descriptor takes the K-direction
+// stride CK as its leading byte offset and the M-direction stride CM as its stride byte offset.
+// A in TMEM (kind::f16): lane m holds row m; 32-bit column c holds elements k = 2c (low half) and
+// 2c + 1 (high half), so one MMA's K = 16 spans 8 columns.
 #pragma once
 
 #include <cstdint>
@@ -123,6 +129,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+// The same with A read from TMEM at column address a_tmem (lane 0 = row 0).
+__device__ __forceinline__ void mma_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive on the mbarrier once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -141,6 +158,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------- registers -> TMEM
+// 32 lanes x 32 bits, 32 consecutive columns: thread i of the warp writes lane (base + i).
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+// Wait until this thread's TMEM stores have completed.
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 }  // namespace tc
 }  // namespace fdas
