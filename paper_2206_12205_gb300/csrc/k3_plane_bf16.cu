@@ -163,20 +163,25 @@ __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_f16(const float2 *
 // MN-major: the 8 consecutive k1 of one (z, n2, s) are one 16-byte row of a core matrix, which is
 // what an epilogue-1 thread (one n2, consecutive k1) writes in one store; the tensor core reads the
 // transposed operand from it.
-//   warp 0       TMEM allocation; lane 0 issues the MMAs (stage 1 of item i+1 before stage 2 of i);
-//                warps 1-3 idle (they complete warpgroup 0 for the register hand-over)
+//   warp 0       TMEM allocation; issues the stage-1 MMAs
+//   warp 1       issues the stage-2 MMAs (warps 2-3 idle: they complete warpgroup 0 for the
+//                register hand-over)
 //   warps 4-11   producer:   A1[slot] row (z, n2), half of its 64 columns, = conj(Yhat_j) G_z in packed
 //                16-bit arithmetic, written with tcgen05.st
 //   warps 12-19  epilogue 1: D1[slot] -> W_S^{n2 k1} (FP32, packed pairs) -> A2[slot]; warps 12-15 and
 //                16-19 take the two halves of k1
 //   warps 20-27  epilogue 2: D2 -> |.|^2 -> plane (halves of k2)
-// TMEM (512 columns): D1 slots at columns 0 and 128, D2 at 256, A1 slots (64 columns) at 384, 448.
-// Shared memory: F1, F2 (32 KB each) and two A2 slots (32 KB each).  Hand-offs are mbarriers:
-//   a1_full[s]  (256 producer arrivals)     s1_done[s] (MMA commit: D1 ready, A1 free)
-//   b2_full[s]  (256 epilogue-1 arrivals: A2 ready, D1 drained)
-//   s2_done[s]  (MMA commit: D2 ready, A2 free)       d2_free (256 epilogue-2 arrivals: D2 drained)
-// The k-th use of a slot waits for phase parity k & 1; every wait is bounded and also gives
-// up when another role has aborted.  The twiddle W_S^{n2 k1} with k1 = k0 + q (k0 a multiple of
+// TMEM (512 columns): three accumulator slots of 128 columns (item k uses slot k mod 3 for D1 and,
+// once epilogue 1 has drained it, for D2) and two A1 slots of 64 columns (item k: k mod 2).
+// Shared memory: F1, F2 (32 KB each) and two A2 slots (32 KB each, item k: k mod 2).
+// Hand-offs are mbarriers, each with one signalling and one waiting role:
+//   a1_full[2]  producer -> MMA (256 arrivals)        a1_free[2]  MMA commit after stage 1 -> producer
+//   d1_full[3]  MMA commit after stage 1 -> epi 1      b2_full[2]  epi 1 -> MMA (256: A2 ready, D1 read)
+//   a2_free[2]  MMA commit after stage 2 -> epi 1      d2_full[3]  MMA commit after stage 2 -> epi 2
+//   d_free[3]   epi 2 -> MMA (256 arrivals: accumulator slot drained)
+// The u-th use of a barrier waits for phase parity u & 1; a role can never be two phases behind
+// (the next phase of every barrier depends on the waiting role's own progress).  Every wait is
+// bounded and also gives up when another role has aborted.  The twiddle W_S^{n2 k1} with k1 = k0 + q (k0 a multiple of
 // 8) is applied as W_S^{n2 q} (per-thread pairs held in registers) then W_S^{n2 k0}.
 constexpr int WS_P0 = 4;                                     // first producer warp
 constexpr int WS_PRODUCERS = 256;                            // warps 4-11
@@ -184,10 +189,10 @@ constexpr int WS_E1 = WS_P0 + WS_PRODUCERS / 32;             // first epilogue-1
 constexpr int WS_E2 = WS_E1 + 8;                             // first epilogue-2 warp (20)
 constexpr int WS_THREADS = (WS_E2 + 8) * 32;                 // 28 warps = 7 warpgroups
 // Registers: 72 a thread at launch (7 warps on each SM sub-partition).  Warpgroup 0 (the MMA
-// warp and three idle warps) gives 32 back; the producers and epilogue 1 take 8 more:
-// 128 x 40 + 256 x 80 + 256 x 80 + 256 x 72 = 896 x 72.
-constexpr int REG_LAUNCH = 72, REG_MMA = 40, REG_WIDE = 80;
-static_assert(128 * REG_MMA + 512 * REG_WIDE + 256 * REG_LAUNCH == WS_THREADS * REG_LAUNCH,
+// warp and three idle warps) and epilogue 2 give 16 and 8 back; the producers and epilogue 1
+// take 8 more: 128 x 56 + 256 x 80 + 256 x 80 + 256 x 64 = 896 x 72.
+constexpr int REG_LAUNCH = 72, REG_MMA = 56, REG_WIDE = 80, REG_E2 = 64;
+static_assert(128 * REG_MMA + 512 * REG_WIDE + 256 * REG_E2 == WS_THREADS * REG_LAUNCH,
               "register split must add up to the launch allocation");
 constexpr uint32_t A2_CM = 128, A2_CK = (TC_M / 8) * 128;    // A2 MN-major: core matrices along M, K
 constexpr uint32_t F_LBO = TC_M * 16, F_SBO = 128;           // F1, F2: dense K-major
@@ -196,13 +201,14 @@ constexpr uint32_t OFF_A2 = 2 * TILE_BYTES;                  // 2 slots
 constexpr uint32_t OFF_BAR = OFF_A2 + 2 * TILE_BYTES;
 constexpr uint32_t WS_SMEM = OFF_BAR + 256;
 constexpr uint32_t WS_TMEM_COLS = 512;
-constexpr uint32_t COL_D1 = 0, COL_D2 = 2 * TC_N, COL_A1 = 3 * TC_N;
+constexpr uint32_t COL_A1 = 3 * TC_N;                        // accumulator slots at 0, 128, 256
 
 struct WsBars {
-    uint64_t a1_full[2], s1_done[2], b2_full[2], s2_done[2], d2_free, drain;
+    uint64_t a1_full[2], a1_free[2], d1_full[3], b2_full[2], a2_free[2], d2_full[3], d_free[3], drain[2];
 };
 
 __device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!tc::mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
@@ -244,12 +250,17 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
     if (tid == 0) {
         for (int s = 0; s < 2; s++) {
             tc::mbar_init(&bars->a1_full[s], WS_PRODUCERS);
-            tc::mbar_init(&bars->s1_done[s], 1);
+            tc::mbar_init(&bars->a1_free[s], 1);
             tc::mbar_init(&bars->b2_full[s], 256);
-            tc::mbar_init(&bars->s2_done[s], 1);
+            tc::mbar_init(&bars->a2_free[s], 1);
         }
-        tc::mbar_init(&bars->d2_free, 256);
-        tc::mbar_init(&bars->drain, 1);
+        for (int s = 0; s < 3; s++) {
+            tc::mbar_init(&bars->d1_full[s], 1);
+            tc::mbar_init(&bars->d2_full[s], 1);
+            tc::mbar_init(&bars->d_free[s], 256);
+        }
+        tc::mbar_init(&bars->drain[0], 1);
+        tc::mbar_init(&bars->drain[1], 1);
         *abort_flag = 0;
     }
     for (int i = tid; i < (int)(2 * TILE_BYTES / 16); i += WS_THREADS)
@@ -269,49 +280,59 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
     const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
 
     if (warp < WS_P0) {
-        // ---------------------------------------------------------------- MMA issuer
+        // ---------------------------------------------------------------- MMA issuers
+        // Warp 0 issues stage 1, warp 1 stage 2: the tensor pipe queues only a few MMAs, so
+        // while one issuer waits on its barriers the other keeps it fed.  Each warp runs its loop
+        // (waits included) in converged control flow and one elected lane issues each MMA and
+        // commit; a commit covers the MMAs of its own warp.
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_MMA));
-        if (warp == 0 && lane == 0 && n_my > 0) {
-            const uint32_t id1 = Ops::idesc, id2 = Ops::idesc | (1u << 15);      // stage 2: A MN-major
-            const uint32_t bF1 = tc::smem_u32(smem + OFF_F1), bF2 = tc::smem_u32(smem + OFF_F2);
-            auto stage1 = [&](int sl) {
-#pragma unroll
-                for (int s = 0; s < TC_K / 16; s++)
-                    tc::mma_tmem_a(tbase + COL_D1 + sl * TC_N, tbase + COL_A1 + sl * (TC_K / 2) + 8 * s,
-                                   tc::smem_desc(bF1 + s * 2 * F_LBO, F_LBO, F_SBO), id1, s > 0 ? 1u : 0u);
-                tc::mma_commit(&bars->s1_done[sl]);
+        if (warp < 2 && n_my > 0) {
+            auto wait = [&](uint64_t *bar, uint32_t parity) {
+                return __shfl_sync(0xffffffffu, (int)ws_wait(bar, parity, abort_flag), 0) != 0;
             };
-            auto stage2 = [&](int sl) {
-                const uint32_t a = tc::smem_u32(smem + OFF_A2 + sl * TILE_BYTES);
-#pragma unroll
-                for (int s = 0; s < TC_K / 16; s++)
-                    tc::mma_bf16(tbase + COL_D2, tc::smem_desc(a + s * 2 * A2_CK, A2_CK, A2_CM),
-                                 tc::smem_desc(bF2 + s * 2 * F_LBO, F_LBO, F_SBO), id2, s > 0 ? 1u : 0u);
-                tc::mma_commit(&bars->s2_done[sl]);
-            };
-            bool ok = ws_wait(&bars->a1_full[0], 0, abort_flag);
-            if (ok) {
-                tc::fence_after_thread_sync();
-                stage1(0);
-            }
-            for (int64_t k = 0; k < n_my && ok; k++) {
-                const int sl = (int)(k & 1);
-                if (k + 1 < n_my) {                                    // stage 1 of the next item
-                    const int sn = (int)((k + 1) & 1);
-                    ok = ws_wait(&bars->a1_full[sn], (uint32_t)(((k + 1) >> 1) & 1), abort_flag);
-                    if (!ok) break;
+            int s3 = 0, u3 = 0;                         // accumulator slot k mod 3 and its use count k / 3
+            if (warp == 0) {
+                const uint32_t id1 = Ops::idesc;
+                const uint64_t f1 = tc::smem_desc(tc::smem_u32(smem + OFF_F1), F_LBO, F_SBO);
+                for (int64_t k = 0; k < n_my; k++) {
+                    if (!wait(&bars->a1_full[k & 1], (uint32_t)((k >> 1) & 1))) break;
+                    if (u3 >= 1 && !wait(&bars->d_free[s3], (uint32_t)((u3 - 1) & 1))) break;
                     tc::fence_after_thread_sync();
-                    stage1(sn);
+                    const uint32_t d = tbase + (uint32_t)s3 * TC_N, a = tbase + COL_A1 + (uint32_t)(k & 1) * (TC_K / 2);
+#pragma unroll
+                    for (int s = 0; s < TC_K / 16; s++)       // descriptor start addresses: 16-byte units
+                        tc::mma_tmem_a_warp(d, a + 8 * s, f1 + (uint64_t)(s * 2 * F_LBO / 16), id1, s > 0 ? 1u : 0u);
+                    tc::mma_commit_warp(&bars->a1_free[k & 1]);
+                    tc::mma_commit_warp(&bars->d1_full[s3]);
+                    if (++s3 == 3) {
+                        s3 = 0;
+                        u3++;
+                    }
                 }
-                ok = ws_wait(&bars->b2_full[sl], (uint32_t)((k >> 1) & 1), abort_flag);   // A2 ready
-                if (ok && k >= 1) ok = ws_wait(&bars->d2_free, (uint32_t)((k - 1) & 1), abort_flag);
-                if (!ok) break;
-                tc::fence_after_thread_sync();
-                stage2(sl);
+            } else {
+                const uint32_t id2 = Ops::idesc | (1u << 15);                  // A MN-major
+                const uint64_t f2 = tc::smem_desc(tc::smem_u32(smem + OFF_F2), F_LBO, F_SBO);
+                const uint64_t a2 = tc::smem_desc(tc::smem_u32(smem + OFF_A2), A2_CK, A2_CM);
+                for (int64_t k = 0; k < n_my; k++) {
+                    if (!wait(&bars->b2_full[k & 1], (uint32_t)((k >> 1) & 1))) break;   // A2 ready, D1 read
+                    tc::fence_after_thread_sync();
+                    const uint32_t d = tbase + (uint32_t)s3 * TC_N;
+                    const uint64_t a = a2 + (uint64_t)((k & 1) * (TILE_BYTES / 16));
+#pragma unroll
+                    for (int s = 0; s < TC_K / 16; s++)
+                        tc::mma_bf16_warp(d, a + (uint64_t)(s * 2 * A2_CK / 16), f2 + (uint64_t)(s * 2 * F_LBO / 16),
+                                          id2, s > 0 ? 1u : 0u);
+                    tc::mma_commit_warp(&bars->a2_free[k & 1]);
+                    tc::mma_commit_warp(&bars->d2_full[s3]);
+                    if (++s3 == 3) {
+                        s3 = 0;
+                        u3++;
+                    }
+                }
             }
-            // drain: every MMA issued above has completed before TMEM can be released
-            tc::mma_commit(&bars->drain);
-            tc::mbar_wait_bounded(&bars->drain, 0, WAIT_CYCLES);
+            // drain: every MMA this warp issued has completed before TMEM can be released
+            tc::mma_commit_warp(&bars->drain[warp]);
+            tc::mbar_wait_bounded(&bars->drain[warp], 0, WAIT_CYCLES);
         }
         __syncwarp();
     } else if (warp < WS_E1) {
@@ -331,7 +352,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
                 yv[c] = __ldg(Yj + c * TC_R);
                 gv[c] = z < K ? __ldg(Gz + c * TC_R) : make_uint4(0, 0, 0, 0);
             }
-            if (k >= 2 && !ws_wait(&bars->s1_done[sl], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+            if (k >= 2 && !ws_wait(&bars->a1_free[sl], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
             tc::fence_after_thread_sync();
             // conj(y) g: Re = yr gr + yi gi, Im = yr gi - yi gr, two n1 per packed pair; written in
             // place over the spectrum words and stored as two 16-column halves
@@ -385,17 +406,19 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
         }
         // A2 byte offset of (m = 64 zl + 32 h, k = n2); k = 64 + n2 (imaginary part) is 8 A2_CK further
         const uint32_t a2_row = (uint32_t)(8 * zl + 4 * h) * A2_CM + (uint32_t)(idx >> 3) * A2_CK + (idx & 7) * 16;
+        int s3 = 0, u3 = 0;                             // slot k mod 3 and its use count k / 3
         for (int64_t k = 0; k < n_my; k++) {
             const int sl = (int)(k & 1);
-            if (!ws_wait(&bars->s1_done[sl], (uint32_t)((k >> 1) & 1), abort_flag)) break;
-            if (k >= 2 && !ws_wait(&bars->s2_done[sl], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+            const uint32_t dcol = (uint32_t)s3 * TC_N;
+            if (!ws_wait(&bars->d1_full[s3], (uint32_t)(u3 & 1), abort_flag)) break;
+            if (k >= 2 && !ws_wait(&bars->a2_free[sl], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
             tc::fence_after_thread_sync();
             unsigned char *a2 = smem + OFF_A2 + sl * TILE_BYTES + a2_row;
 #pragma unroll
             for (int gg = 0; gg < 2; gg++) {
                 uint32_t rr[16], ri[16];
-                tc::tmem_ld16(tbase + lane_base + COL_D1 + sl * TC_N + 32 * h + 16 * gg, rr);
-                tc::tmem_ld16(tbase + lane_base + COL_D1 + sl * TC_N + TC_R + 32 * h + 16 * gg, ri);
+                tc::tmem_ld16(tbase + lane_base + dcol + 32 * h + 16 * gg, rr);
+                tc::tmem_ld16(tbase + lane_base + dcol + TC_R + 32 * h + 16 * gg, ri);
                 tc::tmem_ld_wait();
 #pragma unroll
                 for (int g2 = 0; g2 < 2; g2++) {
@@ -421,17 +444,23 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
             tc::fence_before_thread_sync();
             tc::fence_proxy_async_smem();
             mbar_arrive(&bars->b2_full[sl]);
+            if (++s3 == 3) {
+                s3 = 0;
+                u3++;
+            }
         }
     } else {
         // ---------------------------------------------------------------- epilogue 2
         // thread -> D2 row (zl, k1 = idx), k2 in [32 h, 32 h + 32)
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_E2));
         const int h = (warp - WS_E2) >> 2;
         const int kl = L / TC_R;                        // k2 < L / 64  <=>  bin t = k1 + 64 k2 < L
         int64_t j = it0 / n_groups;
         int grp = (int)(it0 % n_groups);
+        int slot = 0, u3 = 0;                           // slot k mod 3 and its use count k / 3
         for (int64_t k = 0; k < n_my; k++) {
-            const int sl = (int)(k & 1);
-            if (!ws_wait(&bars->s2_done[sl], (uint32_t)((k >> 1) & 1), abort_flag)) break;
+            const uint32_t dcol = (uint32_t)slot * TC_N;
+            if (!ws_wait(&bars->d2_full[slot], (uint32_t)(u3 & 1), abort_flag)) break;
             tc::fence_after_thread_sync();
             const int z = grp * TC_G + zl;
             const int64_t r0 = j * L;
@@ -450,12 +479,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
 #pragma unroll
             for (int gg = 0; gg < 2; gg++) {
                 uint32_t rr[16], ri[16];
-                tc::tmem_ld16(tbase + lane_base + COL_D2 + 32 * h + 16 * gg, rr);
-                tc::tmem_ld16(tbase + lane_base + COL_D2 + TC_R + 32 * h + 16 * gg, ri);
+                tc::tmem_ld16(tbase + lane_base + dcol + 32 * h + 16 * gg, rr);
+                tc::tmem_ld16(tbase + lane_base + dcol + TC_R + 32 * h + 16 * gg, ri);
                 tc::tmem_ld_wait();
-                if (gg == 1) {                                           // D2 drained
+                if (gg == 1) {                                           // accumulator slot drained
                     tc::fence_before_thread_sync();
-                    mbar_arrive(&bars->d2_free);
+                    mbar_arrive(&bars->d_free[slot]);
                 }
 #pragma unroll
                 for (int i = 0; i < 8; i++) {
@@ -464,6 +493,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
                     pw[16 * gg + 2 * i] = p.x;
                     pw[16 * gg + 2 * i + 1] = p.y;
                 }
+            }
+            if (++slot == 3) {
+                slot = 0;
+                u3++;
             }
             typename Ops::Out *prow = plane + (int64_t)(z < K ? z : 0) * nb + r0 + idx + 64 * 32 * h;
             if (kmax >= 32) {
