@@ -203,6 +203,35 @@ def roofline_correlate(w, precision: str, prof):
             "hbm_GBps_algorithmic": (plane_b + n_seg * S * 4) / (ms / 1e3) / 1e9}
 
 
+def _gathers(w, levels):
+    """New harmonic terms read for the given harmonic levels: level H (H = 2^l) adds harmonics
+    H/2 + 1 .. H for each cell of its region (|H z| <= zmax, H r < Nb)."""
+    g = 0
+    for l in levels:
+        H = 1 << l
+        zl = (w.zmax // H) // 2 * 2
+        g += (zl + 1) * (w.nb // H) * (H // 2)
+    return g
+
+
+def roofline_peak_kernel(w, precision: str, kernel: str, prof):
+    """HBM roofline of one of the two peak-search kernels: k4_level1 reads the plane once;
+    k4_levels reads level 2's region of the plane (S_1) and every new harmonic term once."""
+    rec = prof["peaks_kernels"][kernel]
+    ms = rec["ms"] / max(1, rec["n_timed"])
+    eb = 2 if precision == "bf16" else 4
+    if kernel == "k4_level1":
+        nbytes = w.K * w.nb * eb
+    else:
+        zl = (w.zmax // 2) // 2 * 2
+        nbytes = ((zl + 1) * (w.nb // 2) + _gathers(w, range(1, 5))) * eb
+    ach = nbytes / (ms / 1e3) / 1e9
+    peak = MEASURED["hbm_gbs"]
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": _traffic(kernel, precision, w.name), "kernel": kernel, "avg_launch_ms": ms,
+            "bytes_per_launch": nbytes, "peak_note": "of measured: MEASURED_PEAKS hbm_gbs (copy bandwidth)"}
+
+
 def roofline_stage(w, precision: str, stage: str, prof):
     """HBM roofline of a bandwidth-shaped stage (peak search or the long FFT)."""
     n = max(1, prof["n_timed"][stage])
@@ -210,12 +239,7 @@ def roofline_stage(w, precision: str, stage: str, prof):
     eb = 2 if precision == "bf16" else 4
     if stage == "peaks":
         # the plane once, plus the H/2 new harmonic terms per cell of each level 2..16
-        gathers = 0
-        for l in range(1, 5):
-            H = 1 << l
-            zl = (w.zmax // H) // 2 * 2
-            gathers += (zl + 1) * (w.nb // H) * (H // 2)
-        nbytes = (w.K * w.nb + gathers) * eb
+        nbytes = (w.K * w.nb + _gathers(w, range(1, 5))) * eb
         kern = "k4_level1+k4_levels"
     else:
         nbytes = 6 * 8 * (w.nb)                                 # three passes, complex64 in and out
@@ -660,11 +684,20 @@ def own_arm(args):
         if "fp32" in paths and "bf16" in paths:
             paths["speedup_bf16_over_fp32"] = paths["bf16"]["value"] / paths["fp32"]["value"]
 
-    # ---- roofline of the dominant kernel of the step (largest per-step stage time)
-    stage_ms = {k: v / max(1, prof["n_timed"][k]) for k, v in prof["ms"].items()}
-    dominant = max(stage_ms, key=stage_ms.get)
+    # ---- roofline of the dominant kernel of the step (largest per-launch time): the correlation
+    # kernel, one of the two peak-search kernels, or a smaller stage's kernels
+    kernel_ms = {k: v / max(1, prof["n_timed"][k]) for k, v in prof["ms"].items() if k != "peaks"}
+    for k, rec in prof["peaks_kernels"].items():
+        if rec["n_timed"]:
+            kernel_ms[k] = rec["ms"] / rec["n_timed"]
+    dominant = max(kernel_ms, key=kernel_ms.get)
     roof_corr = roofline_correlate(w, precision, prof)
-    roof = roof_corr if dominant == "correlate" else roofline_stage(w, precision, dominant, prof)
+    if dominant == "correlate":
+        roof = roof_corr
+    elif dominant in ("k4_level1", "k4_levels"):
+        roof = roofline_peak_kernel(w, precision, dominant, prof)
+    else:
+        roof = roofline_stage(w, precision, dominant, prof)
 
     refine = None
     if rank == 0 and world == 1 and not args.no_refine and not args.quick:
@@ -694,6 +727,7 @@ def own_arm(args):
             "cpu_baseline": cpu, "e2e": e2e, "refine": refine, "batch": batch, "sensitivity": sensitivity,
             "gpu_launches": int(prof["launches"]), "clocks": clk,
             "stages_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
+            "peak_kernels_ms_per_step": {k: r["ms"] / args.steps for k, r in prof["peaks_kernels"].items()},
         }
         print(json.dumps(line))
     if dist is not None:

@@ -344,6 +344,8 @@ typedef struct {
     int64_t launches;       /* libfdas kernels launched by those calls                          */
     int64_t n_timed[4];     /* timed launch groups per stage: spectrum, segments, correlate, peaks */
     double  ms[4];          /* their summed event times in milliseconds                         */
+    int64_t n_timed_peaks[2]; /* inside the peaks stage: level-1 pass, level 2..16 pass          */
+    double  ms_peaks[2];    /* their summed event times in milliseconds                         */
 } fdas_profile;
 
 /* Stage indices of fdas_profile.ms / n_timed. */
@@ -351,6 +353,9 @@ typedef struct {
 #define FDAS_STAGE_SEGMENTS  1   /* K2: segment FFTs                                              */
 #define FDAS_STAGE_CORRELATE 2   /* K3: multiply, inverse FFT, |.|^2, overlap discard            */
 #define FDAS_STAGE_PEAKS     3   /* K4: harmonic sums and peak list                               */
+/* Indices of fdas_profile.ms_peaks / n_timed_peaks (single kernels inside FDAS_STAGE_PEAKS). */
+#define FDAS_PEAKS_LEVEL1    0   /* harmonic level 1 over the whole plane                         */
+#define FDAS_PEAKS_LEVELS    1   /* levels 2 .. 16 over level 2's region                          */
 
 /*
  * Turn per-stage timing on (enable != 0) or off.  Enabling creates CUDA events (plan-owned)

@@ -62,7 +62,7 @@ cudaError_t launch_plane_any(Plan *p, const float2 *x, const float *scale, char 
 
 extern "C" {
 
-int fdas_version(void) { return 100; }
+int fdas_version(void) { return 101; }
 
 const char *fdas_status_string(fdas_status s) {
     switch (s) {
@@ -360,7 +360,9 @@ fdas_status fdas_profile_read(fdas_plan_t plan, fdas_profile *out, int reset) {
     std::memset(out, 0, sizeof(*out));
     out->calls = pr.calls;
     out->launches = pr.launches;
-    if (pr.n[0] + pr.n[1] + pr.n[2] + pr.n[3] > 0) {
+    int any = 0;
+    for (int s = 0; s < fdas::PROF_STAGES; s++) any += pr.n[s];
+    if (any > 0) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return record(p, e);
         for (int s = 0; s < fdas::PROF_STAGES; s++) {
@@ -371,8 +373,13 @@ fdas_status fdas_profile_read(fdas_plan_t plan, fdas_profile *out, int reset) {
                 if (e != cudaSuccess) return record(p, e);
                 acc += ms;
             }
-            out->ms[s] = acc;
-            out->n_timed[s] = pr.n[s];
+            if (s < 4) {
+                out->ms[s] = acc;
+                out->n_timed[s] = pr.n[s];
+            } else {
+                out->ms_peaks[s - 4] = acc;
+                out->n_timed_peaks[s - 4] = pr.n[s];
+            }
         }
     }
     if (reset) {

@@ -31,7 +31,8 @@ __host__ __device__ constexpr uint32_t tc_s1_pos(int n1, int n2) {
 constexpr int TC_MAX_TAPS = 2048;
 
 // Per-stage CUDA-event timing (fdas_profile_enable / fdas_profile_read).
-constexpr int PROF_STAGES = 4;
+constexpr int PROF_STAGES = 6;                   // the four stages, then the two K4 passes
+constexpr int PROF_PEAKS_LEVEL1 = 4, PROF_PEAKS_LEVELS = 5;
 constexpr int PROF_CAP = 512;
 struct Profiler {
     bool on = false;

@@ -555,11 +555,16 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
     const int64_t n_blocks = (n_units + SCAN_BLOCK - 1) / SCAN_BLOCK;
     p.prof.begin(FDAS_STAGE_PEAKS, st);
     p.prof.launches += lt.n_levels > 1 ? 5 : 4;
+    p.prof.begin(PROF_PEAKS_LEVEL1, st);
     k4_level1<E><<<level1_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt.lev[0], (int)chunks1,
                                                              unit_count, unit_mask);
-    if (lt.n_levels > 1)
+    p.prof.end(PROF_PEAKS_LEVEL1, st);
+    if (lt.n_levels > 1) {
+        p.prof.begin(PROF_PEAKS_LEVELS, st);
         k4_levels<E><<<levels_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2,
                                                                  unit_count, unit_mask);
+        p.prof.end(PROF_PEAKS_LEVELS, st);
+    }
     k4_scan_blocks<<<(unsigned)n_blocks, 1024, 0, st>>>(unit_count, n_units, unit_off, block_off);
     k4_scan_top<<<1, 1024, 0, st>>>(block_off, n_blocks, npeaks, p.cfg.max_peaks, p.d_status);
     const int64_t emit_blocks = std::min<int64_t>((n_units + 255) / 256, 152 * 8);
