@@ -64,7 +64,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("own", "reference"), default="own")
-    ap.add_argument("--precision", choices=("auto", "fp32", "bf16", "bf16_split", "fp16_scaled"), default="auto")
+    ap.add_argument("--precision", choices=("auto", "fp32", "bf16", "bf16_split", "fp16_scaled", "bf16_direct"),
+                    default="auto")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision comparison runs")
@@ -187,6 +188,16 @@ def roofline_correlate(w, precision: str, prof):
                 "traffic": _traffic("k3_plane_fp32", "fp32", w.name), "kernel": "k3_plane_fp32<8192>",
                 "avg_launch_ms": ms, "flops_per_launch": flops,
                 "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz (no measured FP32 figure)"}
+    if precision == "bf16_direct":
+        # the Hankel-matrix GEMM: 2 outputs x 2 m products x 2 flops per (bin, template)
+        flops = 8.0 * w.taps * w.K * w.nb
+        ach = flops / (ms / 1e3) / 1e12
+        peak = MEASURED["bf16_tflops_sustained"]
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": _traffic("k3_plane_direct", precision, w.name), "kernel": "k3_plane_direct",
+                "avg_launch_ms": ms, "flops_per_launch": flops,
+                "peak_note": "of measured: MEASURED_PEAKS bf16_tflops_sustained (cuBLAS bf16 under the power cap)",
+                "hbm_GBps_algorithmic": (w.K * w.nb * 2 + w.nb * 4) / (ms / 1e3) / 1e9}
     S = 4096
     L = (S - w.taps + 1) // 64 * 64
     n_seg = math.ceil(w.nb / L)
@@ -219,7 +230,7 @@ def roofline_peak_kernel(w, precision: str, kernel: str, prof):
     k4_levels reads level 2's region of the plane (S_1) and every new harmonic term once."""
     rec = prof["peaks_kernels"][kernel]
     ms = rec["ms"] / max(1, rec["n_timed"])
-    eb = 2 if precision == "bf16" else 4
+    eb = 2 if precision in ("bf16", "bf16_direct") else 4
     if kernel == "k4_level1":
         nbytes = w.K * w.nb * eb
     else:
@@ -236,7 +247,7 @@ def roofline_stage(w, precision: str, stage: str, prof):
     """HBM roofline of a bandwidth-shaped stage (peak search or the long FFT)."""
     n = max(1, prof["n_timed"][stage])
     ms = prof["ms"][stage] / n
-    eb = 2 if precision == "bf16" else 4
+    eb = 2 if precision in ("bf16", "bf16_direct") else 4
     if stage == "peaks":
         # the plane once, plus the H/2 new harmonic terms per cell of each level 2..16
         nbytes = (w.K * w.nb + _gathers(w, range(1, 5))) * eb
@@ -670,7 +681,7 @@ def own_arm(args):
     # ---- the other precisions on the same GPU and workload (the metric's comparison)
     paths = {}
     if not args.quick and not args.no_compare:
-        for prec in ("fp32", "bf16", "bf16_split", "fp16_scaled"):
+        for prec in ("fp32", "bf16", "bf16_split", "fp16_scaled", "bf16_direct"):
             if prec == precision:
                 continue
             cmp_steps = max(3, min(args.steps, 100))
@@ -720,7 +731,8 @@ def own_arm(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16_split": "bf16-split", "fp16_scaled": "f16-scaled"}.get(precision, "bf16"),
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16_split": "bf16-split", "fp16_scaled": "f16-scaled",
+                                                    "bf16_direct": "bf16-direct"}.get(precision, "bf16"),
             "data": "synthetic: seeded N(0,1) noise + 8 accelerated Gaussian pulse trains (fdas_synth)",
             "config": config_json(w, precision),
             "roofline": roof, "roofline_correlate": roof_corr, "paths": paths or None,

@@ -65,11 +65,18 @@ typedef enum {
                                 accumulation, BF16 plane (Sec. 3)                          */
     FDAS_BF16_SPLIT = 2,     /* compensated hi+lo BF16 operands (three products per MMA step,
                                 about 16 significant bits), FP32 plane                      */
-    FDAS_FP16_SCALED = 3     /* ablation of Sec. 3.2 (FP16 rejected there for its range): FP16
+    FDAS_FP16_SCALED = 3,    /* ablation of Sec. 3.2 (FP16 rejected there for its range): FP16
                                 operands on the tensor cores with a power-of-two scale per
                                 segment (largest component in [0.5, 1)) and the template bank
                                 scaled by the segment length, so no operand overflows and small
                                 ones stay normal; FP32 accumulation; FP32 plane               */
+    FDAS_BF16_DIRECT = 4     /* direct correlation variant: the spectrum (BF16) times the
+                                time-domain taps (BF16) as one tensor-core GEMM per block of
+                                bins (the Hankel matrix of the spectrum against all K
+                                templates), FP32 accumulation, BF16 plane; no segment FFTs.
+                                Needs 2 ceil(K/8) 8 <= 256 and the taps image plus windows in
+                                shared memory (K <= 128; taps <= 256 at K = 85), else
+                                FDAS_E_UNSUPPORTED                                            */
 } fdas_precision;
 
 /* Device status bits (fdas_device_status). */
@@ -106,7 +113,7 @@ typedef struct {
     int32_t K;               /* template rows                                                */
     int32_t seg_valid;       /* L = S - m + 1 plane bins kept per segment                     */
     int64_t n_seg;           /* ceil(Nb / L) overlap-save segments                            */
-    int32_t plane_elem_bytes;/* 2 for FDAS_BF16, else 4                                       */
+    int32_t plane_elem_bytes;/* 2 for FDAS_BF16 and FDAS_BF16_DIRECT, else 4                  */
     int64_t plane_bytes;     /* K * Nb * plane_elem_bytes                                     */
     size_t  workspace_bytes; /* caller-provided scratch for fdas_search                       */
     int64_t cells;           /* K * Nb                                                        */

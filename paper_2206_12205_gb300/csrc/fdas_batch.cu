@@ -332,6 +332,7 @@ fdas_status fdas_batch_make_templates(fdas_batch_t b, void *stream) {
         p->d_tcTw = l->d_tcTw;
         p->d_Gh = l->d_Gh;
         p->d_tcFh = l->d_tcFh;
+        p->d_dimg = l->d_dimg;
         p->borrowed = true;
         e = cudaMalloc((void **)&p->d_status, sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);
@@ -372,7 +373,8 @@ fdas_status fdas_batch_search(fdas_batch_t b, const float *d_series, void *d_wor
             const float *scale = reinterpret_cast<const float *>(ws + p.ws_scale + 8);
             if (e == cudaSuccess) e = fdas::launch_plane_any(p, x, scale, ws, plane, b->cap);
             if (e == cudaSuccess)
-                e = fdas::launch_peaks(p, plane, p.cfg.precision == FDAS_BF16, ws, d_peaks + b->peak_off[i],
+                e = fdas::launch_peaks(p, plane, p.cfg.precision == FDAS_BF16 || p.cfg.precision == FDAS_BF16_DIRECT,
+                                       ws, d_peaks + b->peak_off[i],
                                        d_npeaks + i, (uint32_t)i, b->cap);
         }
         cudaGraph_t g = nullptr;

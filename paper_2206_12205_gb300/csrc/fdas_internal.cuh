@@ -29,6 +29,11 @@ __host__ __device__ constexpr uint32_t tc_s1_pos(int n1, int n2) {
             2u * (uint32_t)((n1 >> 2) & 1)) * 2u + (uint32_t)((n1 >> 1) & 1);
 }
 constexpr int TC_MAX_TAPS = 2048;
+// Element index of (row, k) in a dense K-major no-swizzle operand image of R rows (8-row x 8-element
+// core matrices of 128 bytes; core matrices adjacent along the rows, then along K).
+__host__ __device__ constexpr uint32_t tc_kmajor_elem(uint32_t R, uint32_t row, uint32_t k) {
+    return ((k >> 3) * (R >> 3) + (row >> 3)) * 64u + (row & 7u) * 8u + (k & 7u);
+}
 
 // Per-stage CUDA-event timing (fdas_profile_enable / fdas_profile_read).
 constexpr int PROF_STAGES = 6;                   // the four stages, then the two K4 passes
@@ -74,6 +79,7 @@ struct Plan {
     void *d_tcF;           // BF16 K-major DFT operand images: split hi, split lo, F1, F2 (4 x 32 KB)
     __half2 *d_Gh;         // [K][S] FP16 template bank times S, stage-1 operand order
     void *d_tcFh;          // FP16 K-major DFT operand images F1, F2 (2 x 32 KB)
+    void *d_dimg;          // direct path: conj(taps) real-ified, BF16 K-major operand image
     float2 *d_tcTw;        // W_4096^{n2 k1}, [k1][n2] (32 KB)
     int32_t *d_status;     // sticky device status word
     bool templates_ready;
@@ -128,6 +134,10 @@ cudaError_t launch_segments_fp32(const Plan &p, const float2 *d_x, const float *
                                  cudaStream_t st);
 cudaError_t launch_plane_split(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
                                cudaStream_t st);
+bool direct_geometry(const Plan &p, int *Kpad, uint32_t *smem_bytes, uint32_t *tmem_cols);
+size_t direct_pack_words(const Plan &p);
+cudaError_t launch_plane_direct(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
+                                __nv_bfloat16 *d_plane, cudaStream_t st);
 cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
                              cudaStream_t st);
 // The plane of the plan's precision from a spectrum (x: Nb complex; scale: device factor or NULL).

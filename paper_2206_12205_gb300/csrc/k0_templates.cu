@@ -139,6 +139,25 @@ __global__ void k0_dft(const double2 *__restrict__ taps, int m, int S, const dou
     }
 }
 
+// Operand image of the direct path: row p * Kpad + z, K index 2 q + s (tap q, component s of the
+// spectrum), entries of conj(T_z(q - m/2)) real-ified so that a row dotted with the spectrum's
+// (re, im) pairs gives Re (p = 0) or Im (p = 1) of sum_q Xhat conj(T); rows z >= K are zero.
+// Rounded once from FP64 to BF16, stored K-major in core matrices (8 rows x 16 bytes).
+__global__ void k0_direct_image(const double2 *__restrict__ taps, int K, int m, int Kpad,
+                                __nv_bfloat16 *__restrict__ img) {
+    const int N = 2 * Kpad, KD = 2 * m;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)N * KD) return;
+    const int row = (int)(idx / KD), k = (int)(idx % KD);
+    const int p = row / Kpad, z = row % Kpad, q = k >> 1, sc = k & 1;
+    double v = 0.0;
+    if (z < K) {
+        const double2 t = taps[(size_t)z * m + q];
+        v = p == 0 ? (sc == 0 ? t.x : t.y) : (sc == 0 ? -t.y : t.x);
+    }
+    img[tc_kmajor_elem(N, row, k)] = __double2bfloat16(v);
+}
+
 // exp(-2 pi i j / n) in FP64; f = 2j/n is exact for a power-of-two n and is reduced to
 // (-1, 1] before the libm call, so the argument error stays below pi * 2^-53.
 double2 host_unit(int64_t j, int64_t n) {
@@ -202,6 +221,13 @@ cudaError_t launch_make_templates(Plan &p, cudaStream_t st) {
         k0_taps<<<(n + 127) / 128, 128, 0, st>>>(d_taps, K, m, p.cfg.zmax, gl);
         k0_normalise<<<K, 256, 0, st>>>(d_taps, m, d_eta);
         dim3 grid((S + 255) / 256, K);
+        if (p.d_dimg) {
+            int Kpad = 0;
+            direct_geometry(p, &Kpad, nullptr, nullptr);
+            const int64_t ne = (int64_t)2 * Kpad * 2 * m;
+            k0_direct_image<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(d_taps, K, m, Kpad,
+                                                                            static_cast<__nv_bfloat16 *>(p.d_dimg));
+        }
         const bool tc = S == TC_S_BF16;
         k0_dft<<<grid, 256, 0, st>>>(d_taps, m, S, d_wS, p.d_G,
                                      tc ? reinterpret_cast<__nv_bfloat16 *>(p.d_Gbf) : nullptr,

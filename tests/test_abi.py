@@ -153,3 +153,22 @@ def test_refine_entry_points_check_arguments(lib):
     assert lib.fdas_refine(h, ok, ok, 1, 20, ok, odd, None, None) == fb.FDAS_E_INVALID
     assert lib.fdas_refine(h, ok, ok, 1, 20, ok, None, ctypes.c_void_p(base + 2), None) == fb.FDAS_E_INVALID
     fd.fdas_destroy(p)
+
+
+# ------------------------------------------------------------------ direct correlation variant
+def test_direct_plan_geometry(lib):
+    """FDAS_BF16_DIRECT: a BF16 plane; the taps image (2 ceil(K/8) 8 rows x 2m BF16) and the
+    spectrum windows must fit one CTA's shared memory and 2 ceil(K/8) 8 <= 256, m % 8 == 0."""
+    ok = fd.fdas_plan(fd.make_config(1 << 23, 84, 256, 8192, precision="bf16_direct", max_harm=16))
+    assert ok.info.plane_elem_bytes == 2 and ok.info.K == 85
+    assert ok.info.plane_bytes == 2 * 85 * (1 << 22)
+    # the packed BF16 spectrum (Nb rounded to 512-bin tiles, plus the taps) fits the workspace
+    assert ok.info.workspace_bytes >= 4 * ((1 << 22) + 256)
+    fd.fdas_destroy(ok)
+    for n, zmax, m in ((1 << 16, 128, 64), (1 << 16, 84, 512), (1 << 16, 16, 36)):
+        with pytest.raises(fd.FdasError) as ei:
+            fd.fdas_plan(fd.make_config(n, zmax, m, 1024, precision="bf16_direct"))
+        assert ei.value.status == fb.FDAS_E_UNSUPPORTED, (n, zmax, m)
+    small = fd.fdas_plan(fd.make_config(1 << 11, 0, 8, 1024, precision="bf16_direct"))
+    assert small.info.K == 1
+    fd.fdas_destroy(small)
