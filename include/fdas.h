@@ -95,6 +95,11 @@ typedef struct {
     float   thr[5];      /* peak thresholds on S_H for H = 1, 2, 4, 8, 16                   */
     int32_t max_peaks;   /* capacity of the caller's peak buffer, >= 0                      */
     double  sigma2;      /* 0: estimate sigma2 from the spectrum; > 0: use this value       */
+    int32_t norm_block;  /* 0: one normalisation for the whole spectrum (sigma2 above); a
+                            power of two 64 .. 65536: robust local normalisation instead, each
+                            block of this many bins scaled by sqrt(2 ln 2 / median |X_k|^2)
+                            over the block (k >= 1; exclusive with sigma2 > 0)               */
+    int32_t reserved;    /* must be 0                                                        */
 } fdas_config;
 
 /* One peak record, 16 bytes, ordered by (series, harm, zi, r) in the output list. */

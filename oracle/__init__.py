@@ -53,6 +53,7 @@ def _load():
         sig = {
             "orc_fft": (ctypes.c_int, [P, i64, ctypes.c_int]),
             "orc_spectrum": (ctypes.c_int, [P, i64, f64, P, P]),
+            "orc_spectrum_local": (ctypes.c_int, [P, i64, i64, P]),
             "orc_fresnel": (None, [f64, P, P]),
             "orc_response": (None, [f64, f64, P]),
             "orc_response_quad": (None, [f64, f64, P]),
@@ -95,6 +96,17 @@ def spectrum(x, sigma2: float = 0.0):
     if _load().orc_spectrum(_p(x), x.size, float(sigma2), _p(out), ctypes.byref(s2)) != 0:
         raise ValueError("series length must be a power of two >= 4")
     return out, s2.value
+
+
+def spectrum_local(x, block: int):
+    """Spectrum with robust local normalisation: each block of `block` bins scaled by
+    sqrt(2 ln 2 / median |X_k|^2) over the block (orc_spectrum_local)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    nb = x.size // 2
+    out = np.empty(nb, dtype=np.complex128)
+    if _load().orc_spectrum_local(_p(x), x.size, int(block), _p(out)) != 0:
+        raise ValueError("series length must be a power of two >= 4 and block must divide N/2")
+    return out
 
 
 def fresnel(x):

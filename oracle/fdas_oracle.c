@@ -127,6 +127,42 @@ int orc_spectrum(const float *x, int64_t n, double sigma2_fixed, cplx *xhat, dou
     return 0;
 }
 
+static int cmp_double(const void *pa, const void *pb)
+{
+    const double a = *(const double *)pa, b = *(const double *)pb;
+    return (a > b) - (a < b);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Robust local normalisation (a variant of the noise normalisation above; the paper uses  */
+/* one sigma2 per spectrum).  The raw spectrum X_k (X_0 = 0), then the bins of each block  */
+/* b = [b B, b B + B) scaled by sqrt(2 ln 2 / med_b), med_b the lower median (the element  */
+/* of rank floor((n-1)/2) in ascending order) of |X_k|^2 over the block's n bins k >= 1:   */
+/* |X_k|^2 of noise is exponential, whose median is its mean times ln 2, so normalised     */
+/* noise again has E|Xhat|^2 = 2, block by block; a few signal bins do not move a median.  */
+/* Returns 0, or -1 on bad n / block / allocation failure.                                 */
+/* ------------------------------------------------------------------------------------ */
+int orc_spectrum_local(const float *x, int64_t n, int64_t block, cplx *xhat)
+{
+    if (n < 4 || (n & (n - 1)) != 0) return -1;
+    const int64_t nb = n / 2;
+    if (block < 2 || nb % block != 0) return -1;
+    if (orc_spectrum(x, n, 2.0, xhat, NULL) != 0) return -1;     /* sigma2 = 2: scale 1, raw X */
+    double *pw = (double *)malloc(sizeof(double) * (size_t)block);
+    if (!pw) return -1;
+    for (int64_t b0 = 0; b0 < nb; b0 += block) {
+        int64_t cnt = 0;
+        for (int64_t k = b0; k < b0 + block; k++)
+            if (k >= 1) pw[cnt++] = creal(xhat[k]) * creal(xhat[k]) + cimag(xhat[k]) * cimag(xhat[k]);
+        qsort(pw, (size_t)cnt, sizeof(double), cmp_double);
+        const double med = pw[(cnt - 1) / 2];
+        const double s = med > 0.0 ? sqrt(2.0 * log(2.0) / med) : 0.0;
+        for (int64_t k = b0; k < b0 + block; k++) xhat[k] *= s;
+    }
+    free(pw);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Fresnel integrals C(x) = int_0^x cos(pi t^2/2) dt, S(x) = int_0^x sin(pi t^2/2) dt.   */
 /* Written through F(x) = C + iS = ((1+i)/2) erf(w), w = (sqrt(pi)/2)(1-i) x:            */

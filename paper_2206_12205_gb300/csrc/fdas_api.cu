@@ -64,7 +64,9 @@ cudaError_t launch_plane_any(Plan *p, const float2 *x, const float *scale, char 
 
 extern "C" {
 
-int fdas_version(void) { return 101; }
+static_assert(sizeof(fdas_config) == 72, "fdas_config layout (the Python binding mirrors it)");
+
+int fdas_version(void) { return 102; }
 
 const char *fdas_status_string(fdas_status s) {
     switch (s) {
@@ -93,6 +95,10 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
         return FDAS_E_INVALID;
     if (c.max_peaks < 0) return FDAS_E_INVALID;
     if (!(c.sigma2 >= 0.0)) return FDAS_E_INVALID;   // also rejects NaN
+    if (c.reserved != 0) return FDAS_E_INVALID;
+    if (c.norm_block != 0 && (!is_pow2(c.norm_block) || c.norm_block < 64 || c.norm_block > 65536 ||
+                              c.sigma2 > 0.0 || c.norm_block > c.n_samples / 2))
+        return FDAS_E_INVALID;
     for (int l = 0; l < 5; l++)
         if (c.thr[l] != c.thr[l]) return FDAS_E_INVALID;
     if (c.precision != FDAS_FP32 && c.precision != FDAS_BF16 && c.precision != FDAS_BF16_SPLIT &&
@@ -221,6 +227,9 @@ fdas_status fdas_spectrum(fdas_plan_t plan, const float *d_series, void *d_works
     p->prof.calls++;
     cudaError_t e = fdas::launch_spectrum(*p, d_series, ws, st);
     if (e == cudaSuccess) e = fdas::launch_apply_scale(*p, ws, d_xhat, d_sigma2, st);
+    if (e == cudaSuccess && p->cfg.norm_block)        // local normalisation replaces the global scale
+        e = fdas::launch_local_norm(*p, reinterpret_cast<const float2 *>(ws + p->ws_x),
+                                    reinterpret_cast<float2 *>(d_xhat), st);
     return record(p, e);
 }
 
@@ -262,8 +271,12 @@ fdas_status fdas_search(fdas_plan_t plan, const float *d_series, void *d_workspa
     char *ws = static_cast<char *>(d_workspace);
     p->prof.calls++;
     cudaError_t e = fdas::launch_spectrum(*p, d_series, ws, st);
-    const float2 *x = reinterpret_cast<const float2 *>(ws + p->ws_x);
+    float2 *x = reinterpret_cast<float2 *>(ws + p->ws_x);
     const float *scale = reinterpret_cast<const float *>(ws + p->ws_scale + 8);
+    if (e == cudaSuccess && p->cfg.norm_block) {      // normalised in place, no global scale
+        e = fdas::launch_local_norm(*p, x, x, st);
+        scale = nullptr;
+    }
     if (e == cudaSuccess) e = launch_plane_any(p, x, scale, ws, d_plane, st);
     if (e == cudaSuccess) e = fdas::launch_peaks(*p, d_plane, plane_is_bf16(p), ws, d_peaks, d_npeaks, 0u, st);
     return record(p, e);

@@ -369,8 +369,12 @@ fdas_status fdas_batch_search(fdas_batch_t b, const float *d_series, void *d_wor
         for (size_t i = 0; i < b->plan.size() && e == cudaSuccess; i++) {
             const Plan &p = *b->plan[i];
             e = fdas::launch_spectrum(p, d_series + b->sample_off[i], ws, b->cap);
-            const float2 *x = reinterpret_cast<const float2 *>(ws + p.ws_x);
+            float2 *x = reinterpret_cast<float2 *>(ws + p.ws_x);
             const float *scale = reinterpret_cast<const float *>(ws + p.ws_scale + 8);
+            if (e == cudaSuccess && p.cfg.norm_block) {
+                e = fdas::launch_local_norm(p, x, x, b->cap);
+                scale = nullptr;
+            }
             if (e == cudaSuccess) e = fdas::launch_plane_any(p, x, scale, ws, plane, b->cap);
             if (e == cudaSuccess)
                 e = fdas::launch_peaks(p, plane, p.cfg.precision == FDAS_BF16 || p.cfg.precision == FDAS_BF16_DIRECT,

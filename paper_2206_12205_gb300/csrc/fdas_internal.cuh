@@ -119,6 +119,7 @@ void gauss_legendre(int n, double *xs, double *ws);
 // ---- launchers (each returns cudaGetLastError() of its launches) ----
 cudaError_t launch_make_templates(Plan &p, cudaStream_t st);
 cudaError_t launch_spectrum(const Plan &p, const float *d_series, char *ws, cudaStream_t st);
+cudaError_t launch_local_norm(const Plan &p, const float2 *d_x, float2 *d_out, cudaStream_t st);
 cudaError_t launch_apply_scale(const Plan &p, const char *ws, float *d_xhat, double *d_sigma2,
                                cudaStream_t st);
 cudaError_t launch_plane_fp32(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,

@@ -141,6 +141,44 @@ __global__ void k1_apply_scale(const float2 *__restrict__ X, const float *__rest
     }
 }
 
+// Robust local normalisation: the bins of block b = [b B, b B + B) scaled by
+// sqrt(2 ln 2 / med_b), med_b = the lower median (rank floor((n - 1) / 2) in ascending order) of
+// |X_k|^2 over the block's n bins with k >= 1.  For noise |X_k|^2 is exponential, whose median is
+// its mean times ln 2, so the normalised noise power has mean 2 in every block; a median is not
+// moved by the few bins a signal occupies.  One CTA per block: the powers are sorted in shared
+// memory (bitonic, the excluded DC bin as +inf) and the rank picked exactly.
+__global__ void __launch_bounds__(256) k1_local_norm(const float2 *__restrict__ X, float2 *__restrict__ out, int B) {
+    extern __shared__ float pw[];
+    const int64_t k0 = (int64_t)blockIdx.x * B;
+    for (int i = threadIdx.x; i < B; i += 256) {
+        const float2 v = X[k0 + i];
+        pw[i] = (k0 + i == 0) ? INFINITY : v.x * v.x + v.y * v.y;
+    }
+    __syncthreads();
+    for (int size = 2; size <= B; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < B / 2; i += 256) {
+                const int lo = 2 * i - (i & (stride - 1));          // first of the pair
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const float a = pw[lo], b = pw[hi];
+                if ((a > b) == up) {
+                    pw[lo] = b;
+                    pw[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int n = (k0 == 0) ? B - 1 : B;
+    const float med = pw[(n - 1) / 2];
+    const float s = med > 0.f ? sqrtf(2.0f * 0.69314718f / med) : 0.f;
+    for (int i = threadIdx.x; i < B; i += 256) {
+        const float2 v = X[k0 + i];
+        out[k0 + i] = make_float2(v.x * s, v.y * s);
+    }
+}
+
 template <int M1>
 cudaError_t run_pass_a(const Plan &p, const float2 *z, float2 *B, cudaStream_t st) {
     constexpr int C1 = k1_groups(M1);
@@ -202,6 +240,19 @@ cudaError_t launch_spectrum(const Plan &p, const float *d_series, char *ws, cuda
     if (e != cudaSuccess) return e;
     k1_finalize<<<1, 256, 0, st>>>(partial, p.M1 / (2 * k1_groups(p.M2)), p.nb, p.cfg.sigma2, sigma2, scale);
     p.prof.end(FDAS_STAGE_SPECTRUM, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local_norm(const Plan &p, const float2 *d_x, float2 *d_out, cudaStream_t st) {
+    const int B = p.cfg.norm_block;
+    if (B <= 0 || p.nb % B != 0) return cudaErrorInvalidValue;
+    if (B * sizeof(float) > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k1_local_norm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(B * sizeof(float)));
+        if (e != cudaSuccess) return e;
+    }
+    k1_local_norm<<<(unsigned)(p.nb / B), 256, B * sizeof(float), st>>>(d_x, d_out, B);
+    p.prof.launches += 1;
     return cudaGetLastError();
 }
 
