@@ -99,7 +99,13 @@ typedef struct {
                             power of two 64 .. 65536: robust local normalisation instead, each
                             block of this many bins scaled by sqrt(2 ln 2 / median |X_k|^2)
                             over the block (k >= 1; exclusive with sigma2 > 0)               */
-    int32_t reserved;    /* must be 0                                                        */
+    int32_t harm_mode;   /* 0: harmonic sums anchored at the fundamental, every term on the
+                            grid (S_H(r, z) = sum_h P(h r, h z), H r < Nb, |H z| <= zmax);
+                            1: anchored at the highest harmonic with rounding (a variant):
+                            the cell (r, z) is harmonic H and harmonic j < H is read at
+                            (round(j r / H), the grid z nearest j z / H), halves rounded up,
+                            nested so that S_2H = S_H + the odd j of 2H in increasing j;
+                            every level covers the whole plane; records give the cell      */
 } fdas_config;
 
 /* One peak record, 16 bytes, ordered by (series, harm, zi, r) in the output list. */

@@ -62,6 +62,8 @@ def _load():
             "orc_plane": (ctypes.c_int, [P, i64, ctypes.c_int, ctypes.c_int, P, P]),
             "orc_plane_cells": (ctypes.c_int, [P, i64, ctypes.c_int, ctypes.c_int, P, i64, P, P, P]),
             "orc_peaks_f32": (ctypes.c_int, [P, i64, ctypes.c_int, ctypes.c_int, P, i64, P, P, P, P, P]),
+            "orc_peaks_anch_f32": (ctypes.c_int, [P, i64, ctypes.c_int, ctypes.c_int, P, i64, P, P, P, P, P]),
+            "orc_peaks_anch_f64": (ctypes.c_int, [P, i64, ctypes.c_int, ctypes.c_int, P, i64, P, P, P, P, P]),
             "orc_peaks_f64": (ctypes.c_int, [P, i64, ctypes.c_int, ctypes.c_int, P, i64, P, P, P, P, P]),
             "orc_interp_power": (None, [P, i64, ctypes.c_int, f64, f64, P, P, P]),
             "orc_interp_power_at": (None, [P, i64, ctypes.c_int, i64, f64, f64, P, P, P]),
@@ -207,16 +209,19 @@ def _peaks(fn, plane_arr, zmax, max_harm, thr, max_out, pdtype):
     return out, cnt.value
 
 
-def peaks_f32(plane_f32, zmax: int, max_harm: int, thr, max_out: int = 1 << 20):
-    """Harmonic sums + peak list of a float32 plane, in float32 (given-plane mode)."""
+def peaks_f32(plane_f32, zmax: int, max_harm: int, thr, max_out: int = 1 << 20, anchored: bool = False):
+    """Harmonic sums + peak list of a float32 plane, in float32 (given-plane mode); anchored:
+    the highest-harmonic-anchored sums with rounding."""
     a = np.ascontiguousarray(plane_f32, dtype=np.float32)
-    return _peaks(_load().orc_peaks_f32, a, zmax, max_harm, thr, max_out, np.float32)
+    fn = _load().orc_peaks_anch_f32 if anchored else _load().orc_peaks_f32
+    return _peaks(fn, a, zmax, max_harm, thr, max_out, np.float32)
 
 
-def peaks_f64(plane_f64, zmax: int, max_harm: int, thr, max_out: int = 1 << 20):
+def peaks_f64(plane_f64, zmax: int, max_harm: int, thr, max_out: int = 1 << 20, anchored: bool = False):
     """Harmonic sums + peak list of an FP64 plane."""
     a = np.ascontiguousarray(plane_f64, dtype=np.float64)
-    return _peaks(_load().orc_peaks_f64, a, zmax, max_harm, thr, max_out, np.float64)
+    fn = _load().orc_peaks_anch_f64 if anchored else _load().orc_peaks_f64
+    return _peaks(fn, a, zmax, max_harm, thr, max_out, np.float64)
 
 
 def interp_power(xhat, m: int, r: float, z: float, k0=None):

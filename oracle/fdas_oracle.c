@@ -463,6 +463,64 @@ static double hsum_double(const double *plane, int64_t nb, int zmax, int H, int 
     return s;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Highest-harmonic-anchored harmonic sums with rounding (a variant of the sums above,    */
+/* the form of PRESTO-style searches): the cell (r, i) is harmonic H, and harmonic j of   */
+/* level L is read at r_j = round(j r / L) and at the grid z nearest j z_i / L, halves     */
+/* rounded up:  r_j = floor((2 j r + L) / (2 L)),  i_j = floor((j z_i + L zmax + L)/(2 L)). */
+/* Level 2L's even fractions 2j'/2L = j'/L round exactly as level L's, so the sums nest:  */
+/*   S_1 = P(r, i),  S_2L = S_L + sum_{odd j < 2L, increasing} P(r_j, i_j);               */
+/* every term is on the plane for every (r, i), so each level covers the whole plane.     */
+/* Peaks: the same threshold and 3x3 rule on the S_L grid.                                  */
+/* ------------------------------------------------------------------------------------ */
+#define HSA_BODY(TYPE)                                                                     \
+    int z = -zmax + 2 * i;                                                                 \
+    TYPE s = plane[(int64_t)i * nb + r];                                                   \
+    for (int L = 2; L <= H; L *= 2)                                                        \
+        for (int j = 1; j < L; j += 2) {                                                   \
+            int64_t rj = (2 * (int64_t)j * r + L) / (2 * L);                               \
+            int ij = (j * z + L * zmax + L) / (2 * L);                                     \
+            s = s + plane[(int64_t)ij * nb + rj];                                          \
+        }                                                                                  \
+    return s;
+
+static float hsa_float(const float *plane, int64_t nb, int zmax, int H, int i, int64_t r) { HSA_BODY(float) }
+static double hsa_double(const double *plane, int64_t nb, int zmax, int H, int i, int64_t r) { HSA_BODY(double) }
+
+#define HSA_PEAKS(TYPE)                                                                    \
+    int K = zmax + 1;                                                                      \
+    int64_t cnt = 0;                                                                       \
+    for (int lev = 0; lev < 5; lev++) {                                                    \
+        int H = 1 << lev;                                                                  \
+        if (H > max_harm) break;                                                           \
+        TYPE th = (TYPE)thr[lev];                                                          \
+        for (int i = 0; i < K; i++)                                                        \
+            for (int64_t r = 0; r < nb; r++) {                                             \
+                TYPE s = hsa_##TYPE(plane, nb, zmax, H, i, r);                             \
+                if (!(s > th)) continue;                                                   \
+                int is_peak = 1;                                                           \
+                for (int di = -1; di <= 1 && is_peak; di++) {                              \
+                    int ii = i + di;                                                       \
+                    if (ii < 0 || ii >= K) continue;                                       \
+                    for (int64_t dr = -1; dr <= 1; dr++) {                                 \
+                        if (di == 0 && dr == 0) continue;                                  \
+                        int64_t rr = r + dr;                                               \
+                        if (rr < 0 || rr >= nb) continue;                                  \
+                        TYPE sn = hsa_##TYPE(plane, nb, zmax, H, ii, rr);                  \
+                        int earlier = (di < 0) || (di == 0 && dr < 0);                     \
+                        if (earlier ? !(s > sn) : !(s >= sn)) { is_peak = 0; break; }      \
+                    }                                                                      \
+                }                                                                          \
+                if (!is_peak) continue;                                                    \
+                if (cnt < max_out) {                                                       \
+                    out_h[cnt] = H; out_zi[cnt] = i; out_r[cnt] = r; out_p[cnt] = s;       \
+                }                                                                          \
+                cnt++;                                                                     \
+            }                                                                              \
+    }                                                                                      \
+    *count = cnt;                                                                          \
+    return 0;
+
 static int hs_check(int64_t nb, int zmax, int max_harm)
 {
     if (nb < 1 || zmax < 0 || (zmax & 1)) return -1;
@@ -477,6 +535,23 @@ int orc_peaks_f32(const float *plane, int64_t nb, int zmax, int max_harm, const 
 {
     if (hs_check(nb, zmax, max_harm)) return -1;
     HS_BODY(float)
+}
+
+/* Highest-harmonic-anchored variant, float (given-plane mode) and FP64. */
+int orc_peaks_anch_f32(const float *plane, int64_t nb, int zmax, int max_harm, const double *thr,
+                       int64_t max_out, int32_t *out_h, int32_t *out_zi, int64_t *out_r,
+                       float *out_p, int64_t *count)
+{
+    if (hs_check(nb, zmax, max_harm)) return -1;
+    HSA_PEAKS(float)
+}
+
+int orc_peaks_anch_f64(const double *plane, int64_t nb, int zmax, int max_harm, const double *thr,
+                       int64_t max_out, int32_t *out_h, int32_t *out_zi, int64_t *out_r,
+                       double *out_p, int64_t *count)
+{
+    if (hs_check(nb, zmax, max_harm)) return -1;
+    HSA_PEAKS(double)
 }
 
 /* The same on an FP64 plane. */

@@ -66,7 +66,7 @@ extern "C" {
 
 static_assert(sizeof(fdas_config) == 72, "fdas_config layout (the Python binding mirrors it)");
 
-int fdas_version(void) { return 102; }
+int fdas_version(void) { return 103; }
 
 const char *fdas_status_string(fdas_status s) {
     switch (s) {
@@ -95,7 +95,7 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
         return FDAS_E_INVALID;
     if (c.max_peaks < 0) return FDAS_E_INVALID;
     if (!(c.sigma2 >= 0.0)) return FDAS_E_INVALID;   // also rejects NaN
-    if (c.reserved != 0) return FDAS_E_INVALID;
+    if (c.harm_mode != 0 && c.harm_mode != 1) return FDAS_E_INVALID;
     if (c.norm_block != 0 && (!is_pow2(c.norm_block) || c.norm_block < 64 || c.norm_block > 65536 ||
                               c.sigma2 > 0.0 || c.norm_block > c.n_samples / 2))
         return FDAS_E_INVALID;

@@ -109,6 +109,7 @@ struct LevelDesc {
 struct LevelTable {
     LevelDesc lev[5];
     int n_levels;
+    int anchored;   // 1: highest-harmonic-anchored sums with rounding (every level on the whole plane)
 };
 
 LevelTable make_levels(const Plan &p);

@@ -164,6 +164,26 @@ __device__ __forceinline__ float harm_sum(const E *plane, int64_t nb, int zmax, 
     return s;
 }
 
+// Highest-harmonic-anchored sum with rounding (harm_mode 1): the cell (r, i) is harmonic H; the
+// harmonic j of level L sits at r_j = floor((2 j r + L) / (2 L)) (j r / L rounded, halves up) and
+// row floor((j z + L zmax + L) / (2 L)) (the grid row nearest j z / L, halves up).  Level 2L's
+// even fractions are level L's with the same rounding, so S_2L = S_L + the odd j < 2L in
+// increasing j, S_1 = P; FP32 adds in that order.
+template <typename E>
+__device__ float harm_sum_anch(const E *plane, int64_t nb, int zmax, int H, int i, int64_t r) {
+    const int z = -zmax + 2 * i;
+    float s = ld_plane(plane, (int64_t)i * nb + r);
+    for (int l = 1; (1 << l) <= H; l++) {
+        const int L = 1 << l;
+        for (int j = 1; j < L; j += 2) {
+            const int ij = (j * z + L * zmax + L) >> (l + 1);
+            const int64_t rj = (2 * (int64_t)j * r + L) >> (l + 1);
+            s = __fadd_rn(s, ld_plane(plane, (int64_t)ij * nb + rj));
+        }
+    }
+    return s;
+}
+
 __device__ __forceinline__ bool row_in_level(int i, int K, int zmax, int H) {
     const int z = -zmax + 2 * i;
     return i >= 0 && i < K && abs(H * z) <= zmax;
@@ -230,15 +250,16 @@ __device__ __forceinline__ void add_level(const E *__restrict__ plane, int64_t n
 // The 3x3 rule for a cell of level H holding S_H = v: strictly above the defined neighbours that
 // come earlier in row-major (i, r) order, at least equal to the later ones.
 template <typename E>
-__device__ __noinline__ bool local_max(const E *plane, int64_t nb, int zmax, int K, int H, int64_t rmax, int i, int64_t r, float v) {
+__device__ __noinline__ bool local_max(const E *plane, int64_t nb, int zmax, int K, int H, int64_t rmax, int i, int64_t r, float v,
+                                       bool anchored = false) {
     for (int di = -1; di <= 1; di++) {
         const int ii = i + di;
-        if (!row_in_level(ii, K, zmax, H)) continue;
+        if (anchored ? (ii < 0 || ii >= K) : !row_in_level(ii, K, zmax, H)) continue;
         for (int dr = -1; dr <= 1; dr++) {
             if (di == 0 && dr == 0) continue;
             const int64_t rr = r + dr;
             if (rr < 0 || rr > rmax) continue;
-            const float w = harm_sum(plane, nb, zmax, H, ii, rr);
+            const float w = anchored ? harm_sum_anch(plane, nb, zmax, H, ii, rr) : harm_sum(plane, nb, zmax, H, ii, rr);
             const bool earlier = di < 0 || (di == 0 && dr < 0);
             if (earlier ? !(v > w) : !(v >= w)) return false;
         }
@@ -395,6 +416,75 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_leve
     }
 }
 
+// Levels 2 .. 16 of the highest-harmonic-anchored sums (harm_mode 1) over the whole plane: grid
+// (K rows, ceil(chunks / DETECT_WARPS)), so the blocks in flight share chunk positions across rows
+// and the rows they gather from stay in L2.  A warp owns one (row, 512-bin chunk) and carries the
+// running sums of its lanes' 16 bins through the levels; for each new harmonic j of level L the
+// bins it needs, r_j for the chunk's 512 r, are one span of at most 512 j / L + 1 elements of row
+// i_j, staged through shared memory with coalesced loads.
+constexpr int ANCH_SPAN = CB + 8;
+
+template <typename E>
+__global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4a_levels(const E *__restrict__ plane, int64_t nb,
+                                                                               int zmax, int K, LevelTable lt,
+                                                                               int chunks,
+                                                                               int32_t *__restrict__ unit_count,
+                                                                               uint32_t *__restrict__ unit_mask) {
+    __shared__ float stage[DETECT_WARPS][ANCH_SPAN];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x;
+    const int c = blockIdx.y * DETECT_WARPS + w;
+    if (c >= chunks) return;                         // warp-uniform
+    const int z = -zmax + 2 * i;
+    const int64_t r_first = (int64_t)c * CB;
+    const int64_t rl = r_first + LB * lane;
+    float s[LB];
+    {
+        typename Fmt<E>::Raw raw;
+        Fmt<E>::load_raw(plane + (int64_t)i * nb + rl, raw);
+        Fmt<E>::widen(raw, s);
+    }
+    float *st = stage[w];
+    for (int l = 1; l < lt.n_levels; l++) {
+        const int L = 1 << l;
+        for (int j = 1; j < L; j += 2) {
+            const int ij = (j * z + L * zmax + L) >> (l + 1);
+            const int64_t s0 = (2 * (int64_t)j * r_first + L) >> (l + 1);
+            const int64_t s1 = (2 * (int64_t)j * (r_first + CB - 1) + L) >> (l + 1);
+            const int len = (int)(s1 - s0 + 1);             // <= CB j / L + 1 <= CB
+            const E *row = plane + (int64_t)ij * nb;
+            __syncwarp();
+            for (int t = lane; t < len; t += 32) st[t] = ld_plane(row, s0 + t);
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < LB; e++) {
+                const int64_t rj = (2 * (int64_t)j * (rl + e) + L) >> (l + 1);
+                s[e] = __fadd_rn(s[e], st[rj - s0]);
+            }
+        }
+        const LevelDesc &d = lt.lev[l];
+        float vmax = s[0];
+#pragma unroll
+        for (int e = 1; e < LB; e++) vmax = fmaxf(vmax, s[e]);
+        const int u = (int)d.unit0 + i * (int)d.chunks + c;
+        if (__any_sync(0xffffffffu, vmax > d.thr)) {
+            uint32_t pk = 0;
+            if (vmax > d.thr) {
+                for (int e = 0; e < LB; e++)
+                    if (s[e] > d.thr && local_max(plane, nb, zmax, K, L, d.rmax, i, rl + e, s[e], true)) pk |= 1u << e;
+            }
+            int cnt = __popc(pk);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            const uint32_t hi = __shfl_down_sync(0xffffffffu, pk, 1);
+            if (lane == 0) unit_count[u] = cnt;
+            if (cnt > 0 && !(lane & 1)) unit_mask[(int64_t)u * WORDS + (lane >> 1)] = pk | (hi << 16);
+        } else if (lane == 0) {
+            unit_count[u] = 0;
+        }
+    }
+}
+
 // First-level scan: exclusive prefix of the counts inside each block of SCAN_BLOCK units.
 __global__ void __launch_bounds__(1024) k4_scan_blocks(const int32_t *__restrict__ cnt, int64_t n,
                                                        int32_t *__restrict__ off, int64_t *__restrict__ block_sum) {
@@ -528,7 +618,8 @@ __global__ void __launch_bounds__(256) k4_emit(const E *__restrict__ plane, int6
                     pk.zi = (int16_t)ref.row;
                     pk.harm = (uint8_t)H;
                     pk.pad = 0;
-                    pk.power = harm_sum(plane, nb, zmax, H, ref.row, r);
+                    pk.power = lt.anchored ? harm_sum_anch(plane, nb, zmax, H, ref.row, r)
+                                           : harm_sum(plane, nb, zmax, H, ref.row, r);
                     out[pos] = pk;
                 }
                 pos++;
@@ -559,7 +650,13 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
     k4_level1<E><<<level1_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt.lev[0], (int)chunks1,
                                                              unit_count, unit_mask);
     p.prof.end(PROF_PEAKS_LEVEL1, st);
-    if (lt.n_levels > 1) {
+    if (lt.n_levels > 1 && lt.anchored) {
+        p.prof.begin(PROF_PEAKS_LEVELS, st);
+        const dim3 agrid((unsigned)p.K, (unsigned)((chunks1 + DETECT_WARPS - 1) / DETECT_WARPS));
+        k4a_levels<E><<<agrid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks1, unit_count,
+                                                           unit_mask);
+        p.prof.end(PROF_PEAKS_LEVELS, st);
+    } else if (lt.n_levels > 1) {
         p.prof.begin(PROF_PEAKS_LEVELS, st);
         k4_levels<E><<<levels_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2,
                                                                  unit_count, unit_mask);
@@ -585,11 +682,12 @@ LevelTable make_levels(const Plan &p) {
         if (H > p.cfg.max_harm) break;
         int zl = p.cfg.zmax / H;
         zl -= zl & 1;                               // largest even z with |H z| <= zmax
+        if (p.cfg.harm_mode == 1) zl = p.cfg.zmax;  // anchored at the highest harmonic: whole plane
         LevelDesc &d = lt.lev[n];
         d.H = H;
         d.i_lo = (p.cfg.zmax - zl) / 2;
         d.rows = zl + 1;
-        d.rmax = (p.nb - 1) / H;
+        d.rmax = p.cfg.harm_mode == 1 ? p.nb - 1 : (p.nb - 1) / H;
         d.chunks = (d.rmax + 1 + PEAK_CHUNK - 1) / PEAK_CHUNK;
         d.unit0 = unit0;
         d.thr = p.cfg.thr[l];
@@ -597,6 +695,7 @@ LevelTable make_levels(const Plan &p) {
         n++;
     }
     lt.n_levels = n;
+    lt.anchored = p.cfg.harm_mode == 1;
     return lt;
 }
 

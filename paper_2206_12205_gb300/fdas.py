@@ -55,7 +55,7 @@ class _Config(ctypes.Structure):
     _fields_ = [("n_samples", ctypes.c_int64), ("zmax", ctypes.c_int32), ("taps", ctypes.c_int32),
                 ("seg_len", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_harm", ctypes.c_int32),
                 ("thr", ctypes.c_float * 5), ("max_peaks", ctypes.c_int32), ("sigma2", ctypes.c_double),
-                ("norm_block", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("norm_block", ctypes.c_int32), ("harm_mode", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -212,13 +212,14 @@ class Plan:
 
 def make_config(n_samples: int, zmax: int, taps: int, seg_len: int, precision="fp32", max_harm: int = 1,
                 thr: Sequence[float] = (30.0,) * 5, max_peaks: int = 1 << 16, sigma2: float = 0.0,
-                norm_block: int = 0) -> dict:
+                norm_block: int = 0, harm_mode: int = 0) -> dict:
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     thr = list(thr) + [float(thr[-1])] * (5 - len(thr))
     return dict(n_samples=int(n_samples), zmax=int(zmax), taps=int(taps), seg_len=int(seg_len),
                 precision=int(precision), max_harm=int(max_harm), thr=[float(v) for v in thr[:5]],
-                max_peaks=int(max_peaks), sigma2=float(sigma2), norm_block=int(norm_block))
+                max_peaks=int(max_peaks), sigma2=float(sigma2), norm_block=int(norm_block),
+                harm_mode=int(harm_mode))
 
 
 # ----------------------------------------------------------------------------- entry points
@@ -226,14 +227,14 @@ def _to_config(cfg: dict, c: "_Config"):
     for k in ("n_samples", "zmax", "taps", "seg_len", "precision", "max_harm", "max_peaks", "sigma2"):
         setattr(c, k, cfg[k])
     c.norm_block = int(cfg.get("norm_block", 0))
-    c.reserved = 0
+    c.harm_mode = int(cfg.get("harm_mode", 0))
     for i, v in enumerate(cfg["thr"]):
         c.thr[i] = v
 
 
 def _from_config(c: "_Config") -> dict:
     d = {k: getattr(c, k) for k in ("n_samples", "zmax", "taps", "seg_len", "precision", "max_harm", "max_peaks",
-                                     "sigma2", "norm_block")}
+                                     "sigma2", "norm_block", "harm_mode")}
     d["thr"] = [float(c.thr[i]) for i in range(5)]
     return d
 

@@ -34,14 +34,14 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert fd.fdas_version() == 102
+    assert fd.fdas_version() == 103
     for code in range(8):
         assert fd.status_string(code) and fd.status_string(code) != "unknown status"
     assert fd.status_string(99) == "unknown status"
 
 
 def test_struct_layouts(lib):
-    # int64, 5 x int32, float[5], int32, pad, double, int32 norm_block, int32 reserved (static_assert'ed in C)
+    # int64, 5 x int32, float[5], int32, pad, double, int32 norm_block, int32 harm_mode (static_assert'ed in C)
     assert ctypes.sizeof(fb._Config) == 72
     assert fb.PEAK_DTYPE.itemsize == 16
 
