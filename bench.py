@@ -614,10 +614,10 @@ def own_arm(args):
         if dist is not None:
             dist.barrier()
 
-    def timed_run(prec: str, steps: int, warmup: int, sample_clocks: bool):
+    def timed_run(prec: str, steps: int, warmup: int, sample_clocks: bool, **variant):
         """Exactly `steps` timed searches, L2 flushed before each, CUDA events per step."""
         cfg_ = fd.make_config(w.n, w.zmax, w.taps, w.seg_len, precision=prec, max_harm=MAX_HARM,
-                              thr=THRESHOLDS, max_peaks=MAX_PEAKS)
+                              thr=THRESHOLDS, max_peaks=MAX_PEAKS, **variant)
         s_ = fd.Search(cfg_, device=dev)
         for _ in range(warmup):
             s_.search(x_dev, stream)
@@ -695,6 +695,21 @@ def own_arm(args):
         if "fp32" in paths and "bf16" in paths:
             paths["speedup_bf16_over_fp32"] = paths["bf16"]["value"] / paths["fp32"]["value"]
 
+    # ---- the variants of the search (same workload, BF16): robust local normalisation and the
+    # highest-harmonic-anchored harmonic sums (the direct correlation is a precision in `paths`)
+    variants = None
+    if not args.quick and not args.no_compare:
+        variants = {}
+        for name, kw in (("local_norm_4096", {"norm_block": 4096}), ("harm_anchored", {"harm_mode": 1})):
+            v_steps = max(3, min(args.steps, 20))
+            s_v, ms_v, prof_v, _ = timed_run("bf16", v_steps, args.warmup, False, **kw)
+            variants[name] = {"config": kw, "value": world * cells * v_steps / (ms_v / 1e3), "unit": UNIT,
+                              "ms_per_step": ms_v / v_steps, "steps": v_steps,
+                              "stages_ms_per_step": {k: v / v_steps for k, v in prof_v["ms"].items()},
+                              "peak_kernels_ms_per_step": {k: r["ms"] / v_steps
+                                                           for k, r in prof_v["peaks_kernels"].items()}}
+            del s_v
+
     # ---- roofline of the dominant kernel of the step (largest per-launch time): the correlation
     # kernel, one of the two peak-search kernels, or a smaller stage's kernels
     kernel_ms = {k: v / max(1, prof["n_timed"][k]) for k, v in prof["ms"].items() if k != "peaks"}
@@ -735,7 +750,7 @@ def own_arm(args):
                                                     "bf16_direct": "bf16-direct"}.get(precision, "bf16"),
             "data": "synthetic: seeded N(0,1) noise + 8 accelerated Gaussian pulse trains (fdas_synth)",
             "config": config_json(w, precision),
-            "roofline": roof, "roofline_correlate": roof_corr, "paths": paths or None,
+            "roofline": roof, "roofline_correlate": roof_corr, "paths": paths or None, "variants": variants,
             "cpu_baseline": cpu, "e2e": e2e, "refine": refine, "batch": batch, "sensitivity": sensitivity,
             "gpu_launches": int(prof["launches"]), "clocks": clk,
             "stages_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
