@@ -54,6 +54,8 @@ def _load():
             "orc_fft": (ctypes.c_int, [P, i64, ctypes.c_int]),
             "orc_spectrum": (ctypes.c_int, [P, i64, f64, P, P]),
             "orc_spectrum_local": (ctypes.c_int, [P, i64, i64, P]),
+            "orc_e4m3": (f64, [f64]),
+            "orc_plane_fp8": (ctypes.c_int, [P, i64, ctypes.c_int, ctypes.c_int, P, P]),
             "orc_fresnel": (None, [f64, P, P]),
             "orc_response": (None, [f64, f64, P]),
             "orc_response_quad": (None, [f64, f64, P]),
@@ -108,6 +110,26 @@ def spectrum_local(x, block: int):
     out = np.empty(nb, dtype=np.complex128)
     if _load().orc_spectrum_local(_p(x), x.size, int(block), _p(out)) != 0:
         raise ValueError("series length must be a power of two >= 4 and block must divide N/2")
+    return out
+
+
+def e4m3(v):
+    """FP8 E4M3 rounding (nearest, ties to even, saturating at +-448), elementwise."""
+    a = np.atleast_1d(np.asarray(v, dtype=np.float64))
+    fn = _load().orc_e4m3
+    return np.array([fn(float(t)) for t in a.flat]).reshape(a.shape)
+
+
+def plane_fp8(xhat, zmax: int, m: int, T=None) -> np.ndarray:
+    """The FP8 direct-correlation plane (orc_plane_fp8): E4M3 operands with per-1024-bin-tile
+    and per-template power-of-two scales, FP64 sums."""
+    xhat = np.ascontiguousarray(xhat, dtype=np.complex128)
+    if T is None:
+        T, _ = templates(zmax, m)
+    T = np.ascontiguousarray(T, dtype=np.complex128)
+    out = np.empty((zmax + 1, xhat.size), dtype=np.float64)
+    if _load().orc_plane_fp8(_p(xhat), xhat.size, int(zmax), int(m), _p(T), _p(out)) != 0:
+        raise MemoryError("orc_plane_fp8")
     return out
 
 

@@ -377,6 +377,81 @@ int orc_plane(const cplx *xhat, int64_t nb, int zmax, int m, const cplx *T, doub
     return 0;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* FP8 E4M3 (a precision ablation of the correlation): 1 sign, 4 exponent (bias 7), 3      */
+/* mantissa bits; normal numbers 2^-6 .. 448 = 1.75 x 2^8, subnormals in steps of 2^-9;    */
+/* round to nearest, ties to even, saturating at +-448.                                     */
+/* ------------------------------------------------------------------------------------ */
+double orc_e4m3(double v)
+{
+    double a = fabs(v);
+    if (a == 0.0 || a != a) return v;
+    int E;
+    frexp(a, &E);                       /* a = f 2^E, f in [0.5, 1): floor(log2 a) = E - 1 */
+    int e = E - 1;
+    if (e < -6) e = -6;                 /* subnormal range shares the 2^-6 binade's step  */
+    double step = ldexp(1.0, e - 3);
+    double r = nearbyint(a / step) * step;
+    if (r > 448.0) r = 448.0;
+    return copysign(r, v);
+}
+
+/* Power of two s with M s <= 448 < 2 M s (the largest such scale; 1 when M = 0).          */
+static double e4m3_scale(double M)
+{
+    if (!(M > 0.0)) return 1.0;
+    int E;
+    double f = frexp(M, &E);            /* M = f 2^E, 448 = 0.875 x 2^9                       */
+    return ldexp(1.0, (f <= 0.875 ? 9 : 8) - E);
+}
+
+/* The direct correlation with FP8 operands (the FDAS_FP8_DIRECT ablation), emulated:        */
+/*   tile t = floor(r / 1024): s_t from the largest |Re| or |Im| of Xhat over the window      */
+/*   [1024 t - m/2, 1024 t + 1024 + m/2) (zero outside the spectrum); template z: sigma_z    */
+/*   from the largest |Re| or |Im| of its taps;                                              */
+/*   P(r, z) = |sum_q e4m3(s_t Xhat_{r+q}) conj(e4m3(sigma_z T_z(q)))|^2 / (s_t sigma_z)^2    */
+/* (component-wise rounding; the sum in FP64).                                               */
+int orc_plane_fp8(const cplx *xhat, int64_t nb, int zmax, int m, const cplx *T, double *plane)
+{
+    int K = zmax + 1;
+    const int TILE = 1024;
+    cplx *tq = (cplx *)malloc(sizeof(cplx) * (size_t)K * m);
+    double *sig = (double *)malloc(sizeof(double) * (size_t)K);
+    cplx *wq = (cplx *)malloc(sizeof(cplx) * (size_t)(TILE + m));
+    if (!tq || !sig || !wq) { free(tq); free(sig); free(wq); return -1; }
+    for (int i = 0; i < K; i++) {
+        double M = 0.0;
+        for (int q = 0; q < m; q++) {
+            cplx t = T[(size_t)i * m + q];
+            M = fmax(M, fmax(fabs(creal(t)), fabs(cimag(t))));
+        }
+        sig[i] = e4m3_scale(M);
+        for (int q = 0; q < m; q++) {
+            cplx t = T[(size_t)i * m + q];
+            tq[(size_t)i * m + q] = orc_e4m3(creal(t) * sig[i]) + I * orc_e4m3(cimag(t) * sig[i]);
+        }
+    }
+    for (int64_t t0 = 0; t0 < nb; t0 += TILE) {
+        double M = 0.0;
+        for (int64_t k = t0 - m / 2; k < t0 + TILE + m / 2; k++)
+            if (k >= 0 && k < nb) M = fmax(M, fmax(fabs(creal(xhat[k])), fabs(cimag(xhat[k]))));
+        double st = e4m3_scale(M);
+        for (int j = 0; j < TILE + m; j++) {
+            int64_t k = t0 - m / 2 + j;
+            wq[j] = (k >= 0 && k < nb) ? orc_e4m3(creal(xhat[k]) * st) + I * orc_e4m3(cimag(xhat[k]) * st) : 0.0;
+        }
+        for (int i = 0; i < K; i++)
+            for (int64_t r = t0; r < t0 + TILE && r < nb; r++) {
+                cplx acc = 0.0;
+                for (int q = 0; q < m; q++) acc += wq[(r - t0) + q] * conj(tq[(size_t)i * m + q]);
+                double g = st * sig[i];
+                plane[(size_t)i * nb + r] = (creal(acc) * creal(acc) + cimag(acc) * cimag(acc)) / (g * g);
+            }
+    }
+    free(tq); free(sig); free(wq);
+    return 0;
+}
+
 /* Selected cells (zi[c], r[c]) of the plane, c < n.  Returns 0, or -1 on an index off    */
 /* the plane.                                                                             */
 int orc_plane_cells(const cplx *xhat, int64_t nb, int zmax, int m, const cplx *T,
