@@ -64,7 +64,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("own", "reference"), default="own")
-    ap.add_argument("--precision", choices=("auto", "fp32", "bf16", "bf16_split", "fp16_scaled", "bf16_direct"),
+    ap.add_argument("--precision", choices=("auto", "fp32", "bf16", "bf16_split", "fp16_scaled", "bf16_direct",
+                                           "fp8_direct"),
                     default="auto")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -198,6 +199,17 @@ def roofline_correlate(w, precision: str, prof):
                 "avg_launch_ms": ms, "flops_per_launch": flops,
                 "peak_note": "of measured: MEASURED_PEAKS bf16_tflops_sustained (cuBLAS bf16 under the power cap)",
                 "hbm_GBps_algorithmic": (w.K * w.nb * 2 + w.nb * 4) / (ms / 1e3) / 1e9}
+    if precision == "fp8_direct":
+        # the same GEMM with E4M3 operands: its peak is the measured BF16 one times the nominal
+        # FP8 / BF16 ratio (4.5 / 2.25 PFLOP/s dense)
+        flops = 8.0 * w.taps * w.K * w.nb
+        ach = flops / (ms / 1e3) / 1e12
+        peak = MEASURED["bf16_tflops_sustained"] * 2.0
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": _traffic("k3_plane_direct_f8", precision, w.name), "kernel": "k3_plane_direct_f8",
+                "avg_launch_ms": ms, "flops_per_launch": flops,
+                "peak_note": "of measured: MEASURED_PEAKS bf16_tflops_sustained x 2 (nominal FP8/BF16 dense ratio)",
+                "hbm_GBps_algorithmic": (w.K * w.nb * 4 + w.nb * 8) / (ms / 1e3) / 1e9}
     S = 4096
     L = (S - w.taps + 1) // 64 * 64
     n_seg = math.ceil(w.nb / L)
@@ -681,7 +693,7 @@ def own_arm(args):
     # ---- the other precisions on the same GPU and workload (the metric's comparison)
     paths = {}
     if not args.quick and not args.no_compare:
-        for prec in ("fp32", "bf16", "bf16_split", "fp16_scaled", "bf16_direct"):
+        for prec in ("fp32", "bf16", "bf16_split", "fp16_scaled", "bf16_direct", "fp8_direct"):
             if prec == precision:
                 continue
             cmp_steps = max(3, min(args.steps, 100))
@@ -747,7 +759,7 @@ def own_arm(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16_split": "bf16-split", "fp16_scaled": "f16-scaled",
-                                                    "bf16_direct": "bf16-direct"}.get(precision, "bf16"),
+                                                    "bf16_direct": "bf16-direct", "fp8_direct": "e4m3-direct"}.get(precision, "bf16"),
             "data": "synthetic: seeded N(0,1) noise + 8 accelerated Gaussian pulse trains (fdas_synth)",
             "config": config_json(w, precision),
             "roofline": roof, "roofline_correlate": roof_corr, "paths": paths or None, "variants": variants,

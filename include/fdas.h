@@ -70,12 +70,19 @@ typedef enum {
                                 segment (largest component in [0.5, 1)) and the template bank
                                 scaled by the segment length, so no operand overflows and small
                                 ones stay normal; FP32 accumulation; FP32 plane               */
-    FDAS_BF16_DIRECT = 4     /* direct correlation variant: the spectrum (BF16) times the
+    FDAS_BF16_DIRECT = 4,    /* direct correlation variant: the spectrum (BF16) times the
                                 time-domain taps (BF16) as one tensor-core GEMM per block of
                                 bins (the Hankel matrix of the spectrum against all K
                                 templates), FP32 accumulation, BF16 plane; no segment FFTs.
                                 Needs 2 ceil(K/8) 8 <= 256 and the taps image plus windows in
                                 shared memory (K <= 128; taps <= 256 at K = 85), else
+                                FDAS_E_UNSUPPORTED                                            */
+    FDAS_FP8_DIRECT = 5      /* precision ablation of Sec. 3 below BF16: the direct form with
+                                FP8 E4M3 operands (3 mantissa bits), the spectrum scaled by a
+                                power of two per 1024-bin tile and each template by its own,
+                                so that the largest |Re| or |Im| lands in [224, 448]; FP32
+                                accumulation; FP32 plane with the scales divided out.  Needs
+                                2 ceil(K/8) 8 <= 256 and taps % 16 == 0, else
                                 FDAS_E_UNSUPPORTED                                            */
 } fdas_precision;
 

@@ -56,6 +56,7 @@ def _load():
             "orc_spectrum_local": (ctypes.c_int, [P, i64, i64, P]),
             "orc_e4m3": (f64, [f64]),
             "orc_plane_fp8": (ctypes.c_int, [P, i64, ctypes.c_int, ctypes.c_int, P, P]),
+            "orc_plane_fp8_cells": (ctypes.c_int, [P, i64, ctypes.c_int, ctypes.c_int, P, i64, P, P, P]),
             "orc_fresnel": (None, [f64, P, P]),
             "orc_response": (None, [f64, f64, P]),
             "orc_response_quad": (None, [f64, f64, P]),
@@ -130,6 +131,21 @@ def plane_fp8(xhat, zmax: int, m: int, T=None) -> np.ndarray:
     out = np.empty((zmax + 1, xhat.size), dtype=np.float64)
     if _load().orc_plane_fp8(_p(xhat), xhat.size, int(zmax), int(m), _p(T), _p(out)) != 0:
         raise MemoryError("orc_plane_fp8")
+    return out
+
+
+def plane_fp8_cells(xhat, zmax: int, m: int, T, zi, r) -> np.ndarray:
+    """Selected cells of the FP8 direct-correlation plane (orc_plane_fp8_cells)."""
+    xhat = np.ascontiguousarray(xhat, dtype=np.complex128)
+    T = np.ascontiguousarray(T, dtype=np.complex128)
+    zi = np.ascontiguousarray(zi, dtype=np.int32)
+    r = np.ascontiguousarray(r, dtype=np.int64)
+    out = np.empty(zi.size, dtype=np.float64)
+    rc = _load().orc_plane_fp8_cells(_p(xhat), xhat.size, int(zmax), int(m), _p(T), zi.size, _p(zi), _p(r), _p(out))
+    if rc == -2:
+        raise ValueError("cell index off the plane")
+    if rc != 0:
+        raise MemoryError("orc_plane_fp8_cells")
     return out
 
 

@@ -411,14 +411,11 @@ static double e4m3_scale(double M)
 /*   from the largest |Re| or |Im| of its taps;                                              */
 /*   P(r, z) = |sum_q e4m3(s_t Xhat_{r+q}) conj(e4m3(sigma_z T_z(q)))|^2 / (s_t sigma_z)^2    */
 /* (component-wise rounding; the sum in FP64).                                               */
-int orc_plane_fp8(const cplx *xhat, int64_t nb, int zmax, int m, const cplx *T, double *plane)
+#define FP8_TILE 1024
+
+/* sigma_z and the rounded, scaled taps of every template (tq: K x m, sig: K). */
+static void fp8_taps(const cplx *T, int K, int m, cplx *tq, double *sig)
 {
-    int K = zmax + 1;
-    const int TILE = 1024;
-    cplx *tq = (cplx *)malloc(sizeof(cplx) * (size_t)K * m);
-    double *sig = (double *)malloc(sizeof(double) * (size_t)K);
-    cplx *wq = (cplx *)malloc(sizeof(cplx) * (size_t)(TILE + m));
-    if (!tq || !sig || !wq) { free(tq); free(sig); free(wq); return -1; }
     for (int i = 0; i < K; i++) {
         double M = 0.0;
         for (int q = 0; q < m; q++) {
@@ -431,22 +428,66 @@ int orc_plane_fp8(const cplx *xhat, int64_t nb, int zmax, int m, const cplx *T, 
             tq[(size_t)i * m + q] = orc_e4m3(creal(t) * sig[i]) + I * orc_e4m3(cimag(t) * sig[i]);
         }
     }
-    for (int64_t t0 = 0; t0 < nb; t0 += TILE) {
-        double M = 0.0;
-        for (int64_t k = t0 - m / 2; k < t0 + TILE + m / 2; k++)
-            if (k >= 0 && k < nb) M = fmax(M, fmax(fabs(creal(xhat[k])), fabs(cimag(xhat[k]))));
-        double st = e4m3_scale(M);
-        for (int j = 0; j < TILE + m; j++) {
-            int64_t k = t0 - m / 2 + j;
-            wq[j] = (k >= 0 && k < nb) ? orc_e4m3(creal(xhat[k]) * st) + I * orc_e4m3(cimag(xhat[k]) * st) : 0.0;
-        }
+}
+
+/* s_t of the tile starting at bin t0, and its rounded, scaled window wq[j] = e4m3(s_t Xhat_k), */
+/* k = t0 - m/2 + j, j < 1024 + m.                                                              */
+static double fp8_window(const cplx *xhat, int64_t nb, int m, int64_t t0, cplx *wq)
+{
+    double M = 0.0;
+    for (int64_t k = t0 - m / 2; k < t0 + FP8_TILE + m / 2; k++)
+        if (k >= 0 && k < nb) M = fmax(M, fmax(fabs(creal(xhat[k])), fabs(cimag(xhat[k]))));
+    double st = e4m3_scale(M);
+    for (int j = 0; j < FP8_TILE + m; j++) {
+        int64_t k = t0 - m / 2 + j;
+        wq[j] = (k >= 0 && k < nb) ? orc_e4m3(creal(xhat[k]) * st) + I * orc_e4m3(cimag(xhat[k]) * st) : 0.0;
+    }
+    return st;
+}
+
+static double fp8_cell(const cplx *wq, double st, const cplx *tq, double sig, int m, int64_t j0)
+{
+    cplx acc = 0.0;
+    for (int q = 0; q < m; q++) acc += wq[j0 + q] * conj(tq[q]);
+    double g = st * sig;
+    return (creal(acc) * creal(acc) + cimag(acc) * cimag(acc)) / (g * g);
+}
+
+int orc_plane_fp8(const cplx *xhat, int64_t nb, int zmax, int m, const cplx *T, double *plane)
+{
+    int K = zmax + 1;
+    cplx *tq = (cplx *)malloc(sizeof(cplx) * (size_t)K * m);
+    double *sig = (double *)malloc(sizeof(double) * (size_t)K);
+    cplx *wq = (cplx *)malloc(sizeof(cplx) * (size_t)(FP8_TILE + m));
+    if (!tq || !sig || !wq) { free(tq); free(sig); free(wq); return -1; }
+    fp8_taps(T, K, m, tq, sig);
+    for (int64_t t0 = 0; t0 < nb; t0 += FP8_TILE) {
+        double st = fp8_window(xhat, nb, m, t0, wq);
         for (int i = 0; i < K; i++)
-            for (int64_t r = t0; r < t0 + TILE && r < nb; r++) {
-                cplx acc = 0.0;
-                for (int q = 0; q < m; q++) acc += wq[(r - t0) + q] * conj(tq[(size_t)i * m + q]);
-                double g = st * sig[i];
-                plane[(size_t)i * nb + r] = (creal(acc) * creal(acc) + cimag(acc) * cimag(acc)) / (g * g);
-            }
+            for (int64_t r = t0; r < t0 + FP8_TILE && r < nb; r++)
+                plane[(size_t)i * nb + r] = fp8_cell(wq, st, tq + (size_t)i * m, sig[i], m, r - t0);
+    }
+    free(tq); free(sig); free(wq);
+    return 0;
+}
+
+/* Selected cells (zi[c], r[c]) of the FP8 plane, c < n.  Returns 0, -1 on an allocation     */
+/* failure, -2 on an index off the plane.                                                    */
+int orc_plane_fp8_cells(const cplx *xhat, int64_t nb, int zmax, int m, const cplx *T,
+                        int64_t n, const int32_t *zi, const int64_t *r, double *out)
+{
+    int K = zmax + 1;
+    for (int64_t c = 0; c < n; c++)
+        if (zi[c] < 0 || zi[c] >= K || r[c] < 0 || r[c] >= nb) return -2;
+    cplx *tq = (cplx *)malloc(sizeof(cplx) * (size_t)K * m);
+    double *sig = (double *)malloc(sizeof(double) * (size_t)K);
+    cplx *wq = (cplx *)malloc(sizeof(cplx) * (size_t)(FP8_TILE + m));
+    if (!tq || !sig || !wq) { free(tq); free(sig); free(wq); return -1; }
+    fp8_taps(T, K, m, tq, sig);
+    for (int64_t c = 0; c < n; c++) {
+        int64_t t0 = r[c] / FP8_TILE * FP8_TILE;
+        double st = fp8_window(xhat, nb, m, t0, wq);
+        out[c] = fp8_cell(wq, st, tq + (size_t)zi[c] * m, sig[zi[c]], m, r[c] - t0);
     }
     free(tq); free(sig); free(wq);
     return 0;

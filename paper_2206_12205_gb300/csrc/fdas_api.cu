@@ -33,7 +33,9 @@ fdas_status record(Plan *p, cudaError_t e) {
 
 bool plane_is_bf16(const Plan *p) { return p->cfg.precision == FDAS_BF16 || p->cfg.precision == FDAS_BF16_DIRECT; }
 // the DFT-on-tensor-cores paths (segment spectra, DFT operand images and twiddles)
-bool uses_tensor_path(const Plan *p) { return p->cfg.precision != FDAS_FP32 && p->cfg.precision != FDAS_BF16_DIRECT; }
+bool uses_tensor_path(const Plan *p) {
+    return p->cfg.precision != FDAS_FP32 && p->cfg.precision != FDAS_BF16_DIRECT && p->cfg.precision != FDAS_FP8_DIRECT;
+}
 
 // Alignment the kernels' vector accesses rely on (documented in fdas.h).
 bool aligned(const void *ptr, uintptr_t a) { return (reinterpret_cast<uintptr_t>(ptr) & (a - 1)) == 0; }
@@ -51,6 +53,7 @@ cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale,
         case FDAS_BF16_SPLIT: return launch_plane_split(p, x, scale, ws, static_cast<float *>(d_plane), st);
         case FDAS_FP16_SCALED: return launch_plane_f16(p, x, scale, ws, static_cast<float *>(d_plane), st);
         case FDAS_BF16_DIRECT: return launch_plane_direct(p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
+        case FDAS_FP8_DIRECT: return launch_plane_direct_f8(p, x, scale, static_cast<float *>(d_plane), st);
         default: return launch_plane_fp32(p, x, scale, ws, static_cast<float *>(d_plane), st);
     }
 }
@@ -66,7 +69,7 @@ extern "C" {
 
 static_assert(sizeof(fdas_config) == 72, "fdas_config layout (the Python binding mirrors it)");
 
-int fdas_version(void) { return 103; }
+int fdas_version(void) { return 104; }
 
 const char *fdas_status_string(fdas_status s) {
     switch (s) {
@@ -102,7 +105,7 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     for (int l = 0; l < 5; l++)
         if (c.thr[l] != c.thr[l]) return FDAS_E_INVALID;
     if (c.precision != FDAS_FP32 && c.precision != FDAS_BF16 && c.precision != FDAS_BF16_SPLIT &&
-        c.precision != FDAS_FP16_SCALED && c.precision != FDAS_BF16_DIRECT)
+        c.precision != FDAS_FP16_SCALED && c.precision != FDAS_BF16_DIRECT && c.precision != FDAS_FP8_DIRECT)
         return FDAS_E_INVALID;
     if (c.precision != FDAS_FP32 && c.taps > fdas::TC_MAX_TAPS) return FDAS_E_UNSUPPORTED;
 
@@ -136,13 +139,16 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     p->ws_tmp = off;   off = align_up(off + sizeof(float2) * (size_t)p->M);
     p->ws_part = off;  off = align_up(off + sizeof(double) * (size_t)p->n_part);
     p->ws_scale = off; off = align_up(off + 16);
-    if (c.precision == FDAS_BF16_DIRECT && !fdas::direct_geometry(*p, nullptr, nullptr, nullptr)) {
+    if ((c.precision == FDAS_BF16_DIRECT && !fdas::direct_geometry(*p, nullptr, nullptr, nullptr)) ||
+        (c.precision == FDAS_FP8_DIRECT && !fdas::direct_geometry_f8(*p, nullptr, nullptr, nullptr))) {
         delete p;
         return FDAS_E_UNSUPPORTED;
     }
-    // segment spectra, or the direct path's packed BF16 spectrum
+    // segment spectra, or the BF16 direct path's packed spectrum (the FP8 direct path reads the
+    // spectrum itself)
     const size_t ybytes = c.precision == FDAS_BF16_DIRECT ? sizeof(uint32_t) * fdas::direct_pack_words(*p)
-                                                          : sizeof(float2) * (size_t)p->n_seg * p->S;
+                          : c.precision == FDAS_FP8_DIRECT ? 256
+                                                           : sizeof(float2) * (size_t)p->n_seg * p->S;
     p->ws_y = off;     off = align_up(off + ybytes);
     p->ws_segscale = off; off = align_up(off + sizeof(float) * (size_t)p->n_seg);
     const size_t n_scan_blocks = (size_t)((p->n_units + fdas::PEAK_SCAN_BLOCK - 1) / fdas::PEAK_SCAN_BLOCK);
@@ -200,6 +206,12 @@ fdas_status fdas_make_templates(fdas_plan_t plan, void *stream) {
         int kp = 0;
         fdas::direct_geometry(*p, &kp, nullptr, nullptr);
         alloc((void **)&p->d_dimg, (size_t)2 * kp * 2 * p->m * 2);
+    }
+    if (p->cfg.precision == FDAS_FP8_DIRECT) {
+        int kp = 0;
+        fdas::direct_geometry_f8(*p, &kp, nullptr, nullptr);
+        alloc((void **)&p->d_dimg, (size_t)2 * kp * 2 * p->m);
+        alloc((void **)&p->d_dsig, sizeof(float) * (size_t)kp);
     }
     alloc((void **)&p->d_status, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);
@@ -439,6 +451,7 @@ void fdas_destroy(fdas_plan_t plan) {
         cudaFree(p->d_tcF);
         cudaFree(p->d_tcTw);
         cudaFree(p->d_dimg);
+        cudaFree(p->d_dsig);
         cudaFree(p->d_status);
     }
     for (int s = 0; s < fdas::PROF_STAGES; s++)

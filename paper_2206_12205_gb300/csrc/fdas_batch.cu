@@ -333,6 +333,7 @@ fdas_status fdas_batch_make_templates(fdas_batch_t b, void *stream) {
         p->d_Gh = l->d_Gh;
         p->d_tcFh = l->d_tcFh;
         p->d_dimg = l->d_dimg;
+        p->d_dsig = l->d_dsig;
         p->borrowed = true;
         e = cudaMalloc((void **)&p->d_status, sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);

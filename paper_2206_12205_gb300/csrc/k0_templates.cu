@@ -158,6 +158,64 @@ __global__ void k0_direct_image(const double2 *__restrict__ taps, int K, int m, 
     img[tc_kmajor_elem(N, row, k)] = __double2bfloat16(v);
 }
 
+// E4M3 code of v (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; normal 2^-6 .. 448,
+// subnormal steps of 2^-9), rounded once from FP64 to nearest with ties to even and saturated at
+// +-448 (the FP8 operands of FDAS_FP8_DIRECT).
+__device__ uint8_t e4m3_code(double v) {
+    const uint8_t sgn = signbit(v) ? 0x80 : 0x00;
+    const double a = fabs(v);
+    if (a == 0.0) return sgn;
+    int E;
+    frexp(a, &E);
+    int e = max(E - 1, -6);                      // binade of a; the subnormals share 2^-6's step
+    double q = rint(ldexp(a, 3 - e));            // a in units of the binade's step 2^(e-3)
+    if (q >= 16.0) { q = 8.0; e += 1; }          // rounded up into the next binade
+    if (e > 8 || (e == 8 && q > 14.0)) return sgn | 0x7E;     // 448 = 1.75 x 2^8
+    if (q < 8.0) return sgn | (uint8_t)q;                      // subnormal: exponent field 0
+    return sgn | (uint8_t)(((e + 7) << 3) | ((int)q - 8));
+}
+
+// The FP8 direct path's operand image: the rows of k0_direct_image, scaled per template z by the
+// power of two sigma_z that brings its largest |Re| or |Im| into [224, 448], rounded to E4M3,
+// in K-major core matrices of 8 rows x 16 bytes (element (row, k) at byte
+// ((k / 16) (N / 8) + row / 8) 128 + (row % 8) 16 + k % 16).  dsig[z] = 1 / sigma_z^2 undoes the
+// scale on the plane.  One block per padded template row.
+__global__ void k0_direct_image_f8(const double2 *__restrict__ taps, int K, int m, int Kpad,
+                                   uint8_t *__restrict__ img, float *__restrict__ dsig) {
+    __shared__ double red[256];
+    const int z = blockIdx.x, N = 2 * Kpad;
+    double M = 0.0;
+    if (z < K)
+        for (int q = threadIdx.x; q < m; q += blockDim.x) {
+            const double2 t = taps[(size_t)z * m + q];
+            M = fmax(M, fmax(fabs(t.x), fabs(t.y)));
+        }
+    red[threadIdx.x] = M;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    M = red[0];
+    double sig = 1.0;
+    if (M > 0.0) {
+        int E;
+        const double f = frexp(M, &E);           // M = f 2^E; 448 = 0.875 x 2^9
+        sig = ldexp(1.0, (f <= 0.875 ? 9 : 8) - E);
+    }
+    if (threadIdx.x == 0) dsig[z] = z < K ? (float)(1.0 / (sig * sig)) : 0.f;
+    for (int idx = threadIdx.x; idx < 2 * 2 * m; idx += blockDim.x) {
+        const int p = idx / (2 * m), k = idx % (2 * m), q = k >> 1, sc = k & 1;
+        double v = 0.0;
+        if (z < K) {
+            const double2 t = taps[(size_t)z * m + q];
+            v = (p == 0 ? (sc == 0 ? t.x : t.y) : (sc == 0 ? -t.y : t.x)) * sig;
+        }
+        const int row = p * Kpad + z;
+        img[((size_t)(k >> 4) * (N >> 3) + (row >> 3)) * 128 + (row & 7) * 16 + (k & 15)] = e4m3_code(v);
+    }
+}
+
 // exp(-2 pi i j / n) in FP64; f = 2j/n is exact for a power-of-two n and is reduced to
 // (-1, 1] before the libm call, so the argument error stays below pi * 2^-53.
 double2 host_unit(int64_t j, int64_t n) {
@@ -221,7 +279,12 @@ cudaError_t launch_make_templates(Plan &p, cudaStream_t st) {
         k0_taps<<<(n + 127) / 128, 128, 0, st>>>(d_taps, K, m, p.cfg.zmax, gl);
         k0_normalise<<<K, 256, 0, st>>>(d_taps, m, d_eta);
         dim3 grid((S + 255) / 256, K);
-        if (p.d_dimg) {
+        if (p.d_dimg && p.cfg.precision == FDAS_FP8_DIRECT) {
+            int Kpad = 0;
+            direct_geometry_f8(p, &Kpad, nullptr, nullptr);
+            k0_direct_image_f8<<<(unsigned)Kpad, 256, 0, st>>>(d_taps, K, m, Kpad, static_cast<uint8_t *>(p.d_dimg),
+                                                              p.d_dsig);
+        } else if (p.d_dimg) {
             int Kpad = 0;
             direct_geometry(p, &Kpad, nullptr, nullptr);
             const int64_t ne = (int64_t)2 * Kpad * 2 * m;

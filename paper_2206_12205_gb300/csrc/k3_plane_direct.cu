@@ -20,6 +20,8 @@
 // copies the windows, warps 2-9 read the accumulators (TMEM lanes = a, columns = (p, z)), form
 // |.|^2 and store the BF16 plane.  Two accumulator slots in TMEM, two window slots in shared
 // memory, every mbarrier wait bounded (timeout -> FDAS_DEV_TIMEOUT, MMAs drained, TMEM freed).
+#include <cuda_fp8.h>
+
 #include "fdas_internal.cuh"
 #include "tc_sm100.cuh"
 
@@ -213,7 +215,232 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct(const uint32_
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// FP8 ablation of the direct form (FDAS_FP8_DIRECT): E4M3 operands (3 mantissa bits) with
+// power-of-two scales -- per 1024-bin tile for the spectrum (largest |Re| or |Im| of the tile's
+// window brought into [224, 448]) and per template for the taps -- kind::f8f6f4 MMAs with FP32
+// accumulation, and an FP32 plane times 1 / (s_t sigma_z)^2.  A complex E4M3 pair is 2 bytes, so
+// the Hankel rows 16 bytes apart are r = r0 + 8 a + b: a tile is 1024 bins in 8 sets of 128 rows
+// and keeps 8 shifted copies of its window.
+constexpr int DT8 = 1024;
+
+__device__ __forceinline__ float e4m3_scale(float M) {       // largest 2^k with M 2^k <= 448
+    if (!(M > 0.f)) return 1.f;
+    int E;
+    const float f = frexpf(M, &E);
+    return ldexpf(1.f, (f <= 0.875f ? 9 : 8) - E);
+}
+
+__device__ __forceinline__ uint16_t e4m3x2(float re, float im) {
+    return (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(re, im), __NV_SATFINITE, __NV_E4M3);
+}
+
+__global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct_f8(const float2 *__restrict__ X,
+                                                                      const float *__restrict__ scale_ptr,
+                                                                      const uint4 *__restrict__ Bimg,
+                                                                      const float *__restrict__ tsig,
+                                                                      float *__restrict__ plane, int K, int Kpad, int m,
+                                                                      int64_t nb, int64_t n_tiles, int64_t tiles_per_cta,
+                                                                      uint32_t tmem_cols, int32_t *__restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int N = 2 * Kpad, KD = 2 * m, WW = DT8 + m;             // WW 16-bit words per window copy
+    const uint32_t b_bytes = (uint32_t)N * KD;
+    unsigned char *sB = smem;
+    uint16_t *sW = reinterpret_cast<uint16_t *>(smem + b_bytes);               // [2 slots][8 copies][WW]
+    // 1 / s_t^2 of tile k at [k % 4]: the producer rewrites entry k % 4 for tile k + 4 only after
+    // the MMAs of tile k + 2 are done, which needs the epilogue past tile k
+    float *s_inv2 = reinterpret_cast<float *>(smem + b_bytes + 2u * 8u * WW * 2u);
+    DBars *bars = reinterpret_cast<DBars *>(s_inv2 + 4);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, tmem_cols);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2; s++) {
+            tc::mbar_init(&bars->w_full[s], 32);
+            tc::mbar_init(&bars->w_free[s], 1);
+            tc::mbar_init(&bars->d_full[s], 1);
+            tc::mbar_init(&bars->d_free[s], 256);
+        }
+        tc::mbar_init(&bars->drain, 1);
+        *abort_flag = 0;
+    }
+    for (uint32_t i = tid; i < b_bytes / 16; i += D_WARPS * 32) reinterpret_cast<uint4 *>(sB)[i] = __ldg(Bimg + i);
+    tc::fence_proxy_async_smem();
+    tc::fence_before_thread_sync();
+    __syncthreads();
+    tc::fence_after_thread_sync();
+
+    const uint32_t tbase = *tslot;
+    const int64_t t0 = (int64_t)blockIdx.x * tiles_per_cta;
+    const int64_t t1 = min(n_tiles, t0 + tiles_per_cta);
+    const int64_t n_my = t1 - t0;
+
+    if (warp == 0) {
+        if (n_my > 0) {
+            auto wait = [&](uint64_t *bar, uint32_t parity) {
+                return __shfl_sync(0xffffffffu, (int)d_wait(bar, parity, abort_flag), 0) != 0;
+            };
+            const uint32_t id = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);  // F32 D, E4M3 A, B
+            const uint64_t bdesc = tc::smem_desc(tc::smem_u32(sB), (uint32_t)N * 16, 128);
+            const uint64_t wdesc = tc::smem_desc(tc::smem_u32(sW), 16, 128);
+            bool ok = true;
+            for (int64_t k = 0; k < n_my && ok; k++) {
+                ok = wait(&bars->w_full[k & 1], (uint32_t)((k >> 1) & 1));
+                if (!ok) break;
+                tc::fence_after_thread_sync();
+                for (int b = 0; b < 8 && ok; b++) {
+                    const int64_t u = 8 * k + b;
+                    const int sl = (int)(u & 1);
+                    if (u >= 2) ok = wait(&bars->d_free[sl], (uint32_t)(((u - 2) >> 1) & 1));
+                    if (!ok) break;
+                    tc::fence_after_thread_sync();
+                    const uint64_t a = wdesc + (uint64_t)((((k & 1) * 8 + b) * WW * 2) >> 4);
+                    for (int s = 0; s < KD / 32; s++)                              // 32 bytes of K per MMA
+                        tc::mma_f8_warp(tbase + (uint32_t)sl * N, a + (uint64_t)(2 * s), bdesc + (uint64_t)(s * 2 * N), id,
+                                        s > 0 ? 1u : 0u);
+                    tc::mma_commit_warp(&bars->d_full[sl]);
+                }
+                tc::mma_commit_warp(&bars->w_free[k & 1]);
+            }
+            tc::mma_commit_warp(&bars->drain);
+            tc::mbar_wait_bounded(&bars->drain, 0, D_WAIT);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // window of tile k: Xhat[r0 - m/2 + w], w < WW + 8 (zero off the spectrum), scaled by s_t and
+        // rounded to E4M3 pairs; copy b holds window[b + j], j < WW
+        const float gsc = scale_ptr ? __ldg(scale_ptr) : 1.0f;
+        const int WL = WW + 8;
+        for (int64_t k = 0; k < n_my; k++) {
+            if (k >= 2 && !d_wait(&bars->w_free[k & 1], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+            const int64_t w0 = (t0 + k) * DT8 - m / 2;
+            float M = 0.f;                                                 // over the window's WW bins
+            for (int w = lane; w < WW; w += 32) {
+                const int64_t kk = w0 + w;
+                if (kk >= 0 && kk < nb) {
+                    const float2 v = __ldg(X + kk);
+                    M = fmaxf(M, fmaxf(fabsf(v.x * gsc), fabsf(v.y * gsc)));
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, o));
+            const float st = e4m3_scale(M);
+            uint16_t *dst = sW + (size_t)(k & 1) * 8 * WW;
+            for (int w = lane; w < WL; w += 32) {
+                const int64_t kk = w0 + w;
+                float2 v = make_float2(0.f, 0.f);
+                if (kk >= 0 && kk < nb) {
+                    v = __ldg(X + kk);
+                    v = make_float2(v.x * gsc * st, v.y * gsc * st);
+                }
+                const uint16_t q = e4m3x2(v.x, v.y);
+#pragma unroll
+                for (int b = 0; b < 8; b++) {
+                    const int j = w - b;
+                    if (j >= 0 && j < WW) dst[b * WW + j] = q;
+                }
+            }
+            if (lane == 0) s_inv2[k & 3] = 1.0f / (st * st);
+            tc::fence_proxy_async_smem();
+            d_arrive(&bars->w_full[k & 1]);
+        }
+    } else {
+        const int quad = warp & 3, h = (warp - D_EPI0) >> 2;
+        const int a = 32 * quad + lane, Kh = Kpad / 2;
+        const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+        for (int64_t k = 0; k < n_my; k++) {
+            const int64_t r0 = (t0 + k) * DT8;
+            // the tile's window barrier (acquire of the producer's scale): its next phase needs the
+            // MMAs of this tile done, which need this epilogue, so it cannot run two phases ahead
+            if (!d_wait(&bars->w_full[k & 1], (uint32_t)((k >> 1) & 1), abort_flag)) break;
+            const float si = s_inv2[k & 3];
+            bool ok = true;
+            for (int b = 0; b < 8; b++) {
+                const int64_t u = 8 * k + b;
+                const int sl = (int)(u & 1);
+                if (!d_wait(&bars->d_full[sl], (uint32_t)((u >> 1) & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_thread_sync();
+                const int64_t r = r0 + 8 * a + b;
+                const bool in = r < nb;
+                const uint32_t col = tbase + lane_base + (uint32_t)sl * N;
+                for (int z0 = h * Kh; z0 < h * Kh + Kh; z0 += 4) {
+                    uint32_t re[4], im[4];
+                    tmem_ld4(col + z0, re);
+                    tmem_ld4(col + Kpad + z0, im);
+                    tc::tmem_ld_wait();
+                    if (z0 + 4 >= h * Kh + Kh) {
+                        tc::fence_before_thread_sync();
+                        d_arrive(&bars->d_free[sl]);
+                    }
+                    if (in) {
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            const int z = z0 + e;
+                            if (z < K) {
+                                const float xr = __uint_as_float(re[e]), xi = __uint_as_float(im[e]);
+                                plane[(int64_t)z * nb + r] = (xr * xr + xi * xi) * si * __ldg(tsig + z);
+                            }
+                        }
+                    }
+                }
+            }
+            if (!ok) break;
+        }
+    }
+    tc::fence_before_thread_sync();
+    __syncthreads();
+    if (tid == 0 && *abort_flag) atomicOr(status, FDAS_DEV_TIMEOUT);
+    if (warp == 0) {
+        tc::fence_after_thread_sync();
+        tc::tmem_dealloc(tbase, tmem_cols);
+    }
+}
+
 }  // namespace
+
+bool direct_geometry_f8(const Plan &p, int *Kpad, uint32_t *smem_bytes, uint32_t *tmem_cols) {
+    const int kp = (p.K + 7) / 8 * 8;
+    const int N = 2 * kp;
+    if (N > 256 || p.m % 16 != 0) return false;
+    const uint64_t need = (uint64_t)N * 2 * p.m + 2ull * 8 * (DT8 + p.m) * 2 + 16 + sizeof(DBars) + 16;
+    if (need > 227 * 1024) return false;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)(2 * N)) cols <<= 1;
+    if (Kpad) *Kpad = kp;
+    if (smem_bytes) *smem_bytes = (uint32_t)std::max<uint64_t>(need, D_MIN_SMEM);
+    if (tmem_cols) *tmem_cols = cols;
+    return true;
+}
+
+cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float *d_scale, float *d_plane,
+                                   cudaStream_t st) {
+    int Kpad = 0;
+    uint32_t smem = 0, cols = 0;
+    if (!p.d_dimg || !p.d_dsig || !direct_geometry_f8(p, &Kpad, &smem, &cols)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k3_plane_direct_f8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t n_tiles = (p.nb + DT8 - 1) / DT8;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
+    const int64_t ctas = std::min<int64_t>(n_tiles, (int64_t)sms);
+    const int64_t per = (n_tiles + ctas - 1) / ctas;
+    const int64_t grid = (n_tiles + per - 1) / per;
+    p.prof.begin(FDAS_STAGE_CORRELATE, st);
+    k3_plane_direct_f8<<<(unsigned)grid, D_WARPS * 32, smem, st>>>(d_x, d_scale, reinterpret_cast<const uint4 *>(p.d_dimg),
+                                                                   p.d_dsig, d_plane, p.K, Kpad, p.m, p.nb, n_tiles, per,
+                                                                   cols, p.d_status);
+    p.prof.end(FDAS_STAGE_CORRELATE, st);
+    p.prof.launches += 1;
+    return cudaGetLastError();
+}
 
 // Geometry of the direct path for a plan: padded template count, shared memory, TMEM columns.
 bool direct_geometry(const Plan &p, int *Kpad, uint32_t *smem_bytes, uint32_t *tmem_cols) {

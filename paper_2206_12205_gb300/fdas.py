@@ -17,10 +17,10 @@ import numpy as np
 from . import build as _build
 
 FDAS_OK, FDAS_E_INVALID, FDAS_E_UNSUPPORTED, FDAS_E_NOMEM, FDAS_E_CUDA, FDAS_E_OVERFLOW, FDAS_E_TIMEOUT, FDAS_E_STATE = range(8)
-FDAS_FP32, FDAS_BF16, FDAS_BF16_SPLIT, FDAS_FP16_SCALED, FDAS_BF16_DIRECT = 0, 1, 2, 3, 4
+FDAS_FP32, FDAS_BF16, FDAS_BF16_SPLIT, FDAS_FP16_SCALED, FDAS_BF16_DIRECT, FDAS_FP8_DIRECT = 0, 1, 2, 3, 4, 5
 FDAS_DEV_PEAK_OVERFLOW, FDAS_DEV_TIMEOUT = 0x1, 0x2
 PRECISIONS = {"fp32": FDAS_FP32, "bf16": FDAS_BF16, "bf16_split": FDAS_BF16_SPLIT, "fp16_scaled": FDAS_FP16_SCALED,
-              "bf16_direct": FDAS_BF16_DIRECT}
+              "bf16_direct": FDAS_BF16_DIRECT, "fp8_direct": FDAS_FP8_DIRECT}
 
 # every symbol include/fdas.h declares
 EXPORTED = (

@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert fd.fdas_version() == 103
+    assert fd.fdas_version() == 104
     for code in range(8):
         assert fd.status_string(code) and fd.status_string(code) != "unknown status"
     assert fd.status_string(99) == "unknown status"
@@ -171,5 +171,21 @@ def test_direct_plan_geometry(lib):
             fd.fdas_plan(fd.make_config(n, zmax, m, 1024, precision="bf16_direct"))
         assert ei.value.status == fb.FDAS_E_UNSUPPORTED, (n, zmax, m)
     small = fd.fdas_plan(fd.make_config(1 << 11, 0, 8, 1024, precision="bf16_direct"))
+    assert small.info.K == 1
+    fd.fdas_destroy(small)
+
+
+def test_fp8_direct_plan_geometry(lib):
+    """FDAS_FP8_DIRECT: an FP32 plane; 2 ceil(K/8) 8 <= 256 and taps % 16 == 0 (a 32-byte MMA
+    K-step is 16 complex E4M3 pairs), else unsupported."""
+    ok = fd.fdas_plan(fd.make_config(1 << 23, 84, 256, 8192, precision="fp8_direct", max_harm=16))
+    assert ok.info.plane_elem_bytes == 4 and ok.info.K == 85
+    assert ok.info.plane_bytes == 4 * 85 * (1 << 22)
+    fd.fdas_destroy(ok)
+    for n, zmax, m in ((1 << 16, 128, 64), (1 << 16, 16, 40), (1 << 16, 16, 8)):
+        with pytest.raises(fd.FdasError) as ei:
+            fd.fdas_plan(fd.make_config(n, zmax, m, 1024, precision="fp8_direct"))
+        assert ei.value.status == fb.FDAS_E_UNSUPPORTED, (n, zmax, m)
+    small = fd.fdas_plan(fd.make_config(1 << 11, 0, 16, 1024, precision="fp8_direct"))
     assert small.info.K == 1
     fd.fdas_destroy(small)

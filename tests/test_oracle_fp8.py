@@ -55,3 +55,19 @@ def test_fp8_plane_against_exact_plane():
     xi[0] = 0
     p8 = oracle.plane_fp8(xi, 0, 8)
     assert np.allclose(p8[0], np.abs(xi) ** 2, rtol=0, atol=1e-9)
+
+
+def test_fp8_cells_are_the_planes_cells():
+    """The sampled-cell form (used at sizes the full plane would take hours for) agrees bit for
+    bit with the full FP8 plane, tile edges and the last bins included."""
+    n, zmax, m = 1 << 13, 6, 32
+    x = (synth.noise(n, synth.rng_for(73, 1)) + synth.chirp(n, 0.2, 1500.0, 3.0)).astype(np.float32)
+    xh, _ = oracle.spectrum(x)
+    T, _ = oracle.templates(zmax, m)
+    full = oracle.plane_fp8(xh, zmax, m, T)
+    r = np.array([0, 1, 1023, 1024, 1025, 2047, 3000, n // 2 - 1] * 3, dtype=np.int64)
+    zi = np.repeat(np.array([0, 3, zmax], dtype=np.int32), 8)
+    got = oracle.plane_fp8_cells(xh, zmax, m, T, zi, r)
+    assert np.array_equal(got, full[zi, r])
+    with pytest.raises(ValueError):
+        oracle.plane_fp8_cells(xh, zmax, m, T, np.array([zmax + 1], np.int32), np.array([0]))
