@@ -53,7 +53,7 @@ cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale,
         case FDAS_BF16_SPLIT: return launch_plane_split(p, x, scale, ws, static_cast<float *>(d_plane), st);
         case FDAS_FP16_SCALED: return launch_plane_f16(p, x, scale, ws, static_cast<float *>(d_plane), st);
         case FDAS_BF16_DIRECT: return launch_plane_direct(p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
-        case FDAS_FP8_DIRECT: return launch_plane_direct_f8(p, x, scale, static_cast<float *>(d_plane), st);
+        case FDAS_FP8_DIRECT: return launch_plane_direct_f8(p, x, scale, ws, static_cast<float *>(d_plane), st);
         default: return launch_plane_fp32(p, x, scale, ws, static_cast<float *>(d_plane), st);
     }
 }
@@ -140,7 +140,7 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     p->ws_part = off;  off = align_up(off + sizeof(double) * (size_t)p->n_part);
     p->ws_scale = off; off = align_up(off + 16);
     if ((c.precision == FDAS_BF16_DIRECT && !fdas::direct_geometry(*p, nullptr, nullptr, nullptr)) ||
-        (c.precision == FDAS_FP8_DIRECT && !fdas::direct_geometry_f8(*p, nullptr, nullptr, nullptr))) {
+        (c.precision == FDAS_FP8_DIRECT && !fdas::direct_geometry_f8(*p, nullptr, nullptr))) {
         delete p;
         return FDAS_E_UNSUPPORTED;
     }
@@ -208,10 +208,10 @@ fdas_status fdas_make_templates(fdas_plan_t plan, void *stream) {
         alloc((void **)&p->d_dimg, (size_t)2 * kp * 2 * p->m * 2);
     }
     if (p->cfg.precision == FDAS_FP8_DIRECT) {
-        int kp = 0;
-        fdas::direct_geometry_f8(*p, &kp, nullptr, nullptr);
-        alloc((void **)&p->d_dimg, (size_t)2 * kp * 2 * p->m);
-        alloc((void **)&p->d_dsig, sizeof(float) * (size_t)kp);
+        int groups = 0;
+        fdas::direct_geometry_f8(*p, &groups, nullptr);
+        alloc((void **)&p->d_dimg, (size_t)groups * 64 * 2 * p->m);
+        alloc((void **)&p->d_dsig, sizeof(float) * 32 * (size_t)groups);
     }
     alloc((void **)&p->d_status, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);

@@ -80,7 +80,7 @@ struct Plan {
     __half2 *d_Gh;         // [K][S] FP16 template bank times S, stage-1 operand order
     void *d_tcFh;          // FP16 K-major DFT operand images F1, F2 (2 x 32 KB)
     void *d_dimg;          // direct paths: conj(taps) real-ified, K-major operand image (BF16 or E4M3)
-    float *d_dsig;         // FP8 direct path: 1 / sigma_z^2 per template row (the taps' scales)
+    float *d_dsig;         // FP8 direct path: 1 / sigma_z^2 per template (the taps' scales), 32 per group
     float2 *d_tcTw;        // W_4096^{n2 k1}, [k1][n2] (32 KB)
     int32_t *d_status;     // sticky device status word
     bool templates_ready;
@@ -139,8 +139,8 @@ cudaError_t launch_plane_split(const Plan &p, const float2 *d_x, const float *d_
                                cudaStream_t st);
 bool direct_geometry(const Plan &p, int *Kpad, uint32_t *smem_bytes, uint32_t *tmem_cols);
 size_t direct_pack_words(const Plan &p);
-bool direct_geometry_f8(const Plan &p, int *Kpad, uint32_t *smem_bytes, uint32_t *tmem_cols);
-cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float *d_scale, float *d_plane,
+bool direct_geometry_f8(const Plan &p, int *n_groups, uint32_t *smem_bytes);
+cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
                                    cudaStream_t st);
 cudaError_t launch_plane_direct(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
                                 __nv_bfloat16 *d_plane, cudaStream_t st);

@@ -176,14 +176,15 @@ __device__ uint8_t e4m3_code(double v) {
 }
 
 // The FP8 direct path's operand image: the rows of k0_direct_image, scaled per template z by the
-// power of two sigma_z that brings its largest |Re| or |Im| into [224, 448], rounded to E4M3,
-// in K-major core matrices of 8 rows x 16 bytes (element (row, k) at byte
-// ((k / 16) (N / 8) + row / 8) 128 + (row % 8) 16 + k % 16).  dsig[z] = 1 / sigma_z^2 undoes the
-// scale on the plane.  One block per padded template row.
-__global__ void k0_direct_image_f8(const double2 *__restrict__ taps, int K, int m, int Kpad,
-                                   uint8_t *__restrict__ img, float *__restrict__ dsig) {
+// power of two sigma_z that brings its largest |Re| or |Im| into [224, 448], rounded to E4M3, in
+// groups of 32 templates: group g = z / 32 holds 64 rows (row p 32 + z % 32, p = 0 for the Re
+// output, 1 for Im) x 2m bytes, K-major in core matrices of 8 rows x 16 bytes (element (row, k)
+// at byte g 128 m + ((k / 16) 8 + row / 8) 128 + (row % 8) 16 + k % 16).  dsig[z] = 1 / sigma_z^2
+// undoes the scale on the plane.  One block per padded template.
+__global__ void k0_direct_image_f8(const double2 *__restrict__ taps, int K, int m, uint8_t *__restrict__ img,
+                                   float *__restrict__ dsig) {
     __shared__ double red[256];
-    const int z = blockIdx.x, N = 2 * Kpad;
+    const int z = blockIdx.x;
     double M = 0.0;
     if (z < K)
         for (int q = threadIdx.x; q < m; q += blockDim.x) {
@@ -211,8 +212,9 @@ __global__ void k0_direct_image_f8(const double2 *__restrict__ taps, int K, int 
             const double2 t = taps[(size_t)z * m + q];
             v = (p == 0 ? (sc == 0 ? t.x : t.y) : (sc == 0 ? -t.y : t.x)) * sig;
         }
-        const int row = p * Kpad + z;
-        img[((size_t)(k >> 4) * (N >> 3) + (row >> 3)) * 128 + (row & 7) * 16 + (k & 15)] = e4m3_code(v);
+        const int row = p * 32 + (z & 31);
+        img[(size_t)(z >> 5) * 128 * m + ((size_t)(k >> 4) * 8 + (row >> 3)) * 128 + (row & 7) * 16 + (k & 15)] =
+            e4m3_code(v);
     }
 }
 
@@ -280,10 +282,10 @@ cudaError_t launch_make_templates(Plan &p, cudaStream_t st) {
         k0_normalise<<<K, 256, 0, st>>>(d_taps, m, d_eta);
         dim3 grid((S + 255) / 256, K);
         if (p.d_dimg && p.cfg.precision == FDAS_FP8_DIRECT) {
-            int Kpad = 0;
-            direct_geometry_f8(p, &Kpad, nullptr, nullptr);
-            k0_direct_image_f8<<<(unsigned)Kpad, 256, 0, st>>>(d_taps, K, m, Kpad, static_cast<uint8_t *>(p.d_dimg),
-                                                              p.d_dsig);
+            int groups = 0;
+            direct_geometry_f8(p, &groups, nullptr);
+            k0_direct_image_f8<<<(unsigned)(32 * groups), 256, 0, st>>>(d_taps, K, m, static_cast<uint8_t *>(p.d_dimg),
+                                                                       p.d_dsig);
         } else if (p.d_dimg) {
             int Kpad = 0;
             direct_geometry(p, &Kpad, nullptr, nullptr);

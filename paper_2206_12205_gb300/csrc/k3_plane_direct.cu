@@ -219,10 +219,28 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct(const uint32_
 // FP8 ablation of the direct form (FDAS_FP8_DIRECT): E4M3 operands (3 mantissa bits) with
 // power-of-two scales -- per 1024-bin tile for the spectrum (largest |Re| or |Im| of the tile's
 // window brought into [224, 448]) and per template for the taps -- kind::f8f6f4 MMAs with FP32
-// accumulation, and an FP32 plane times 1 / (s_t sigma_z)^2.  A complex E4M3 pair is 2 bytes, so
-// the Hankel rows 16 bytes apart are r = r0 + 8 a + b: a tile is 1024 bins in 8 sets of 128 rows
-// and keeps 8 shifted copies of its window.
+// accumulation, and an FP32 plane times 1 / (s_t sigma_z)^2.
+//
+// A complex E4M3 pair is 2 bytes, so the Hankel rows 16 bytes apart are r = r0 + 8 a + b: a tile
+// is 1024 bins in 8 sets b of 128 rows, and keeps 8 shifted copies of its window.  A lane of the
+// accumulator thus holds bins 8 apart; an FP32 plane written set by set would touch every 32-byte
+// sector eight times.  Instead the templates go in groups of 32 (N = 64: Re and Im rows), and the
+// eight sets of one group sit in eight TMEM slots of 64 columns (all 512): the epilogue drains
+// slot b into registers and frees it at once, and after the eighth set every thread holds eight
+// consecutive bins per template -- one whole sector, written with two 16-byte stores.
+//
+// Warp 0 issues the MMAs, warp 1 stages the FP32 spectrum window of the next tile in shared
+// memory with one bulk copy (cp.async.bulk, completion on an mbarrier), takes its maximum and
+// writes the 8 rounded copies, warps 2-9 drain the slots (two warps per TMEM lane quarter, 16
+// templates each) and store the plane.  Every wait is bounded (FDAS_DEV_TIMEOUT), copies in
+// flight are awaited and TMEM is freed before exit.
 constexpr int DT8 = 1024;
+constexpr int F8_TPG = 32;                       // templates per group (N = 64)
+constexpr int F8_N = 2 * F8_TPG;
+
+struct DBars8 {
+    uint64_t w_full[2], w_free[2], raw_full[2], s_full[4], d_full[8], d_free[8], drain;
+};
 
 __device__ __forceinline__ float e4m3_scale(float M) {       // largest 2^k with M 2^k <= 448
     if (!(M > 0.f)) return 1.f;
@@ -235,39 +253,58 @@ __device__ __forceinline__ uint16_t e4m3x2(float re, float im) {
     return (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(re, im), __NV_SATFINITE, __NV_E4M3);
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Untiled bulk copy global -> shared; both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+                 : "memory");
+}
+
 __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct_f8(const float2 *__restrict__ X,
                                                                       const float *__restrict__ scale_ptr,
                                                                       const uint4 *__restrict__ Bimg,
                                                                       const float *__restrict__ tsig,
-                                                                      float *__restrict__ plane, int K, int Kpad, int m,
+                                                                      float *__restrict__ plane, int K, int n_groups, int m,
                                                                       int64_t nb, int64_t n_tiles, int64_t tiles_per_cta,
-                                                                      uint32_t tmem_cols, int32_t *__restrict__ status) {
+                                                                      int32_t *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int N = 2 * Kpad, KD = 2 * m, WW = DT8 + m;             // WW 16-bit words per window copy
-    const uint32_t b_bytes = (uint32_t)N * KD;
+    const int WW = DT8 + m, WL = WW + 8;                           // window copy / raw window (bins)
+    const uint32_t b_bytes = (uint32_t)n_groups * F8_N * 2 * m;
     unsigned char *sB = smem;
     uint16_t *sW = reinterpret_cast<uint16_t *>(smem + b_bytes);               // [2 slots][8 copies][WW]
-    // 1 / s_t^2 of tile k at [k % 4]: the producer rewrites entry k % 4 for tile k + 4 only after
-    // the MMAs of tile k + 2 are done, which needs the epilogue past tile k
-    float *s_inv2 = reinterpret_cast<float *>(smem + b_bytes + 2u * 8u * WW * 2u);
-    DBars *bars = reinterpret_cast<DBars *>(s_inv2 + 4);
+    float2 *sRaw = reinterpret_cast<float2 *>(smem + b_bytes + 32u * WW);      // [2 slots][WL]
+    // 1 / s_t^2 of tile k at [k % 4], published by s_full[k % 4]: entry k % 4 is rewritten for tile
+    // k + 4 only after the MMAs of tile k + 2 are done, which needs the epilogue past tile k + 1
+    float *s_inv2 = reinterpret_cast<float *>(sRaw + 2 * WL);
+    DBars8 *bars = reinterpret_cast<DBars8 *>(s_inv2 + 4);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
-        tc::tmem_alloc(tslot, tmem_cols);
+        tc::tmem_alloc(tslot, 512);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
         for (int s = 0; s < 2; s++) {
             tc::mbar_init(&bars->w_full[s], 32);
             tc::mbar_init(&bars->w_free[s], 1);
+            tc::mbar_init(&bars->raw_full[s], 1);
+        }
+        for (int s = 0; s < 4; s++) tc::mbar_init(&bars->s_full[s], 1);
+        for (int s = 0; s < 8; s++) {
             tc::mbar_init(&bars->d_full[s], 1);
             tc::mbar_init(&bars->d_free[s], 256);
         }
         tc::mbar_init(&bars->drain, 1);
         *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (uint32_t i = tid; i < b_bytes / 16; i += D_WARPS * 32) reinterpret_cast<uint4 *>(sB)[i] = __ldg(Bimg + i);
     tc::fence_proxy_async_smem();
@@ -279,31 +316,36 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct_f8(const floa
     const int64_t t0 = (int64_t)blockIdx.x * tiles_per_cta;
     const int64_t t1 = min(n_tiles, t0 + tiles_per_cta);
     const int64_t n_my = t1 - t0;
+    const int KD = 2 * m;                                          // bytes of K per row
 
     if (warp == 0) {
+        // ------------------------------------------------------------------ MMA issuer
         if (n_my > 0) {
             auto wait = [&](uint64_t *bar, uint32_t parity) {
                 return __shfl_sync(0xffffffffu, (int)d_wait(bar, parity, abort_flag), 0) != 0;
             };
-            const uint32_t id = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);  // F32 D, E4M3 A, B
-            const uint64_t bdesc = tc::smem_desc(tc::smem_u32(sB), (uint32_t)N * 16, 128);
-            const uint64_t wdesc = tc::smem_desc(tc::smem_u32(sW), 16, 128);
+            const uint32_t id = (1u << 4) | ((uint32_t)(F8_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);  // F32 D, E4M3
+            // B: group g's 64 rows x KD bytes, core matrices 8 rows x 16 bytes, K-direction stride 1 KB
+            const uint64_t bdesc = tc::smem_desc(tc::smem_u32(sB), F8_N * 16, 128);
+            const uint64_t wdesc = tc::smem_desc(tc::smem_u32(sW), 16, 128);   // Hankel rows 16 B apart
             bool ok = true;
             for (int64_t k = 0; k < n_my && ok; k++) {
                 ok = wait(&bars->w_full[k & 1], (uint32_t)((k >> 1) & 1));
                 if (!ok) break;
                 tc::fence_after_thread_sync();
-                for (int b = 0; b < 8 && ok; b++) {
-                    const int64_t u = 8 * k + b;
-                    const int sl = (int)(u & 1);
-                    if (u >= 2) ok = wait(&bars->d_free[sl], (uint32_t)(((u - 2) >> 1) & 1));
-                    if (!ok) break;
-                    tc::fence_after_thread_sync();
-                    const uint64_t a = wdesc + (uint64_t)((((k & 1) * 8 + b) * WW * 2) >> 4);
-                    for (int s = 0; s < KD / 32; s++)                              // 32 bytes of K per MMA
-                        tc::mma_f8_warp(tbase + (uint32_t)sl * N, a + (uint64_t)(2 * s), bdesc + (uint64_t)(s * 2 * N), id,
-                                        s > 0 ? 1u : 0u);
-                    tc::mma_commit_warp(&bars->d_full[sl]);
+                for (int g = 0; g < n_groups && ok; g++) {
+                    const int64_t use = k * n_groups + g;                  // use count of every slot
+                    const uint64_t bg = bdesc + (uint64_t)((g * F8_N * KD) >> 4);
+                    for (int b = 0; b < 8 && ok; b++) {
+                        if (use >= 1) ok = wait(&bars->d_free[b], (uint32_t)((use - 1) & 1));
+                        if (!ok) break;
+                        tc::fence_after_thread_sync();
+                        const uint64_t a = wdesc + (uint64_t)((((k & 1) * 8 + b) * WW * 2) >> 4);
+                        for (int s = 0; s < KD / 32; s++)                  // 32 bytes of K per MMA
+                            tc::mma_f8_warp(tbase + (uint32_t)(b * F8_N), a + (uint64_t)(2 * s),
+                                            bg + (uint64_t)(s * 2 * F8_N), id, s > 0 ? 1u : 0u);
+                        tc::mma_commit_warp(&bars->d_full[b]);
+                    }
                 }
                 tc::mma_commit_warp(&bars->w_free[k & 1]);
             }
@@ -312,30 +354,51 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct_f8(const floa
         }
         __syncwarp();
     } else if (warp == 1) {
-        // window of tile k: Xhat[r0 - m/2 + w], w < WW + 8 (zero off the spectrum), scaled by s_t and
-        // rounded to E4M3 pairs; copy b holds window[b + j], j < WW
+        // ------------------------------------------------------------------ window producer
+        // raw window of tile k: Xhat[w0 + w], w < WL, w0 = 1024 (t0 + k) - m/2; the part inside the
+        // spectrum arrives by one bulk copy, the rest reads as zero
         const float gsc = scale_ptr ? __ldg(scale_ptr) : 1.0f;
-        const int WL = WW + 8;
-        for (int64_t k = 0; k < n_my; k++) {
-            if (k >= 2 && !d_wait(&bars->w_free[k & 1], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+        auto span = [&](int64_t k, int64_t &lo, int64_t &hi) {
             const int64_t w0 = (t0 + k) * DT8 - m / 2;
-            float M = 0.f;                                                 // over the window's WW bins
-            for (int w = lane; w < WW; w += 32) {
-                const int64_t kk = w0 + w;
-                if (kk >= 0 && kk < nb) {
-                    const float2 v = __ldg(X + kk);
-                    M = fmaxf(M, fmaxf(fabsf(v.x * gsc), fabsf(v.y * gsc)));
-                }
+            lo = w0 < 0 ? 0 : w0;
+            hi = w0 + WL > nb ? nb : w0 + WL;
+        };
+        auto issue = [&](int64_t k) {
+            tc::fence_proxy_async_smem();                             // the slot's earlier reads, then
+            __syncwarp();                                             // the bulk copy that overwrites it
+            if (lane == 0) {
+                int64_t lo, hi;
+                span(k, lo, hi);
+                const int64_t w0 = (t0 + k) * DT8 - m / 2;
+                mbar_expect_tx(&bars->raw_full[k & 1], (uint32_t)((hi - lo) * 8));
+                bulk_g2s(sRaw + (k & 1) * WL + (lo - w0), X + lo, (uint32_t)((hi - lo) * 8), &bars->raw_full[k & 1]);
+            }
+        };
+        int64_t issued = 0, landed = 0;
+        if (n_my > 0) issue(issued++);
+        for (int64_t k = 0; k < n_my; k++) {
+            if (issued < n_my) issue(issued++);
+            if (!d_wait(&bars->raw_full[k & 1], (uint32_t)((k >> 1) & 1), abort_flag)) break;
+            landed = k + 1;
+            if (k >= 2 && !d_wait(&bars->w_free[k & 1], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
+            int64_t lo, hi;
+            span(k, lo, hi);
+            const int64_t w0 = (t0 + k) * DT8 - m / 2;
+            const int wlo = (int)(lo - w0), whi = (int)(hi - w0);
+            const float2 *raw = sRaw + (k & 1) * WL;
+            float M = 0.f;                                             // over the window's WW bins
+            for (int w = wlo + lane; w < min(whi, WW); w += 32) {
+                const float2 v = raw[w];
+                M = fmaxf(M, fmaxf(fabsf(v.x * gsc), fabsf(v.y * gsc)));
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, o));
             const float st = e4m3_scale(M);
             uint16_t *dst = sW + (size_t)(k & 1) * 8 * WW;
             for (int w = lane; w < WL; w += 32) {
-                const int64_t kk = w0 + w;
                 float2 v = make_float2(0.f, 0.f);
-                if (kk >= 0 && kk < nb) {
-                    v = __ldg(X + kk);
+                if (w >= wlo && w < whi) {
+                    v = raw[w];
                     v = make_float2(v.x * gsc * st, v.y * gsc * st);
                 }
                 const uint16_t q = e4m3x2(v.x, v.y);
@@ -345,54 +408,63 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct_f8(const floa
                     if (j >= 0 && j < WW) dst[b * WW + j] = q;
                 }
             }
-            if (lane == 0) s_inv2[k & 3] = 1.0f / (st * st);
+            if (lane == 0) {
+                s_inv2[k & 3] = 1.0f / (st * st);
+                d_arrive(&bars->s_full[k & 3]);
+            }
             tc::fence_proxy_async_smem();
             d_arrive(&bars->w_full[k & 1]);
         }
+        // copies still in flight land before the CTA exits
+        for (int64_t k = landed; k < issued; k++)
+            tc::mbar_wait_bounded(&bars->raw_full[k & 1], (uint32_t)((k >> 1) & 1), D_WAIT);
     } else {
+        // ------------------------------------------------------------------ epilogue
         const int quad = warp & 3, h = (warp - D_EPI0) >> 2;
-        const int a = 32 * quad + lane, Kh = Kpad / 2;
+        const int a = 32 * quad + lane;
         const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
-        for (int64_t k = 0; k < n_my; k++) {
-            const int64_t r0 = (t0 + k) * DT8;
-            // the tile's window barrier (acquire of the producer's scale): its next phase needs the
-            // MMAs of this tile done, which need this epilogue, so it cannot run two phases ahead
-            if (!d_wait(&bars->w_full[k & 1], (uint32_t)((k >> 1) & 1), abort_flag)) break;
+        bool ok = true;
+        for (int64_t k = 0; k < n_my && ok; k++) {
+            if (!d_wait(&bars->s_full[k & 3], (uint32_t)((k >> 2) & 1), abort_flag)) break;
             const float si = s_inv2[k & 3];
-            bool ok = true;
-            for (int b = 0; b < 8; b++) {
-                const int64_t u = 8 * k + b;
-                const int sl = (int)(u & 1);
-                if (!d_wait(&bars->d_full[sl], (uint32_t)((u >> 1) & 1), abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                tc::fence_after_thread_sync();
-                const int64_t r = r0 + 8 * a + b;
-                const bool in = r < nb;
-                const uint32_t col = tbase + lane_base + (uint32_t)sl * N;
-                for (int z0 = h * Kh; z0 < h * Kh + Kh; z0 += 4) {
-                    uint32_t re[4], im[4];
-                    tmem_ld4(col + z0, re);
-                    tmem_ld4(col + Kpad + z0, im);
-                    tc::tmem_ld_wait();
-                    if (z0 + 4 >= h * Kh + Kh) {
-                        tc::fence_before_thread_sync();
-                        d_arrive(&bars->d_free[sl]);
-                    }
-                    if (in) {
+            const int64_t r = (t0 + k) * DT8 + 8 * a;                  // this thread's 8 bins r .. r + 7
+            for (int g = 0; g < n_groups && ok; g++) {
+                const int64_t use = k * n_groups + g;
+                float pw[8][16];
 #pragma unroll
-                        for (int e = 0; e < 4; e++) {
-                            const int z = z0 + e;
-                            if (z < K) {
-                                const float xr = __uint_as_float(re[e]), xi = __uint_as_float(im[e]);
-                                plane[(int64_t)z * nb + r] = (xr * xr + xi * xi) * si * __ldg(tsig + z);
-                            }
+                for (int b = 0; b < 8; b++) {
+                    if (!d_wait(&bars->d_full[b], (uint32_t)(use & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_thread_sync();
+                    uint32_t re[16], im[16];
+                    const uint32_t col = tbase + lane_base + (uint32_t)(b * F8_N + 16 * h);
+                    tc::tmem_ld16(col, re);
+                    tc::tmem_ld16(col + F8_TPG, im);
+                    tc::tmem_ld_wait();
+                    tc::fence_before_thread_sync();
+                    d_arrive(&bars->d_free[b]);
+#pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        const float xr = __uint_as_float(re[e]), xi = __uint_as_float(im[e]);
+                        pw[b][e] = (xr * xr + xi * xi) * si;
+                    }
+                }
+                if (!ok) break;
+                if (r + 8 <= nb) {
+#pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        const int z = g * F8_TPG + 16 * h + e;
+                        if (z < K) {
+                            const float ts = __ldg(tsig + z);
+                            float4 *o = reinterpret_cast<float4 *>(plane + (int64_t)z * nb + r);
+                            o[0] = make_float4(pw[0][e] * ts, pw[1][e] * ts, pw[2][e] * ts, pw[3][e] * ts);
+                            o[1] = make_float4(pw[4][e] * ts, pw[5][e] * ts, pw[6][e] * ts, pw[7][e] * ts);
                         }
                     }
                 }
             }
-            if (!ok) break;
         }
     }
     tc::fence_before_thread_sync();
@@ -400,33 +472,40 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct_f8(const floa
     if (tid == 0 && *abort_flag) atomicOr(status, FDAS_DEV_TIMEOUT);
     if (warp == 0) {
         tc::fence_after_thread_sync();
-        tc::tmem_dealloc(tbase, tmem_cols);
+        tc::tmem_dealloc(tbase, 512);
     }
 }
 
 }  // namespace
 
-bool direct_geometry_f8(const Plan &p, int *Kpad, uint32_t *smem_bytes, uint32_t *tmem_cols) {
-    const int kp = (p.K + 7) / 8 * 8;
-    const int N = 2 * kp;
-    if (N > 256 || p.m % 16 != 0) return false;
-    const uint64_t need = (uint64_t)N * 2 * p.m + 2ull * 8 * (DT8 + p.m) * 2 + 16 + sizeof(DBars) + 16;
+// FP8 direct path geometry: template groups of 32 and the shared memory (the groups' taps image,
+// two slots of 8 window copies, two raw FP32 windows, scales and barriers).
+bool direct_geometry_f8(const Plan &p, int *n_groups, uint32_t *smem_bytes) {
+    if (p.m % 16 != 0) return false;
+    const int G = (p.K + F8_TPG - 1) / F8_TPG;
+    const uint64_t WW = DT8 + (uint64_t)p.m, WL = WW + 8;
+    const uint64_t need = (uint64_t)G * F8_N * 2 * p.m + 32 * WW + 16 * WL + 16 + sizeof(DBars8) + 16;
     if (need > 227 * 1024) return false;
-    uint32_t cols = 32;
-    while (cols < (uint32_t)(2 * N)) cols <<= 1;
-    if (Kpad) *Kpad = kp;
+    if (n_groups) *n_groups = G;
     if (smem_bytes) *smem_bytes = (uint32_t)std::max<uint64_t>(need, D_MIN_SMEM);
-    if (tmem_cols) *tmem_cols = cols;
     return true;
 }
 
-cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float *d_scale, float *d_plane,
+cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
                                    cudaStream_t st) {
-    int Kpad = 0;
-    uint32_t smem = 0, cols = 0;
-    if (!p.d_dimg || !p.d_dsig || !direct_geometry_f8(p, &Kpad, &smem, &cols)) return cudaErrorInvalidValue;
+    int G = 0;
+    uint32_t smem = 0;
+    if (!p.d_dimg || !p.d_dsig || !direct_geometry_f8(p, &G, &smem)) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k3_plane_direct_f8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // the bulk copies read the spectrum from 16-byte boundaries: a spectrum on an 8-byte one is
+    // first copied to the (256-byte aligned) scratch area
+    if ((reinterpret_cast<uintptr_t>(d_x) & 15) != 0) {
+        float2 *tmp = reinterpret_cast<float2 *>(ws + p.ws_tmp);
+        e = cudaMemcpyAsync(tmp, d_x, sizeof(float2) * (size_t)p.nb, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        d_x = tmp;
+    }
     const int64_t n_tiles = (p.nb + DT8 - 1) / DT8;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
@@ -435,8 +514,8 @@ cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float
     const int64_t grid = (n_tiles + per - 1) / per;
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_direct_f8<<<(unsigned)grid, D_WARPS * 32, smem, st>>>(d_x, d_scale, reinterpret_cast<const uint4 *>(p.d_dimg),
-                                                                   p.d_dsig, d_plane, p.K, Kpad, p.m, p.nb, n_tiles, per,
-                                                                   cols, p.d_status);
+                                                                   p.d_dsig, d_plane, p.K, G, p.m, p.nb, n_tiles, per,
+                                                                   p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 1;
     return cudaGetLastError();

@@ -176,15 +176,19 @@ def test_direct_plan_geometry(lib):
 
 
 def test_fp8_direct_plan_geometry(lib):
-    """FDAS_FP8_DIRECT: an FP32 plane; 2 ceil(K/8) 8 <= 256 and taps % 16 == 0 (a 32-byte MMA
-    K-step is 16 complex E4M3 pairs), else unsupported."""
+    """FDAS_FP8_DIRECT: an FP32 plane; taps % 16 == 0 (a 32-byte MMA K-step is 16 complex E4M3
+    pairs) and the taps image (ceil(K/32) groups x 64 rows x 2m bytes) plus the windows within one
+    CTA's shared memory, else unsupported."""
     ok = fd.fdas_plan(fd.make_config(1 << 23, 84, 256, 8192, precision="fp8_direct", max_harm=16))
     assert ok.info.plane_elem_bytes == 4 and ok.info.K == 85
     assert ok.info.plane_bytes == 4 * 85 * (1 << 22)
     fd.fdas_destroy(ok)
-    for n, zmax, m in ((1 << 16, 128, 64), (1 << 16, 16, 40), (1 << 16, 16, 8)):
+    wide = fd.fdas_plan(fd.make_config(1 << 16, 1022, 16, 1024, precision="fp8_direct"))
+    assert wide.info.K == 1023
+    fd.fdas_destroy(wide)
+    for n, zmax, m, S in ((1 << 16, 16, 40, 1024), (1 << 16, 16, 8, 1024), (1 << 16, 84, 2048, 8192)):
         with pytest.raises(fd.FdasError) as ei:
-            fd.fdas_plan(fd.make_config(n, zmax, m, 1024, precision="fp8_direct"))
+            fd.fdas_plan(fd.make_config(n, zmax, m, S, precision="fp8_direct"))
         assert ei.value.status == fb.FDAS_E_UNSUPPORTED, (n, zmax, m)
     small = fd.fdas_plan(fd.make_config(1 << 11, 0, 16, 1024, precision="fp8_direct"))
     assert small.info.K == 1

@@ -69,7 +69,8 @@ def _accumulation_eps(got, ref, S):
 
 
 @pytest.mark.parametrize("n,zmax,m", [(1 << 16, 16, 64), (1 << 11, 0, 16), (1 << 18, 84, 256),
-                                       (1 << 12, 2, 32), (1 << 14, 126, 16), (1 << 13, 10, 208)])
+                                       (1 << 12, 2, 32), (1 << 14, 126, 16), (1 << 13, 10, 208),
+                                       (1 << 13, 254, 32), (1 << 12, 62, 496)])
 def test_fp8_plane_matches_emulation(n, zmax, m):
     x = (synth.noise(n, synth.rng_for(74, n.bit_length())) + synth.chirp(n, 0.25, n / 13.3, zmax * 0.6)).astype(np.float32)
     s = _search(n, zmax, m)
@@ -85,6 +86,26 @@ def test_fp8_plane_matches_emulation(n, zmax, m):
     print(f"fp8 n={n} zmax={zmax} m={m}: accumulation eps max {e.max():.2e} (2^{np.log2(max(e.max(), 1e-30)):.1f}), "
           f"identical cells {np.mean(got == ref.astype(np.float32)):.3f}")
     assert e.max() <= EPS
+    assert fd.fdas_device_status(s.plan) == 0
+
+
+def test_fp8_spectrum_on_an_8_byte_boundary():
+    """The bulk copies read the spectrum from 16-byte boundaries; a spectrum that starts on an
+    8-byte one (allowed by the interface) gives the same plane, bit for bit."""
+    n, zmax, m = 1 << 15, 20, 64
+    x = (synth.noise(n, synth.rng_for(74, 99)) + synth.chirp(n, 0.3, 3000.2, 5.1)).astype(np.float32)
+    xdev, _ = _shared_spectrum(x)
+    s = _search(n, zmax, m)
+    s.plane_from_spectrum(xdev)
+    torch.cuda.synchronize()
+    want = s.plane_2d().clone()
+    buf = torch.zeros(xdev.numel() + 2, dtype=torch.float32, device="cuda")
+    buf[2:].copy_(xdev)
+    shifted = buf[2:]
+    assert shifted.data_ptr() % 16 == 8
+    s.plane_from_spectrum(shifted)
+    torch.cuda.synchronize()
+    assert torch.equal(s.plane_2d(), want)
     assert fd.fdas_device_status(s.plan) == 0
 
 
