@@ -245,6 +245,9 @@ def roofline_peak_kernel(w, precision: str, kernel: str, prof):
     eb = 2 if precision in ("bf16", "bf16_direct") else 4
     if kernel == "k4_level1":
         nbytes = w.K * w.nb * eb
+    elif kernel == "k4_level1_marked":
+        # the unit marks read and the level-1 counts written (the marked units' few cells aside)
+        nbytes = w.K * (w.nb // 512) * (1 + 4)
     else:
         zl = (w.zmax // 2) // 2 * 2
         nbytes = ((zl + 1) * (w.nb // 2) + _gathers(w, range(1, 5))) * eb
@@ -654,6 +657,10 @@ def own_arm(args):
         clk_ = clocks_.stop() if clocks_ else None
         prof_ = fd.fdas_profile_read(s_.plan, reset=True)
         fd.fdas_profile_enable(s_.plan, False)
+        if prof_.get("level1_fused"):
+            # level 1 visited only the units the plane kernel marked: its timed kernel is that one
+            pk_ = prof_["peaks_kernels"]
+            prof_["peaks_kernels"] = {("k4_level1_marked" if k == "k4_level1" else k): v for k, v in pk_.items()}
         tot = sum(a_.elapsed_time(b_) for a_, b_ in zip(starts, ends))
         t_ = torch.tensor([tot], dtype=torch.float64, device=dev)
         if dist is not None:
@@ -732,7 +739,7 @@ def own_arm(args):
     roof_corr = roofline_correlate(w, precision, prof)
     if dominant == "correlate":
         roof = roof_corr
-    elif dominant in ("k4_level1", "k4_levels"):
+    elif dominant in ("k4_level1", "k4_level1_marked", "k4_levels"):
         roof = roofline_peak_kernel(w, precision, dominant, prof)
     else:
         roof = roofline_stage(w, precision, dominant, prof)

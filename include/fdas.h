@@ -371,6 +371,10 @@ typedef struct {
     double  ms[4];          /* their summed event times in milliseconds                         */
     int64_t n_timed_peaks[2]; /* inside the peaks stage: level-1 pass, level 2..16 pass          */
     double  ms_peaks[2];    /* their summed event times in milliseconds                         */
+    int64_t level1_fused;   /* peak searches whose level-1 pass visited only the 512-bin units
+                               that the tensor-core plane kernel (FDAS_BF16, FDAS_FP16_SCALED,
+                               inside fdas_search / fdas_batch_search) marked as holding a value
+                               above thr[0], instead of reading the whole plane                */
 } fdas_profile;
 
 /* Stage indices of fdas_profile.ms / n_timed. */
@@ -379,7 +383,7 @@ typedef struct {
 #define FDAS_STAGE_CORRELATE 2   /* K3: multiply, inverse FFT, |.|^2, overlap discard            */
 #define FDAS_STAGE_PEAKS     3   /* K4: harmonic sums and peak list                               */
 /* Indices of fdas_profile.ms_peaks / n_timed_peaks (single kernels inside FDAS_STAGE_PEAKS). */
-#define FDAS_PEAKS_LEVEL1    0   /* harmonic level 1 over the whole plane                         */
+#define FDAS_PEAKS_LEVEL1    0   /* harmonic level 1 over the whole plane (or its marked units)   */
 #define FDAS_PEAKS_LEVELS    1   /* levels 2 .. 16 over level 2's region                          */
 
 /*

@@ -47,11 +47,11 @@ bool args_aligned(const void *series, const void *xhat, const void *ws, const vo
 
 namespace fdas {
 cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale, char *ws, void *d_plane,
-                             cudaStream_t st) {
+                             cudaStream_t st, uint8_t *l1flag) {
     switch (p.cfg.precision) {
-        case FDAS_BF16: return launch_plane_bf16(p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
+        case FDAS_BF16: return launch_plane_bf16(p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st, l1flag);
         case FDAS_BF16_SPLIT: return launch_plane_split(p, x, scale, ws, static_cast<float *>(d_plane), st);
-        case FDAS_FP16_SCALED: return launch_plane_f16(p, x, scale, ws, static_cast<float *>(d_plane), st);
+        case FDAS_FP16_SCALED: return launch_plane_f16(p, x, scale, ws, static_cast<float *>(d_plane), st, l1flag);
         case FDAS_BF16_DIRECT: return launch_plane_direct(p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
         case FDAS_FP8_DIRECT: return launch_plane_direct_f8(p, x, scale, ws, static_cast<float *>(d_plane), st);
         default: return launch_plane_fp32(p, x, scale, ws, static_cast<float *>(d_plane), st);
@@ -60,8 +60,9 @@ cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale,
 }  // namespace fdas
 
 namespace {
-cudaError_t launch_plane_any(Plan *p, const float2 *x, const float *scale, char *ws, void *d_plane, cudaStream_t st) {
-    return fdas::launch_plane_any(*p, x, scale, ws, d_plane, st);
+cudaError_t launch_plane_any(Plan *p, const float2 *x, const float *scale, char *ws, void *d_plane, cudaStream_t st,
+                             uint8_t *l1flag = nullptr) {
+    return fdas::launch_plane_any(*p, x, scale, ws, d_plane, st, l1flag);
 }
 }  // namespace
 
@@ -69,7 +70,7 @@ extern "C" {
 
 static_assert(sizeof(fdas_config) == 72, "fdas_config layout (the Python binding mirrors it)");
 
-int fdas_version(void) { return 104; }
+int fdas_version(void) { return 105; }
 
 const char *fdas_status_string(fdas_status s) {
     switch (s) {
@@ -156,6 +157,7 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     p->ws_uoff = off;   off = align_up(off + sizeof(int32_t) * (size_t)p->n_units);
     p->ws_umask = off;  off = align_up(off + sizeof(uint32_t) * (fdas::PEAK_CHUNK / 32) * (size_t)p->n_units);
     p->ws_ublock = off; off = align_up(off + sizeof(int64_t) * n_scan_blocks);
+    p->ws_l1flag = off; off = align_up(off + (size_t)p->K * (size_t)(p->nb / fdas::PEAK_CHUNK));
     p->ws_bytes = off;
     p->device = -1;
     *plan = p;
@@ -289,8 +291,10 @@ fdas_status fdas_search(fdas_plan_t plan, const float *d_series, void *d_workspa
         e = fdas::launch_local_norm(*p, x, x, st);
         scale = nullptr;
     }
-    if (e == cudaSuccess) e = launch_plane_any(p, x, scale, ws, d_plane, st);
-    if (e == cudaSuccess) e = fdas::launch_peaks(*p, d_plane, plane_is_bf16(p), ws, d_peaks, d_npeaks, 0u, st);
+    // the tensor-core plane kernels mark the level-1 units as they store the plane
+    uint8_t *l1flag = fdas::level1_fusable(*p) ? reinterpret_cast<uint8_t *>(ws + p->ws_l1flag) : nullptr;
+    if (e == cudaSuccess) e = launch_plane_any(p, x, scale, ws, d_plane, st, l1flag);
+    if (e == cudaSuccess) e = fdas::launch_peaks(*p, d_plane, plane_is_bf16(p), ws, d_peaks, d_npeaks, 0u, st, l1flag);
     return record(p, e);
 }
 
@@ -399,6 +403,7 @@ fdas_status fdas_profile_read(fdas_plan_t plan, fdas_profile *out, int reset) {
     std::memset(out, 0, sizeof(*out));
     out->calls = pr.calls;
     out->launches = pr.launches;
+    out->level1_fused = pr.level1_fused;
     int any = 0;
     for (int s = 0; s < fdas::PROF_STAGES; s++) any += pr.n[s];
     if (any > 0) {
@@ -422,7 +427,7 @@ fdas_status fdas_profile_read(fdas_plan_t plan, fdas_profile *out, int reset) {
         }
     }
     if (reset) {
-        pr.calls = pr.launches = 0;
+        pr.calls = pr.launches = pr.level1_fused = 0;
         for (int s = 0; s < fdas::PROF_STAGES; s++) pr.n[s] = 0;
     }
     return FDAS_OK;

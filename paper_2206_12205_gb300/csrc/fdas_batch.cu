@@ -376,11 +376,12 @@ fdas_status fdas_batch_search(fdas_batch_t b, const float *d_series, void *d_wor
                 e = fdas::launch_local_norm(p, x, x, b->cap);
                 scale = nullptr;
             }
-            if (e == cudaSuccess) e = fdas::launch_plane_any(p, x, scale, ws, plane, b->cap);
+            uint8_t *l1flag = fdas::level1_fusable(p) ? reinterpret_cast<uint8_t *>(ws + p.ws_l1flag) : nullptr;
+            if (e == cudaSuccess) e = fdas::launch_plane_any(p, x, scale, ws, plane, b->cap, l1flag);
             if (e == cudaSuccess)
                 e = fdas::launch_peaks(p, plane, p.cfg.precision == FDAS_BF16 || p.cfg.precision == FDAS_BF16_DIRECT,
                                        ws, d_peaks + b->peak_off[i],
-                                       d_npeaks + i, (uint32_t)i, b->cap);
+                                       d_npeaks + i, (uint32_t)i, b->cap, l1flag);
         }
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);

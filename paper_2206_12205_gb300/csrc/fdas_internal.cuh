@@ -43,7 +43,7 @@ struct Profiler {
     bool on = false;
     cudaEvent_t ev[PROF_STAGES][PROF_CAP][2] = {};
     int n[PROF_STAGES] = {};
-    int64_t calls = 0, launches = 0;
+    int64_t calls = 0, launches = 0, level1_fused = 0;
     void begin(int stage, cudaStream_t st) {
         if (on && n[stage] < PROF_CAP) cudaEventRecord(ev[stage][n[stage]][0], st);
     }
@@ -67,7 +67,8 @@ struct Plan {
     int n_levels;
     int64_t n_units;
     // workspace layout (byte offsets inside the caller's workspace)
-    size_t ws_x, ws_tmp, ws_part, ws_scale, ws_y, ws_segscale, ws_ucount, ws_uoff, ws_umask, ws_ublock, ws_bytes;
+    size_t ws_x, ws_tmp, ws_part, ws_scale, ws_y, ws_segscale, ws_ucount, ws_uoff, ws_umask, ws_ublock, ws_l1flag,
+        ws_bytes;
     int n_part;
     // plan-owned device memory
     int device;
@@ -129,8 +130,10 @@ cudaError_t launch_plane_fp32(const Plan &p, const float2 *d_x, const float *d_s
 // The same kernels with the segment spectra (n_seg * S complex64) at d_yhat instead of the workspace.
 cudaError_t launch_plane_fp32_scratch(const Plan &p, const float2 *d_x, const float *d_scale, float2 *d_yhat,
                                       float *d_plane, cudaStream_t st);
+// l1flag (optional, K x Nb/512 bytes): the plane kernel zeroes it and marks every 512-bin unit of
+// a row holding a stored value above the level-1 threshold (the level-1 pass then reads only those).
 cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
-                              __nv_bfloat16 *d_plane, cudaStream_t st);
+                              __nv_bfloat16 *d_plane, cudaStream_t st, uint8_t *l1flag = nullptr);
 cudaError_t launch_prepare_bf16(Plan &p, cudaStream_t st);
 // FP32 segment spectra for 4096-bin segments (the split-BF16 path's input).
 cudaError_t launch_segments_fp32(const Plan &p, const float2 *d_x, const float *d_scale, float2 *d_yhat,
@@ -145,12 +148,17 @@ cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float
 cudaError_t launch_plane_direct(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
                                 __nv_bfloat16 *d_plane, cudaStream_t st);
 cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
-                             cudaStream_t st);
+                             cudaStream_t st, uint8_t *l1flag = nullptr);
+// Whether the plan's plane kernel can mark the level-1 units (the tensor-core DFT paths).
+bool level1_fusable(const Plan &p);
 // The plane of the plan's precision from a spectrum (x: Nb complex; scale: device factor or NULL).
 cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale, char *ws, void *d_plane,
-                             cudaStream_t st);
+                             cudaStream_t st, uint8_t *l1flag = nullptr);
+// l1flag: the unit marks of the plane kernel that wrote d_plane (level 1 then visits only the
+// marked units), or NULL for the full level-1 pass over the plane.
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
-                         fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st);
+                         fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st,
+                         const uint8_t *l1flag = nullptr);
 cudaError_t launch_band_max(const Plan &p, const void *d_plane, bool bf16, const int64_t *d_lo, const int64_t *d_hi,
                             int n_bands, int64_t max_width, unsigned long long *d_slot, float *d_value,
                             int64_t *d_r, int32_t *d_zi, cudaStream_t st);

@@ -65,6 +65,8 @@ struct OpsBF16 {
     static constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_N);
     __device__ __forceinline__ static uint32_t pack(float lo, float hi) { return pack_bf16x2(lo, hi); }
     __device__ __forceinline__ static Out out(float pw, float) { return __float2bfloat16_rn(pw); }
+    // the stored value as the peak search reads it (BF16 widened exactly)
+    __device__ __forceinline__ static float stored(float pw, float) { return __bfloat162float(__float2bfloat16_rn(pw)); }
 };
 struct OpsF16 {
     using V = __half2;
@@ -72,6 +74,7 @@ struct OpsF16 {
     static constexpr uint32_t idesc = tc::idesc_f16_f32(TC_M, TC_N);
     __device__ __forceinline__ static uint32_t pack(float lo, float hi) { return pack_f16x2(lo, hi); }
     __device__ __forceinline__ static Out out(float pw, float unscale) { return pw * unscale; }
+    __device__ __forceinline__ static float stored(float pw, float unscale) { return pw * unscale; }
 };
 
 // Segment FFTs (FP32 CUDA-core block FFT), stored as BF16 pairs in the stage-1 order.
@@ -235,6 +238,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
                                                              typename Ops::Out *__restrict__ plane, int K, int64_t nb,
                                                              int L, int64_t n_items, int n_groups,
                                                              int64_t items_per_cta, const float *__restrict__ unscale,
+                                                             uint8_t *__restrict__ l1flag, int64_t chunks1, float thr1,
                                                              int32_t *__restrict__ status) {
     using V = typename Ops::V;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -499,6 +503,20 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
                 u3++;
             }
             typename Ops::Out *prow = plane + (int64_t)(z < K ? z : 0) * nb + r0 + idx + 64 * 32 * h;
+            // level-1 marks: the 512-bin units of row z holding a stored value above thr1 (rounding
+            // is monotone, so the largest value decides whether any does)
+            if (l1flag != nullptr && kmax > 0) {
+                float vmax = pw[0];
+#pragma unroll
+                for (int i = 1; i < 32; i++) vmax = fmaxf(vmax, pw[i]);
+                if (Ops::stored(vmax, us) > thr1) {
+                    uint8_t *frow = l1flag + (int64_t)z * chunks1;
+                    const int64_t b0 = r0 + idx + 64 * 32 * h;
+#pragma unroll
+                    for (int i = 0; i < 32; i++)
+                        if (i < kmax && Ops::stored(pw[i], us) > thr1) frow[(b0 + 64 * i) >> 9] = 1;
+                }
+            }
             if (kmax >= 32) {
 #pragma unroll
                 for (int i = 0; i < 32; i++) prow[64 * i] = Ops::out(pw[i], us);
@@ -783,8 +801,20 @@ static cudaError_t prepare_plane_tc() {
     return cudaFuncSetAttribute(k3_plane_tc<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM);
 }
 
+static_assert(PEAK_CHUNK == 512, "the level-1 marks index units as bin >> 9");
+
+bool level1_fusable(const Plan &p) {
+    return p.cfg.precision == FDAS_BF16 || p.cfg.precision == FDAS_FP16_SCALED;
+}
+
+// Clear the level-1 unit marks before the plane kernel sets them.
+static cudaError_t clear_marks(const Plan &p, uint8_t *l1flag, cudaStream_t st) {
+    if (!l1flag) return cudaSuccess;
+    return cudaMemsetAsync(l1flag, 0, (size_t)p.K * (size_t)(p.nb / PEAK_CHUNK), st);
+}
+
 cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
-                              __nv_bfloat16 *d_plane, cudaStream_t st) {
+                              __nv_bfloat16 *d_plane, cudaStream_t st, uint8_t *l1flag) {
     if (p.S != TC_S_BF16) return cudaErrorInvalidValue;
     uint4 *Y = reinterpret_cast<uint4 *>(ws + p.ws_y);
     const size_t smem2 = sizeof(float2) * fft_smem_entries(TC_S_BF16);
@@ -804,10 +834,13 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
     const int64_t ctas = std::min<int64_t>(n_items, (int64_t)sms);     // one persistent CTA per SM
     const int64_t per = (n_items + ctas - 1) / ctas;
     const int64_t grid = (n_items + per - 1) / per;
+    e = clear_marks(p, l1flag, st);
+    if (e != cudaSuccess) return e;
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_tc<OpsBF16><<<(unsigned)grid, WS_THREADS, WS_SMEM, st>>>(
         Y, reinterpret_cast<const uint4 *>(p.d_Gbf), reinterpret_cast<const uint4 *>(p.d_tcF) + 2 * TILE_BYTES / 16,
-        p.d_tcTw, d_plane, p.K, p.nb, p.L, n_items, n_groups, per, nullptr, p.d_status);
+        p.d_tcTw, d_plane, p.K, p.nb, p.L, n_items, n_groups, per, nullptr, l1flag, p.nb / PEAK_CHUNK, p.cfg.thr[0],
+        p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 2;
     return cudaGetLastError();
@@ -815,7 +848,7 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
 
 // FP16-scaled ablation: scaled FP16 segment spectra, the FP16 bank (S G) and DFT image, FP32 plane.
 cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
-                             cudaStream_t st) {
+                             cudaStream_t st, uint8_t *l1flag) {
     if (p.S != TC_S_BF16 || !p.d_Gh || !p.d_tcFh) return cudaErrorInvalidValue;
     uint4 *Y = reinterpret_cast<uint4 *>(ws + p.ws_y);
     float *unscale = reinterpret_cast<float *>(ws + p.ws_segscale);
@@ -837,10 +870,12 @@ cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_sc
     const int64_t ctas = std::min<int64_t>(n_items, (int64_t)sms);
     const int64_t per = (n_items + ctas - 1) / ctas;
     const int64_t grid = (n_items + per - 1) / per;
+    e = clear_marks(p, l1flag, st);
+    if (e != cudaSuccess) return e;
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_tc<OpsF16><<<(unsigned)grid, WS_THREADS, WS_SMEM, st>>>(
         Y, reinterpret_cast<const uint4 *>(p.d_Gh), reinterpret_cast<const uint4 *>(p.d_tcFh), p.d_tcTw, d_plane,
-        p.K, p.nb, p.L, n_items, n_groups, per, unscale, p.d_status);
+        p.K, p.nb, p.L, n_items, n_groups, per, unscale, l1flag, p.nb / PEAK_CHUNK, p.cfg.thr[0], p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 2;
     return cudaGetLastError();

@@ -388,6 +388,40 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_L1_MIN_BLOCKS) k4_l
     }
 }
 
+// Level 1 after a plane kernel that marked its units (flags[u] != 0: the unit u = i chunks + c holds
+// a stored value above the threshold): a warp takes 32 units, writes a zero count for the unmarked
+// ones and runs the level-1 test of k4_level1 on each marked one (a handful per plane).  The
+// plane is not streamed; the result is the same as k4_level1's.
+template <typename E>
+__global__ void __launch_bounds__(DETECT_WARPS * 32) k4_level1_marked(const E *__restrict__ plane, int64_t nb, int zmax,
+                                                                    int K, LevelDesc d, int64_t n_units1,
+                                                                    const uint8_t *__restrict__ flags,
+                                                                    int32_t *__restrict__ unit_count,
+                                                                    uint32_t *__restrict__ unit_mask) {
+    const int lane = threadIdx.x & 31;
+    const int64_t u0 = ((int64_t)blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * 32;
+    if (u0 >= n_units1) return;                      // warp-uniform
+    const int64_t u = u0 + lane;
+    const bool marked = u < n_units1 && flags[u] != 0;
+    if (u < n_units1 && !marked) unit_count[d.unit0 + u] = 0;
+    uint32_t todo = __ballot_sync(0xffffffffu, marked);
+    while (todo) {
+        const int64_t uu = u0 + (__ffs(todo) - 1);
+        todo &= todo - 1;
+        const int i = (int)(uu / d.chunks);
+        const int64_t rl = (uu - (int64_t)i * d.chunks) * CB + LB * lane;
+        typename Fmt<E>::Raw raw;
+        Fmt<E>::load_raw(plane + (int64_t)i * nb + rl, raw);
+        const uint32_t pk = Fmt<E>::max16(raw) > d.thr ? level1_peaks(plane, nb, zmax, K, d, i, rl) : 0u;
+        int cnt = __popc(pk);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        const uint32_t hi = __shfl_down_sync(0xffffffffu, pk, 1);
+        if (lane == 0) unit_count[d.unit0 + uu] = cnt;
+        if (cnt > 0 && !(lane & 1)) unit_mask[(d.unit0 + uu) * WORDS + (lane >> 1)] = pk | (hi << 16);
+    }
+}
+
 // Levels 2 .. 16 over level 2's region (rows i_lo .. i_lo + rows - 1 of level 2, chunks up to its
 // rmax): grid (ceil(chunks2 / (DETECT_WARPS * CPW)), rows2); each warp re-reads S_1 of CPW chunks
 // and carries the running sums through the levels in registers.
@@ -630,7 +664,7 @@ __global__ void __launch_bounds__(256) k4_emit(const E *__restrict__ plane, int6
 
 template <typename E>
 cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks, int32_t *npeaks, uint32_t series,
-                      cudaStream_t st) {
+                      cudaStream_t st, const uint8_t *l1flag) {
     const LevelTable lt = make_levels(p);
     int32_t *unit_count = reinterpret_cast<int32_t *>(ws + p.ws_ucount);
     int32_t *unit_off = reinterpret_cast<int32_t *>(ws + p.ws_uoff);
@@ -647,8 +681,16 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
     p.prof.begin(FDAS_STAGE_PEAKS, st);
     p.prof.launches += lt.n_levels > 1 ? 5 : 4;
     p.prof.begin(PROF_PEAKS_LEVEL1, st);
-    k4_level1<E><<<level1_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt.lev[0], (int)chunks1,
-                                                             unit_count, unit_mask);
+    if (l1flag) {
+        const int64_t n1 = (int64_t)p.K * chunks1;
+        const int64_t blocks = (n1 + DETECT_WARPS * 32 - 1) / (DETECT_WARPS * 32);
+        k4_level1_marked<E><<<(unsigned)blocks, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt.lev[0], n1,
+                                                                          l1flag, unit_count, unit_mask);
+        p.prof.level1_fused++;
+    } else {
+        k4_level1<E><<<level1_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt.lev[0], (int)chunks1,
+                                                                 unit_count, unit_mask);
+    }
     p.prof.end(PROF_PEAKS_LEVEL1, st);
     if (lt.n_levels > 1 && lt.anchored) {
         p.prof.begin(PROF_PEAKS_LEVELS, st);
@@ -700,11 +742,11 @@ LevelTable make_levels(const Plan &p) {
 }
 
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws, fdas_peak *d_peaks,
-                         int32_t *d_npeaks, uint32_t series, cudaStream_t st) {
+                         int32_t *d_npeaks, uint32_t series, cudaStream_t st, const uint8_t *l1flag) {
     if (bf16)
         return run_peaks<__nv_bfloat16>(p, reinterpret_cast<const __nv_bfloat16 *>(d_plane), ws, d_peaks, d_npeaks,
-                                        series, st);
-    return run_peaks<float>(p, reinterpret_cast<const float *>(d_plane), ws, d_peaks, d_npeaks, series, st);
+                                        series, st, l1flag);
+    return run_peaks<float>(p, reinterpret_cast<const float *>(d_plane), ws, d_peaks, d_npeaks, series, st, l1flag);
 }
 
 }  // namespace fdas

@@ -66,7 +66,8 @@ class _Info(ctypes.Structure):
 
 class _Profile(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("launches", ctypes.c_int64), ("n_timed", ctypes.c_int64 * 4),
-                ("ms", ctypes.c_double * 4), ("n_timed_peaks", ctypes.c_int64 * 2), ("ms_peaks", ctypes.c_double * 2)]
+                ("ms", ctypes.c_double * 4), ("n_timed_peaks", ctypes.c_int64 * 2), ("ms_peaks", ctypes.c_double * 2),
+                ("level1_fused", ctypes.c_int64)]
 
 
 _lib = None
@@ -402,7 +403,8 @@ def fdas_profile_read(plan: Plan, reset: bool = True) -> dict:
             "ms": {STAGES[i]: float(pr.ms[i]) for i in range(4)},
             "n_timed": {STAGES[i]: int(pr.n_timed[i]) for i in range(4)},
             "peaks_kernels": {name: {"ms": float(pr.ms_peaks[i]), "n_timed": int(pr.n_timed_peaks[i])}
-                              for i, name in enumerate(("k4_level1", "k4_levels"))}}
+                              for i, name in enumerate(("k4_level1", "k4_levels"))},
+            "level1_fused": int(pr.level1_fused)}
 
 
 def fdas_destroy(plan: Plan):

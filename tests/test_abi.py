@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert fd.fdas_version() == 104
+    assert fd.fdas_version() == 105
     for code in range(8):
         assert fd.status_string(code) and fd.status_string(code) != "unknown status"
     assert fd.status_string(99) == "unknown status"
