@@ -14,7 +14,10 @@
 //   finalize (one CTA):              fixed-order sum of the partials -> sigma2, scale.
 // The lanes of a warp interleave over the CTA's columns (pass A) or rows (pass B), so every
 // global access of a warp covers whole 32-byte sectors instead of strided single elements.
-// Twiddles W_N^e come from a two-level FP32 table (W_N^e = hi[e >> 13] * lo[e & 8191]).
+// Twiddles W_N^e come from a two-level FP32 table (W_N^e = hi[e >> 13] * lo[e & 8191]), looked
+// up once per thread and once per (column, i) in pass A, once per thread and once per i in pass B
+// (the factor W_N^{M1 T i} = W_64^i that steps through a thread's 32 outputs).
+// sum |X_k|^2: FP32 over a thread's 32 bins, FP64 from there on (GB300's FP64 rate is low).
 #include "block_fft.cuh"
 #include "fdas_internal.cuh"
 
@@ -29,45 +32,60 @@ __device__ __forceinline__ float2 twN(const float2 *__restrict__ lo, const float
 // FFTs of one CTA: groups per CTA (bounded by 1024 threads and the shared memory) and the
 // padding between the groups' shared-memory regions (16 words: groups interleaved in a warp
 // fall on different banks).
-constexpr int k1_groups(int S) { return S >= 8192 ? 1 : (S >= 4096 ? 2 : 4); }
+#ifndef FDAS_K1A_GROUPS
+#define FDAS_K1A_GROUPS 4                // pass-A columns per CTA for FFT lengths up to 2048
+#endif
+#ifndef FDAS_K1B_GROUPS
+#define FDAS_K1B_GROUPS 2                // pass-B row pairs per CTA for FFT lengths up to 2048
+#endif
+constexpr int k1_groups_a(int S) { return S >= 8192 ? 1 : (S >= 4096 ? 2 : FDAS_K1A_GROUPS); }
+constexpr int k1_groups_b(int S) { return S >= 8192 ? 1 : (S >= 4096 ? 2 : FDAS_K1B_GROUPS); }
 constexpr int K1_GPAD = 8;
 #ifndef FDAS_K1A_MIN_BLOCKS
 #define FDAS_K1A_MIN_BLOCKS 1            // resident pass-A blocks per SM the registers must allow
 #endif
+#ifndef FDAS_K1B_MIN_BLOCKS
+#define FDAS_K1B_MIN_BLOCKS 2            // resident pass-B blocks per SM the registers must allow
+#endif
+
 
 template <int M1>
-__global__ void __launch_bounds__(k1_groups(M1) * (M1 / 32), FDAS_K1A_MIN_BLOCKS) k1_pass_a(const float2 *__restrict__ z,
+__global__ void __launch_bounds__(k1_groups_a(M1) * (M1 / 32), FDAS_K1A_MIN_BLOCKS) k1_pass_a(const float2 *__restrict__ z,
                                                                      const float2 *__restrict__ tw,
                                                                      const float2 *__restrict__ lo,
                                                                      const float2 *__restrict__ hi,
                                                                      float2 *__restrict__ B, int M2) {
-    constexpr int T = M1 / 32, C1 = k1_groups(M1);
+    constexpr int T = M1 / 32, C1 = k1_groups_a(M1);
     constexpr int E = fft_smem_entries(M1) + K1_GPAD;
     extern __shared__ float2 sm[];        // C1 * E entries
+    __shared__ float2 wi[C1][32];         // W_N^{2 n2 T i} of each column
     const int g = threadIdx.x % C1, t = threadIdx.x / C1;
     const int n2 = blockIdx.x * C1 + g;
+    for (int i = t; i < 32; i += T) wi[g][i] = twN(lo, hi, 2 * (int64_t)n2 * T * i);   // T < 32 for M1 < 1024
     float2 v[32];
 #pragma unroll
     for (int i = 0; i < 32; i++) v[i] = __ldg(z + (int64_t)(t + i * T) * M2 + n2);
+    const float2 wt = twN(lo, hi, 2 * (int64_t)n2 * t);
     block_fft<M1>(v, sm + g * E, tw, t);
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < 32; i++) {
         const int k1 = t + i * T;
-        // W_M^{n2 k1} = W_N^{2 n2 k1}
-        B[(int64_t)k1 * M2 + n2] = cmul(v[i], twN(lo, hi, 2 * (int64_t)n2 * k1));
+        // W_M^{n2 k1} = W_N^{2 n2 k1} = W_N^{2 n2 t} W_N^{2 n2 T i}
+        B[(int64_t)k1 * M2 + n2] = cmul(v[i], cmul(wt, wi[g][i]));
     }
 }
 
 // Groups 0 .. C2-1 take rows a = p C2 + g; groups C2 .. 2 C2 - 1 their partners M1 - a (row 0,
 // its own partner, lends its partner slot to row M1/2, the other self-partnered row).
 template <int M2>
-__global__ void __launch_bounds__(2 * k1_groups(M2) * (M2 / 32)) k1_pass_b(const float2 *__restrict__ B,
+__global__ void __launch_bounds__(2 * k1_groups_b(M2) * (M2 / 32), FDAS_K1B_MIN_BLOCKS) k1_pass_b(const float2 *__restrict__ B,
                                                                          const float2 *__restrict__ tw,
                                                                          const float2 *__restrict__ lo,
                                                                          const float2 *__restrict__ hi,
                                                                          float2 *__restrict__ X,
                                                                          double *__restrict__ partial, int M1) {
-    constexpr int T = M2 / 32, C2 = k1_groups(M2), G = 2 * C2;
+    constexpr int T = M2 / 32, C2 = k1_groups_b(M2), G = 2 * C2;
     constexpr int E = fft_smem_entries(M2) + K1_GPAD;
     extern __shared__ float2 smb[];       // G * E entries
     __shared__ double red[G * T];
@@ -75,6 +93,8 @@ __global__ void __launch_bounds__(2 * k1_groups(M2) * (M2 / 32)) k1_pass_b(const
     const int a = blockIdx.x * C2 + (g % C2);
     const int row = g < C2 ? a : (a == 0 ? M1 / 2 : M1 - a);
     float2 *sm = smb + g * E;
+    __shared__ float2 w64[32];            // W_N^{M1 T i} = W_64^i
+    for (int i = threadIdx.x; i < 32; i += G * T) w64[i] = twN(lo, hi, (int64_t)M1 * T * i);
     float2 v[32];
 #pragma unroll
     for (int i = 0; i < 32; i++) v[i] = __ldg(B + (int64_t)row * M2 + t + i * T);
@@ -87,7 +107,8 @@ __global__ void __launch_bounds__(2 * k1_groups(M2) * (M2 / 32)) k1_pass_b(const
     const bool self = (row == 0) || (row == M1 / 2);
     const int gp = self ? g : (g < C2 ? g + C2 : g - C2);
     const float2 *smp = smb + gp * E;
-    double acc = 0.0;
+    const float2 wt = twN(lo, hi, row + (int64_t)M1 * t);   // W_N^k = W_N^{row + M1 t} W_64^i
+    float acc = 0.f;
 #pragma unroll
     for (int i = 0; i < 32; i++) {
         const int k2 = t + i * T;
@@ -99,12 +120,12 @@ __global__ void __launch_bounds__(2 * k1_groups(M2) * (M2 / 32)) k1_pass_b(const
         const float2 dv = make_float2(0.5f * (zk.x - zc.x), 0.5f * (zk.y + zc.y));
         const float2 ov = make_float2(dv.y, -dv.x);
         const int64_t k = row + (int64_t)M1 * k2;
-        float2 xk = cadd(ev, cmul(twN(lo, hi, k), ov));
+        float2 xk = cadd(ev, cmul(cmul(wt, w64[i]), ov));
         if (k == 0) xk = make_float2(0.f, 0.f);
         X[k] = xk;
-        acc += (double)xk.x * xk.x + (double)xk.y * xk.y;
+        acc = fmaf(xk.x, xk.x, fmaf(xk.y, xk.y, acc));
     }
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = (double)acc;
     __syncthreads();
     for (int s = G * T / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
@@ -181,7 +202,7 @@ __global__ void __launch_bounds__(256) k1_local_norm(const float2 *__restrict__ 
 
 template <int M1>
 cudaError_t run_pass_a(const Plan &p, const float2 *z, float2 *B, cudaStream_t st) {
-    constexpr int C1 = k1_groups(M1);
+    constexpr int C1 = k1_groups_a(M1);
     const size_t smem = sizeof(float2) * C1 * (fft_smem_entries(M1) + K1_GPAD);
     auto kern = k1_pass_a<M1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -192,7 +213,7 @@ cudaError_t run_pass_a(const Plan &p, const float2 *z, float2 *B, cudaStream_t s
 
 template <int M2>
 cudaError_t run_pass_b(const Plan &p, const float2 *B, float2 *X, double *partial, cudaStream_t st) {
-    constexpr int C2 = k1_groups(M2);
+    constexpr int C2 = k1_groups_b(M2);
     const size_t smem = 2 * C2 * sizeof(float2) * (fft_smem_entries(M2) + K1_GPAD);
     auto kern = k1_pass_b<M2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -238,7 +259,7 @@ cudaError_t launch_spectrum(const Plan &p, const float *d_series, char *ws, cuda
         case 8192: e = run_pass_b<8192>(p, B, X, partial, st); break;
     }
     if (e != cudaSuccess) return e;
-    k1_finalize<<<1, 256, 0, st>>>(partial, p.M1 / (2 * k1_groups(p.M2)), p.nb, p.cfg.sigma2, sigma2, scale);
+    k1_finalize<<<1, 256, 0, st>>>(partial, p.M1 / (2 * k1_groups_b(p.M2)), p.nb, p.cfg.sigma2, sigma2, scale);
     p.prof.end(FDAS_STAGE_SPECTRUM, st);
     return cudaGetLastError();
 }
