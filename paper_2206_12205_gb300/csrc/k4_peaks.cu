@@ -9,14 +9,15 @@
 // earlier neighbours in row-major (i, r) order, >= later ones, undefined neighbours ignored).
 //
 // The defined regions nest (level 2H's lies inside level H's), so one pass builds every level:
-// a warp owns one (row i, chunk of CB bins) of the plane, lane l the 16 consecutive bins
-// r0 + 16 l .. r0 + 16 l + 15, and the running sums S_H of those bins stay in registers.  S_1 = P
-// comes from two (BF16) or four (FP32) 16-byte loads; S_2H = S_H + sum_{h = H+1 .. 2H} P(h r, i_h)
-// adds the new harmonics in order, so every S_H is bit-identical to the direct sum.  A harmonic
-// h whose 16 values span few 16-byte vectors (h r for 16 consecutive r covers 15 h + 1 elements)
-// is read with vector loads and the needed elements picked at compile time; larger h with scalar
-// gathers.  A lane tests its 16 values against the threshold through their maximum; only cells
-// above it (a handful per plane) recompute their 3x3 neighbourhood's sums to decide the peak.
+// a warp owns one (row i, chunk of CB = 512 bins) of the plane and the running sums S_H of its
+// bins stay in registers; S_2H = S_H + sum_{h = H+1 .. 2H} P(h r, i_h) adds the new harmonics in
+// order, so every S_H is bit-identical to the direct sum.  Level 1 (a stream over the whole plane,
+// or over the units the plane kernel marked) gives lane l the 16 consecutive bins r0 + 16 l ..
+// r0 + 16 l + 15, read as 16-byte vectors.  Levels 2 .. 16 interleave instead -- lane l holds
+// r0 + l + 32 e, e < 16 -- so that one warp-wide load of harmonic h reads 32 elements h apart,
+// a span of whole sectors, where consecutive bins per lane would touch 32 sectors per load.  A
+// lane tests its 16 values against the threshold through their maximum; only cells above it (a
+// handful per plane) recompute their 3x3 neighbourhood's sums to decide the peak.
 //
 // Output order (H, i, r) without a sort: a "unit" is (level, row, chunk of CB bins), units
 // are numbered in that order, and
@@ -39,7 +40,7 @@ constexpr int WORDS = CB / 32;           // mask words per unit
 constexpr int SCAN_BLOCK = PEAK_SCAN_BLOCK;
 constexpr int DETECT_WARPS = 8;          // warps per k4_level1 / k4_levels block
 #ifndef FDAS_K4_CPW
-#define FDAS_K4_CPW 2                    // chunks per k4_levels warp
+#define FDAS_K4_CPW 1                    // chunks per k4_levels warp
 #endif
 constexpr int CPW = FDAS_K4_CPW;
 static_assert((CPW & (CPW - 1)) == 0 && CPW <= 2, "chunks per warp: 1 or 2 (chunks1 >= 2 is a power of two)");
@@ -47,7 +48,7 @@ static_assert((CPW & (CPW - 1)) == 0 && CPW <= 2, "chunks per warp: 1 or 2 (chun
 #define FDAS_K4_L1_MIN_BLOCKS 2          // resident k4_level1 blocks per SM the registers must allow
 #endif
 #ifndef FDAS_K4_MIN_BLOCKS
-#define FDAS_K4_MIN_BLOCKS 2             // resident k4_levels blocks per SM the registers must allow
+#define FDAS_K4_MIN_BLOCKS 3             // resident k4_levels blocks per SM the registers must allow
 #endif
 
 static_assert(LB == 16, "a lane owns 16 bins: two BF16 or four FP32 16-byte vectors");
@@ -189,59 +190,31 @@ __device__ __forceinline__ bool row_in_level(int i, int K, int zmax, int H) {
     return i >= 0 && i < K && abs(H * z) <= zmax;
 }
 
-// s[e] += P(h (rl + e), i_h) for the lane's 16 bins, row pointer `row` of i_h.  The elements
-// h rl .. h rl + 15 h lie in NV consecutive 16-byte vectors starting at h rl (16-byte aligned:
-// rl is a multiple of 16); up to 8 vectors (h <= 4) are cheaper than 16 gathers and keep the
-// registers in check (levels 8 and 16, under 2 % of the cells, gather).  The last vector ends at
-// or before h (rl + 16) - 1, inside the row (h rl + 16 h <= nb for H >= h).
-template <typename E, int h>
-__device__ __forceinline__ void add_harmonic(const E *__restrict__ row, int64_t rl, float (&s)[LB]) {
-    constexpr int EPV = Fmt<E>::EPV;
-    constexpr int NV = (15 * h + 1 + EPV - 1) / EPV;
-    if constexpr (NV <= 8) {
-        const E *p = row + (int64_t)h * rl;
+// Levels 2 .. 16 interleave the bins: lane l of a warp owns bins r0 + l + 32 e (e < 16) of its
+// 512-bin chunk, so one load of harmonic h for the whole warp reads the 32 elements h (r0 + l +
+// 32 e), l < 32 -- a span of 32 h elements, whole sectors -- instead of 32 lanes each touching
+// their own sectors.  s[e] += P(h r, i_h) for the lane's bins r = rb + 32 e with r <= rmax (then
+// h r <= H rmax < Nb); the sums keep the order h = 1..H.
+template <typename E>
+__device__ __forceinline__ void add_harmonic(const E *__restrict__ row, int h, int64_t rb, int64_t rmax, float (&s)[LB]) {
+    float v[LB];
 #pragma unroll
-        for (int k = 0; k < NV; k++) {
-            float v[EPV];
-            Fmt<E>::load(p + k * EPV, v);
-#pragma unroll
-            for (int e = 0; e < LB; e++)
-                if ((h * e) / EPV == k) s[e] = __fadd_rn(s[e], v[(h * e) % EPV]);
-        }
-    } else {
-        float v[LB];
-#pragma unroll
-        for (int e = 0; e < LB; e++) v[e] = ld_plane(row, (int64_t)h * (rl + e));
-#pragma unroll
-        for (int e = 0; e < LB; e++) s[e] = __fadd_rn(s[e], v[e]);
+    for (int e = 0; e < LB; e++) {
+        const int64_t r = rb + 32 * e;
+        v[e] = r <= rmax ? ld_plane(row, (int64_t)h * r) : 0.0f;
     }
+#pragma unroll
+    for (int e = 0; e < LB; e++) s[e] = __fadd_rn(s[e], v[e]);
 }
 
 // S_H from S_{H/2}: the new harmonics h = H/2 + 1 .. H in order.
 template <typename E, int H>
-__device__ __forceinline__ void add_level(const E *__restrict__ plane, int64_t nb, int zmax, int z, int64_t rl,
-                                          float (&s)[LB]) {
+__device__ __forceinline__ void add_level(const E *__restrict__ plane, int64_t nb, int zmax, int z, int64_t rb,
+                                          int64_t rmax, float (&s)[LB]) {
 #pragma unroll
     for (int q = 0; q < H / 2; q++) {
         const int h = H / 2 + 1 + q;
-        const E *row = plane + (int64_t)((h * z + zmax) >> 1) * nb;
-        switch (h) {   // compile-time after unrolling
-            case 2: add_harmonic<E, 2>(row, rl, s); break;
-            case 3: add_harmonic<E, 3>(row, rl, s); break;
-            case 4: add_harmonic<E, 4>(row, rl, s); break;
-            case 5: add_harmonic<E, 5>(row, rl, s); break;
-            case 6: add_harmonic<E, 6>(row, rl, s); break;
-            case 7: add_harmonic<E, 7>(row, rl, s); break;
-            case 8: add_harmonic<E, 8>(row, rl, s); break;
-            case 9: add_harmonic<E, 9>(row, rl, s); break;
-            case 10: add_harmonic<E, 10>(row, rl, s); break;
-            case 11: add_harmonic<E, 11>(row, rl, s); break;
-            case 12: add_harmonic<E, 12>(row, rl, s); break;
-            case 13: add_harmonic<E, 13>(row, rl, s); break;
-            case 14: add_harmonic<E, 14>(row, rl, s); break;
-            case 15: add_harmonic<E, 15>(row, rl, s); break;
-            default: add_harmonic<E, 16>(row, rl, s); break;
-        }
+        add_harmonic<E>(plane + (int64_t)((h * z + zmax) >> 1) * nb, h, rb, rmax, s);
         // keep one harmonic's loads in flight at a time (bounds the registers of levels 8, 16)
         asm volatile("" ::: "memory");
     }
@@ -267,41 +240,44 @@ __device__ __noinline__ bool local_max(const E *plane, int64_t nb, int zmax, int
     return true;
 }
 
-// One level H of one (row, chunk): S_H from S_{H/2} (H > 1), then the unit's count and mask.
+// One level H > 1 of one (row, chunk), lane bins rb + 32 e: S_H from S_{H/2}, then the unit's count
+// and mask (word e of the mask, bins 32 e .. 32 e + 31 of the chunk, is the warp's ballot of bit e).
 // Returns false when the chunk lies outside level H's region (the regions nest: stop there).
 template <typename E, int H>
 __device__ __forceinline__ bool level_step(const E *__restrict__ plane, int64_t nb, int zmax, int K,
-                                           const LevelDesc &d, int i, int z, int chunk, int64_t rl, float (&s)[LB],
-                                           float vmax, int32_t *__restrict__ unit_count,
-                                           uint32_t *__restrict__ unit_mask) {
+                                           const LevelDesc &d, int i, int z, int chunk, int64_t rb, float (&s)[LB],
+                                           int32_t *__restrict__ unit_count, uint32_t *__restrict__ unit_mask) {
     const int lane = threadIdx.x & 31;
-    if (H > 1) {
-        if (!row_in_level(i, K, zmax, H) || (int64_t)chunk * CB > d.rmax) return false;   // warp-uniform
-        // d.rmax + 1 = Nb / H is a multiple of 16: a lane's bins are all in or all out
-        if (rl <= d.rmax) {
-            add_level<E, H>(plane, nb, zmax, z, rl, s);
-            vmax = s[0];
+    if (!row_in_level(i, K, zmax, H) || (int64_t)chunk * CB > d.rmax) return false;   // warp-uniform
+    add_level<E, H>(plane, nb, zmax, z, rb, d.rmax, s);
+    float vmax = -INFINITY;
 #pragma unroll
-            for (int e = 1; e < LB; e++) vmax = fmaxf(vmax, s[e]);
-        } else {
-            vmax = -INFINITY;
-        }
-    }
+    for (int e = 0; e < LB; e++)
+        if (rb + 32 * e <= d.rmax) vmax = fmaxf(vmax, s[e]);
     // unit indices fit 32 bits (at most 1023 rows x 2^17 chunks per level, five levels)
     const int u = (int)d.unit0 + (i - d.i_lo) * (int)d.chunks + chunk;
     if (__any_sync(0xffffffffu, vmax > d.thr)) {
         uint32_t pk = 0;
         if (vmax > d.thr) {
 #pragma unroll
-            for (int e = 0; e < LB; e++)
-                if (s[e] > d.thr && local_max(plane, nb, zmax, K, H, d.rmax, i, rl + e, s[e])) pk |= 1u << e;
+            for (int e = 0; e < LB; e++) {
+                const int64_t r = rb + 32 * e;
+                if (r <= d.rmax && s[e] > d.thr && local_max(plane, nb, zmax, K, H, d.rmax, i, r, s[e])) pk |= 1u << e;
+            }
         }
         int cnt = __popc(pk);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        const uint32_t hi = __shfl_down_sync(0xffffffffu, pk, 1);
         if (lane == 0) unit_count[u] = cnt;
-        if (cnt > 0 && !(lane & 1)) unit_mask[(int64_t)u * WORDS + (lane >> 1)] = pk | (hi << 16);
+        if (cnt > 0) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int e = 0; e < LB; e++) {
+                const uint32_t b = __ballot_sync(0xffffffffu, (pk >> e) & 1u);
+                if (lane == e) word = b;
+            }
+            if (lane < WORDS) unit_mask[(int64_t)u * WORDS + lane] = word;
+        }
     } else if (lane == 0) {
         unit_count[u] = 0;
     }
@@ -309,31 +285,35 @@ __device__ __forceinline__ bool level_step(const E *__restrict__ plane, int64_t 
 }
 
 // Levels 4, 8 and 16 (under 10 % of the cells): out of line, so that their gathers do not set
-// the register budget of the common path (levels 1 and 2).
+// the register budget of the common path (level 2).
 template <typename E>
 __device__ __noinline__ void high_levels(const E *__restrict__ plane, int64_t nb, int zmax, int K,
-                                         const LevelTable *lt, int i, int z, int chunk, int64_t rl,
+                                         const LevelTable *lt, int i, int z, int chunk, int64_t rb,
                                          const float *s_in, int32_t *__restrict__ unit_count,
                                          uint32_t *__restrict__ unit_mask) {
     float s[LB];
 #pragma unroll
     for (int e = 0; e < LB; e++) s[e] = s_in[e];
     const int n = lt->n_levels;
-    if (!level_step<E, 4>(plane, nb, zmax, K, lt->lev[2], i, z, chunk, rl, s, 0.0f, unit_count, unit_mask)) return;
-    if (n < 4 || !level_step<E, 8>(plane, nb, zmax, K, lt->lev[3], i, z, chunk, rl, s, 0.0f, unit_count, unit_mask))
+    if (!level_step<E, 4>(plane, nb, zmax, K, lt->lev[2], i, z, chunk, rb, s, unit_count, unit_mask)) return;
+    if (n < 4 || !level_step<E, 8>(plane, nb, zmax, K, lt->lev[3], i, z, chunk, rb, s, unit_count, unit_mask))
         return;
-    if (n > 4) level_step<E, 16>(plane, nb, zmax, K, lt->lev[4], i, z, chunk, rl, s, 0.0f, unit_count, unit_mask);
+    if (n > 4) level_step<E, 16>(plane, nb, zmax, K, lt->lev[4], i, z, chunk, rb, s, unit_count, unit_mask);
 }
 
-// Levels 2 .. of one (row, chunk) inside level 2's region; s holds S_1 on entry.
+// Levels 2 .. of one (row, chunk) inside level 2's region; s holds S_1 of the lane's bins on entry.
 template <typename E>
 __device__ __forceinline__ void detect_chunk(const E *__restrict__ plane, int64_t nb, int zmax, int K,
-                                             const LevelTable &lt, int i, int z, int chunk, int64_t rl,
+                                             const LevelTable &lt, int i, int z, int chunk, int64_t rb,
                                              float (&s)[LB], int32_t *__restrict__ unit_count,
                                              uint32_t *__restrict__ unit_mask) {
-    if (!level_step<E, 2>(plane, nb, zmax, K, lt.lev[1], i, z, chunk, rl, s, 0.0f, unit_count, unit_mask)) return;
-    if (lt.n_levels > 2 && row_in_level(i, K, zmax, 4) && (int64_t)chunk * CB <= lt.lev[2].rmax)
-        high_levels<E>(plane, nb, zmax, K, &lt, i, z, chunk, rl, s, unit_count, unit_mask);
+    if (!level_step<E, 2>(plane, nb, zmax, K, lt.lev[1], i, z, chunk, rb, s, unit_count, unit_mask)) return;
+    if (lt.n_levels > 2 && row_in_level(i, K, zmax, 4) && (int64_t)chunk * CB <= lt.lev[2].rmax) {
+        float t[LB];                                 // the out-of-line call's copy (S_2 stays in registers)
+#pragma unroll
+        for (int e = 0; e < LB; e++) t[e] = s[e];
+        high_levels<E>(plane, nb, zmax, K, &lt, i, z, chunk, rb, t, unit_count, unit_mask);
+    }
 }
 
 // The level-1 peaks among a lane's 16 bins rl .. rl + 15 of row i (a lane holding a value above
@@ -424,7 +404,7 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32) k4_level1_marked(const E *_
 
 // Levels 2 .. 16 over level 2's region (rows i_lo .. i_lo + rows - 1 of level 2, chunks up to its
 // rmax): grid (ceil(chunks2 / (DETECT_WARPS * CPW)), rows2); each warp re-reads S_1 of CPW chunks
-// and carries the running sums through the levels in registers.
+// (interleaved bins, see add_harmonic) and carries the running sums through the levels in registers.
 template <typename E>
 __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_levels(const E *__restrict__ plane, int64_t nb, int zmax, int K,
                                                               LevelTable lt, int chunks2,
@@ -436,16 +416,17 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_leve
     if (c0 >= chunks2) return;                       // warp-uniform
     const int z = -zmax + 2 * i;
     const E *row = plane + (int64_t)i * nb;
-    typename Fmt<E>::Raw raw[CPW];
+    float s1[CPW][LB];                               // S_1 of the lane's bins r0 + lane + 32 e
 #pragma unroll
     for (int c = 0; c < CPW; c++)
-        if (c0 + c < chunks2) Fmt<E>::load_raw(row + (int64_t)(c0 + c) * CB + LB * lane, raw[c]);
+        if (c0 + c < chunks2) {
+#pragma unroll
+            for (int e = 0; e < LB; e++) s1[c][e] = ld_plane(row, (int64_t)(c0 + c) * CB + lane + 32 * e);
+        }
 #pragma unroll
     for (int c = 0; c < CPW; c++) {
         if (c0 + c >= chunks2) break;
-        float s[LB];
-        Fmt<E>::widen(raw[c], s);
-        detect_chunk<E>(plane, nb, zmax, K, lt, i, z, c0 + c, (int64_t)(c0 + c) * CB + LB * lane, s, unit_count,
+        detect_chunk<E>(plane, nb, zmax, K, lt, i, z, c0 + c, (int64_t)(c0 + c) * CB + lane, s1[c], unit_count,
                         unit_mask);
     }
 }
