@@ -48,7 +48,7 @@ static_assert((CPW & (CPW - 1)) == 0 && CPW <= 2, "chunks per warp: 1 or 2 (chun
 #define FDAS_K4_L1_MIN_BLOCKS 2          // resident k4_level1 blocks per SM the registers must allow
 #endif
 #ifndef FDAS_K4_MIN_BLOCKS
-#define FDAS_K4_MIN_BLOCKS 3             // resident k4_levels blocks per SM the registers must allow
+#define FDAS_K4_MIN_BLOCKS 2             // resident k4_levels blocks per SM the registers must allow
 #endif
 
 static_assert(LB == 16, "a lane owns 16 bins: two BF16 or four FP32 16-byte vectors");
@@ -243,13 +243,13 @@ __device__ __noinline__ bool local_max(const E *plane, int64_t nb, int zmax, int
 // One level H > 1 of one (row, chunk), lane bins rb + 32 e: S_H from S_{H/2}, then the unit's count
 // and mask (word e of the mask, bins 32 e .. 32 e + 31 of the chunk, is the warp's ballot of bit e).
 // Returns false when the chunk lies outside level H's region (the regions nest: stop there).
-template <typename E, int H>
+template <typename E, int H, bool ADD = true>
 __device__ __forceinline__ bool level_step(const E *__restrict__ plane, int64_t nb, int zmax, int K,
                                            const LevelDesc &d, int i, int z, int chunk, int64_t rb, float (&s)[LB],
                                            int32_t *__restrict__ unit_count, uint32_t *__restrict__ unit_mask) {
     const int lane = threadIdx.x & 31;
     if (!row_in_level(i, K, zmax, H) || (int64_t)chunk * CB > d.rmax) return false;   // warp-uniform
-    add_level<E, H>(plane, nb, zmax, z, rb, d.rmax, s);
+    if (ADD) add_level<E, H>(plane, nb, zmax, z, rb, d.rmax, s);
     float vmax = -INFINITY;
 #pragma unroll
     for (int e = 0; e < LB; e++)
@@ -301,13 +301,14 @@ __device__ __noinline__ void high_levels(const E *__restrict__ plane, int64_t nb
     if (n > 4) level_step<E, 16>(plane, nb, zmax, K, lt->lev[4], i, z, chunk, rb, s, unit_count, unit_mask);
 }
 
-// Levels 2 .. of one (row, chunk) inside level 2's region; s holds S_1 of the lane's bins on entry.
+// Levels 2 .. of one (row, chunk) inside level 2's region; s holds S_2 of the lane's bins on entry
+// (the caller reads S_1 and the second harmonic together).
 template <typename E>
 __device__ __forceinline__ void detect_chunk(const E *__restrict__ plane, int64_t nb, int zmax, int K,
                                              const LevelTable &lt, int i, int z, int chunk, int64_t rb,
                                              float (&s)[LB], int32_t *__restrict__ unit_count,
                                              uint32_t *__restrict__ unit_mask) {
-    if (!level_step<E, 2>(plane, nb, zmax, K, lt.lev[1], i, z, chunk, rb, s, unit_count, unit_mask)) return;
+    if (!level_step<E, 2, false>(plane, nb, zmax, K, lt.lev[1], i, z, chunk, rb, s, unit_count, unit_mask)) return;
     if (lt.n_levels > 2 && row_in_level(i, K, zmax, 4) && (int64_t)chunk * CB <= lt.lev[2].rmax) {
         float t[LB];                                 // the out-of-line call's copy (S_2 stays in registers)
 #pragma unroll
@@ -416,17 +417,26 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_leve
     if (c0 >= chunks2) return;                       // warp-uniform
     const int z = -zmax + 2 * i;
     const E *row = plane + (int64_t)i * nb;
-    float s1[CPW][LB];                               // S_1 of the lane's bins r0 + lane + 32 e
+    const E *row2 = plane + (int64_t)((2 * z + zmax) >> 1) * nb;      // harmonic 2
+    const int64_t rmax2 = lt.lev[1].rmax;
+    float s2[CPW][LB];                               // S_2 of the lane's bins r0 + lane + 32 e
 #pragma unroll
     for (int c = 0; c < CPW; c++)
         if (c0 + c < chunks2) {
+            float v[LB];
 #pragma unroll
-            for (int e = 0; e < LB; e++) s1[c][e] = ld_plane(row, (int64_t)(c0 + c) * CB + lane + 32 * e);
+            for (int e = 0; e < LB; e++) {           // S_1 and the second harmonic, all loads at once
+                const int64_t r = (int64_t)(c0 + c) * CB + lane + 32 * e;
+                s2[c][e] = ld_plane(row, r);
+                v[e] = r <= rmax2 ? ld_plane(row2, 2 * r) : 0.0f;
+            }
+#pragma unroll
+            for (int e = 0; e < LB; e++) s2[c][e] = __fadd_rn(s2[c][e], v[e]);
         }
 #pragma unroll
     for (int c = 0; c < CPW; c++) {
         if (c0 + c >= chunks2) break;
-        detect_chunk<E>(plane, nb, zmax, K, lt, i, z, c0 + c, (int64_t)(c0 + c) * CB + lane, s1[c], unit_count,
+        detect_chunk<E>(plane, nb, zmax, K, lt, i, z, c0 + c, (int64_t)(c0 + c) * CB + lane, s2[c], unit_count,
                         unit_mask);
     }
 }
