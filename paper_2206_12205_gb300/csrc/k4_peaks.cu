@@ -443,11 +443,75 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_leve
 
 // Levels 2 .. 16 of the highest-harmonic-anchored sums (harm_mode 1) over the whole plane: grid
 // (K rows, ceil(chunks / DETECT_WARPS)), so the blocks in flight share chunk positions across rows
-// and the rows they gather from stay in L2.  A warp owns one (row, 512-bin chunk) and carries the
-// running sums of its lanes' 16 bins through the levels; for each new harmonic j of level L the
-// bins it needs, r_j for the chunk's 512 r, are one span of at most 512 j / L + 1 elements of row
-// i_j, staged through shared memory with coalesced loads.
-constexpr int ANCH_SPAN = CB + 8;
+// and the rows they gather from stay in L2.  A warp owns one (row, 512-bin chunk) with the lane
+// bins interleaved (lane l holds r0 + l + 32 e) and carries the running sums through the levels.
+// For each new harmonic j of level L, the terms r_j = floor((2 j r + L) / (2 L)) of 32
+// consecutive r are at most 32 consecutive elements of row i_j, so each warp-wide load reads one
+// or two sectors; a harmonic's 16 loads per lane are issued together.
+// S_L from S_{L/2} for the anchored sums: the odd harmonics j < L in increasing order, the loads
+// of two harmonics in flight together (32 per lane).  2 j r + L < 2^31 (r < Nb <= 2^26, j < 16),
+// so the index arithmetic is 32-bit.
+template <typename E, int LOG>
+__device__ __forceinline__ void anch_add_level(const E *__restrict__ plane, int64_t nb, int zmax, int z, uint32_t rb,
+                                               float (&s)[LB]) {
+    constexpr int L = 1 << LOG;
+#pragma unroll
+    for (int j0 = 1; j0 < L; j0 += 4) {
+        float v[2][LB];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int j = j0 + 2 * q;
+            if (j < L) {
+                const int ij = (j * z + L * zmax + L) >> (LOG + 1);
+                const E *rowj = plane + (int64_t)ij * nb;
+                const uint32_t b = 2u * (uint32_t)j * rb + (uint32_t)L;
+#pragma unroll
+                for (int e = 0; e < LB; e++) v[q][e] = ld_plane(rowj, (int64_t)((b + 64u * (uint32_t)(j * e)) >> (LOG + 1)));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+            if (j0 + 2 * q < L) {
+#pragma unroll
+                for (int e = 0; e < LB; e++) s[e] = __fadd_rn(s[e], v[q][e]);
+            }
+        asm volatile("" ::: "memory");
+    }
+}
+
+// The count and mask of one anchored unit (row i, chunk c) of level L, lane bins rb + 32 e.
+template <typename E>
+__device__ __forceinline__ void anch_unit(const E *__restrict__ plane, int64_t nb, int zmax, int K, const LevelDesc &d,
+                                          int L, int i, int c, int64_t rb, const float (&s)[LB],
+                                          int32_t *__restrict__ unit_count, uint32_t *__restrict__ unit_mask) {
+    const int lane = threadIdx.x & 31;
+    float vmax = s[0];
+#pragma unroll
+    for (int e = 1; e < LB; e++) vmax = fmaxf(vmax, s[e]);
+    const int u = (int)d.unit0 + i * (int)d.chunks + c;
+    if (__any_sync(0xffffffffu, vmax > d.thr)) {
+        uint32_t pk = 0;
+        if (vmax > d.thr) {
+            for (int e = 0; e < LB; e++)
+                if (s[e] > d.thr && local_max(plane, nb, zmax, K, L, d.rmax, i, rb + 32 * e, s[e], true)) pk |= 1u << e;
+        }
+        int cnt = __popc(pk);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) unit_count[u] = cnt;
+        if (cnt > 0) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int e = 0; e < LB; e++) {
+                const uint32_t bal = __ballot_sync(0xffffffffu, (pk >> e) & 1u);
+                if (lane == e) word = bal;
+            }
+            if (lane < WORDS) unit_mask[(int64_t)u * WORDS + lane] = word;
+        }
+    } else if (lane == 0) {
+        unit_count[u] = 0;
+    }
+}
 
 template <typename E>
 __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4a_levels(const E *__restrict__ plane, int64_t nb,
@@ -455,59 +519,29 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4a_lev
                                                                                int chunks,
                                                                                int32_t *__restrict__ unit_count,
                                                                                uint32_t *__restrict__ unit_mask) {
-    __shared__ float stage[DETECT_WARPS][ANCH_SPAN];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x;
     const int c = blockIdx.y * DETECT_WARPS + w;
     if (c >= chunks) return;                         // warp-uniform
     const int z = -zmax + 2 * i;
-    const int64_t r_first = (int64_t)c * CB;
-    const int64_t rl = r_first + LB * lane;
+    const int64_t rb = (int64_t)c * CB + lane;
     float s[LB];
     {
-        typename Fmt<E>::Raw raw;
-        Fmt<E>::load_raw(plane + (int64_t)i * nb + rl, raw);
-        Fmt<E>::widen(raw, s);
+        const E *row = plane + (int64_t)i * nb;
+#pragma unroll
+        for (int e = 0; e < LB; e++) s[e] = ld_plane(row, rb + 32 * e);
     }
-    float *st = stage[w];
-    for (int l = 1; l < lt.n_levels; l++) {
-        const int L = 1 << l;
-        for (int j = 1; j < L; j += 2) {
-            const int ij = (j * z + L * zmax + L) >> (l + 1);
-            const int64_t s0 = (2 * (int64_t)j * r_first + L) >> (l + 1);
-            const int64_t s1 = (2 * (int64_t)j * (r_first + CB - 1) + L) >> (l + 1);
-            const int len = (int)(s1 - s0 + 1);             // <= CB j / L + 1 <= CB
-            const E *row = plane + (int64_t)ij * nb;
-            __syncwarp();
-            for (int t = lane; t < len; t += 32) st[t] = ld_plane(row, s0 + t);
-            __syncwarp();
-#pragma unroll
-            for (int e = 0; e < LB; e++) {
-                const int64_t rj = (2 * (int64_t)j * (rl + e) + L) >> (l + 1);
-                s[e] = __fadd_rn(s[e], st[rj - s0]);
-            }
-        }
-        const LevelDesc &d = lt.lev[l];
-        float vmax = s[0];
-#pragma unroll
-        for (int e = 1; e < LB; e++) vmax = fmaxf(vmax, s[e]);
-        const int u = (int)d.unit0 + i * (int)d.chunks + c;
-        if (__any_sync(0xffffffffu, vmax > d.thr)) {
-            uint32_t pk = 0;
-            if (vmax > d.thr) {
-                for (int e = 0; e < LB; e++)
-                    if (s[e] > d.thr && local_max(plane, nb, zmax, K, L, d.rmax, i, rl + e, s[e], true)) pk |= 1u << e;
-            }
-            int cnt = __popc(pk);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            const uint32_t hi = __shfl_down_sync(0xffffffffu, pk, 1);
-            if (lane == 0) unit_count[u] = cnt;
-            if (cnt > 0 && !(lane & 1)) unit_mask[(int64_t)u * WORDS + (lane >> 1)] = pk | (hi << 16);
-        } else if (lane == 0) {
-            unit_count[u] = 0;
-        }
-    }
+    anch_add_level<E, 1>(plane, nb, zmax, z, (uint32_t)rb, s);
+    anch_unit<E>(plane, nb, zmax, K, lt.lev[1], 2, i, c, rb, s, unit_count, unit_mask);
+    if (lt.n_levels < 3) return;
+    anch_add_level<E, 2>(plane, nb, zmax, z, (uint32_t)rb, s);
+    anch_unit<E>(plane, nb, zmax, K, lt.lev[2], 4, i, c, rb, s, unit_count, unit_mask);
+    if (lt.n_levels < 4) return;
+    anch_add_level<E, 3>(plane, nb, zmax, z, (uint32_t)rb, s);
+    anch_unit<E>(plane, nb, zmax, K, lt.lev[3], 8, i, c, rb, s, unit_count, unit_mask);
+    if (lt.n_levels < 5) return;
+    anch_add_level<E, 4>(plane, nb, zmax, z, (uint32_t)rb, s);
+    anch_unit<E>(plane, nb, zmax, K, lt.lev[4], 16, i, c, rb, s, unit_count, unit_mask);
 }
 
 // First-level scan: exclusive prefix of the counts inside each block of SCAN_BLOCK units.
