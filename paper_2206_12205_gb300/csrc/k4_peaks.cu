@@ -448,18 +448,22 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_leve
 // For each new harmonic j of level L, the terms r_j = floor((2 j r + L) / (2 L)) of 32
 // consecutive r are at most 32 consecutive elements of row i_j, so each warp-wide load reads one
 // or two sectors; a harmonic's 16 loads per lane are issued together.
+#ifndef FDAS_K4A_BATCH
+#define FDAS_K4A_BATCH 2                 // anchored harmonics whose loads are issued together
+#endif
 // S_L from S_{L/2} for the anchored sums: the odd harmonics j < L in increasing order, the loads
-// of two harmonics in flight together (32 per lane).  2 j r + L < 2^31 (r < Nb <= 2^26, j < 16),
+// of FDAS_K4A_BATCH harmonics in flight together (16 per harmonic and lane).  2 j r + L < 2^31 (r < Nb <= 2^26, j < 16),
 // so the index arithmetic is 32-bit.
 template <typename E, int LOG>
 __device__ __forceinline__ void anch_add_level(const E *__restrict__ plane, int64_t nb, int zmax, int z, uint32_t rb,
                                                float (&s)[LB]) {
     constexpr int L = 1 << LOG;
+    constexpr int NB = FDAS_K4A_BATCH;
 #pragma unroll
-    for (int j0 = 1; j0 < L; j0 += 4) {
-        float v[2][LB];
+    for (int j0 = 1; j0 < L; j0 += 2 * NB) {
+        float v[NB][LB];
 #pragma unroll
-        for (int q = 0; q < 2; q++) {
+        for (int q = 0; q < NB; q++) {
             const int j = j0 + 2 * q;
             if (j < L) {
                 const int ij = (j * z + L * zmax + L) >> (LOG + 1);
@@ -470,7 +474,7 @@ __device__ __forceinline__ void anch_add_level(const E *__restrict__ plane, int6
             }
         }
 #pragma unroll
-        for (int q = 0; q < 2; q++)
+        for (int q = 0; q < NB; q++)
             if (j0 + 2 * q < L) {
 #pragma unroll
                 for (int e = 0; e < LB; e++) s[e] = __fadd_rn(s[e], v[q][e]);
