@@ -44,7 +44,7 @@ def _peaks_equal(a, b):
         assert np.float32(x["power"]).tobytes() == np.float32(y["power"]).tobytes()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16_scaled", "bf16_direct", "fp8_direct"])
 def test_batch_equals_series_searched_alone(precision):
     wl = _small_batch()
     cfgs = _cfgs(wl, precision)
