@@ -126,7 +126,7 @@ cudaError_t launch_local_norm(const Plan &p, const float2 *d_x, float2 *d_out, c
 cudaError_t launch_apply_scale(const Plan &p, const char *ws, float *d_xhat, double *d_sigma2,
                                cudaStream_t st);
 cudaError_t launch_plane_fp32(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
-                              float *d_plane, cudaStream_t st);
+                              float *d_plane, cudaStream_t st, uint8_t *l1flag = nullptr);
 // The same kernels with the segment spectra (n_seg * S complex64) at d_yhat instead of the workspace.
 cudaError_t launch_plane_fp32_scratch(const Plan &p, const float2 *d_x, const float *d_scale, float2 *d_yhat,
                                       float *d_plane, cudaStream_t st);
@@ -149,7 +149,7 @@ cudaError_t launch_plane_direct(const Plan &p, const float2 *d_x, const float *d
                                 __nv_bfloat16 *d_plane, cudaStream_t st);
 cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
                              cudaStream_t st, uint8_t *l1flag = nullptr);
-// Whether the plan's plane kernel can mark the level-1 units (the tensor-core DFT paths).
+// Whether the plan's plane kernel can mark the level-1 units (the FP32 and tensor-core DFT paths).
 bool level1_fusable(const Plan &p);
 // The plane of the plan's precision from a spectrum (x: Nb complex; scale: device factor or NULL).
 cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale, char *ws, void *d_plane,

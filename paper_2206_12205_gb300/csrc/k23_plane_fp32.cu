@@ -11,7 +11,9 @@
 //       unnormalised), forward FFT, Yhat stored [n_seg][S].
 //   K3 (one CTA per segment and run of templates): complex multiply fused into the FFT's
 //       coalesced loads, forward FFT, |.|^2 and overlap discard fused into its coalesced
-//       stores: the plane is written exactly once and nothing else touches HBM in bulk.
+//       stores: the plane is written exactly once and nothing else touches HBM in bulk.  Inside
+//       a search it also marks the 512-bin units holding a power above the level-1 threshold
+//       (the level-1 pass of the peak search then visits only those).
 #include "block_fft.cuh"
 #include "fdas_internal.cuh"
 
@@ -46,7 +48,8 @@ __global__ void __launch_bounds__(S / 32) k2_segments(const float2 *__restrict__
 template <int S>
 __global__ void __launch_bounds__(S / 32) k3_plane_fp32(const float2 *__restrict__ Y, const float2 *__restrict__ G,
                                                         const float2 *__restrict__ tw, float *__restrict__ plane,
-                                                        int K, int zb, int64_t nb, int L) {
+                                                        int K, int zb, int64_t nb, int L, uint8_t *__restrict__ l1flag,
+                                                        int64_t chunks1, float thr1) {
     constexpr int T = S / 32;
     extern __shared__ float2 sm[];
     const int t = threadIdx.x;
@@ -66,17 +69,29 @@ __global__ void __launch_bounds__(S / 32) k3_plane_fp32(const float2 *__restrict
         }
         block_fft<S>(v, sm, tw, t);
         float *row = plane + (int64_t)z * nb + r0;
+        float vm[4] = {0.f, 0.f, 0.f, 0.f};          // four short max chains (latency)
 #pragma unroll
         for (int i = 0; i < 32; i++) {
             const int o = t + i * T;
-            if (o < lim) row[o] = v[i].x * v[i].x + v[i].y * v[i].y;
+            const float pw = v[i].x * v[i].x + v[i].y * v[i].y;
+            vm[i & 3] = fmaxf(vm[i & 3], pw);
+            if (o < lim) row[o] = pw;
+        }
+        const float vmax = fmaxf(fmaxf(vm[0], vm[1]), fmaxf(vm[2], vm[3]));
+        if (l1flag != nullptr && vmax > thr1) {      // rare: recompute the same powers
+            uint8_t *frow = l1flag + (int64_t)z * chunks1;
+#pragma unroll
+            for (int i = 0; i < 32; i++) {
+                const int o = t + i * T;
+                if (o < lim && v[i].x * v[i].x + v[i].y * v[i].y > thr1) frow[(r0 + o) >> 9] = 1;
+            }
         }
     }
 }
 
 template <int S>
 cudaError_t run_plane(const Plan &p, const float2 *d_x, const float *d_scale, float2 *Y, float *plane,
-                      cudaStream_t st) {
+                      cudaStream_t st, uint8_t *l1flag) {
     const size_t smem = sizeof(float2) * fft_smem_entries(S);
     cudaError_t e = cudaFuncSetAttribute(k2_segments<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -92,8 +107,13 @@ cudaError_t run_plane(const Plan &p, const float2 *d_x, const float *d_scale, fl
     int zb = (int)std::max<int64_t>(1, std::min<int64_t>(16, (p.n_seg * p.K) / (152 * 8)));
     if (p.tune_zb > 0) zb = std::min(p.tune_zb, p.K);
     dim3 grid((unsigned)p.n_seg, (unsigned)((p.K + zb - 1) / zb));
+    if (l1flag) {
+        e = cudaMemsetAsync(l1flag, 0, (size_t)p.K * (size_t)(p.nb / PEAK_CHUNK), st);
+        if (e != cudaSuccess) return e;
+    }
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
-    k3_plane_fp32<S><<<grid, S / 32, smem, st>>>(Y, p.d_G, p.d_tw, plane, p.K, zb, p.nb, p.L);
+    k3_plane_fp32<S><<<grid, S / 32, smem, st>>>(Y, p.d_G, p.d_tw, plane, p.K, zb, p.nb, p.L, l1flag,
+                                                 p.nb / PEAK_CHUNK, p.cfg.thr[0]);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 1;
     return cudaGetLastError();
@@ -101,14 +121,16 @@ cudaError_t run_plane(const Plan &p, const float2 *d_x, const float *d_scale, fl
 
 }  // namespace
 
+static_assert(PEAK_CHUNK == 512, "the level-1 marks index units as bin >> 9");
+
 cudaError_t launch_plane_fp32(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
-                              cudaStream_t st) {
+                              cudaStream_t st, uint8_t *l1flag) {
     float2 *Y = reinterpret_cast<float2 *>(ws + p.ws_y);
     switch (p.S) {
-        case 1024: return run_plane<1024>(p, d_x, d_scale, Y, d_plane, st);
-        case 2048: return run_plane<2048>(p, d_x, d_scale, Y, d_plane, st);
-        case 4096: return run_plane<4096>(p, d_x, d_scale, Y, d_plane, st);
-        case 8192: return run_plane<8192>(p, d_x, d_scale, Y, d_plane, st);
+        case 1024: return run_plane<1024>(p, d_x, d_scale, Y, d_plane, st, l1flag);
+        case 2048: return run_plane<2048>(p, d_x, d_scale, Y, d_plane, st, l1flag);
+        case 4096: return run_plane<4096>(p, d_x, d_scale, Y, d_plane, st, l1flag);
+        case 8192: return run_plane<8192>(p, d_x, d_scale, Y, d_plane, st, l1flag);
     }
     return cudaErrorInvalidValue;
 }
@@ -129,10 +151,10 @@ cudaError_t launch_segments_fp32(const Plan &p, const float2 *d_x, const float *
 cudaError_t launch_plane_fp32_scratch(const Plan &p, const float2 *d_x, const float *d_scale, float2 *d_yhat,
                                       float *d_plane, cudaStream_t st) {
     switch (p.S) {
-        case 1024: return run_plane<1024>(p, d_x, d_scale, d_yhat, d_plane, st);
-        case 2048: return run_plane<2048>(p, d_x, d_scale, d_yhat, d_plane, st);
-        case 4096: return run_plane<4096>(p, d_x, d_scale, d_yhat, d_plane, st);
-        case 8192: return run_plane<8192>(p, d_x, d_scale, d_yhat, d_plane, st);
+        case 1024: return run_plane<1024>(p, d_x, d_scale, d_yhat, d_plane, st, nullptr);
+        case 2048: return run_plane<2048>(p, d_x, d_scale, d_yhat, d_plane, st, nullptr);
+        case 4096: return run_plane<4096>(p, d_x, d_scale, d_yhat, d_plane, st, nullptr);
+        case 8192: return run_plane<8192>(p, d_x, d_scale, d_yhat, d_plane, st, nullptr);
     }
     return cudaErrorInvalidValue;
 }
