@@ -372,7 +372,7 @@ typedef struct {
     int64_t n_timed_peaks[2]; /* inside the peaks stage: level-1 pass, level 2..16 pass          */
     double  ms_peaks[2];    /* their summed event times in milliseconds                         */
     int64_t level1_fused;   /* peak searches whose level-1 pass visited only the 512-bin units
-                               that the plane kernel (FDAS_FP32, FDAS_BF16, FDAS_FP16_SCALED,
+                               that the plane kernel (every precision but FDAS_BF16_SPLIT,
                                inside fdas_search / fdas_batch_search) marked as holding a value
                                above thr[0], instead of reading the whole plane                */
 } fdas_profile;

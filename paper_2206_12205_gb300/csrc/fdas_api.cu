@@ -52,8 +52,9 @@ cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale,
         case FDAS_BF16: return launch_plane_bf16(p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st, l1flag);
         case FDAS_BF16_SPLIT: return launch_plane_split(p, x, scale, ws, static_cast<float *>(d_plane), st);
         case FDAS_FP16_SCALED: return launch_plane_f16(p, x, scale, ws, static_cast<float *>(d_plane), st, l1flag);
-        case FDAS_BF16_DIRECT: return launch_plane_direct(p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st);
-        case FDAS_FP8_DIRECT: return launch_plane_direct_f8(p, x, scale, ws, static_cast<float *>(d_plane), st);
+        case FDAS_BF16_DIRECT:
+            return launch_plane_direct(p, x, scale, ws, static_cast<__nv_bfloat16 *>(d_plane), st, l1flag);
+        case FDAS_FP8_DIRECT: return launch_plane_direct_f8(p, x, scale, ws, static_cast<float *>(d_plane), st, l1flag);
         default: return launch_plane_fp32(p, x, scale, ws, static_cast<float *>(d_plane), st, l1flag);
     }
 }

@@ -144,12 +144,12 @@ bool direct_geometry(const Plan &p, int *Kpad, uint32_t *smem_bytes, uint32_t *t
 size_t direct_pack_words(const Plan &p);
 bool direct_geometry_f8(const Plan &p, int *n_groups, uint32_t *smem_bytes);
 cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
-                                   cudaStream_t st);
+                                   cudaStream_t st, uint8_t *l1flag = nullptr);
 cudaError_t launch_plane_direct(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
-                                __nv_bfloat16 *d_plane, cudaStream_t st);
+                                __nv_bfloat16 *d_plane, cudaStream_t st, uint8_t *l1flag = nullptr);
 cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
                              cudaStream_t st, uint8_t *l1flag = nullptr);
-// Whether the plan's plane kernel can mark the level-1 units (the FP32 and tensor-core DFT paths).
+// Whether the plan's plane kernel marks the level-1 units (every precision's plane kernel).
 bool level1_fusable(const Plan &p);
 // The plane of the plan's precision from a spectrum (x: Nb complex; scale: device factor or NULL).
 cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale, char *ws, void *d_plane,

@@ -804,7 +804,8 @@ static cudaError_t prepare_plane_tc() {
 static_assert(PEAK_CHUNK == 512, "the level-1 marks index units as bin >> 9");
 
 bool level1_fusable(const Plan &p) {
-    return p.cfg.precision == FDAS_FP32 || p.cfg.precision == FDAS_BF16 || p.cfg.precision == FDAS_FP16_SCALED;
+    return p.cfg.precision == FDAS_FP32 || p.cfg.precision == FDAS_BF16 || p.cfg.precision == FDAS_FP16_SCALED ||
+           p.cfg.precision == FDAS_BF16_DIRECT || p.cfg.precision == FDAS_FP8_DIRECT;
 }
 
 // Clear the level-1 unit marks before the plane kernel sets them.

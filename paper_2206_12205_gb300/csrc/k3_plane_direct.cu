@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct(const uint32_
                                                                    __nv_bfloat16 *__restrict__ plane, int K, int Kpad,
                                                                    int m, int64_t nb, int64_t n_tiles,
                                                                    int64_t tiles_per_cta, uint32_t tmem_cols,
-                                                                   int32_t *__restrict__ status) {
+                                                                   uint8_t *__restrict__ l1flag, int64_t chunks1,
+                                                                   float thr1, int32_t *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int N = 2 * Kpad, KD = 2 * m, WW = DT + m;
     const uint32_t b_bytes = (uint32_t)N * KD * 2;
@@ -197,7 +198,10 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct(const uint32_
                             const int z = z0 + e;
                             if (z < K) {
                                 const float xr = __uint_as_float(re[e]), xi = __uint_as_float(im[e]);
-                                plane[(int64_t)z * nb + r] = __float2bfloat16_rn(xr * xr + xi * xi);
+                                const __nv_bfloat16 v = __float2bfloat16_rn(xr * xr + xi * xi);
+                                plane[(int64_t)z * nb + r] = v;
+                                // level-1 mark of the unit (z, r / 512) when the stored value is above thr1
+                                if (l1flag != nullptr && __bfloat162float(v) > thr1) l1flag[(int64_t)z * chunks1 + (r >> 9)] = 1;
                             }
                         }
                     }
@@ -272,7 +276,8 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct_f8(const floa
                                                                       const float *__restrict__ tsig,
                                                                       float *__restrict__ plane, int K, int n_groups, int m,
                                                                       int64_t nb, int64_t n_tiles, int64_t tiles_per_cta,
-                                                                      int32_t *__restrict__ status) {
+                                                                      uint8_t *__restrict__ l1flag, int64_t chunks1,
+                                                                      float thr1, int32_t *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int WW = DT8 + m, WL = WW + 8;                           // window copy / raw window (bins)
     const uint32_t b_bytes = (uint32_t)n_groups * F8_N * 2 * m;
@@ -459,8 +464,14 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct_f8(const floa
                         if (z < K) {
                             const float ts = __ldg(tsig + z);
                             float4 *o = reinterpret_cast<float4 *>(plane + (int64_t)z * nb + r);
-                            o[0] = make_float4(pw[0][e] * ts, pw[1][e] * ts, pw[2][e] * ts, pw[3][e] * ts);
-                            o[1] = make_float4(pw[4][e] * ts, pw[5][e] * ts, pw[6][e] * ts, pw[7][e] * ts);
+                            const float4 lo = make_float4(pw[0][e] * ts, pw[1][e] * ts, pw[2][e] * ts, pw[3][e] * ts);
+                            const float4 hi = make_float4(pw[4][e] * ts, pw[5][e] * ts, pw[6][e] * ts, pw[7][e] * ts);
+                            o[0] = lo;
+                            o[1] = hi;
+                            // level-1 mark: the 8 bins lie in one 512-bin unit
+                            if (l1flag != nullptr &&
+                                fmaxf(fmaxf(fmaxf(lo.x, lo.y), fmaxf(lo.z, lo.w)), fmaxf(fmaxf(hi.x, hi.y), fmaxf(hi.z, hi.w))) > thr1)
+                                l1flag[(int64_t)z * chunks1 + (r >> 9)] = 1;
                         }
                     }
                 }
@@ -492,7 +503,7 @@ bool direct_geometry_f8(const Plan &p, int *n_groups, uint32_t *smem_bytes) {
 }
 
 cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float *d_scale, char *ws, float *d_plane,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, uint8_t *l1flag) {
     int G = 0;
     uint32_t smem = 0;
     if (!p.d_dimg || !p.d_dsig || !direct_geometry_f8(p, &G, &smem)) return cudaErrorInvalidValue;
@@ -506,6 +517,10 @@ cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float
         if (e != cudaSuccess) return e;
         d_x = tmp;
     }
+    if (l1flag) {
+        e = cudaMemsetAsync(l1flag, 0, (size_t)p.K * (size_t)(p.nb / PEAK_CHUNK), st);
+        if (e != cudaSuccess) return e;
+    }
     const int64_t n_tiles = (p.nb + DT8 - 1) / DT8;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
@@ -515,7 +530,7 @@ cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_direct_f8<<<(unsigned)grid, D_WARPS * 32, smem, st>>>(d_x, d_scale, reinterpret_cast<const uint4 *>(p.d_dimg),
                                                                    p.d_dsig, d_plane, p.K, G, p.m, p.nb, n_tiles, per,
-                                                                   p.d_status);
+                                                                   l1flag, p.nb / PEAK_CHUNK, p.cfg.thr[0], p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 1;
     return cudaGetLastError();
@@ -542,7 +557,7 @@ size_t direct_pack_words(const Plan &p) {
 }
 
 cudaError_t launch_plane_direct(const Plan &p, const float2 *d_x, const float *d_scale, char *ws,
-                                __nv_bfloat16 *d_plane, cudaStream_t st) {
+                                __nv_bfloat16 *d_plane, cudaStream_t st, uint8_t *l1flag) {
     int Kpad = 0;
     uint32_t smem = 0, cols = 0;
     if (!p.d_dimg || !direct_geometry(p, &Kpad, &smem, &cols)) return cudaErrorInvalidValue;
@@ -555,6 +570,10 @@ cudaError_t launch_plane_direct(const Plan &p, const float2 *d_x, const float *d
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k3_plane_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (l1flag) {
+        e = cudaMemsetAsync(l1flag, 0, (size_t)p.K * (size_t)(p.nb / PEAK_CHUNK), st);
+        if (e != cudaSuccess) return e;
+    }
     const int64_t n_tiles = (p.nb + DT - 1) / DT;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
@@ -563,7 +582,8 @@ cudaError_t launch_plane_direct(const Plan &p, const float2 *d_x, const float *d
     const int64_t grid = (n_tiles + per - 1) / per;
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_direct<<<(unsigned)grid, D_WARPS * 32, smem, st>>>(Xb, reinterpret_cast<const uint4 *>(p.d_dimg), d_plane,
-                                                                p.K, Kpad, p.m, p.nb, n_tiles, per, cols, p.d_status);
+                                                                p.K, Kpad, p.m, p.nb, n_tiles, per, cols, l1flag,
+                                                                p.nb / PEAK_CHUNK, p.cfg.thr[0], p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 2;
     return cudaGetLastError();

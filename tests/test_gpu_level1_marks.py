@@ -1,9 +1,10 @@
-"""The level-1 pass fused into the plane kernel (FP32 and tensor-core paths): inside fdas_search
-the plane kernel marks every 512-bin unit of a row that holds a stored value above thr[0], and
-level 1 visits only those units instead of reading the whole plane.  The peak list must be the one the full level-1
-pass (fdas_peaks on the same plane) gives, record for record -- the full pass is the one the
-parity tests pin to the oracle -- for thresholds from "a handful of units" to "nearly all", the
-FP32 and both tensor-core precisions, ragged segment tails and the last bins of the rows."""
+"""The level-1 pass fused into the plane kernel (every precision but the split one): inside
+fdas_search the plane kernel marks every 512-bin unit of a row that holds a stored value above
+thr[0], and level 1 visits only those units instead of reading the whole plane.  The peak list
+must be the one the full level-1 pass (fdas_peaks on the same plane) gives, record for record --
+the full pass is the one the parity tests pin to the oracle -- for thresholds from "a handful of
+units" to "nearly all", every precision with marks, ragged segment tails and the last bins of the
+rows."""
 import numpy as np
 import pytest
 import torch
@@ -30,7 +31,7 @@ def _series(n, seed):
     return x.astype(np.float32)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16_scaled"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16_scaled", "bf16_direct", "fp8_direct"])
 @pytest.mark.parametrize("thr1", [3.0, 12.0, 40.0])
 def test_marked_level1_equals_full_pass(precision, thr1):
     n, zmax, m = 1 << 18, 32, 128
