@@ -248,6 +248,17 @@ fdas_status fdas_band_max(fdas_plan_t plan, const void *d_plane, const int64_t *
 fdas_status fdas_get_templates(fdas_plan_t plan, float *d_out, void *stream);
 
 /*
+ * Failure-detection self-check of the bounded waits.  Launches one block on the stream whose
+ * thread waits on an mbarrier that nothing arrives on, in the bounded form every wait of the
+ * plane kernels has, for at most max_cycles SM clock cycles (1 .. 2^36; at 2 GHz 2e9 is about
+ * one second).  When the bound runs out the block sets FDAS_DEV_TIMEOUT in the plan's status
+ * word and returns, leaving the context usable; read it with fdas_device_status.  Needs
+ * fdas_make_templates first (the status word).  Errors: FDAS_E_INVALID, FDAS_E_STATE,
+ * FDAS_E_CUDA.
+ */
+fdas_status fdas_check_timeout(fdas_plan_t plan, int64_t max_cycles, void *stream);
+
+/*
  * Read (and clear when clear != 0) the plan's sticky device status word
  * (FDAS_DEV_* bits).  Synchronises the device.  Errors: FDAS_E_INVALID, FDAS_E_CUDA.
  */

@@ -6,6 +6,7 @@
 #include <new>
 
 #include "fdas_internal.cuh"
+#include "tc_sm100.cuh"
 
 using fdas::Plan;
 
@@ -46,6 +47,16 @@ bool args_aligned(const void *series, const void *xhat, const void *ws, const vo
 }  // namespace
 
 namespace fdas {
+// One thread waits on a fresh mbarrier (phase 0 completes only on an arrival that never comes)
+// for at most max_cycles, then records the timeout: the bounded wait of the plane kernels.
+__global__ void wait_check(int64_t max_cycles, int32_t *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        if (!tc::mbar_wait_bounded(&bar, 0, (long long)max_cycles)) atomicOr(status, FDAS_DEV_TIMEOUT);
+    }
+}
+
 cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale, char *ws, void *d_plane,
                              cudaStream_t st, uint8_t *l1flag) {
     switch (p.cfg.precision) {
@@ -366,6 +377,14 @@ fdas_status fdas_get_templates(fdas_plan_t plan, float *d_out, void *stream) {
     cudaError_t e = cudaMemcpyAsync(d_out, p->d_G, sizeof(float2) * (size_t)p->K * p->S, cudaMemcpyDeviceToDevice,
                                     static_cast<cudaStream_t>(stream));
     return record(p, e);
+}
+
+fdas_status fdas_check_timeout(fdas_plan_t plan, int64_t max_cycles, void *stream) {
+    if (!plan || max_cycles < 1 || max_cycles > (int64_t{1} << 36)) return FDAS_E_INVALID;
+    Plan *p = P(plan);
+    if (!p->templates_ready || !p->d_status) return FDAS_E_STATE;
+    fdas::wait_check<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(max_cycles, p->d_status);
+    return record(p, cudaGetLastError());
 }
 
 fdas_status fdas_device_status(fdas_plan_t plan, int32_t *bits, int clear) {

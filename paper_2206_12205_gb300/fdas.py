@@ -30,7 +30,7 @@ EXPORTED = (
     "fdas_plane_static", "fdas_interp_power", "fdas_refine",
     "fdas_batch_plan", "fdas_batch_autotune", "fdas_batch_make_templates", "fdas_batch_search",
     "fdas_batch_get_info", "fdas_batch_series_info", "fdas_batch_device_status", "fdas_batch_last_error",
-    "fdas_batch_destroy", "fdas_band_max",
+    "fdas_batch_destroy", "fdas_band_max", "fdas_check_timeout",
 )
 REFINE_MAX_STEPS = 1000
 STATIC_SCRATCH_BYTES = 40 << 20
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "fdas_search": (S, [V, V, V, V, V, V, V]),
         "fdas_get_templates": (S, [V, V, V]),
         "fdas_device_status": (S, [V, ctypes.POINTER(I32), ctypes.c_int]),
+        "fdas_check_timeout": (S, [V, I64, V]),
         "fdas_last_error": (ctypes.c_char_p, [V]),
         "fdas_destroy": (None, [V]),
         "fdas_status_string": (ctypes.c_char_p, [S]),
@@ -383,6 +384,11 @@ def fdas_get_templates(plan: Plan, out, stream=None):
     K, S = plan.info.K, plan.cfg["seg_len"]
     _check(load().fdas_get_templates(plan.handle, _dev_ptr(out, "out", torch.float32, 8 * K * S),
                                      _stream_ptr(stream)), "fdas_get_templates", plan)
+
+
+def fdas_check_timeout(plan: Plan, max_cycles: int, stream=None):
+    """Launch the bounded-wait self-check (sets FDAS_DEV_TIMEOUT after max_cycles SM cycles)."""
+    _check(load().fdas_check_timeout(plan.handle, int(max_cycles), _stream_ptr(stream)), "fdas_check_timeout", plan)
 
 
 def fdas_device_status(plan: Plan, clear: bool = True) -> int:

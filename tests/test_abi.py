@@ -193,3 +193,14 @@ def test_fp8_direct_plan_geometry(lib):
     small = fd.fdas_plan(fd.make_config(1 << 11, 0, 16, 1024, precision="fp8_direct"))
     assert small.info.K == 1
     fd.fdas_destroy(small)
+
+
+def test_check_timeout_arguments(lib):
+    """The bounded-wait self-check validates on the host: a bound out of range is invalid, and
+    it needs the plan's status word (templates made) first."""
+    p = fd.fdas_plan(fd.make_config(1 << 16, 16, 64, 1024))
+    assert lib.fdas_check_timeout(None, 1000, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_check_timeout(p.handle, 0, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_check_timeout(p.handle, (1 << 36) + 1, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_check_timeout(p.handle, 1000, None) == fb.FDAS_E_STATE
+    fd.fdas_destroy(p)
