@@ -11,7 +11,7 @@
 //                                    M1-k1 both in shared memory,
 //                                    X_k = (Z_k + conj Z_{M-k})/2 - (i/2) W_N^k (Z_k - conj Z_{M-k}),
 //                                    k < M, and a per-CTA FP64 partial of sum |X_k|^2;
-//   finalize (one CTA):              fixed-order sum of the partials -> sigma2, scale.
+//   finalize (pass B's last block):  fixed-order sum of the partials -> sigma2, scale.
 // The lanes of a warp interleave over the CTA's columns (pass A) or rows (pass B), so every
 // global access of a warp covers whole 32-byte sectors instead of strided single elements.
 // Twiddles W_N^e come from a two-level FP32 table (W_N^e = hi[e >> 13] * lo[e & 8191]), looked
@@ -54,13 +54,15 @@ __global__ void __launch_bounds__(k1_groups_a(M1) * (M1 / 32), FDAS_K1A_MIN_BLOC
                                                                      const float2 *__restrict__ tw,
                                                                      const float2 *__restrict__ lo,
                                                                      const float2 *__restrict__ hi,
-                                                                     float2 *__restrict__ B, int M2) {
+                                                                     float2 *__restrict__ B, int M2,
+                                                                     unsigned int *__restrict__ ticket) {
     constexpr int T = M1 / 32, C1 = k1_groups_a(M1);
     constexpr int E = fft_smem_entries(M1) + K1_GPAD;
     extern __shared__ float2 sm[];        // C1 * E entries
     __shared__ float2 wi[C1][32];         // W_N^{2 n2 T i} of each column
     const int g = threadIdx.x % C1, t = threadIdx.x / C1;
     const int n2 = blockIdx.x * C1 + g;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;   // pass B's block count, read after this kernel
     for (int i = t; i < 32; i += T) wi[g][i] = twN(lo, hi, 2 * (int64_t)n2 * T * i);   // T < 32 for M1 < 1024
     float2 v[32];
 #pragma unroll
@@ -84,7 +86,10 @@ __global__ void __launch_bounds__(2 * k1_groups_b(M2) * (M2 / 32), FDAS_K1B_MIN_
                                                                          const float2 *__restrict__ lo,
                                                                          const float2 *__restrict__ hi,
                                                                          float2 *__restrict__ X,
-                                                                         double *__restrict__ partial, int M1) {
+                                                                         double *__restrict__ partial, int M1,
+                                                                         unsigned int *__restrict__ ticket, int64_t nb,
+                                                                         double sigma2_fixed, double *__restrict__ sigma2_out,
+                                                                         float *__restrict__ scale_out) {
     constexpr int T = M2 / 32, C2 = k1_groups_b(M2), G = 2 * C2;
     constexpr int E = fft_smem_entries(M2) + K1_GPAD;
     extern __shared__ float2 smb[];       // G * E entries
@@ -131,18 +136,22 @@ __global__ void __launch_bounds__(2 * k1_groups_b(M2) * (M2 / 32), FDAS_K1B_MIN_
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
-}
-
-// sigma2 = (sum of partials, fixed order) / (Nb - 1) unless fixed; scale = sqrt(2 / sigma2).
-__global__ void k1_finalize(const double *__restrict__ partial, int n, int64_t nb, double sigma2_fixed,
-                            double *__restrict__ sigma2_out, float *__restrict__ scale_out) {
-    __shared__ double red[256];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += 256) acc += partial[i];
-    red[threadIdx.x] = acc;
+    // the last block to finish sums the partials in a fixed order: sigma2 = sum / (Nb - 1) unless
+    // fixed, scale = sqrt(2 / sigma2)
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
+    if (!last) return;                    // block-uniform
+    __threadfence();
+    double tot = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += G * T) tot += __ldcg(partial + i);
+    red[threadIdx.x] = tot;
+    __syncthreads();
+    for (int s = G * T / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
@@ -201,24 +210,26 @@ __global__ void __launch_bounds__(256) k1_local_norm(const float2 *__restrict__ 
 }
 
 template <int M1>
-cudaError_t run_pass_a(const Plan &p, const float2 *z, float2 *B, cudaStream_t st) {
+cudaError_t run_pass_a(const Plan &p, const float2 *z, float2 *B, unsigned int *ticket, cudaStream_t st) {
     constexpr int C1 = k1_groups_a(M1);
     const size_t smem = sizeof(float2) * C1 * (fft_smem_entries(M1) + K1_GPAD);
     auto kern = k1_pass_a<M1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<p.M2 / C1, C1 * (M1 / 32), smem, st>>>(z, p.d_tw, p.d_twn_lo, p.d_twn_hi, B, p.M2);
+    kern<<<p.M2 / C1, C1 * (M1 / 32), smem, st>>>(z, p.d_tw, p.d_twn_lo, p.d_twn_hi, B, p.M2, ticket);
     return cudaGetLastError();
 }
 
 template <int M2>
-cudaError_t run_pass_b(const Plan &p, const float2 *B, float2 *X, double *partial, cudaStream_t st) {
+cudaError_t run_pass_b(const Plan &p, const float2 *B, float2 *X, double *partial, unsigned int *ticket,
+                       double *sigma2, float *scale, cudaStream_t st) {
     constexpr int C2 = k1_groups_b(M2);
     const size_t smem = 2 * C2 * sizeof(float2) * (fft_smem_entries(M2) + K1_GPAD);
     auto kern = k1_pass_b<M2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<p.M1 / (2 * C2), 2 * C2 * (M2 / 32), smem, st>>>(B, p.d_tw, p.d_twn_lo, p.d_twn_hi, X, partial, p.M1);
+    kern<<<p.M1 / (2 * C2), 2 * C2 * (M2 / 32), smem, st>>>(B, p.d_tw, p.d_twn_lo, p.d_twn_hi, X, partial, p.M1,
+                                                              ticket, p.nb, p.cfg.sigma2, sigma2, scale);
     return cudaGetLastError();
 }
 
@@ -231,35 +242,35 @@ cudaError_t launch_spectrum(const Plan &p, const float *d_series, char *ws, cuda
     double *partial = reinterpret_cast<double *>(ws + p.ws_part);
     double *sigma2 = reinterpret_cast<double *>(ws + p.ws_scale);
     float *scale = reinterpret_cast<float *>(ws + p.ws_scale + 8);
+    unsigned int *ticket = reinterpret_cast<unsigned int *>(ws + p.ws_scale + 12);
     p.prof.begin(FDAS_STAGE_SPECTRUM, st);
-    p.prof.launches += 3;
+    p.prof.launches += 2;
     cudaError_t e = cudaErrorInvalidValue;
     switch (p.M1) {
-        case 32: e = run_pass_a<32>(p, z, B, st); break;
-        case 64: e = run_pass_a<64>(p, z, B, st); break;
-        case 128: e = run_pass_a<128>(p, z, B, st); break;
-        case 256: e = run_pass_a<256>(p, z, B, st); break;
-        case 512: e = run_pass_a<512>(p, z, B, st); break;
-        case 1024: e = run_pass_a<1024>(p, z, B, st); break;
-        case 2048: e = run_pass_a<2048>(p, z, B, st); break;
-        case 4096: e = run_pass_a<4096>(p, z, B, st); break;
-        case 8192: e = run_pass_a<8192>(p, z, B, st); break;
+        case 32: e = run_pass_a<32>(p, z, B, ticket, st); break;
+        case 64: e = run_pass_a<64>(p, z, B, ticket, st); break;
+        case 128: e = run_pass_a<128>(p, z, B, ticket, st); break;
+        case 256: e = run_pass_a<256>(p, z, B, ticket, st); break;
+        case 512: e = run_pass_a<512>(p, z, B, ticket, st); break;
+        case 1024: e = run_pass_a<1024>(p, z, B, ticket, st); break;
+        case 2048: e = run_pass_a<2048>(p, z, B, ticket, st); break;
+        case 4096: e = run_pass_a<4096>(p, z, B, ticket, st); break;
+        case 8192: e = run_pass_a<8192>(p, z, B, ticket, st); break;
     }
     if (e != cudaSuccess) return e;
     e = cudaErrorInvalidValue;
     switch (p.M2) {
-        case 32: e = run_pass_b<32>(p, B, X, partial, st); break;
-        case 64: e = run_pass_b<64>(p, B, X, partial, st); break;
-        case 128: e = run_pass_b<128>(p, B, X, partial, st); break;
-        case 256: e = run_pass_b<256>(p, B, X, partial, st); break;
-        case 512: e = run_pass_b<512>(p, B, X, partial, st); break;
-        case 1024: e = run_pass_b<1024>(p, B, X, partial, st); break;
-        case 2048: e = run_pass_b<2048>(p, B, X, partial, st); break;
-        case 4096: e = run_pass_b<4096>(p, B, X, partial, st); break;
-        case 8192: e = run_pass_b<8192>(p, B, X, partial, st); break;
+        case 32: e = run_pass_b<32>(p, B, X, partial, ticket, sigma2, scale, st); break;
+        case 64: e = run_pass_b<64>(p, B, X, partial, ticket, sigma2, scale, st); break;
+        case 128: e = run_pass_b<128>(p, B, X, partial, ticket, sigma2, scale, st); break;
+        case 256: e = run_pass_b<256>(p, B, X, partial, ticket, sigma2, scale, st); break;
+        case 512: e = run_pass_b<512>(p, B, X, partial, ticket, sigma2, scale, st); break;
+        case 1024: e = run_pass_b<1024>(p, B, X, partial, ticket, sigma2, scale, st); break;
+        case 2048: e = run_pass_b<2048>(p, B, X, partial, ticket, sigma2, scale, st); break;
+        case 4096: e = run_pass_b<4096>(p, B, X, partial, ticket, sigma2, scale, st); break;
+        case 8192: e = run_pass_b<8192>(p, B, X, partial, ticket, sigma2, scale, st); break;
     }
     if (e != cudaSuccess) return e;
-    k1_finalize<<<1, 256, 0, st>>>(partial, p.M1 / (2 * k1_groups_b(p.M2)), p.nb, p.cfg.sigma2, sigma2, scale);
     p.prof.end(FDAS_STAGE_SPECTRUM, st);
     return cudaGetLastError();
 }

@@ -23,7 +23,8 @@
 // are numbered in that order, and
 //   pass A (k4_level1 over the plane, k4_levels over level 2's region) writes each unit's peak
 //     count and, when non-zero, its CB-bit mask;
-//   pass B (k4_scan_blocks, k4_scan_top) turns the counts into exclusive offsets + total;
+//   pass B (k4_scan_blocks; its last block scans the block sums) turns the counts into exclusive
+//     offsets + total;
 //   pass C (k4_emit, one warp per unit, empty units skipped) recomputes S_H at the few
 //   marked cells and writes the records at offset + rank.
 #include <cmath>
@@ -338,9 +339,11 @@ template <typename E>
 __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_L1_MIN_BLOCKS) k4_level1(const E *__restrict__ plane, int64_t nb, int zmax,
                                                               int K, LevelDesc d, int chunks1,
                                                               int32_t *__restrict__ unit_count,
-                                                              uint32_t *__restrict__ unit_mask) {
+                                                              uint32_t *__restrict__ unit_mask,
+                                                              unsigned int *__restrict__ ticket) {
     constexpr int CPW1 = Fmt<E>::EPV == 8 ? 4 : 2;
     const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ticket = 0;   // k4_scan_blocks' count
     const int i = blockIdx.y;
     const int c0 = (blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * CPW1;
     if (c0 >= chunks1) return;                       // warp-uniform
@@ -378,8 +381,10 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32) k4_level1_marked(const E *_
                                                                     int K, LevelDesc d, int64_t n_units1,
                                                                     const uint8_t *__restrict__ flags,
                                                                     int32_t *__restrict__ unit_count,
-                                                                    uint32_t *__restrict__ unit_mask) {
+                                                                    uint32_t *__restrict__ unit_mask,
+                                                                    unsigned int *__restrict__ ticket) {
     const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;                      // k4_scan_blocks' count
     const int64_t u0 = ((int64_t)blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * 32;
     if (u0 >= n_units1) return;                      // warp-uniform
     const int64_t u = u0 + lane;
@@ -548,9 +553,45 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4a_lev
     anch_unit<E>(plane, nb, zmax, K, lt.lev[4], 16, i, c, rb, s, unit_count, unit_mask);
 }
 
+// Second level (the last block of k4_scan_blocks, 1024 threads, fixed order): block offsets in
+// place, total count, overflow flag.
+__device__ __forceinline__ void scan_top(int64_t *__restrict__ block_sum, int64_t nblocks, int32_t *__restrict__ npeaks,
+                                         int max_peaks, int32_t *__restrict__ status) {
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t b0 = 0; b0 < nblocks; b0 += 1024) {
+        const int64_t b = b0 + threadIdx.x;
+        const int64_t v = (b < nblocks) ? __ldcg(block_sum + b) : 0;
+        int64_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        int64_t before = carry;
+        for (int w = 0; w < warp; w++) before += warp_tot[w];
+        if (b < nblocks) block_sum[b] = before + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int64_t total = carry;
+        *npeaks = (int32_t)(total < 0x7fffffff ? total : 0x7fffffff);
+        if (total > max_peaks) atomicOr(status, FDAS_DEV_PEAK_OVERFLOW);
+    }
+}
+
 // First-level scan: exclusive prefix of the counts inside each block of SCAN_BLOCK units.
 __global__ void __launch_bounds__(1024) k4_scan_blocks(const int32_t *__restrict__ cnt, int64_t n,
-                                                       int32_t *__restrict__ off, int64_t *__restrict__ block_sum) {
+                                                       int32_t *__restrict__ off, int64_t *__restrict__ block_sum,
+                                                       unsigned int *__restrict__ ticket, int32_t *__restrict__ npeaks,
+                                                       int max_peaks, int32_t *__restrict__ status) {
     __shared__ int32_t warp_tot[32];
     const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x * 4;
     int32_t v[4];
@@ -574,7 +615,10 @@ __global__ void __launch_bounds__(1024) k4_scan_blocks(const int32_t *__restrict
             if (lane >= o) ti += y;
         }
         warp_tot[lane] = ti - t;                 // exclusive warp offsets
-        if (lane == 31) block_sum[blockIdx.x] = ti;
+        if (lane == 31) {
+            block_sum[blockIdx.x] = ti;
+            __threadfence();                             // before this block's ticket below
+        }
     }
     __syncthreads();
     int32_t run = warp_tot[warp] + incl - sum;
@@ -583,40 +627,16 @@ __global__ void __launch_bounds__(1024) k4_scan_blocks(const int32_t *__restrict
         if (base + k < n) off[base + k] = run;
         run += v[k];
     }
-}
-
-// Second level (one CTA, fixed order): block offsets in place, total count, overflow flag.
-__global__ void __launch_bounds__(1024) k4_scan_top(int64_t *__restrict__ block_sum, int64_t nblocks,
-                                                    int32_t *__restrict__ npeaks, int max_peaks,
-                                                    int32_t *__restrict__ status) {
-    __shared__ int64_t warp_tot[32];
-    __shared__ int64_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t b0 = 0; b0 < nblocks; b0 += 1024) {
-        const int64_t b = b0 + threadIdx.x;
-        const int64_t v = (b < nblocks) ? block_sum[b] : 0;
-        int64_t incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) warp_tot[warp] = incl;
-        __syncthreads();
-        int64_t before = carry;
-        for (int w = 0; w < warp; w++) before += warp_tot[w];
-        if (b < nblocks) block_sum[b] = before + incl - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = before + incl;
-        __syncthreads();
-    }
+    // the last block to finish scans the block sums (the second level)
+    __shared__ bool last;
     if (threadIdx.x == 0) {
-        const int64_t total = carry;
-        *npeaks = (int32_t)(total < 0x7fffffff ? total : 0x7fffffff);
-        if (total > max_peaks) atomicOr(status, FDAS_DEV_PEAK_OVERFLOW);
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!last) return;                               // block-uniform
+    __threadfence();
+    scan_top(block_sum, (int64_t)gridDim.x, npeaks, max_peaks, status);
 }
 
 struct UnitRef {
@@ -707,18 +727,19 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
                            (unsigned)(lt.n_levels > 1 ? lt.lev[1].rows : 0));
     const int64_t n_units = p.n_units;
     const int64_t n_blocks = (n_units + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    unsigned int *ticket = reinterpret_cast<unsigned int *>(block_off + n_blocks);   // zeroed by level 1
     p.prof.begin(FDAS_STAGE_PEAKS, st);
-    p.prof.launches += lt.n_levels > 1 ? 5 : 4;
+    p.prof.launches += lt.n_levels > 1 ? 4 : 3;
     p.prof.begin(PROF_PEAKS_LEVEL1, st);
     if (l1flag) {
         const int64_t n1 = (int64_t)p.K * chunks1;
         const int64_t blocks = (n1 + DETECT_WARPS * 32 - 1) / (DETECT_WARPS * 32);
         k4_level1_marked<E><<<(unsigned)blocks, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt.lev[0], n1,
-                                                                          l1flag, unit_count, unit_mask);
+                                                                          l1flag, unit_count, unit_mask, ticket);
         p.prof.level1_fused++;
     } else {
         k4_level1<E><<<level1_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt.lev[0], (int)chunks1,
-                                                                 unit_count, unit_mask);
+                                                                 unit_count, unit_mask, ticket);
     }
     p.prof.end(PROF_PEAKS_LEVEL1, st);
     if (lt.n_levels > 1 && lt.anchored) {
@@ -733,8 +754,8 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
                                                                  unit_count, unit_mask);
         p.prof.end(PROF_PEAKS_LEVELS, st);
     }
-    k4_scan_blocks<<<(unsigned)n_blocks, 1024, 0, st>>>(unit_count, n_units, unit_off, block_off);
-    k4_scan_top<<<1, 1024, 0, st>>>(block_off, n_blocks, npeaks, p.cfg.max_peaks, p.d_status);
+    k4_scan_blocks<<<(unsigned)n_blocks, 1024, 0, st>>>(unit_count, n_units, unit_off, block_off, ticket, npeaks,
+                                                       p.cfg.max_peaks, p.d_status);
     const int64_t emit_blocks = std::min<int64_t>((n_units + 255) / 256, 152 * 8);
     k4_emit<E><<<(unsigned)emit_blocks, 256, 0, st>>>(plane, p.nb, p.cfg.zmax, lt, n_units, unit_count, unit_off,
                                                        block_off, unit_mask, peaks, p.cfg.max_peaks, series);
