@@ -29,6 +29,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -111,7 +112,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # the raw samples go to $FDAS_CLOCKS_CSV when set (to keep them), else to a temporary file
+        self.path = os.environ.get("FDAS_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
+                                                                       f"fdas_clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def start(self):
         try:
