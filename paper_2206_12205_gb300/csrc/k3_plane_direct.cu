@@ -220,10 +220,12 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct(const uint32_
 }
 
 // ---------------------------------------------------------------------------------------
-// FP8 ablation of the direct form (FDAS_FP8_DIRECT): E4M3 operands (3 mantissa bits) with
-// power-of-two scales -- per 1024-bin tile for the spectrum (largest |Re| or |Im| of the tile's
-// window brought into [224, 448]) and per template for the taps -- kind::f8f6f4 MMAs with FP32
-// accumulation, and an FP32 plane times 1 / (s_t sigma_z)^2.
+// FP8 ablation of the direct form (FDAS_FP8_DIRECT): the paper argues BF16 suffices for the
+// correlation (Sec. 3, judged by Eq. perc_diff); this path takes one step further down, to E4M3
+// operands (3 mantissa bits) with power-of-two scales -- per 1024-bin tile for the spectrum
+// (largest |Re| or |Im| of the tile's window brought into [224, 448]) and per template for the
+// taps -- kind::f8f6f4 MMAs with FP32 accumulation, and an FP32 plane times 1 / (s_t sigma_z)^2.
+// Inside a search the epilogue also marks the 512-bin units holding a power above thr[0].
 //
 // A complex E4M3 pair is 2 bytes, so the Hankel rows 16 bytes apart are r = r0 + 8 a + b: a tile
 // is 1024 bins in 8 sets b of 128 rows, and keeps 8 shifted copies of its window.  A lane of the
