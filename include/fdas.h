@@ -82,8 +82,9 @@ typedef enum {
                                 power of two per 1024-bin tile and each template by its own,
                                 so that the largest |Re| or |Im| lands in [224, 448]; FP32
                                 accumulation; FP32 plane with the scales divided out.  Needs
-                                2 ceil(K/8) 8 <= 256 and taps % 16 == 0, else
-                                FDAS_E_UNSUPPORTED                                            */
+                                taps % 16 == 0 and the taps image (ceil(K/32) x 64 rows x 2
+                                taps bytes) plus the windows in one CTA's shared memory (taps
+                                <= 256 at K = 85), else FDAS_E_UNSUPPORTED                     */
 } fdas_precision;
 
 /* Device status bits (fdas_device_status). */
