@@ -84,7 +84,7 @@ typedef enum {
                                 accumulation; FP32 plane with the scales divided out.  Needs
                                 taps % 16 == 0 and the taps image (ceil(K/32) x 64 rows x 2
                                 taps bytes) plus the windows in one CTA's shared memory (taps
-                                <= 256 at K = 85), else FDAS_E_UNSUPPORTED                     */
+                                <= 416 at K = 85), else FDAS_E_UNSUPPORTED                     */
 } fdas_precision;
 
 /* Device status bits (fdas_device_status). */
