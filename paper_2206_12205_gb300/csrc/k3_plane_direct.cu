@@ -193,16 +193,23 @@ __global__ void __launch_bounds__(D_WARPS * 32, 1) k3_plane_direct(const uint32_
                         d_arrive(&bars->d_free[sl]);
                     }
                     if (in) {
+                        float vs[4];
 #pragma unroll
                         for (int e = 0; e < 4; e++) {
                             const int z = z0 + e;
+                            vs[e] = -INFINITY;
                             if (z < K) {
                                 const float xr = __uint_as_float(re[e]), xi = __uint_as_float(im[e]);
                                 const __nv_bfloat16 v = __float2bfloat16_rn(xr * xr + xi * xi);
                                 plane[(int64_t)z * nb + r] = v;
-                                // level-1 mark of the unit (z, r / 512) when the stored value is above thr1
-                                if (l1flag != nullptr && __bfloat162float(v) > thr1) l1flag[(int64_t)z * chunks1 + (r >> 9)] = 1;
+                                vs[e] = __bfloat162float(v);
                             }
+                        }
+                        // level-1 marks of the units (z, r / 512) whose stored value is above thr1 (rare)
+                        if (l1flag != nullptr && fmaxf(fmaxf(vs[0], vs[1]), fmaxf(vs[2], vs[3])) > thr1) {
+#pragma unroll
+                            for (int e = 0; e < 4; e++)
+                                if (vs[e] > thr1) l1flag[(int64_t)(z0 + e) * chunks1 + (r >> 9)] = 1;
                         }
                     }
                 }
