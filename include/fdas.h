@@ -24,16 +24,19 @@
  *     I(q, z) = int_0^1 exp(i pi (z u^2 - 2 q u)) du, scaled to unit norm (Sec. 3.3).
  *   - Plane: P[i][r] = | sum_q Xhat[r+q] conj(T_i(q)) |^2, r = 0..Nb-1, row-major [K][Nb]
  *     (r contiguous); Xhat is zero outside [0, Nb).  Element type is bfloat16 (the upper
- *     16 bits of the float) for FDAS_BF16 and float otherwise.
- *   - The tensor-core precisions (FDAS_BF16, FDAS_BF16_SPLIT, FDAS_FP16_SCALED) run their overlap-save with
- *     4096-bin segments whatever seg_len says (the plane does not depend on it) and accept
- *     at most 2048 taps.
+ *     16 bits of the float) for FDAS_BF16 and FDAS_BF16_DIRECT, float otherwise.
+ *   - The tensor-core DFT precisions (FDAS_BF16, FDAS_BF16_SPLIT, FDAS_FP16_SCALED) run their
+ *     overlap-save with 4096-bin segments whatever seg_len says (the plane does not depend
+ *     on it) and accept at most 2048 taps.
  *   - All device pointers are CUDA device addresses on the current device; the caller
  *     owns them.  Alignment: series and spectra 8 bytes, plane 16 bytes, workspace 256
  *     bytes, peak list and counts 4 bytes (cudaMalloc'd and torch buffers satisfy all of
- *     these); a misaligned pointer is rejected with FDAS_E_INVALID.  Streams are cudaStream_t values passed as void* (NULL = default
- *     stream).  Calls are asynchronous unless stated.  Nothing inside fdas_spectrum,
- *     fdas_plane, fdas_peaks or fdas_search allocates memory.
+ *     these); a misaligned pointer is rejected with FDAS_E_INVALID.  Streams are
+ *     cudaStream_t values passed as void* (NULL = default stream).  Calls are asynchronous
+ *     unless stated.  Nothing inside fdas_spectrum, fdas_plane, fdas_peaks or fdas_search
+ *     allocates memory.
+ *   - A workspace serves one call at a time: it holds the call's spectrum, segment spectra,
+ *     peak units and counters, so calls that share one must be ordered (one stream).
  *   - Errors are returned as fdas_status; nothing is thrown across the ABI.  Device-side
  *     conditions (peak-list overflow, a wait that ran out) are recorded in a sticky
  *     per-plan status word read by fdas_device_status.
