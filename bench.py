@@ -545,7 +545,7 @@ def batch_bench(dev, stream, reps: int = 5, warmup: int = 2, loop_reps: int = 2)
 
 
 # ------------------------------------------------------------------------------ sensitivity sweep
-SENS_FORMS = ("fp32", "bf16", "bf16_split", "fp16_scaled")
+SENS_FORMS = ("fp32", "bf16", "bf16_split", "fp16_scaled", "bf16_direct", "fp8_direct")
 SENS_BANDS = 8
 
 
