@@ -39,7 +39,7 @@ constexpr int CB = PEAK_CHUNK;           // bins per unit (a warp's chunk)
 constexpr int LB = CB / 32;              // bins per lane (16)
 constexpr int WORDS = CB / 32;           // mask words per unit
 constexpr int SCAN_BLOCK = PEAK_SCAN_BLOCK;
-constexpr int DETECT_WARPS = 8;          // warps per k4_level1 / k4_levels block
+constexpr int DETECT_WARPS = 4;          // warps per k4_level1 / k4_levels block
 #ifndef FDAS_K4_CPW
 #define FDAS_K4_CPW 1                    // chunks per k4_levels warp
 #endif
@@ -49,7 +49,7 @@ static_assert((CPW & (CPW - 1)) == 0 && CPW <= 2, "chunks per warp: 1 or 2 (chun
 #define FDAS_K4_L1_MIN_BLOCKS 2          // resident k4_level1 blocks per SM the registers must allow
 #endif
 #ifndef FDAS_K4_MIN_BLOCKS
-#define FDAS_K4_MIN_BLOCKS 2             // resident k4_levels blocks per SM the registers must allow
+#define FDAS_K4_MIN_BLOCKS 4             // resident k4_levels blocks per SM the registers must allow
 #endif
 
 static_assert(LB == 16, "a lane owns 16 bins: two BF16 or four FP32 16-byte vectors");
