@@ -18,7 +18,9 @@
  *   - Nb = N/2 frequency bins (the Nyquist bin is dropped), bin 0 (DC) is set to zero.
  *   - Spectrum normalisation: Xhat = X * sqrt(2/sigma2), sigma2 = mean |X_k|^2 over
  *     k = 1..Nb-1 (or the fixed value in fdas_config.sigma2), so that noise-only plane
- *     cells follow chi^2 with 2 degrees of freedom (Sec. 5.1).
+ *     cells follow chi^2 with 2 degrees of freedom (Sec. 5.1).  A series with no power
+ *     outside DC (all zero or constant: sigma2 = 0) normalises to Xhat = 0, a zero plane
+ *     and no candidates.
  *   - Templates: K = zmax + 1 rows at z_i = -zmax + 2i (z = fdot T^2 in bins, Eq. fdotz);
  *     m taps at q = -m/2 .. m/2-1 of the response of a constant-fdot sinusoid
  *     I(q, z) = int_0^1 exp(i pi (z u^2 - 2 q u)) du, scaled to unit norm (Sec. 3.3).

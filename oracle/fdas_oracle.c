@@ -103,6 +103,9 @@ int orc_fft(cplx *a, int64_t n, int sign)
 /*   X_0 := 0 (DC removed, Sec. 3.2)                                                     */
 /*   sigma2 = mean_{k=1..nb-1} |X_k|^2, or the caller's fixed value if sigma2_fixed > 0    */
 /*   Xhat_k = X_k * sqrt(2 / sigma2): white noise then has E|Xhat|^2 = 2 (chi^2, 2 dof)   */
+/*   sigma2 = 0 (a series with no power outside DC: zero or constant): Xhat = 0, so the    */
+/*   plane is zero and nothing is detected, the same choice the local variant makes for a  */
+/*   block whose median power is 0.                                                        */
 /* xhat receives nb complex values.  Returns 0, or -1 on bad n / allocation failure.      */
 /* ------------------------------------------------------------------------------------ */
 int orc_spectrum(const float *x, int64_t n, double sigma2_fixed, cplx *xhat, double *sigma2_out)
@@ -120,7 +123,7 @@ int orc_spectrum(const float *x, int64_t n, double sigma2_fixed, cplx *xhat, dou
         for (int64_t k = 1; k < nb; k++) acc += creal(a[k]) * creal(a[k]) + cimag(a[k]) * cimag(a[k]);
         sigma2 = acc / (double)(nb - 1);
     }
-    double scale = sqrt(2.0 / sigma2);
+    double scale = sigma2 > 0.0 ? sqrt(2.0 / sigma2) : 0.0;
     for (int64_t k = 0; k < nb; k++) xhat[k] = a[k] * scale;
     if (sigma2_out) *sigma2_out = sigma2;
     free(a);

@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(2 * k1_groups_b(M2) * (M2 / 32), FDAS_K1B_MIN_
         __syncthreads();
     }
     // the last block to finish sums the partials in a fixed order: sigma2 = sum / (Nb - 1) unless
-    // fixed, scale = sqrt(2 / sigma2)
+    // fixed, scale = sqrt(2 / sigma2); a series with no power outside DC (sigma2 = 0) gets scale 0,
+    // a zero spectrum and plane, as the local variant does for a block of median power 0
     __shared__ bool last;
     if (threadIdx.x == 0) {
         partial[blockIdx.x] = red[0];
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(2 * k1_groups_b(M2) * (M2 / 32), FDAS_K1B_MIN_
     if (threadIdx.x == 0) {
         const double sigma2 = sigma2_fixed > 0.0 ? sigma2_fixed : red[0] / (double)(nb - 1);
         *sigma2_out = sigma2;
-        *scale_out = (float)sqrt(2.0 / sigma2);
+        *scale_out = sigma2 > 0.0 ? (float)sqrt(2.0 / sigma2) : 0.f;
     }
 }
 

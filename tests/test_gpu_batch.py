@@ -68,6 +68,27 @@ def test_batch_equals_series_searched_alone(precision):
     assert fd.fdas_batch_device_status(bs.batch) == 0
 
 
+def test_batch_zero_series_reports_nothing():
+    """A series of zeros inside a batch (sigma2 = 0) yields an empty list and leaves every other
+    series' list unchanged."""
+    wl = _small_batch(n_series=6, seed=81)
+    bs = fb.BatchSearch(_cfgs(wl, "bf16"))
+    dev = torch.from_numpy(wl.packed).cuda()
+    bs.search(dev)
+    torch.cuda.synchronize()
+    before = [a.copy() for a in bs.peak_lists()]
+    z = 3
+    dev[int(wl.offsets[z]): int(wl.offsets[z]) + wl.series[z].n] = 0.0
+    bs.search(dev)
+    torch.cuda.synchronize()
+    after = bs.peak_lists()
+    assert len(before[z]) > 0 and len(after[z]) == 0
+    for i in range(len(wl.series)):
+        if i != z:
+            _peaks_equal(after[i], before[i])
+    assert fd.fdas_batch_device_status(bs.batch) == 0
+
+
 def test_batch_fp32_against_oracle():
     """FP32 batch series against the oracle's FP64 search of the same series: the same peaks
     (level, row, bin), powers within the FP32 plane tolerance (1e-5 of max(P, 2) per summed term),

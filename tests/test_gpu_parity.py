@@ -83,6 +83,24 @@ def test_spectrum_fixed_sigma2():
     assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "bf16_split", "fp16_scaled", "bf16_direct", "fp8_direct"])
+def test_zero_series_gives_zero_plane(precision):
+    """A series with no power outside DC: sigma2 = 0, and, as in the oracle, the normalised
+    spectrum, the plane and the candidate list are empty (no 0 * inf) on every path."""
+    n = 1 << 16
+    s = _search(n, 16, 64, 8192, precision=precision, max_harm=16, thr=(0.0,) * 5, max_peaks=64)
+    x = torch.zeros(n, dtype=torch.float32, device="cuda")
+    xh = s.spectrum(x)
+    torch.cuda.synchronize()
+    assert s.sigma2.item() == 0.0 and not bool(xh.any())
+    s.plane.fill_(1.0)
+    s.search(x)
+    torch.cuda.synchronize()
+    assert fd.fdas_device_status(s.plan) == 0
+    assert not bool(s.plane.float().any())
+    assert int(s.npeaks.item()) == 0
+
+
 # ------------------------------------------------------------------ plane (K2 + K3)
 @pytest.mark.parametrize("n,zmax,m,S", [
     (1 << 16, 16, 64, 1024),      # the plain FP32 workload's shape

@@ -71,6 +71,29 @@ def test_spectrum_fixed_sigma2(oracle_mod):
     assert abs(abs(xhat[100]) - 512.0 * math.sqrt(2.0 / 1024.0)) <= 1e-3
 
 
+def test_spectrum_without_power_outside_dc(oracle_mod):
+    """A zero or constant series has X_k = 0 for every k >= 1 (the DFT of a constant is a delta
+    at DC), so sigma2 = 0; the normalisation then gives the zero spectrum, a zero plane and no
+    candidates (no 0 * inf).  A constant's DFT is exactly zero off DC in FP64 butterflies."""
+    n, zmax, m = 1024, 6, 32
+    for c in (0.0, 3.25, -7.0):
+        x = np.full(n, c, dtype=np.float32)
+        xhat, s2 = oracle_mod.spectrum(x)
+        assert s2 == 0.0 and not np.any(xhat)
+        pl = oracle_mod.plane(xhat, zmax, m)
+        assert pl.shape == (zmax + 1, n // 2) and not np.any(pl)
+        rec, cnt = oracle_mod.peaks_f64(pl, zmax, 16, (0.0,) * 5)
+        assert cnt == 0 and len(rec) == 0
+    # a fixed sigma2 still applies; the local variant's zero-median blocks agree
+    xhat, s2 = oracle_mod.spectrum(np.zeros(n, dtype=np.float32), sigma2=5.0)
+    assert s2 == 5.0 and not np.any(xhat)
+    assert not np.any(oracle_mod.spectrum_local(np.full(n, 2.0, dtype=np.float32), 64))
+    # the smallest non-zero case is normalised as usual: one tone's bin carries all the power
+    x = synth.chirp(n, 1.0, 37.0, 0.0).astype(np.float32)
+    xhat, s2 = oracle_mod.spectrum(x)
+    assert abs(np.sum(np.abs(xhat[1:]) ** 2) - 2.0 * (n // 2 - 1)) <= 1e-9 * n
+
+
 # ---------------------------------------------------------------- Fresnel and response
 def test_fresnel_matches_scipy(oracle_mod):
     x = np.concatenate([np.linspace(-12.0, 12.0, 4801), np.linspace(12.0, 600.0, 2001),
