@@ -228,6 +228,7 @@ fdas_status fdas_make_templates(fdas_plan_t plan, void *stream) {
         alloc((void **)&p->d_dsig, sizeof(float) * 32 * (size_t)groups);
     }
     alloc((void **)&p->d_status, sizeof(int32_t));
+    if (e == cudaSuccess) e = fdas::upload_levels_order(*p);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = fdas::launch_make_templates(*p, st);
     if (e == cudaSuccess && uses_tensor_path(p)) e = fdas::launch_prepare_bf16(*p, st);
@@ -477,6 +478,7 @@ void fdas_destroy(fdas_plan_t plan) {
         cudaFree(p->d_tcTw);
         cudaFree(p->d_dimg);
         cudaFree(p->d_dsig);
+        cudaFree(p->d_k4order);
         cudaFree(p->d_status);
     }
     for (int s = 0; s < fdas::PROF_STAGES; s++)

@@ -334,6 +334,8 @@ fdas_status fdas_batch_make_templates(fdas_batch_t b, void *stream) {
         p->d_tcFh = l->d_tcFh;
         p->d_dimg = l->d_dimg;
         p->d_dsig = l->d_dsig;
+        p->d_k4order = l->d_k4order;
+        p->k4order_n = l->k4order_n;
         p->borrowed = true;
         e = cudaMalloc((void **)&p->d_status, sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);

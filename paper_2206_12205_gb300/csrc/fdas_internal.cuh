@@ -83,6 +83,8 @@ struct Plan {
     void *d_dimg;          // direct paths: conj(taps) real-ified, K-major operand image (BF16 or E4M3)
     float *d_dsig;         // FP8 direct path: 1 / sigma_z^2 per template (the taps' scales), 32 per group
     float2 *d_tcTw;        // W_4096^{n2 k1}, [k1][n2] (32 KB)
+    uint32_t *d_k4order;   // k4_levels block order over level 2's region: row << 16 | chunk group, by z / r
+    int64_t k4order_n;     // its length (rows x chunk groups)
     int32_t *d_status;     // sticky device status word
     bool templates_ready;
     bool borrowed;         // template bank and tables belong to another plan (a batch's group leader)
@@ -156,6 +158,8 @@ cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale,
                              cudaStream_t st, uint8_t *l1flag = nullptr);
 // l1flag: the unit marks of the plane kernel that wrote d_plane (level 1 then visits only the
 // marked units), or NULL for the full level-1 pass over the plane.
+// Builds and uploads p.d_k4order (host sort at template time; synchronous copy).
+cudaError_t upload_levels_order(Plan &p);
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
                          fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st,
                          const uint8_t *l1flag = nullptr);

@@ -27,7 +27,9 @@
 //     offsets + total;
 //   pass C (k4_emit, one warp per unit, empty units skipped) recomputes S_H at the few
 //   marked cells and writes the records at offset + rank.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "fdas_internal.cuh"
 
@@ -409,16 +411,20 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32) k4_level1_marked(const E *_
 }
 
 // Levels 2 .. 16 over level 2's region (rows i_lo .. i_lo + rows - 1 of level 2, chunks up to its
-// rmax): grid (ceil(chunks2 / (DETECT_WARPS * CPW)), rows2); each warp re-reads S_1 of CPW chunks
-// (interleaved bins, see add_harmonic) and carries the running sums through the levels in registers.
+// rmax): one block per (row, group of DETECT_WARPS * CPW chunks), taken in the ray order of
+// upload_levels_order (order[blockIdx.x]); each warp re-reads S_1 of CPW chunks (interleaved
+// bins, see add_harmonic) and carries the running sums through the levels in registers.
 template <typename E>
 __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_levels(const E *__restrict__ plane, int64_t nb, int zmax, int K,
                                                               LevelTable lt, int chunks2,
+                                                              const uint32_t *__restrict__ order,
                                                               int32_t *__restrict__ unit_count,
                                                               uint32_t *__restrict__ unit_mask) {
     const int lane = threadIdx.x & 31;
-    const int i = lt.lev[1].i_lo + blockIdx.y;
-    const int c0 = (blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * CPW;
+    const uint32_t o = __ldg(order + blockIdx.x);    // (row in the region) << 16 | chunk group
+    if ((int)(o >> 16) >= lt.lev[1].rows) return;    // block-uniform
+    const int i = lt.lev[1].i_lo + (int)(o >> 16);
+    const int c0 = ((int)(o & 0xffffu) * DETECT_WARPS + (threadIdx.x >> 5)) * CPW;
     if (c0 >= chunks2) return;                       // warp-uniform
     const int z = -zmax + 2 * i;
     const E *row = plane + (int64_t)i * nb;
@@ -723,8 +729,9 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
     constexpr int CPW1 = Fmt<E>::EPV == 8 ? 4 : 2;
     const dim3 level1_grid((unsigned)((chunks1 + DETECT_WARPS * CPW1 - 1) / (DETECT_WARPS * CPW1)), (unsigned)p.K);
     const int64_t chunks2 = lt.n_levels > 1 ? lt.lev[1].chunks : 0;
-    const dim3 levels_grid((unsigned)((chunks2 + DETECT_WARPS * CPW - 1) / (DETECT_WARPS * CPW)),
-                           (unsigned)(lt.n_levels > 1 ? lt.lev[1].rows : 0));
+    if (lt.n_levels > 1 && !lt.anchored &&
+        (!p.d_k4order || p.k4order_n != (int64_t)lt.lev[1].rows * ((chunks2 + DETECT_WARPS * CPW - 1) / (DETECT_WARPS * CPW))))
+        return cudaErrorInvalidValue;                // the block order was not built for this region
     const int64_t n_units = p.n_units;
     const int64_t n_blocks = (n_units + SCAN_BLOCK - 1) / SCAN_BLOCK;
     unsigned int *ticket = reinterpret_cast<unsigned int *>(block_off + n_blocks);   // zeroed by level 1
@@ -750,8 +757,8 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
         p.prof.end(PROF_PEAKS_LEVELS, st);
     } else if (lt.n_levels > 1) {
         p.prof.begin(PROF_PEAKS_LEVELS, st);
-        k4_levels<E><<<levels_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2,
-                                                                 unit_count, unit_mask);
+        k4_levels<E><<<(unsigned)p.k4order_n, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2,
+                                                                          p.d_k4order, unit_count, unit_mask);
         p.prof.end(PROF_PEAKS_LEVELS, st);
     }
     k4_scan_blocks<<<(unsigned)n_blocks, 1024, 0, st>>>(unit_count, n_units, unit_off, block_off, ticket, npeaks,
@@ -765,6 +772,19 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
 
 }  // namespace
 
+// Level H's region: rows [i_lo, i_lo + rows) and bins r <= rmax.  Plain sums: the rows with
+// |H z| <= zmax and H r < Nb; anchored sums: the whole plane.
+static void level_region(const Plan &p, int H, bool anchored, LevelDesc &d) {
+    int zl = p.cfg.zmax / H;
+    zl -= zl & 1;                                   // largest even z with |H z| <= zmax
+    if (anchored) zl = p.cfg.zmax;
+    d.H = H;
+    d.i_lo = (p.cfg.zmax - zl) / 2;
+    d.rows = zl + 1;
+    d.rmax = anchored ? p.nb - 1 : (p.nb - 1) / H;
+    d.chunks = (d.rmax + 1 + PEAK_CHUNK - 1) / PEAK_CHUNK;
+}
+
 LevelTable make_levels(const Plan &p) {
     LevelTable lt{};
     int64_t unit0 = 0;
@@ -772,15 +792,8 @@ LevelTable make_levels(const Plan &p) {
     for (int l = 0; l < 5; l++) {
         const int H = 1 << l;
         if (H > p.cfg.max_harm) break;
-        int zl = p.cfg.zmax / H;
-        zl -= zl & 1;                               // largest even z with |H z| <= zmax
-        if (p.cfg.harm_mode == 1) zl = p.cfg.zmax;  // anchored at the highest harmonic: whole plane
         LevelDesc &d = lt.lev[n];
-        d.H = H;
-        d.i_lo = (p.cfg.zmax - zl) / 2;
-        d.rows = zl + 1;
-        d.rmax = p.cfg.harm_mode == 1 ? p.nb - 1 : (p.nb - 1) / H;
-        d.chunks = (d.rmax + 1 + PEAK_CHUNK - 1) / PEAK_CHUNK;
+        level_region(p, H, p.cfg.harm_mode == 1, d);
         d.unit0 = unit0;
         d.thr = p.cfg.thr[l];
         unit0 += (int64_t)d.rows * d.chunks;
@@ -789,6 +802,42 @@ LevelTable make_levels(const Plan &p) {
     lt.n_levels = n;
     lt.anchored = p.cfg.harm_mode == 1;
     return lt;
+}
+
+// The order in which k4_levels takes the (row, chunk group) blocks of level 2's region.  Cell
+// (r, z) gathers its harmonics at (h r, h z): on the ray from the origin through (r, z), where
+// every other cell of that ray gathers too, and the rest of each gathered sector belongs to
+// neighbouring rays.  Taking the blocks by increasing z / r (of the group's middle bin; ties by
+// row, then group) brings all reads of a plane sector into a short stretch of the kernel's
+// progress, so the sector comes from DRAM about once; row after row, the harmonic rows of rows
+// far apart were fetched again (about twice the bytes).  Built for level 2's region whatever
+// max_harm and harm_mode say, so that plans of one shape can share it.
+cudaError_t upload_levels_order(Plan &p) {
+    LevelDesc d{};
+    level_region(p, 2, false, d);
+    const int64_t per = DETECT_WARPS * CPW;           // chunks per block
+    const int64_t groups = (d.chunks + per - 1) / per;
+    if (d.rows >= (1 << 16) || groups >= (1 << 16)) return cudaErrorInvalidValue;
+    struct Item {
+        double key;
+        uint32_t code;
+    };
+    std::vector<Item> items;
+    items.reserve((size_t)(d.rows * groups));
+    for (int a = 0; a < d.rows; a++) {
+        const int z = -p.cfg.zmax + 2 * (d.i_lo + a);
+        for (int64_t g = 0; g < groups; g++)
+            items.push_back({(double)z / ((double)(g * per) + 0.5 * (double)per), ((uint32_t)a << 16) | (uint32_t)g});
+    }
+    std::sort(items.begin(), items.end(),
+              [](const Item &x, const Item &y) { return x.key < y.key || (x.key == y.key && x.code < y.code); });
+    std::vector<uint32_t> order(items.size());
+    for (size_t k = 0; k < items.size(); k++) order[k] = items[k].code;
+    p.k4order_n = (int64_t)order.size();
+    cudaError_t e = cudaMalloc((void **)&p.d_k4order, sizeof(uint32_t) * order.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p.d_k4order, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice);
+    return e;
 }
 
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws, fdas_peak *d_peaks,
