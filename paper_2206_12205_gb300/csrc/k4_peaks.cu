@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32) k4_level1_marked(const E *_
 }
 
 // Levels 2 .. 16 over level 2's region (rows i_lo .. i_lo + rows - 1 of level 2, chunks up to its
-// rmax): one block per (row, group of DETECT_WARPS * CPW chunks), taken in the ray order of
+// rmax): one block per (row, group of DETECT_WARPS * CPW chunks), taken in one of the orders of
 // upload_levels_order (order[blockIdx.x]); each warp re-reads S_1 of CPW chunks (interleaved
 // bins, see add_harmonic) and carries the running sums through the levels in registers.
 template <typename E>
@@ -757,8 +757,9 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
         p.prof.end(PROF_PEAKS_LEVELS, st);
     } else if (lt.n_levels > 1) {
         p.prof.begin(PROF_PEAKS_LEVELS, st);
+        const uint32_t *order = p.d_k4order + (sizeof(E) == 4 ? p.k4order_n : 0);   // FP32: by ray
         k4_levels<E><<<(unsigned)p.k4order_n, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2,
-                                                                          p.d_k4order, unit_count, unit_mask);
+                                                                          order, unit_count, unit_mask);
         p.prof.end(PROF_PEAKS_LEVELS, st);
     }
     k4_scan_blocks<<<(unsigned)n_blocks, 1024, 0, st>>>(unit_count, n_units, unit_off, block_off, ticket, npeaks,
@@ -804,14 +805,19 @@ LevelTable make_levels(const Plan &p) {
     return lt;
 }
 
-// The order in which k4_levels takes the (row, chunk group) blocks of level 2's region.  Cell
-// (r, z) gathers its harmonics at (h r, h z): on the ray from the origin through (r, z), where
-// every other cell of that ray gathers too, and the rest of each gathered sector belongs to
-// neighbouring rays.  Taking the blocks by increasing z / r (of the group's middle bin; ties by
-// row, then group) brings all reads of a plane sector into a short stretch of the kernel's
-// progress, so the sector comes from DRAM about once; row after row, the harmonic rows of rows
-// far apart were fetched again (about twice the bytes).  Built for level 2's region whatever
-// max_harm and harm_mode say, so that plans of one shape can share it.
+// Two orders in which k4_levels can take the (row, chunk group) blocks of level 2's region,
+// stored one after the other (k4order_n entries each):
+//   - row by row (groups in increasing order within a row): the blocks in flight stream one row
+//     and the matching span of its harmonic rows;
+//   - by ray: cell (r, z) gathers its harmonics at (h r, h z), on the ray from the origin through
+//     (r, z), where every other cell of that ray gathers too, and the rest of each gathered
+//     sector belongs to neighbouring rays.  Taking the blocks by increasing z / r (of the group's
+//     middle bin; ties by row, then group) brings all reads of a plane sector into a short
+//     stretch of the kernel's progress, so it comes from DRAM about once instead of about twice.
+// The FP32 plane (DRAM-bound row by row) takes the ray order, the BF16 plane, where the row
+// streams were faster than the ray order's scattered spans at half the bytes, takes the rows.
+// Built for level 2's region whatever max_harm and harm_mode say, so that plans of one shape
+// can share it.
 cudaError_t upload_levels_order(Plan &p) {
     LevelDesc d{};
     level_region(p, 2, false, d);
@@ -829,11 +835,13 @@ cudaError_t upload_levels_order(Plan &p) {
         for (int64_t g = 0; g < groups; g++)
             items.push_back({(double)z / ((double)(g * per) + 0.5 * (double)per), ((uint32_t)a << 16) | (uint32_t)g});
     }
+    const size_t n = items.size();
+    std::vector<uint32_t> order(2 * n);
+    for (size_t k = 0; k < n; k++) order[k] = items[k].code;          // row by row
     std::sort(items.begin(), items.end(),
               [](const Item &x, const Item &y) { return x.key < y.key || (x.key == y.key && x.code < y.code); });
-    std::vector<uint32_t> order(items.size());
-    for (size_t k = 0; k < items.size(); k++) order[k] = items[k].code;
-    p.k4order_n = (int64_t)order.size();
+    for (size_t k = 0; k < n; k++) order[n + k] = items[k].code;      // by ray
+    p.k4order_n = (int64_t)n;
     cudaError_t e = cudaMalloc((void **)&p.d_k4order, sizeof(uint32_t) * order.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(p.d_k4order, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice);
