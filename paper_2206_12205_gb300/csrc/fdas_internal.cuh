@@ -83,8 +83,8 @@ struct Plan {
     void *d_dimg;          // direct paths: conj(taps) real-ified, K-major operand image (BF16 or E4M3)
     float *d_dsig;         // FP8 direct path: 1 / sigma_z^2 per template (the taps' scales), 32 per group
     float2 *d_tcTw;        // W_4096^{n2 k1}, [k1][n2] (32 KB)
-    uint32_t *d_k4order;   // k4_levels block orders over level 2's region (row << 16 | chunk group): rows, then rays
-    int64_t k4order_n;     // the length of each (rows x chunk groups)
+    uint32_t *d_k4order;   // ray order of level 2's (row << 16 | chunk group) blocks for k4_levels_ordered
+    int64_t k4order_n;     // its length (rows x chunk groups)
     int32_t *d_status;     // sticky device status word
     bool templates_ready;
     bool borrowed;         // template bank and tables belong to another plan (a batch's group leader)

@@ -50,6 +50,9 @@ static_assert((CPW & (CPW - 1)) == 0 && CPW <= 2, "chunks per warp: 1 or 2 (chun
 #ifndef FDAS_K4_L1_MIN_BLOCKS
 #define FDAS_K4_L1_MIN_BLOCKS 2          // resident k4_level1 blocks per SM the registers must allow
 #endif
+#ifndef FDAS_K4_RAY_BF16
+#define FDAS_K4_RAY_BF16 1               // 1: the BF16 plane's levels in ray order too (the FP32 plane's always are)
+#endif
 #ifndef FDAS_K4_MIN_BLOCKS
 #define FDAS_K4_MIN_BLOCKS 4             // resident k4_levels blocks per SM the registers must allow
 #endif
@@ -410,22 +413,14 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32) k4_level1_marked(const E *_
     }
 }
 
-// Levels 2 .. 16 over level 2's region (rows i_lo .. i_lo + rows - 1 of level 2, chunks up to its
-// rmax): one block per (row, group of DETECT_WARPS * CPW chunks), taken in one of the orders of
-// upload_levels_order (order[blockIdx.x]); each warp re-reads S_1 of CPW chunks (interleaved
-// bins, see add_harmonic) and carries the running sums through the levels in registers.
+// Levels 2 .. 16 of one (row i, CPW chunks from c0) of level 2's region: each warp re-reads S_1
+// of its chunks (interleaved bins, see add_harmonic) and carries the running sums through the
+// levels in registers.
 template <typename E>
-__global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_levels(const E *__restrict__ plane, int64_t nb, int zmax, int K,
-                                                              LevelTable lt, int chunks2,
-                                                              const uint32_t *__restrict__ order,
-                                                              int32_t *__restrict__ unit_count,
-                                                              uint32_t *__restrict__ unit_mask) {
+__device__ __forceinline__ void levels_group(const E *__restrict__ plane, int64_t nb, int zmax, int K,
+                                             const LevelTable &lt, int chunks2, int i, int c0,
+                                             int32_t *__restrict__ unit_count, uint32_t *__restrict__ unit_mask) {
     const int lane = threadIdx.x & 31;
-    const uint32_t o = __ldg(order + blockIdx.x);    // (row in the region) << 16 | chunk group
-    if ((int)(o >> 16) >= lt.lev[1].rows) return;    // block-uniform
-    const int i = lt.lev[1].i_lo + (int)(o >> 16);
-    const int c0 = ((int)(o & 0xffffu) * DETECT_WARPS + (threadIdx.x >> 5)) * CPW;
-    if (c0 >= chunks2) return;                       // warp-uniform
     const int z = -zmax + 2 * i;
     const E *row = plane + (int64_t)i * nb;
     const E *row2 = plane + (int64_t)((2 * z + zmax) >> 1) * nb;      // harmonic 2
@@ -449,6 +444,40 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_leve
         if (c0 + c >= chunks2) break;
         detect_chunk<E>(plane, nb, zmax, K, lt, i, z, c0 + c, (int64_t)(c0 + c) * CB + lane, s2[c], unit_count,
                         unit_mask);
+    }
+}
+
+// Level 2's region row by row: grid (ceil(chunks2 / (DETECT_WARPS * CPW)), rows2), blocks of
+// DETECT_WARPS warps on consecutive chunks of one row.
+template <typename E>
+__global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_levels(const E *__restrict__ plane, int64_t nb, int zmax, int K,
+                                                              LevelTable lt, int chunks2,
+                                                              int32_t *__restrict__ unit_count,
+                                                              uint32_t *__restrict__ unit_mask) {
+    const int c0 = (blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * CPW;
+    if (c0 >= chunks2) return;                       // warp-uniform
+    levels_group<E>(plane, nb, zmax, K, lt, chunks2, lt.lev[1].i_lo + blockIdx.y, c0, unit_count, unit_mask);
+}
+
+// Level 2's region in the ray order of upload_levels_order: a persistent grid whose block b takes
+// the entries b, b + gridDim.x, ... of the order (so the blocks in flight keep to a short stretch
+// of it), each entry a (row << 16 | chunk group); the next entry's code is loaded while the
+// current one runs, which keeps the table's latency off the critical path.
+template <typename E>
+__global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_levels_ordered(const E *__restrict__ plane, int64_t nb, int zmax, int K,
+                                                                      LevelTable lt, int chunks2,
+                                                                      const uint32_t *__restrict__ order, int64_t n_order,
+                                                                      int32_t *__restrict__ unit_count,
+                                                                      uint32_t *__restrict__ unit_mask) {
+    int64_t idx = blockIdx.x;
+    uint32_t next = idx < n_order ? __ldg(order + idx) : 0u;
+    for (; idx < n_order; idx += gridDim.x) {
+        const uint32_t o = next;
+        if (idx + gridDim.x < n_order) next = __ldg(order + idx + gridDim.x);
+        if ((int)(o >> 16) >= lt.lev[1].rows) continue;                       // block-uniform
+        const int c0 = ((int)(o & 0xffffu) * DETECT_WARPS + (threadIdx.x >> 5)) * CPW;
+        if (c0 >= chunks2) continue;                                          // warp-uniform
+        levels_group<E>(plane, nb, zmax, K, lt, chunks2, lt.lev[1].i_lo + (int)(o >> 16), c0, unit_count, unit_mask);
     }
 }
 
@@ -729,6 +758,8 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
     constexpr int CPW1 = Fmt<E>::EPV == 8 ? 4 : 2;
     const dim3 level1_grid((unsigned)((chunks1 + DETECT_WARPS * CPW1 - 1) / (DETECT_WARPS * CPW1)), (unsigned)p.K);
     const int64_t chunks2 = lt.n_levels > 1 ? lt.lev[1].chunks : 0;
+    const dim3 levels_grid((unsigned)((chunks2 + DETECT_WARPS * CPW - 1) / (DETECT_WARPS * CPW)),
+                           (unsigned)(lt.n_levels > 1 ? lt.lev[1].rows : 0));
     if (lt.n_levels > 1 && !lt.anchored &&
         (!p.d_k4order || p.k4order_n != (int64_t)lt.lev[1].rows * ((chunks2 + DETECT_WARPS * CPW - 1) / (DETECT_WARPS * CPW))))
         return cudaErrorInvalidValue;                // the block order was not built for this region
@@ -757,9 +788,17 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
         p.prof.end(PROF_PEAKS_LEVELS, st);
     } else if (lt.n_levels > 1) {
         p.prof.begin(PROF_PEAKS_LEVELS, st);
-        const uint32_t *order = p.d_k4order + (sizeof(E) == 4 ? p.k4order_n : 0);   // FP32: by ray
-        k4_levels<E><<<(unsigned)p.k4order_n, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2,
-                                                                          order, unit_count, unit_mask);
+        if (sizeof(E) == 4 || FDAS_K4_RAY_BF16) {
+            int sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
+            const int64_t blocks = std::min<int64_t>(p.k4order_n, (int64_t)std::max(sms, 1) * FDAS_K4_MIN_BLOCKS);
+            k4_levels_ordered<E><<<(unsigned)blocks, DETECT_WARPS * 32, 0, st>>>(
+                plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2, p.d_k4order, p.k4order_n, unit_count,
+                unit_mask);
+        } else {
+            k4_levels<E><<<levels_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2,
+                                                                     unit_count, unit_mask);
+        }
         p.prof.end(PROF_PEAKS_LEVELS, st);
     }
     k4_scan_blocks<<<(unsigned)n_blocks, 1024, 0, st>>>(unit_count, n_units, unit_off, block_off, ticket, npeaks,
@@ -805,19 +844,14 @@ LevelTable make_levels(const Plan &p) {
     return lt;
 }
 
-// Two orders in which k4_levels can take the (row, chunk group) blocks of level 2's region,
-// stored one after the other (k4order_n entries each):
-//   - row by row (groups in increasing order within a row): the blocks in flight stream one row
-//     and the matching span of its harmonic rows;
-//   - by ray: cell (r, z) gathers its harmonics at (h r, h z), on the ray from the origin through
-//     (r, z), where every other cell of that ray gathers too, and the rest of each gathered
-//     sector belongs to neighbouring rays.  Taking the blocks by increasing z / r (of the group's
-//     middle bin; ties by row, then group) brings all reads of a plane sector into a short
-//     stretch of the kernel's progress, so it comes from DRAM about once instead of about twice.
-// The FP32 plane (DRAM-bound row by row) takes the ray order, the BF16 plane, where the row
-// streams were faster than the ray order's scattered spans at half the bytes, takes the rows.
-// Built for level 2's region whatever max_harm and harm_mode say, so that plans of one shape
-// can share it.
+// The order in which k4_levels_ordered takes the (row, chunk group) blocks of level 2's region.
+// Cell (r, z) gathers its harmonics at (h r, h z), on the ray from the origin through (r, z),
+// where every other cell of that ray gathers too, and the rest of each gathered sector belongs
+// to neighbouring rays.  Taking the blocks by increasing z / r (of the group's middle bin; ties
+// by row, then group) brings all reads of a plane sector into a short stretch of the kernel's
+// progress, so it comes from DRAM about once; row by row (k4_levels) the harmonic rows of rows
+// far apart are fetched again, about twice the bytes.  Built for level 2's region whatever
+// max_harm and harm_mode say, so that plans of one shape can share it.
 cudaError_t upload_levels_order(Plan &p) {
     LevelDesc d{};
     level_region(p, 2, false, d);
@@ -835,13 +869,11 @@ cudaError_t upload_levels_order(Plan &p) {
         for (int64_t g = 0; g < groups; g++)
             items.push_back({(double)z / ((double)(g * per) + 0.5 * (double)per), ((uint32_t)a << 16) | (uint32_t)g});
     }
-    const size_t n = items.size();
-    std::vector<uint32_t> order(2 * n);
-    for (size_t k = 0; k < n; k++) order[k] = items[k].code;          // row by row
     std::sort(items.begin(), items.end(),
               [](const Item &x, const Item &y) { return x.key < y.key || (x.key == y.key && x.code < y.code); });
-    for (size_t k = 0; k < n; k++) order[n + k] = items[k].code;      // by ray
-    p.k4order_n = (int64_t)n;
+    std::vector<uint32_t> order(items.size());
+    for (size_t k = 0; k < items.size(); k++) order[k] = items[k].code;
+    p.k4order_n = (int64_t)order.size();
     cudaError_t e = cudaMalloc((void **)&p.d_k4order, sizeof(uint32_t) * order.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(p.d_k4order, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice);
