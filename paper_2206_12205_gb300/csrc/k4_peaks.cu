@@ -790,7 +790,7 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
     } else if (lt.n_levels > 1) {
         p.prof.begin(PROF_PEAKS_LEVELS, st);
         if (sizeof(E) == 4 || FDAS_K4_RAY_BF16) {
-            // BF16 plane: a persistent grid (0.182 ms against 0.299 ms for one block per entry at
+            // BF16 plane: a persistent grid (0.182 ms against 0.238 ms for one block per entry at
             // N = 2^23, 85 templates); FP32 plane: one block per entry (0.219 ms against 0.322 ms
             // persistent, its entries carry twice the bytes and the static stride balances worse)
             int sms = 0;
