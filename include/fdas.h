@@ -224,6 +224,20 @@ fdas_status fdas_peaks(fdas_plan_t plan, const void *d_plane, void *d_workspace,
                        fdas_peak *d_peaks, int32_t *d_npeaks, void *stream);
 
 /*
+ * The order in which fdas_peaks searches levels 2..16 over level 2's region (the harmonic sums
+ * above; rows with |2 z_i| <= zmax, bins r < Nb/2 rounded up to 512-bin chunks), as blocks of
+ * four consecutive chunks of one row: entry k = (row - first row of the region) << 16 | block.
+ * Cell (r, z) gathers harmonic h at (h r, h z), on its own ray through the origin, so the blocks
+ * are taken by increasing z / (middle bin of the block), ties by row then block, which keeps the
+ * reads of each plane sector close together in time.  Host only (computed from the plan; the
+ * same table is uploaded by fdas_make_templates).  h_order (host, nullable) receives
+ * *n_out entries when capacity >= *n_out.
+ * Errors: FDAS_E_INVALID (NULL plan or n_out, capacity too small for a non-NULL h_order);
+ * FDAS_E_UNSUPPORTED if the region has 2^16 rows or blocks or more (outside the plan limits).
+ */
+fdas_status fdas_levels_order(fdas_plan_t plan, uint32_t *h_order, int64_t capacity, int64_t *n_out);
+
+/*
  * Whole path for one series: fdas_spectrum (into the workspace), fdas_plane, fdas_peaks.
  * d_plane must hold plane_bytes.  Same errors as the three steps.
  */

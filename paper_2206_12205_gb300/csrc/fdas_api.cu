@@ -82,7 +82,7 @@ extern "C" {
 
 static_assert(sizeof(fdas_config) == 72, "fdas_config layout (the Python binding mirrors it)");
 
-int fdas_version(void) { return 105; }
+int fdas_version(void) { return 106; }
 
 const char *fdas_status_string(fdas_status s) {
     switch (s) {
@@ -174,6 +174,17 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     p->device = -1;
     *plan = p;
     if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+    return FDAS_OK;
+}
+
+fdas_status fdas_levels_order(fdas_plan_t plan, uint32_t *h_order, int64_t capacity, int64_t *n_out) {
+    if (!plan || !n_out) return FDAS_E_INVALID;
+    std::vector<uint32_t> order;
+    if (!fdas::levels_order(*P(plan), order)) return FDAS_E_UNSUPPORTED;
+    *n_out = (int64_t)order.size();
+    if (!h_order) return FDAS_OK;
+    if (capacity < *n_out) return FDAS_E_INVALID;
+    std::copy(order.begin(), order.end(), h_order);
     return FDAS_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/fdas.h"
 
@@ -158,7 +159,9 @@ cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale,
                              cudaStream_t st, uint8_t *l1flag = nullptr);
 // l1flag: the unit marks of the plane kernel that wrote d_plane (level 1 then visits only the
 // marked units), or NULL for the full level-1 pass over the plane.
-// Builds and uploads p.d_k4order (host sort at template time; synchronous copy).
+// The ray order of level 2's blocks (host; false if the region does not fit the 16-bit fields),
+// and its upload into p.d_k4order at template time (synchronous copy).
+bool levels_order(const Plan &p, std::vector<uint32_t> &order);
 cudaError_t upload_levels_order(Plan &p);
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
                          fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st,

@@ -857,12 +857,12 @@ LevelTable make_levels(const Plan &p) {
 // progress, so it comes from DRAM about once; row by row (k4_levels) the harmonic rows of rows
 // far apart are fetched again, about twice the bytes.  Built for level 2's region whatever
 // max_harm and harm_mode say, so that plans of one shape can share it.
-cudaError_t upload_levels_order(Plan &p) {
+bool levels_order(const Plan &p, std::vector<uint32_t> &order) {
     LevelDesc d{};
     level_region(p, 2, false, d);
     const int64_t per = DETECT_WARPS * CPW;           // chunks per block
     const int64_t groups = (d.chunks + per - 1) / per;
-    if (d.rows >= (1 << 16) || groups >= (1 << 16)) return cudaErrorInvalidValue;
+    if (d.rows >= (1 << 16) || groups >= (1 << 16)) return false;
     struct Item {
         double key;
         uint32_t code;
@@ -876,8 +876,14 @@ cudaError_t upload_levels_order(Plan &p) {
     }
     std::sort(items.begin(), items.end(),
               [](const Item &x, const Item &y) { return x.key < y.key || (x.key == y.key && x.code < y.code); });
-    std::vector<uint32_t> order(items.size());
+    order.resize(items.size());
     for (size_t k = 0; k < items.size(); k++) order[k] = items[k].code;
+    return true;
+}
+
+cudaError_t upload_levels_order(Plan &p) {
+    std::vector<uint32_t> order;
+    if (!levels_order(p, order)) return cudaErrorInvalidValue;
     p.k4order_n = (int64_t)order.size();
     cudaError_t e = cudaMalloc((void **)&p.d_k4order, sizeof(uint32_t) * order.size());
     if (e == cudaSuccess)

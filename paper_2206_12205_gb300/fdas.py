@@ -30,7 +30,7 @@ EXPORTED = (
     "fdas_plane_static", "fdas_interp_power", "fdas_refine",
     "fdas_batch_plan", "fdas_batch_autotune", "fdas_batch_make_templates", "fdas_batch_search",
     "fdas_batch_get_info", "fdas_batch_series_info", "fdas_batch_device_status", "fdas_batch_last_error",
-    "fdas_batch_destroy", "fdas_band_max", "fdas_check_timeout",
+    "fdas_batch_destroy", "fdas_band_max", "fdas_check_timeout", "fdas_levels_order",
 )
 REFINE_MAX_STEPS = 1000
 STATIC_SCRATCH_BYTES = 40 << 20
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "fdas_get_templates": (S, [V, V, V]),
         "fdas_device_status": (S, [V, ctypes.POINTER(I32), ctypes.c_int]),
         "fdas_check_timeout": (S, [V, I64, V]),
+        "fdas_levels_order": (S, [V, V, I64, ctypes.POINTER(I64)]),
         "fdas_last_error": (ctypes.c_char_p, [V]),
         "fdas_destroy": (None, [V]),
         "fdas_status_string": (ctypes.c_char_p, [S]),
@@ -384,6 +385,16 @@ def fdas_get_templates(plan: Plan, out, stream=None):
     K, S = plan.info.K, plan.cfg["seg_len"]
     _check(load().fdas_get_templates(plan.handle, _dev_ptr(out, "out", torch.float32, 8 * K * S),
                                      _stream_ptr(stream)), "fdas_get_templates", plan)
+
+
+def fdas_levels_order(plan: Plan) -> np.ndarray:
+    """The order of level 2's (row << 16 | 4-chunk block) entries the level search takes (host)."""
+    lib = load()
+    n = ctypes.c_int64(0)
+    _check(lib.fdas_levels_order(plan.handle, None, 0, ctypes.byref(n)), "fdas_levels_order", plan)
+    out = np.zeros(n.value, dtype=np.uint32)
+    _check(lib.fdas_levels_order(plan.handle, out.ctypes.data, out.size, ctypes.byref(n)), "fdas_levels_order", plan)
+    return out
 
 
 def fdas_check_timeout(plan: Plan, max_cycles: int, stream=None):

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2206_12205_gb300 as fd
@@ -34,7 +35,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert fd.fdas_version() == 105
+    assert fd.fdas_version() == 106
     for code in range(8):
         assert fd.status_string(code) and fd.status_string(code) != "unknown status"
     assert fd.status_string(99) == "unknown status"
@@ -204,3 +205,41 @@ def test_check_timeout_arguments(lib):
     assert lib.fdas_check_timeout(p.handle, (1 << 36) + 1, None) == fb.FDAS_E_INVALID
     assert lib.fdas_check_timeout(p.handle, 1000, None) == fb.FDAS_E_STATE
     fd.fdas_destroy(p)
+
+
+@pytest.mark.parametrize("n,zmax", [(1 << 23, 84), (1 << 12, 0), (1 << 13, 10), (1 << 16, 6), (1 << 27, 200)])
+def test_levels_order_is_the_ray_order(lib, n, zmax):
+    """The level-2 search order: every (row, 4-chunk block) of level 2's region exactly once
+    (rows with |2 z| <= zmax, bins below Nb/2 in 512-bin chunks), sorted by z over the block's
+    middle bin, ties by row then block; computed on the host from the plan alone."""
+    plan = fd.fdas_plan(fd.make_config(n, zmax, 32, 1024, max_harm=16))
+    order = fd.fdas_levels_order(plan)
+    nb = n // 2
+    zl = zmax // 2
+    zl -= zl & 1
+    rows = zl + 1
+    chunks = ((nb - 1) // 2 + 1 + 511) // 512
+    blocks = (chunks + 3) // 4
+    assert order.size == rows * blocks
+    a, g = (order >> 16).astype(np.int64), (order & 0xFFFF).astype(np.int64)
+    assert np.array_equal(np.sort(a * blocks + g), np.arange(rows * blocks))        # a permutation
+    z = -zl + 2 * a                                                                # z of the row
+    key = z / (4.0 * g + 2.0)                                                      # middle of 4 chunks
+    assert np.all(np.diff(key) >= 0)
+    tie = np.diff(key) == 0
+    code = order.astype(np.int64)
+    assert np.all(np.diff(code)[tie] > 0)
+    zero = z == 0                                                                  # the z = 0 row: blocks in order
+    assert np.array_equal(g[zero], np.arange(blocks))
+    fd.fdas_destroy(plan)
+
+
+def test_levels_order_arguments(lib):
+    plan = fd.fdas_plan(fd.make_config(1 << 14, 8, 32, 1024))
+    n = ctypes.c_int64(-1)
+    assert lib.fdas_levels_order(None, None, 0, ctypes.byref(n)) == fb.FDAS_E_INVALID
+    assert lib.fdas_levels_order(plan.handle, None, 0, None) == fb.FDAS_E_INVALID
+    assert lib.fdas_levels_order(plan.handle, None, 0, ctypes.byref(n)) == fb.FDAS_OK and n.value > 0
+    buf = np.zeros(n.value, dtype=np.uint32)
+    assert lib.fdas_levels_order(plan.handle, buf.ctypes.data, n.value - 1, ctypes.byref(n)) == fb.FDAS_E_INVALID
+    fd.fdas_destroy(plan)
