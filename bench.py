@@ -7,7 +7,8 @@ discard), harmonic sums (1..16 harmonics) and the peak list; the template bank i
 at plan time.  Workload: N = 2^23 samples at 64 us of seeded Gaussian noise with 8 injected
 accelerated pulse trains, 85 templates (zmax 84), 256 taps, 8192-bin segments.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16|bf16_split]
+  python bench.py [--gpus N] [--steps K] [--warmup W]
+                  [--precision fp32|bf16|bf16_split|fp16_scaled|bf16_direct|fp8_direct]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
 Beside the plane metric, the line carries "refine": sub-bin refinement of 100k candidates seeded
