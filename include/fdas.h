@@ -135,7 +135,8 @@ typedef struct {
 typedef struct {
     int64_t nb;              /* N/2 frequency bins                                           */
     int32_t K;               /* template rows                                                */
-    int32_t seg_valid;       /* L = S - m + 1 plane bins kept per segment                     */
+    int32_t seg_valid;       /* L plane bins kept per segment: S - m + 1 rounded down to a
+                                multiple of 32 (FP32) or of 64 (tensor-core DFT paths)          */
     int64_t n_seg;           /* ceil(Nb / L) overlap-save segments                            */
     int32_t plane_elem_bytes;/* 2 for FDAS_BF16 and FDAS_BF16_DIRECT, else 4                  */
     int64_t plane_bytes;     /* K * Nb * plane_elem_bytes                                     */
@@ -335,10 +336,12 @@ fdas_status fdas_refine(fdas_plan_t plan, const float *d_xhat, const fdas_cand *
  * Batched search over many series: dispersion-measure trials of uneven length and zmax, one
  * configuration each (the paper searches every trial of a dedispersed observation; Sec. 2.1).
  * Series with the same (n_samples, zmax, taps, seg_len, precision) share one template bank.
- * All series run back to back in one CUDA graph (captured on a library-owned stream the first
- * time a set of buffers is seen, relaunched on the caller's stream afterwards), reusing one
- * workspace and one plane buffer sized for the largest series, so device memory does not grow
- * with the number of series.
+ * All series run in one CUDA graph (captured on a library-owned stream the first time a set of
+ * buffers is seen, relaunched on the caller's stream afterwards).  The graph has `lanes`
+ * concurrent branches (default 1; fdas_batch_set_lanes, or chosen by fdas_batch_autotune): the
+ * series are dealt to the lanes largest first, each to the least loaded, and run back to back
+ * inside a lane; each lane reuses one workspace slice and one plane buffer sized for the largest
+ * series, so device memory (lanes x that) does not grow with the number of series.
  */
 typedef struct fdas_batch_s *fdas_batch_t;
 
@@ -354,13 +357,25 @@ fdas_status fdas_batch_plan(const fdas_config *cfgs, int32_t n_series, fdas_batc
  * Autotune (optional, before fdas_batch_make_templates; allocates and runs on the current
  * device): for each FP32 group, time the segment lengths S = 1024 .. 8192 (S >= 2 taps) and
  * 1 .. 16 templates per correlation CTA on a zero spectrum, keep the fastest and re-plan the
- * group's series with it (the plane does not depend on S).  Choices are read from and written
- * to the JSON file cache_path (nullable: no cache), keyed by the device and the group shape.
- * The workspace size may change: read it again with fdas_batch_get_info.
+ * group's series with it (the plane does not depend on S); then build the template banks and
+ * time the whole batch on a zero input at 1 .. 4 lanes and keep the fastest (this allocates the
+ * packed input's size and four lanes' workspace for the duration of the call).  Choices are read
+ * from and written to the JSON file cache_path (nullable: no cache), keyed by the device and the
+ * group's or the batch's shape.  The workspace size may change: read it again with
+ * fdas_batch_get_info.
  * Errors: FDAS_E_STATE after templates exist; FDAS_E_INVALID when the cache cannot be written;
  * FDAS_E_NOMEM, FDAS_E_CUDA.
  */
 fdas_status fdas_batch_autotune(fdas_batch_t batch, const char *cache_path, void *stream);
+
+/*
+ * Set the number of concurrent lanes of a batch (1 .. FDAS_BATCH_MAX_LANES; host only, any time
+ * before a search; the next fdas_batch_search captures its graph again).  *workspace_bytes
+ * (nullable) receives the new workspace size, lanes x (the largest series' scratch + plane).
+ * Peak lists do not depend on the lane count.  Errors: FDAS_E_INVALID.
+ */
+#define FDAS_BATCH_MAX_LANES 8
+fdas_status fdas_batch_set_lanes(fdas_batch_t batch, int32_t lanes, size_t *workspace_bytes);
 
 /* Build the template banks (one per group) on the current device.  Synchronises the stream. */
 fdas_status fdas_batch_make_templates(fdas_batch_t batch, void *stream);

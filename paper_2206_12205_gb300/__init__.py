@@ -10,6 +10,7 @@ from . import build  # noqa: F401
 from .fdas import (  # noqa: F401
     CAND_DTYPE, FDAS_BF16, FDAS_BF16_SPLIT, FDAS_FP32, PEAK_DTYPE, PRECISIONS, Batch, FdasError, Plan, Search,
     fdas_batch_autotune, fdas_batch_destroy, fdas_batch_device_status, fdas_batch_make_templates, fdas_batch_plan,
+    fdas_batch_set_lanes,
     fdas_band_max, fdas_batch_search, fdas_destroy, fdas_device_status, fdas_get_templates, fdas_interp_power, fdas_make_templates, fdas_peaks,
     fdas_levels_order, fdas_plan, fdas_plane, fdas_plane_static, fdas_profile_enable, fdas_profile_read, fdas_refine,
     fdas_search,

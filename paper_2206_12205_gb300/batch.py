@@ -38,10 +38,12 @@ class BatchSearch:
     """A planned batch with its device buffers (torch-owned): workspace, peak regions, counts."""
 
     def __init__(self, cfgs: Sequence[dict], device="cuda", autotune_cache: Optional[str] = None,
-                 autotune: bool = False, stream=None):
+                 autotune: bool = False, stream=None, lanes: Optional[int] = None):
         import torch
         self.device = torch.device(device)
         self.batch = _f.fdas_batch_plan(cfgs)
+        if lanes is not None:
+            _f.fdas_batch_set_lanes(self.batch, lanes)
         if autotune:
             _f.fdas_batch_autotune(self.batch, autotune_cache, stream)
         _f.fdas_batch_make_templates(self.batch, stream)

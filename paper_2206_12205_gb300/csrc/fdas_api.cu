@@ -130,7 +130,9 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     p->K = c.zmax + 1;
     p->m = c.taps;
     p->S = c.seg_len;
-    p->L = p->S - p->m + 1;
+    // FP32 path: stride a multiple of 32 bins, so each warp's plane stores cover whole 128-byte
+    // lines (any L <= S - m + 1 gives the same plane)
+    p->L = (p->S - p->m + 1) / 32 * 32;
     if (c.precision != FDAS_FP32) {
         // tensor-core path: 4096-bin segments, stride a multiple of 64 (same plane for any L)
         p->S = fdas::TC_S_BF16;

@@ -2,19 +2,24 @@
 //
 // A batch holds one plan per series.  Series with the same (N, zmax, taps, segment length,
 // precision) form a group that shares one template bank and twiddle tables (built once by the
-// group's first plan).  fdas_batch_search runs every series through K1 -> K2/K3 -> K4 back to
-// back in one CUDA graph: the graph is captured on a library-owned stream the first time a set
-// of buffers is seen and relaunched on the caller's stream afterwards, so a batch costs one
-// launch on the host.  All series reuse one workspace and one plane buffer (each sized for the
-// largest series): stream order keeps a series' peak search ahead of the next series' plane,
-// so the device memory is bounded by the largest series, whatever the batch size.
+// group's first plan).  fdas_batch_search runs every series through K1 -> K2/K3 -> K4 in one
+// CUDA graph: the graph is captured on a library-owned stream the first time a set of buffers is
+// seen and relaunched on the caller's stream afterwards, so a batch costs one launch on the host.
 //
-// The autotuner (fdas_batch_autotune) times the FP32 path's candidate segment lengths
-// S in {1024, 2048, 4096, 8192} (S >= 2 taps) and templates per correlation CTA
-// {1, 2, 4, 8, 16} for each group on the current device, keeps the fastest, and caches the
-// choices in a small JSON file keyed by the device and the group's shape.  The tensor-core
-// paths have no free launch parameters (4096-bin segments, one persistent CTA per SM), so
-// their entries record the fixed choice.
+// Lanes: the series are spread over `lanes` concurrent branches of the graph (largest cost
+// first, each to the least loaded lane), each branch with its own workspace slice and plane
+// buffer sized for the largest series; inside a lane the series run back to back (stream order
+// keeps a series' peak search ahead of the lane's next plane).  While one lane's plane kernel
+// drains its last items or its small peak-search launches leave SMs idle, another lane's
+// kernels fill them, and the launch gaps between kernels overlap.  Device memory is lanes x
+// (workspace + plane) of the largest series, whatever the batch size.
+//
+// The autotuner (fdas_batch_autotune) times, for each FP32 group, the candidate segment lengths
+// S in {1024, 2048, 4096, 8192} (S >= 2 taps) and templates per correlation CTA {1, 2, 4, 8, 16}
+// on a zero spectrum and keeps the fastest (the tensor-core paths have no per-group launch
+// choice: 4096-bin segments, one persistent CTA per SM); then it times the whole batch on a
+// zero input at 1 .. 4 lanes and keeps the fastest.  Choices are cached in a small JSON file
+// keyed by the device and the group's (or the batch's) shape.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -45,12 +50,18 @@ struct fdas_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const void *g_series = nullptr, *g_ws = nullptr, *g_peaks = nullptr, *g_npeaks = nullptr;
+    int lanes = 1;                         // concurrent branches of the graph
+    std::vector<int> lane_of;              // per series: its lane
+    size_t lane_bytes = 0;                 // workspace slice of one lane (series scratch + plane)
+    std::vector<cudaStream_t> lane_st;     // capture streams of the lanes
+    std::vector<cudaEvent_t> lane_ev;      // fork (0) and the lanes' joins (1 ..)
     std::string last_error;
 };
 
 namespace {
 
 constexpr size_t ALIGN = 256;
+constexpr int BATCH_TUNE_LANES = 4;        // lane counts the autotuner times
 size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 bool aligned(const void *ptr, uintptr_t a) { return (reinterpret_cast<uintptr_t>(ptr) & (a - 1)) == 0; }
 
@@ -121,7 +132,23 @@ void layout(fdas_batch_s *b) {
     b->total_cells = cells;
     b->ws_series = align_up(ws);
     b->plane_bytes = align_up(pl);
-    b->ws_bytes = b->ws_series + b->plane_bytes;
+    b->lane_bytes = b->ws_series + b->plane_bytes;
+    b->ws_bytes = (size_t)b->lanes * b->lane_bytes;
+    // lanes: largest cost (plane cells) first, each to the least loaded lane (lowest on ties)
+    std::vector<int> idx(n);
+    std::vector<int64_t> cost(n);
+    for (int i = 0; i < n; i++) {
+        idx[i] = i;
+        cost[i] = (int64_t)(b->cfg[i].zmax + 1) * (b->cfg[i].n_samples / 2);
+    }
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    std::vector<int64_t> load(b->lanes, 0);
+    b->lane_of.assign(n, 0);
+    for (int i : idx) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        b->lane_of[i] = l;
+        load[l] += cost[i];
+    }
 }
 
 void drop_graph(fdas_batch_s *b) {
@@ -134,11 +161,13 @@ void drop_graph(fdas_batch_s *b) {
 
 // ---------------------------------------------------------------- autotune cache (JSON)
 struct TuneChoice {
-    int seg_len = 0, zb = 0;
+    int seg_len = 0, zb = 0, lanes = 0;    // lanes: batch entries only
     double ms = 0.0;
 };
 
-// One entry per line, as written by save_cache: "  \"key\": {\"seg_len\": S, \"zb\": Z, \"ms\": T},"
+// One entry per line, as written by save_cache:
+//   "  \"key\": {\"seg_len\": S, \"zb\": Z, \"lanes\": N, \"ms\": T},"
+// (entries without the lanes field are read too)
 std::map<std::string, TuneChoice> load_cache(const char *path) {
     std::map<std::string, TuneChoice> m;
     if (!path) return m;
@@ -148,7 +177,9 @@ std::map<std::string, TuneChoice> load_cache(const char *path) {
     while (std::fgets(line, sizeof line, f)) {
         char key[256];
         TuneChoice c;
-        if (std::sscanf(line, " \"%255[^\"]\": {\"seg_len\": %d, \"zb\": %d, \"ms\": %lf", key, &c.seg_len, &c.zb,
+        if (std::sscanf(line, " \"%255[^\"]\": {\"seg_len\": %d, \"zb\": %d, \"lanes\": %d, \"ms\": %lf", key,
+                        &c.seg_len, &c.zb, &c.lanes, &c.ms) == 5 ||
+            std::sscanf(line, " \"%255[^\"]\": {\"seg_len\": %d, \"zb\": %d, \"ms\": %lf", key, &c.seg_len, &c.zb,
                         &c.ms) == 4)
             m[key] = c;
     }
@@ -164,8 +195,9 @@ bool save_cache(const char *path, const std::map<std::string, TuneChoice> &m) {
     std::fprintf(f, "{\n \"fdas_autotune\": 1,\n \"entries\": {\n");
     size_t k = 0;
     for (const auto &kv : m) {
-        std::fprintf(f, "  \"%s\": {\"seg_len\": %d, \"zb\": %d, \"ms\": %.6f}%s\n", kv.first.c_str(),
-                     kv.second.seg_len, kv.second.zb, kv.second.ms, ++k < m.size() ? "," : "");
+        std::fprintf(f, "  \"%s\": {\"seg_len\": %d, \"zb\": %d, \"lanes\": %d, \"ms\": %.6f}%s\n",
+                     kv.first.c_str(), kv.second.seg_len, kv.second.zb, kv.second.lanes, kv.second.ms,
+                     ++k < m.size() ? "," : "");
     }
     std::fprintf(f, " }\n}\n");
     std::fclose(f);
@@ -212,6 +244,64 @@ fdas_status time_plane(const fdas_config &c, int zb, cudaStream_t st, double *ms
     fdas_destroy(p);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FDAS_E_NOMEM : FDAS_E_CUDA;
     return s;
+}
+
+// Cache key of a whole batch: the device and an FNV-1a digest of its series' shapes in order.
+std::string batch_key(const fdas_batch_s *b, int device) {
+    uint64_t h = 1469598103934665603ull;
+    for (const fdas_config &c : b->cfg) {
+        const std::string k = group_key(c);
+        for (unsigned char ch : k) h = (h ^ ch) * 1099511628211ull;
+        h = (h ^ 0xffu) * 1099511628211ull;
+    }
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, device);
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "batch:sm%d%d_x%d:n%zu:h%016llx", prop.major, prop.minor, prop.multiProcessorCount,
+                  b->plan.size(), (unsigned long long)h);
+    return buf;
+}
+
+// The lanes' capture streams and the fork / join events (created on first use, kept until the
+// batch is destroyed).
+cudaError_t ensure_lanes(fdas_batch_s *b) {
+    cudaError_t e = cudaSuccess;
+    while ((int)b->lane_st.size() < b->lanes && e == cudaSuccess) {
+        cudaStream_t st = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->lane_st.push_back(st);
+    }
+    while ((int)b->lane_ev.size() < b->lanes + 1 && e == cudaSuccess) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->lane_ev.push_back(ev);
+    }
+    return e;
+}
+
+// The best of two event-timed fdas_batch_search calls on a zero input at `lanes` lanes (after one
+// call that captures the graph).  Buffers are the caller's (sized for the most lanes timed).
+fdas_status time_batch(fdas_batch_s *b, int lanes, const float *series, void *ws, fdas_peak *peaks, int32_t *npeaks,
+                       cudaStream_t st, double *ms_out) {
+    fdas_status s = fdas_batch_set_lanes(b, lanes, nullptr);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best = 1e30;
+    for (int r = 0; r < 3 && e == cudaSuccess && s == FDAS_OK; r++) {
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        s = fdas_batch_search(b, series, ws, peaks, npeaks, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) best = std::min(best, (double)ms);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    *ms_out = best;
+    if (s != FDAS_OK) return s;
+    return record(b, e);
 }
 
 }  // namespace
@@ -298,6 +388,46 @@ fdas_status fdas_batch_autotune(fdas_batch_t b, const char *cache_path, void *st
     }
     layout(b);
     drop_graph(b);
+    // lanes: the whole batch on a zero input (the plane and peak kernels' time hardly depends on
+    // the data), 1 .. BATCH_TUNE_LANES lanes
+    const std::string bk = batch_key(b, dev);
+    auto bt = cache.find(bk);
+    int lanes = 1;
+    if (bt != cache.end() && bt->second.lanes >= 1 && bt->second.lanes <= FDAS_BATCH_MAX_LANES) {
+        lanes = bt->second.lanes;
+    } else {
+        fdas_status s = fdas_batch_make_templates(b, stream);
+        if (s != FDAS_OK) return s;
+        const size_t ws_max = (size_t)BATCH_TUNE_LANES * b->lane_bytes;
+        void *series = nullptr, *ws = nullptr, *peaks = nullptr, *npk = nullptr;
+        e = cudaMalloc(&series, sizeof(float) * (size_t)b->total_samples);
+        if (e == cudaSuccess) e = cudaMalloc(&ws, ws_max);
+        if (e == cudaSuccess) e = cudaMalloc(&peaks, sizeof(fdas_peak) * (size_t)std::max<int64_t>(1, b->total_peaks));
+        if (e == cudaSuccess) e = cudaMalloc(&npk, sizeof(int32_t) * b->plan.size());
+        if (e == cudaSuccess) e = cudaMemsetAsync(series, 0, sizeof(float) * (size_t)b->total_samples, st);
+        TuneChoice choice;
+        double best = 1e30;
+        for (int l = 1; l <= BATCH_TUNE_LANES && e == cudaSuccess && s == FDAS_OK; l++) {
+            double ms = 0.0;
+            s = time_batch(b, l, static_cast<const float *>(series), ws, static_cast<fdas_peak *>(peaks),
+                           static_cast<int32_t *>(npk), st, &ms);
+            if (s == FDAS_OK && ms < best) {
+                best = ms;
+                choice.lanes = l;
+                choice.ms = ms;
+            }
+        }
+        cudaFree(series);
+        cudaFree(ws);
+        cudaFree(peaks);
+        cudaFree(npk);
+        if (e != cudaSuccess) return record(b, e);
+        if (s != FDAS_OK) return s;
+        lanes = choice.lanes;
+        cache[bk] = choice;
+        changed = true;
+    }
+    fdas_batch_set_lanes(b, lanes, nullptr);
     if (changed && !save_cache(cache_path, cache)) {
         b->last_error = std::string("cannot write the autotune cache ") + cache_path;
         return FDAS_E_INVALID;
@@ -365,25 +495,38 @@ fdas_status fdas_batch_search(fdas_batch_t b, const float *d_series, void *d_wor
     if (!(b->exec && b->g_series == d_series && b->g_ws == d_workspace && b->g_peaks == d_peaks &&
           b->g_npeaks == d_npeaks)) {
         drop_graph(b);
-        char *ws = static_cast<char *>(d_workspace);
-        void *plane = ws + b->ws_series;
-        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = ensure_lanes(b);
         if (e != cudaSuccess) return record(b, e);
+        char *ws0 = static_cast<char *>(d_workspace);
+        e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return record(b, e);
+        // fork: every lane branches from the capture stream
+        e = cudaEventRecord(b->lane_ev[0], b->cap);
+        for (int l = 0; l < b->lanes && e == cudaSuccess; l++) e = cudaStreamWaitEvent(b->lane_st[l], b->lane_ev[0], 0);
         for (size_t i = 0; i < b->plan.size() && e == cudaSuccess; i++) {
             const Plan &p = *b->plan[i];
-            e = fdas::launch_spectrum(p, d_series + b->sample_off[i], ws, b->cap);
+            const int lane = b->lane_of[i];
+            cudaStream_t st_l = b->lane_st[lane];
+            char *ws = ws0 + (size_t)lane * b->lane_bytes;
+            void *plane = ws + b->ws_series;
+            e = fdas::launch_spectrum(p, d_series + b->sample_off[i], ws, st_l);
             float2 *x = reinterpret_cast<float2 *>(ws + p.ws_x);
             const float *scale = reinterpret_cast<const float *>(ws + p.ws_scale + 8);
             if (e == cudaSuccess && p.cfg.norm_block) {
-                e = fdas::launch_local_norm(p, x, x, b->cap);
+                e = fdas::launch_local_norm(p, x, x, st_l);
                 scale = nullptr;
             }
             uint8_t *l1flag = fdas::level1_fusable(p) ? reinterpret_cast<uint8_t *>(ws + p.ws_l1flag) : nullptr;
-            if (e == cudaSuccess) e = fdas::launch_plane_any(p, x, scale, ws, plane, b->cap, l1flag);
+            if (e == cudaSuccess) e = fdas::launch_plane_any(p, x, scale, ws, plane, st_l, l1flag);
             if (e == cudaSuccess)
                 e = fdas::launch_peaks(p, plane, p.cfg.precision == FDAS_BF16 || p.cfg.precision == FDAS_BF16_DIRECT,
                                        ws, d_peaks + b->peak_off[i],
-                                       d_npeaks + i, (uint32_t)i, b->cap, l1flag);
+                                       d_npeaks + i, (uint32_t)i, st_l, l1flag);
+        }
+        // join: the capture stream waits for every lane
+        for (int l = 0; l < b->lanes && e == cudaSuccess; l++) {
+            e = cudaEventRecord(b->lane_ev[1 + l], b->lane_st[l]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->lane_ev[1 + l], 0);
         }
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
@@ -401,6 +544,15 @@ fdas_status fdas_batch_search(fdas_batch_t b, const float *d_series, void *d_wor
         b->g_npeaks = d_npeaks;
     }
     return record(b, cudaGraphLaunch(b->exec, st));
+}
+
+fdas_status fdas_batch_set_lanes(fdas_batch_t b, int32_t lanes, size_t *workspace_bytes) {
+    if (!b || lanes < 1 || lanes > FDAS_BATCH_MAX_LANES) return FDAS_E_INVALID;
+    b->lanes = lanes;
+    layout(b);
+    drop_graph(b);
+    if (workspace_bytes) *workspace_bytes = b->ws_bytes;
+    return FDAS_OK;
 }
 
 fdas_status fdas_batch_get_info(fdas_batch_t b, int32_t *n_series, size_t *workspace_bytes, int64_t *total_samples,
@@ -445,6 +597,8 @@ void fdas_batch_destroy(fdas_batch_t b) {
     if (b->device >= 0) cudaDeviceSynchronize();
     drop_graph(b);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaStream_t st : b->lane_st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->lane_ev) cudaEventDestroy(ev);
     // followers first: they borrow their group leader's device memory
     for (size_t i = 0; i < b->plan.size(); i++)
         if (b->plan[i]->borrowed) fdas_destroy(b->plan[i]);

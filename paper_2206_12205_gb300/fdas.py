@@ -30,6 +30,7 @@ EXPORTED = (
     "fdas_plane_static", "fdas_interp_power", "fdas_refine",
     "fdas_batch_plan", "fdas_batch_autotune", "fdas_batch_make_templates", "fdas_batch_search",
     "fdas_batch_get_info", "fdas_batch_series_info", "fdas_batch_device_status", "fdas_batch_last_error",
+    "fdas_batch_set_lanes",
     "fdas_batch_destroy", "fdas_band_max", "fdas_check_timeout", "fdas_levels_order",
 )
 REFINE_MAX_STEPS = 1000
@@ -122,6 +123,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "fdas_batch_device_status": (S, [V, ctypes.POINTER(I32), ctypes.c_int]),
         "fdas_batch_last_error": (ctypes.c_char_p, [V]),
         "fdas_batch_destroy": (None, [V]),
+        "fdas_batch_set_lanes": (S, [V, I32, ctypes.POINTER(SZ)]),
         "fdas_band_max": (S, [V, V, V, V, I32, V, V, V, V, V]),
     }
     for name, (res, args) in sig.items():
@@ -494,6 +496,14 @@ def fdas_batch_autotune(batch: Batch, cache_path: Optional[str] = None, stream=N
     path = cache_path.encode() if cache_path else None
     _check_batch(load().fdas_batch_autotune(batch.handle, path, _stream_ptr(stream)), "fdas_batch_autotune", batch)
     batch.refresh()
+
+
+def fdas_batch_set_lanes(batch: Batch, lanes: int) -> int:
+    """Concurrent lanes of the batch's graph; returns the new workspace size in bytes."""
+    ws = ctypes.c_size_t()
+    _check_batch(load().fdas_batch_set_lanes(batch.handle, int(lanes), ctypes.byref(ws)), "fdas_batch_set_lanes", batch)
+    batch.refresh()
+    return int(ws.value)
 
 
 def fdas_batch_make_templates(batch: Batch, stream=None):

@@ -52,7 +52,7 @@ def test_struct_layouts(lib):
                                          (1 << 12, 8, 512, 1024), (1 << 13, 2, 16, 2048)])
 def test_plan_sizes(lib, n, zmax, m, S):
     p = fd.fdas_plan(fd.make_config(n, zmax, m, S, max_harm=16))
-    nb, L = n // 2, S - m + 1
+    nb, L = n // 2, (S - m + 1) // 32 * 32          # stride rounded down to whole 32-bin runs
     assert p.info.nb == nb and p.info.K == zmax + 1 and p.info.seg_valid == L
     assert p.info.n_seg == -(-nb // L)
     assert p.info.cells == (zmax + 1) * nb and p.info.plane_bytes == 4 * p.info.cells

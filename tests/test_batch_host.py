@@ -57,6 +57,24 @@ def test_batch_plan_layout(lib):
     fd.fdas_batch_destroy(b)                     # a second destroy is a no-op
 
 
+def test_batch_lanes_layout(lib):
+    """fdas_batch_set_lanes (host only): the workspace is lanes x (largest scratch + largest
+    plane); out-of-range lane counts are rejected and leave the batch as it was."""
+    cfgs = _cfgs([(1 << 14, 4), (1 << 16, 16), (1 << 15, 10), (1 << 13, 0), (1 << 16, 16)])
+    b = fd.fdas_batch_plan(cfgs)
+    one = b.workspace_bytes
+    for lanes in (1, 2, 3, 8):
+        assert fd.fdas_batch_set_lanes(b, lanes) == lanes * one
+        assert b.workspace_bytes == lanes * one
+    for bad in (0, -1, 9):
+        with pytest.raises(fd.FdasError) as ei:
+            fd.fdas_batch_set_lanes(b, bad)
+        assert ei.value.status == fbind.FDAS_E_INVALID
+    assert b.workspace_bytes == 8 * one
+    assert lib.fdas_batch_set_lanes(None, 2, None) == fbind.FDAS_E_INVALID
+    fd.fdas_batch_destroy(b)
+
+
 def test_batch_plan_rejects(lib):
     with pytest.raises(fd.FdasError):
         fd.fdas_batch_plan([])

@@ -68,6 +68,28 @@ def test_batch_equals_series_searched_alone(precision):
     assert fd.fdas_batch_device_status(bs.batch) == 0
 
 
+@pytest.mark.parametrize("precision,lanes", [("fp32", 3), ("bf16", 2), ("bf16", 4)])
+def test_batch_lanes_give_the_same_lists(precision, lanes):
+    """Concurrent lanes (the graph's parallel branches, each with its own workspace and plane
+    buffer) change only the schedule: every series' list is the one-lane list, record for record,
+    and the lanes' workspaces do not overlap (a series would otherwise read another's plane)."""
+    wl = _small_batch(n_series=11, seed=84)
+    cfgs = _cfgs(wl, precision)
+    dev = torch.from_numpy(wl.packed).cuda()
+    one = fb.BatchSearch(cfgs)
+    one.search(dev)
+    many = fb.BatchSearch(cfgs, lanes=lanes)
+    assert many.batch.workspace_bytes == lanes * one.batch.workspace_bytes
+    for _ in range(2):                                  # capture, then relaunch
+        many.npeaks.zero_()
+        many.search(dev)
+        torch.cuda.synchronize()
+        for x, y in zip(one.peak_lists(), many.peak_lists()):
+            _peaks_equal(x, y)
+    assert sum(len(x) for x in one.peak_lists()) > 0
+    assert fd.fdas_batch_device_status(many.batch) == 0
+
+
 def test_batch_zero_series_reports_nothing():
     """A series of zeros inside a batch (sigma2 = 0) yields an empty list and leaves every other
     series' list unchanged."""
@@ -149,9 +171,14 @@ def test_batch_autotune_cache(tmp_path):
     with open(cache) as f:
         entries = json.load(f)["entries"]
     groups = {s.group for s in b1.series}
-    assert len(entries) == len(groups)
-    for e in entries.values():
+    per_group = {k: e for k, e in entries.items() if not k.startswith("batch:")}
+    per_batch = {k: e for k, e in entries.items() if k.startswith("batch:")}
+    assert len(per_group) == len(groups) and len(per_batch) == 1
+    for e in per_group.values():
         assert e["seg_len"] in (1024, 2048, 4096, 8192) and e["zb"] in (1, 2, 4, 8, 16) and e["ms"] > 0
+    (eb,) = per_batch.values()
+    assert 1 <= eb["lanes"] <= 4 and eb["ms"] > 0
+    assert b1.workspace_bytes % eb["lanes"] == 0        # lanes x one lane's scratch and plane
     chosen = [s.cfg["seg_len"] for s in b1.series]
     # a second batch reads the cache: the same choices, no new timing
     b2 = fd.fdas_batch_plan(cfgs)

@@ -240,15 +240,19 @@ def test_full_size_spectrum(pulse_train_case):
     assert abs(s.sigma2.item() - s2) <= 1e-5 * s2
 
 
-def test_full_size_plane_sampled(pulse_train_case):
-    """N = 2^23, 85 templates, 256 taps, 8192-bin segments, in the launch configuration the
-    benchmark times: sampled cells (random, segment edges, the ragged tail, each train's
-    fundamental) against the oracle evaluated cell by cell on the same spectrum."""
+@pytest.mark.parametrize("seg_len", [8192, 2048])
+def test_full_size_plane_sampled(pulse_train_case, seg_len):
+    """N = 2^23, 85 templates, 256 taps, with the workload's 8192-bin segments and with the
+    2048-bin segments the benchmark's FP32 path runs (its launch configuration): sampled cells
+    (random, segment edges, the ragged tail, each train's fundamental) against the oracle
+    evaluated cell by cell on the same spectrum."""
     w, s, xr, _, xr32 = pulse_train_case
+    if seg_len != w.seg_len:
+        s = _search(w.n, w.zmax, w.taps, seg_len, max_harm=16, thr=FULL_THR, max_peaks=1 << 16)
     xh = xr32.view(np.complex64).astype(np.complex128)
     s.plane_from_spectrum(_to_dev(xr32))
     torch.cuda.synchronize()
-    K, nb, L = w.K, w.nb, w.seg_len - w.taps + 1
+    K, nb, L = w.K, w.nb, s.plan.info.seg_valid
     rng = np.random.default_rng(7)
     zi = list(rng.integers(0, K, 3000))
     r = list(rng.integers(0, nb, 3000))
