@@ -624,6 +624,58 @@ def batch_bench(dev, stream, reps: int = 5, warmup: int = 2, loop_reps: int = 2,
     }
 
 
+def sharded_batch_bench(dev, stream, dist, rank: int, world: int, reps: int = 5, warmup: int = 2, lanes: int = 3):
+    """The batching workload split over the job's GPUs: series dealt by shard_series (largest cost
+    first, each to the least loaded rank), each rank synthesising and searching only its share as
+    one batch (no exchange during the search), timed between barriers, the max over ranks; then
+    the per-series peak lists gathered on rank 0 (the only data that travels)."""
+    import torch
+
+    import fdas_synth as synth
+    import paper_2206_12205_gb300 as fd
+    from paper_2206_12205_gb300 import batch as fbat
+
+    shapes = synth._batch_shapes(2, BATCH_SERIES, synth.BATCH_N, synth.BATCH_ZMAX)
+    mine = fbat.shard_series([fbat.series_cost(n, z) for n, z in shapes], world)[rank]
+    wl = synth.batch_workload(n_series=BATCH_SERIES, series=mine, workers=min(16, os.cpu_count() or 1))
+    packed = torch.from_numpy(wl.packed).to(dev)
+    cfgs = [fd.make_config(w.n, w.zmax, w.taps, w.seg_len, precision="bf16", max_harm=MAX_HARM, thr=THRESHOLDS,
+                           max_peaks=4096) for w in wl.series]
+    bs = fbat.BatchSearch(cfgs, device=dev, stream=stream, lanes=lanes)
+    for _ in range(warmup):
+        bs.search(packed, stream)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        dist.barrier()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bs.search(packed, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms.append(float(t.item()))
+    ms_batch = statistics.median(ms)
+    assert fd.fdas_batch_device_status(bs.batch) == 0
+    lists = fbat.gather_peak_lists(mine, bs.peak_lists(), BATCH_SERIES, dist)
+    cells = [None] * world
+    dist.all_gather_object(cells, wl.total_cells)
+    del bs, packed
+    if rank != 0:
+        return None
+    total = sum(cells)
+    return {
+        "metric": "f-z plane cells/s over a batch of series split across GPUs (BF16)",
+        "value": total / (ms_batch / 1e3), "unit": "cells/s", "series": BATCH_SERIES, "cells": total,
+        "ms_per_batch": ms_batch, "lanes": lanes, "scaling": "strong",
+        "cells_per_rank": cells, "peaks_gathered": int(sum(len(x) for x in lists)),
+        "how": "series split by batch.shard_series (no data-path collective); per-rank batch timed between "
+               "barriers, max over ranks; peak lists gathered on rank 0 with gather_object",
+    }
+
+
 # ------------------------------------------------------------------------------ sensitivity sweep
 SENS_FORMS = ("fp32", "bf16", "bf16_split", "fp16_scaled", "bf16_direct", "fp8_direct")
 SENS_BANDS = 8
@@ -880,6 +932,8 @@ def own_arm(args):
     batch = None
     if rank == 0 and world == 1 and not args.no_batch and not args.quick:
         batch = batch_bench(dev, stream)
+    elif world > 1 and not args.no_batch and not args.quick:
+        batch = sharded_batch_bench(dev, stream, dist, rank, world)
     sensitivity = None
     if rank == 0 and world == 1 and not args.no_sensitivity and not args.quick:
         sensitivity = sensitivity_bench(dev, stream, args.sensitivity_series)

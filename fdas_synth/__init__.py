@@ -266,21 +266,25 @@ def _batch_worker(args):
 
 def batch_workload(config_index: int = 2, n_series: int = 256, tsamp: float = 64e-6, n_choices=BATCH_N,
                    zmax_choices=BATCH_ZMAX, max_trains: int = 2, duty: float = 0.05, snr=(5.0, 30.0),
-                   seg_len: int = 8192, workers: int = 1) -> BatchWorkload:
+                   seg_len: int = 8192, workers: int = 1, series=None) -> BatchWorkload:
     """Batching case: n_series series, each with N drawn from {2^21, 2^22, 2^23}, zmax from
     {20, 50, 84} (K = zmax + 1, taps from taps_for_zmax), 0 .. max_trains injected pulse trains
     (periods 1-20 ms, z uniform within 95% of the series' zmax, 5% duty, SNR 5-30), unit
     Gaussian noise, float32.  Series s draws from the generator seeded (config_index, s), so the
-    result does not depend on `workers` (processes started with spawn, filling shared memory)."""
-    shapes = _batch_shapes(config_index, n_series, n_choices, zmax_choices)
-    offsets = np.zeros(n_series, dtype=np.int64)
+    result does not depend on `workers` (processes started with spawn, filling shared memory).
+    `series` (optional): only these series indices of the n_series, packed in that order (one
+    rank's share of a batch split over GPUs); each is the same as in the whole batch."""
+    all_shapes = _batch_shapes(config_index, n_series, n_choices, zmax_choices)
+    index = list(range(n_series)) if series is None else [int(s) for s in series]
+    shapes = [all_shapes[s] for s in index]
+    offsets = np.zeros(len(index), dtype=np.int64)
     o = 0
-    for s, (n, _) in enumerate(shapes):
-        offsets[s] = o
+    for k, (n, _) in enumerate(shapes):
+        offsets[k] = o
         o += n
     total = o
-    jobs = [(config_index, s, tuple(n_choices), tuple(zmax_choices), tsamp, max_trains, duty, snr, int(offsets[s]), n)
-            for s, (n, zmax) in enumerate(shapes)]
+    jobs = [(config_index, s, tuple(n_choices), tuple(zmax_choices), tsamp, max_trains, duty, snr, int(offsets[k]), n)
+            for k, (s, (n, zmax)) in enumerate(zip(index, shapes))]
     trains = {}
     if workers <= 1:
         packed = np.empty(total, dtype=np.float32)
@@ -302,7 +306,7 @@ def batch_workload(config_index: int = 2, n_series: int = 256, tsamp: float = 64
             shm.close()
             shm.unlink()
     meta = []
-    for s, (n, zmax) in enumerate(shapes):
+    for s, (n, zmax) in zip(index, shapes):
         m = taps_for_zmax(zmax)
         meta.append(Workload(f"batch{config_index}_s{s}_n{n}_z{zmax}_m{m}", n, tsamp, zmax, m, seg_len,
                              np.empty(0, dtype=np.float32), trains[s]))

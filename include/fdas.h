@@ -200,7 +200,11 @@ fdas_status fdas_plane(fdas_plan_t plan, const float *d_xhat, void *d_workspace,
  *     (e.g. S = 8192 up to N = 2^23); larger ones return FDAS_E_UNSUPPORTED with the sizes in
  *     fdas_last_error.
  *   - The first call on a device looks up the array's device address (once per device, with
- *     that device current); make that first call before any stream capture.
+ *     that device current); make that first call before any stream capture.  The address is
+ *     kept for the life of the process: after cudaDeviceReset of that device, do not call
+ *     fdas_plane_static again in the same process.
+ *   - The plan's device (the one current at fdas_make_templates) must be current, else
+ *     FDAS_E_INVALID (with both device numbers in fdas_last_error).
  *   - All calls share the one array: calls whose work overlaps on the GPU (different streams,
  *     or different plans at once) race on it.  Each call overwrites the whole part it reads,
  *     so no clearing is needed between calls.

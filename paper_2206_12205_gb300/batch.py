@@ -34,6 +34,37 @@ def shard_series(costs: Sequence[int], world: int) -> List[List[int]]:
     return [sorted(p) for p in parts]
 
 
+def gather_peak_lists(mine: Sequence[int], lists: Sequence[np.ndarray], n_series: int, dist, dst: int = 0):
+    """After a sharded search: each rank holds the peak lists of its own series `mine` (in that
+    order, as its sub-batch numbered them).  Their `series` fields (where present) are set to the
+    series' index in the whole batch and the lists gathered on rank `dst`, which receives one list
+    per series of the whole batch (other ranks receive None).  Only these lists travel between
+    ranks; the search itself exchanges nothing."""
+    if len(mine) != len(lists):
+        raise ValueError("one peak list per series of the rank's share")
+    local = []
+    for s, a in zip(mine, lists):
+        a = np.array(a, copy=True)
+        if a.dtype.names and "series" in a.dtype.names:
+            a["series"] = int(s)
+        local.append((int(s), a))
+    world = dist.get_world_size()
+    parts = [None] * world if dist.get_rank() == dst else None
+    dist.gather_object(local, parts, dst=dst)
+    if dist.get_rank() != dst:
+        return None
+    out: List[Optional[np.ndarray]] = [None] * n_series
+    for part in parts:
+        for s, a in part:
+            if out[s] is not None:
+                raise RuntimeError(f"series {s} searched by two ranks")
+            out[s] = a
+    missing = [s for s, a in enumerate(out) if a is None]
+    if missing:
+        raise RuntimeError(f"series {missing[:8]} searched by no rank")
+    return out
+
+
 class BatchSearch:
     """A planned batch with its device buffers (torch-owned): workspace, peak regions, counts."""
 

@@ -492,6 +492,7 @@ void fdas_destroy(fdas_plan_t plan) {
         cudaFree(p->d_dimg);
         cudaFree(p->d_dsig);
         cudaFree(p->d_k4order);
+        cudaFree(p->d_k4order_a);
         cudaFree(p->d_status);
     }
     for (int s = 0; s < fdas::PROF_STAGES; s++)

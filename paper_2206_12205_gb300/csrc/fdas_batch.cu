@@ -82,8 +82,8 @@ fdas_status plan_one(const fdas_config &c, fdas_plan_s **out) {
 
 std::string group_key(const fdas_config &c) {
     char buf[160];
-    std::snprintf(buf, sizeof buf, "p%d:n%lld:z%d:m%d:s%d", c.precision, (long long)c.n_samples, c.zmax, c.taps,
-                  c.seg_len);
+    std::snprintf(buf, sizeof buf, "p%d:n%lld:z%d:m%d:s%d:h%d", c.precision, (long long)c.n_samples, c.zmax, c.taps,
+                  c.seg_len, c.harm_mode);
     return buf;
 }
 
@@ -466,6 +466,8 @@ fdas_status fdas_batch_make_templates(fdas_batch_t b, void *stream) {
         p->d_dsig = l->d_dsig;
         p->d_k4order = l->d_k4order;
         p->k4order_n = l->k4order_n;
+        p->d_k4order_a = l->d_k4order_a;
+        p->k4order_a_n = l->k4order_a_n;
         p->borrowed = true;
         e = cudaMalloc((void **)&p->d_status, sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);

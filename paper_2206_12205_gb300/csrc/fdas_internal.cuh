@@ -86,6 +86,8 @@ struct Plan {
     float2 *d_tcTw;        // W_4096^{n2 k1}, [k1][n2] (32 KB)
     uint32_t *d_k4order;   // ray order of level 2's (row << 16 | chunk group) blocks for k4_levels_ordered
     int64_t k4order_n;     // its length (rows x chunk groups)
+    uint32_t *d_k4order_a; // harm_mode 1: ray order of the whole plane's (row << 16 | 4-chunk group) blocks
+    int64_t k4order_a_n;   // its length (K x chunk groups)
     int32_t *d_status;     // sticky device status word
     bool templates_ready;
     bool borrowed;         // template bank and tables belong to another plan (a batch's group leader)
@@ -161,7 +163,7 @@ cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale,
 // marked units), or NULL for the full level-1 pass over the plane.
 // The ray order of level 2's blocks (host; false if the region does not fit the 16-bit fields),
 // and its upload into p.d_k4order at template time (synchronous copy).
-bool levels_order(const Plan &p, std::vector<uint32_t> &order);
+bool levels_order(const Plan &p, std::vector<uint32_t> &order, bool anchored = false);
 cudaError_t upload_levels_order(Plan &p);
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
                          fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st,

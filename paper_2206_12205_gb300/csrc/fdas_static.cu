@@ -24,14 +24,13 @@ static __device__ __align__(256) unsigned char g_plane_scratch[kScratchBytes];
 std::mutex g_mutex;
 void *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_plane_scratch on the current device (looked up once per device; in
-// host code the symbol name itself is only a host-side stand-in, never a device address).
-cudaError_t scratch_on_current_device(void **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+// Device address of g_plane_scratch on device dev, which must be current (looked up once per
+// device; in host code the symbol name itself is only a host-side stand-in, never a device
+// address).
+cudaError_t scratch_on_device(int dev, void **out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mutex);
+    cudaError_t e = cudaSuccess;
     if (!g_scratch_addr[dev]) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_plane_scratch);
@@ -62,8 +61,19 @@ extern "C" fdas_status fdas_plane_static(fdas_plan_t plan, const float *d_xhat, 
         p->last_error = msg;
         return FDAS_E_UNSUPPORTED;
     }
+    // the plan's templates and twiddles live on the device it was built on: the scratch must be
+    // that device's copy of the array
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && dev != p->device) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "fdas_plane_static: device %d is current, the plan's templates are on device %d",
+                      dev, p->device);
+        p->last_error = msg;
+        return FDAS_E_INVALID;
+    }
     void *scratch = nullptr;
-    cudaError_t e = scratch_on_current_device(&scratch);
+    if (e == cudaSuccess) e = scratch_on_device(dev, &scratch);
     if (e == cudaSuccess) {
         p->prof.calls++;
         e = fdas::launch_plane_fp32_scratch(*p, reinterpret_cast<const float2 *>(d_xhat), nullptr,

@@ -201,27 +201,33 @@ __device__ __forceinline__ bool row_in_level(int i, int K, int zmax, int H) {
 // 32 e), l < 32 -- a span of 32 h elements, whole sectors -- instead of 32 lanes each touching
 // their own sectors.  s[e] += P(h r, i_h) for the lane's bins r = rb + 32 e with r <= rmax (then
 // h r <= H rmax < Nb); the sums keep the order h = 1..H.
-template <typename E>
-__device__ __forceinline__ void add_harmonic(const E *__restrict__ row, int h, int64_t rb, int64_t rmax, float (&s)[LB]) {
-    float v[LB];
-#pragma unroll
-    for (int e = 0; e < LB; e++) {
-        const int64_t r = rb + 32 * e;
-        v[e] = r <= rmax ? ld_plane(row, (int64_t)h * r) : 0.0f;
-    }
-#pragma unroll
-    for (int e = 0; e < LB; e++) s[e] = __fadd_rn(s[e], v[e]);
-}
-
-// S_H from S_{H/2}: the new harmonics h = H/2 + 1 .. H in order.
+// S_H from S_{H/2}: the new harmonics h = H/2 + 1 .. H in order, the loads of FDAS_K4_HBATCH
+// harmonics in flight together (16 per harmonic and lane; the adds keep the order h = 1..H).
+#ifndef FDAS_K4_HBATCH
+#define FDAS_K4_HBATCH 1                 // 2 measured 0.210 ms against 0.180 ms for 1 (BF16, N = 2^23)
+#endif
 template <typename E, int H>
 __device__ __forceinline__ void add_level(const E *__restrict__ plane, int64_t nb, int zmax, int z, int64_t rb,
                                           int64_t rmax, float (&s)[LB]) {
+    constexpr int NB = FDAS_K4_HBATCH < H / 2 ? FDAS_K4_HBATCH : H / 2;
 #pragma unroll
-    for (int q = 0; q < H / 2; q++) {
-        const int h = H / 2 + 1 + q;
-        add_harmonic<E>(plane + (int64_t)((h * z + zmax) >> 1) * nb, h, rb, rmax, s);
-        // keep one harmonic's loads in flight at a time (bounds the registers of levels 8, 16)
+    for (int q0 = 0; q0 < H / 2; q0 += NB) {
+        float v[NB][LB];
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            const int h = H / 2 + 1 + q0 + q;
+            const E *row = plane + (int64_t)((h * z + zmax) >> 1) * nb;
+#pragma unroll
+            for (int e = 0; e < LB; e++) {
+                const int64_t r = rb + 32 * e;
+                v[q][e] = r <= rmax ? ld_plane(row, (int64_t)h * r) : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NB; q++)
+#pragma unroll
+            for (int e = 0; e < LB; e++) s[e] = __fadd_rn(s[e], v[q][e]);
+        // bound the loads in flight (the registers of levels 8, 16)
         asm volatile("" ::: "memory");
     }
 }
@@ -414,7 +420,7 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32) k4_level1_marked(const E *_
 }
 
 // Levels 2 .. 16 of one (row i, CPW chunks from c0) of level 2's region: each warp re-reads S_1
-// of its chunks (interleaved bins, see add_harmonic) and carries the running sums through the
+// of its chunks (interleaved bins, see add_level) and carries the running sums through the
 // levels in registers.
 template <typename E>
 __device__ __forceinline__ void levels_group(const E *__restrict__ plane, int64_t nb, int zmax, int K,
@@ -494,7 +500,9 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_leve
 #endif
 // S_L from S_{L/2} for the anchored sums: the odd harmonics j < L in increasing order, the loads
 // of FDAS_K4A_BATCH harmonics in flight together (16 per harmonic and lane).  2 j r + L < 2^31 (r < Nb <= 2^26, j < 16),
-// so the index arithmetic is 32-bit.
+// so the index arithmetic is 32-bit.  Lane bin r = rb + 32 e gathers at (2 j r + L) >> (LOG + 1) =
+// ((2 j rb + L) >> (LOG + 1)) + 32 j e / L exactly (64 j e is a multiple of 2 L for L <= 32), so one
+// index per harmonic and lane serves all 16 loads, which then differ by compile-time offsets.
 template <typename E, int LOG>
 __device__ __forceinline__ void anch_add_level(const E *__restrict__ plane, int64_t nb, int zmax, int z, uint32_t rb,
                                                float (&s)[LB]) {
@@ -508,10 +516,11 @@ __device__ __forceinline__ void anch_add_level(const E *__restrict__ plane, int6
             const int j = j0 + 2 * q;
             if (j < L) {
                 const int ij = (j * z + L * zmax + L) >> (LOG + 1);
-                const E *rowj = plane + (int64_t)ij * nb;
-                const uint32_t b = 2u * (uint32_t)j * rb + (uint32_t)L;
+                const uint32_t b = (2u * (uint32_t)j * rb + (uint32_t)L) >> (LOG + 1);
+                const E *rowj = plane + (int64_t)ij * nb + b;
+                static_assert(LOG + 1 <= 6, "the e-offsets are exact while 2 L divides 64");
 #pragma unroll
-                for (int e = 0; e < LB; e++) v[q][e] = ld_plane(rowj, (int64_t)((b + 64u * (uint32_t)(j * e)) >> (LOG + 1)));
+                for (int e = 0; e < LB; e++) v[q][e] = ld_plane(rowj, (int64_t)((64 * j * e) >> (LOG + 1)));
             }
         }
 #pragma unroll
@@ -558,16 +567,12 @@ __device__ __forceinline__ void anch_unit(const E *__restrict__ plane, int64_t n
     }
 }
 
+// Levels 2 .. 16 of the anchored sums for one (row i, chunk c), lane bins rb + 32 e.
 template <typename E>
-__global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4a_levels(const E *__restrict__ plane, int64_t nb,
-                                                                               int zmax, int K, LevelTable lt,
-                                                                               int chunks,
-                                                                               int32_t *__restrict__ unit_count,
-                                                                               uint32_t *__restrict__ unit_mask) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int i = blockIdx.x;
-    const int c = blockIdx.y * DETECT_WARPS + w;
-    if (c >= chunks) return;                         // warp-uniform
+__device__ __forceinline__ void anch_chunk(const E *__restrict__ plane, int64_t nb, int zmax, int K, const LevelTable &lt,
+                                           int i, int c, int32_t *__restrict__ unit_count,
+                                           uint32_t *__restrict__ unit_mask) {
+    const int lane = threadIdx.x & 31;
     const int z = -zmax + 2 * i;
     const int64_t rb = (int64_t)c * CB + lane;
     float s[LB];
@@ -587,6 +592,32 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4a_lev
     if (lt.n_levels < 5) return;
     anch_add_level<E, 4>(plane, nb, zmax, z, (uint32_t)rb, s);
     anch_unit<E>(plane, nb, zmax, K, lt.lev[4], 16, i, c, rb, s, unit_count, unit_mask);
+}
+
+template <typename E>
+__global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4a_levels(const E *__restrict__ plane, int64_t nb,
+                                                                               int zmax, int K, LevelTable lt,
+                                                                               int chunks,
+                                                                               int32_t *__restrict__ unit_count,
+                                                                               uint32_t *__restrict__ unit_mask) {
+    const int c = blockIdx.y * DETECT_WARPS + (threadIdx.x >> 5);
+    if (c >= chunks) return;                         // warp-uniform
+    anch_chunk<E>(plane, nb, zmax, K, lt, blockIdx.x, c, unit_count, unit_mask);
+}
+
+// The anchored levels in the ray order of upload_levels_order (whole plane, entries
+// row << 16 | chunk group): the gathers of cell (r, z) lie on the segment from the origin to
+// (r, z), so blocks taken by increasing z / r read each plane sector within a short stretch of
+// the kernel's progress (from DRAM about once, where the row-major grid re-fetches the sectors of
+// each fraction j / L of the chunk positions).  One block per entry.
+template <typename E>
+__global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4a_levels_ordered(
+    const E *__restrict__ plane, int64_t nb, int zmax, int K, LevelTable lt, int chunks,
+    const uint32_t *__restrict__ order, int32_t *__restrict__ unit_count, uint32_t *__restrict__ unit_mask) {
+    const uint32_t o = __ldg(order + blockIdx.x);
+    const int c = (int)(o & 0xffffu) * DETECT_WARPS + (threadIdx.x >> 5);
+    if (c >= chunks) return;                         // warp-uniform
+    anch_chunk<E>(plane, nb, zmax, K, lt, (int)(o >> 16), c, unit_count, unit_mask);
 }
 
 // Second level (the last block of k4_scan_blocks, 1024 threads, fixed order): block offsets in
@@ -783,9 +814,15 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
     p.prof.end(PROF_PEAKS_LEVEL1, st);
     if (lt.n_levels > 1 && lt.anchored) {
         p.prof.begin(PROF_PEAKS_LEVELS, st);
-        const dim3 agrid((unsigned)p.K, (unsigned)((chunks1 + DETECT_WARPS - 1) / DETECT_WARPS));
-        k4a_levels<E><<<agrid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks1, unit_count,
-                                                           unit_mask);
+        const int64_t agroups = (chunks1 + DETECT_WARPS - 1) / DETECT_WARPS;
+        if (p.d_k4order_a && p.k4order_a_n == (int64_t)p.K * agroups) {
+            k4a_levels_ordered<E><<<(unsigned)p.k4order_a_n, DETECT_WARPS * 32, 0, st>>>(
+                plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks1, p.d_k4order_a, unit_count, unit_mask);
+        } else {
+            const dim3 agrid((unsigned)p.K, (unsigned)agroups);
+            k4a_levels<E><<<agrid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks1,
+                                                               unit_count, unit_mask);
+        }
         p.prof.end(PROF_PEAKS_LEVELS, st);
     } else if (lt.n_levels > 1) {
         p.prof.begin(PROF_PEAKS_LEVELS, st);
@@ -857,10 +894,10 @@ LevelTable make_levels(const Plan &p) {
 // progress, so it comes from DRAM about once; row by row (k4_levels) the harmonic rows of rows
 // far apart are fetched again, about twice the bytes.  Built for level 2's region whatever
 // max_harm and harm_mode say, so that plans of one shape can share it.
-bool levels_order(const Plan &p, std::vector<uint32_t> &order) {
+bool levels_order(const Plan &p, std::vector<uint32_t> &order, bool anchored) {
     LevelDesc d{};
-    level_region(p, 2, false, d);
-    const int64_t per = DETECT_WARPS * CPW;           // chunks per block
+    level_region(p, 2, anchored, d);                  // anchored: the whole plane
+    const int64_t per = DETECT_WARPS * (anchored ? 1 : CPW);   // chunks per block
     const int64_t groups = (d.chunks + per - 1) / per;
     if (d.rows >= (1 << 16) || groups >= (1 << 16)) return false;
     struct Item {
@@ -883,11 +920,18 @@ bool levels_order(const Plan &p, std::vector<uint32_t> &order) {
 
 cudaError_t upload_levels_order(Plan &p) {
     std::vector<uint32_t> order;
-    if (!levels_order(p, order)) return cudaErrorInvalidValue;
+    if (!levels_order(p, order, false)) return cudaErrorInvalidValue;
     p.k4order_n = (int64_t)order.size();
     cudaError_t e = cudaMalloc((void **)&p.d_k4order, sizeof(uint32_t) * order.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(p.d_k4order, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice);
+    // the anchored sums' whole-plane order, for plans that use them
+    if (e == cudaSuccess && p.cfg.harm_mode == 1 && levels_order(p, order, true)) {
+        p.k4order_a_n = (int64_t)order.size();
+        e = cudaMalloc((void **)&p.d_k4order_a, sizeof(uint32_t) * order.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p.d_k4order_a, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice);
+    }
     return e;
 }
 

@@ -175,3 +175,81 @@ def test_shard_and_gather_two_gloo_ranks(tmp_path):
     assert res["parts"] == fb.shard_series(costs, 2)
     assert res["series"] == list(range(len(costs)))
     assert abs(res["loads"][0] - res["loads"][1]) <= max(costs)
+
+
+# ------------------------------------------------------------------ sharded search, gathered lists
+SHARD_KW = dict(config_index=85, n_series=7, n_choices=(1 << 12, 1 << 13), zmax_choices=(4, 8), snr=(20.0, 40.0))
+SHARD_THR = (14.0, 18.0, 22.0)
+
+
+def _oracle_lists(wl):
+    """Each series' peak list from the FP64 oracle's whole search (the stand-in for a rank's batch
+    search on a machine without a GPU), with the series field a rank's sub-batch would give it."""
+    import oracle
+    out = []
+    for k, w in enumerate(wl.series):
+        x = wl.packed[int(wl.offsets[k]): int(wl.offsets[k]) + w.n]
+        pk = oracle.search(x, w.zmax, w.taps, 4, SHARD_THR)["peaks"]
+        a = np.zeros(len(pk), dtype=fbind.PEAK_DTYPE)
+        a["series"] = k
+        a["r"], a["zi"], a["harm"], a["power"] = pk["r"], pk["zi"], pk["h"], pk["power"]
+        out.append(a)
+    return out
+
+
+def _shard_rank(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        shapes = synth._batch_shapes(SHARD_KW["config_index"], SHARD_KW["n_series"], SHARD_KW["n_choices"],
+                                     SHARD_KW["zmax_choices"])
+        mine = fb.shard_series([fb.series_cost(n, z) for n, z in shapes], world)[rank]
+        wl = synth.batch_workload(series=mine, **SHARD_KW)       # only this rank's series
+        lists = fb.gather_peak_lists(mine, _oracle_lists(wl), SHARD_KW["n_series"], dist)
+        if rank == 0:
+            np.savez(out_path, *lists)
+        else:
+            assert lists is None
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_search_gathers_the_single_rank_lists(tmp_path):
+    """Two gloo ranks each search only their share of a batch (split by shard_series, inputs
+    synthesised per rank) and gather the per-series lists on rank 0: the result equals one
+    process searching the whole batch, list for list, with each record's series field the
+    series' index in the whole batch."""
+    import oracle
+    import torch.multiprocessing as tmp
+    oracle.build()
+    out = str(tmp_path / "lists.npz")
+    tmp.spawn(_shard_rank, args=(2, _free_port(), out), nprocs=2, join=True)
+    got = np.load(out)
+    whole = _oracle_lists(synth.batch_workload(**SHARD_KW))
+    assert len(got.files) == len(whole) == SHARD_KW["n_series"]
+    assert sum(len(a) for a in whole) > 0
+    for s, want in enumerate(whole):
+        g = got[f"arr_{s}"]
+        assert np.all(g["series"] == s)
+        want = want.copy()
+        want["series"] = s
+        assert g.tobytes() == want.tobytes()
+
+
+def test_gather_rejects_overlapping_shares():
+    class FakeDist:                                   # one process standing in for rank 0 of two
+        def get_world_size(self):
+            return 2
+
+        def get_rank(self):
+            return 0
+
+        def gather_object(self, obj, parts, dst=0):
+            parts[0] = obj
+            parts[1] = obj                            # the other rank searched the same series
+
+    a = np.zeros(1, dtype=fbind.PEAK_DTYPE)
+    with pytest.raises(RuntimeError):
+        fb.gather_peak_lists([0], [a], 2, FakeDist())
