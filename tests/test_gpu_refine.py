@@ -215,6 +215,57 @@ def _crb_sigma(P):
     return np.sqrt(48.0 / (math.pi ** 2 * P)), np.sqrt(180.0 / (math.pi ** 2 * P))
 
 
+# Fisher-matrix inverse of (r, z) per unit peak power: Cov = CRB_COV / P (noise mean 2), with the
+# errors strongly anti-correlated (rho = -90 / sqrt(48 180) = -0.968), so the joint test of a 2-D
+# error is its Mahalanobis distance d^2 = delta' Cov^-1 delta, chi^2 with 2 degrees of freedom for
+# an estimator at the bound: mean 2, and d^2 <= 11.83 with the 3-sigma probability 0.9973.
+CRB_COV = np.array([[48.0, -90.0], [-90.0, 180.0]]) / math.pi ** 2
+D2_3SIGMA = 11.829
+
+
+def _mahalanobis2(delta, P):
+    return np.einsum("ni,ij,nj->n", delta, np.linalg.inv(CRB_COV), delta) * np.asarray(P, dtype=np.float64)
+
+
+@pytest.mark.parametrize("p0", [30.0, 240.0])
+def test_refine_attains_the_cramer_rao_bound(p0):
+    """Independent noise realisations: 500 chirps of peak power p0 (unit noise, sigma2 = N fixed),
+    256 bins apart in one series so that each sees its own noise, refined from the nearest integer
+    bins.  At p0 = 240 the scatter of the refined points about the truths is the bound's: mean d^2
+    near 2, 3-sigma coverage near 0.9973, per-axis variances within a few tens of percent of the
+    bound, no bias.  At p0 = 30 (the detection threshold of the differentiation workload) the
+    maximum-likelihood scatter exceeds the bound, as it does near threshold (measured: variance
+    ratios ~1.35, mean d^2 ~2.8, coverage ~0.97)."""
+    n, m, count = 1 << 18, 64, 500
+    rng = np.random.default_rng(int(p0) + 17)
+    r0 = 512 + 256 * np.arange(count) + rng.uniform(-0.5, 0.5, count)
+    z0 = rng.uniform(-10.0, 10.0, count)
+    x = rng.standard_normal(n)
+    amp = math.sqrt(2.0 * p0 / n)                    # peak power p0 with sigma2 = N
+    for k in range(count):
+        x += synth.chirp(n, amp, r0[k], z0[k], rng.uniform(0.0, 2.0 * math.pi))
+    s = fd.Search(fd.make_config(n, 2, m, 1024, sigma2=float(n)))
+    xh = s.spectrum(torch.from_numpy(x.astype(np.float32)).cuda()).clone()
+    seeds = _pts(np.stack([np.round(r0), np.round(z0)], 1))
+    pts, power, _ = rf.refine(s.plan, xh, seeds, steps=20)
+    torch.cuda.synchronize()
+    delta = pts.cpu().numpy() - np.stack([r0, z0], 1)
+    d2 = _mahalanobis2(delta, p0)
+    cov = np.cov(delta.T) * p0
+    ratio = (cov[0, 0] / CRB_COV[0, 0], cov[1, 1] / CRB_COV[1, 1])
+    cover = np.mean(d2 <= D2_3SIGMA)
+    print(f"p0 {p0}: mean d2 {d2.mean():.3f}, coverage {cover:.4f}, variance / bound {ratio[0]:.3f} {ratio[1]:.3f}")
+    if p0 >= 100.0:
+        assert 1.6 <= d2.mean() <= 2.6
+        assert cover >= 0.98
+        assert 0.8 <= ratio[0] <= 1.3 and 0.8 <= ratio[1] <= 1.3
+        sr, sz = math.sqrt(CRB_COV[0, 0] / p0), math.sqrt(CRB_COV[1, 1] / p0)
+        assert abs(delta[:, 0].mean()) <= 0.15 * sr and abs(delta[:, 1].mean()) <= 0.15 * sz
+    else:
+        assert d2.mean() <= 3.5 and cover >= 0.93
+        assert ratio[0] <= 1.8 and ratio[1] <= 1.8
+
+
 def test_refine_matches_oracle_ascent():
     """Noisy chirps (P ~ 82 in unit noise), seeds at the nearest integer bins of the truth and at
     uniform offsets within half a bin: the device ascent (20 FP32 steps + 1 FP64 step) against
@@ -356,3 +407,24 @@ def test_refine_full_size_sampled():
     # near the detection threshold (P ~ 30) the maximum-likelihood scatter exceeds the bound
     # and a few seeds climb a neighbouring noise peak instead
     assert inside.mean() >= 0.8
+    # Per truth, the seeds end on the local maxima of that truth's noise realisation.  A truth has a
+    # dominant peak when most of its seeds end on its highest maximum; candidates on a dominant peak
+    # pass the joint 3-sigma test (Mahalanobis, the errors being strongly correlated along
+    # dr ~ -dz / 2); a truth without one is lost to the noise (measured: one of the 16, whose seeds
+    # climb 42 maxima, the highest a noise peak 1.7 bins and 2.9 z-bins away).
+    on_peak = np.zeros(pts.shape[0], dtype=bool)
+    lost = 0
+    for t in range(wl.truths.shape[0]):
+        sel = np.flatnonzero(wl.truth_index == t)
+        top = pts[sel[np.argmax(power[sel, 0])]]
+        on = np.all(np.abs(pts[sel] - top) <= [0.01, 0.02], axis=1)
+        if on.mean() >= 0.5:
+            on_peak[sel[on]] = True
+        else:
+            lost += 1
+    d2 = _mahalanobis2(pts - tr, power[:, 0])
+    cover = np.mean(d2[on_peak] <= D2_3SIGMA)
+    print("on a dominant peak", on_peak.mean(), "lost truths", lost, "joint 3-sigma coverage there", cover,
+          "mean d2", d2[on_peak].mean())
+    assert lost <= 2 and on_peak.mean() >= 0.8
+    assert cover >= 0.97
