@@ -170,8 +170,11 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
     p->ws_ucount = off; off = align_up(off + sizeof(int32_t) * (size_t)p->n_units);
     p->ws_uoff = off;   off = align_up(off + sizeof(int32_t) * (size_t)p->n_units);
     p->ws_umask = off;  off = align_up(off + sizeof(uint32_t) * (fdas::PEAK_CHUNK / 32) * (size_t)p->n_units);
-    p->ws_ublock = off; off = align_up(off + sizeof(int64_t) * (n_scan_blocks + 1));   // + the scan's ticket
+    // block sums + the scan's ticket + the level search's work count
+    p->ws_ublock = off; off = align_up(off + sizeof(int64_t) * (n_scan_blocks + 2));
     p->ws_l1flag = off; off = align_up(off + (size_t)p->K * (size_t)(p->nb / fdas::PEAK_CHUNK));
+    // the level search's work list (the entries of its block order that are not skipped)
+    p->ws_k4work = off; off = align_up(off + sizeof(uint32_t) * (size_t)std::max<int64_t>(1, fdas::levels_order_size(*p)));
     p->ws_bytes = off;
     p->device = -1;
     *plan = p;

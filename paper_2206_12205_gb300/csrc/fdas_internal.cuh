@@ -69,7 +69,7 @@ struct Plan {
     int64_t n_units;
     // workspace layout (byte offsets inside the caller's workspace)
     size_t ws_x, ws_tmp, ws_part, ws_scale, ws_y, ws_segscale, ws_ucount, ws_uoff, ws_umask, ws_ublock, ws_l1flag,
-        ws_bytes;
+        ws_k4work, ws_bytes;
     int n_part;
     // plan-owned device memory
     int device;
@@ -156,6 +156,14 @@ cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_sc
                              cudaStream_t st, uint8_t *l1flag = nullptr);
 // Whether the plan's plane kernel marks the level-1 units (every precision's plane kernel).
 bool level1_fusable(const Plan &p);
+// The threshold of the plane kernels' unit marks: a 512-bin unit is marked when it holds a stored
+// value above min(thr[0], thr[1] / 2) (thr[0] alone without level 2).  The level-1 pass visits
+// only marked units and tests them against thr[0]; the level search skips a chunk outside level
+// 4's region whose unit and its second harmonic's two units are unmarked, since there every
+// P(r) + P(2 r) rounds to at most 2 (thr[1] / 2) = thr[1] (exact halving, monotone rounding).
+inline float mark_threshold(const Plan &p) {
+    return p.cfg.max_harm >= 2 ? fminf(p.cfg.thr[0], p.cfg.thr[1] * 0.5f) : p.cfg.thr[0];
+}
 // The plane of the plan's precision from a spectrum (x: Nb complex; scale: device factor or NULL).
 cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale, char *ws, void *d_plane,
                              cudaStream_t st, uint8_t *l1flag = nullptr);
@@ -164,6 +172,7 @@ cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale,
 // The ray order of level 2's blocks (host; false if the region does not fit the 16-bit fields),
 // and its upload into p.d_k4order at template time (synchronous copy).
 bool levels_order(const Plan &p, std::vector<uint32_t> &order, bool anchored = false);
+int64_t levels_order_size(const Plan &p);   // entries of the plain order (level 2's region)
 cudaError_t upload_levels_order(Plan &p);
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
                          fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st,

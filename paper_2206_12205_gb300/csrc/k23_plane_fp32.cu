@@ -174,7 +174,7 @@ cudaError_t run_correlate(const Plan &p, const float2 *Y, float *plane, cudaStre
     }
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_fp32<S, DB, MINB, PRE><<<(unsigned)grid, S / 16, smem, st>>>(Y, p.d_G, p.d_tw, plane, p.K, groups, p.nb,
-                                                                        p.L, l1flag, p.nb / PEAK_CHUNK, p.cfg.thr[0]);
+                                                                        p.L, l1flag, p.nb / PEAK_CHUNK, mark_threshold(p));
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 1;
     return cudaGetLastError();

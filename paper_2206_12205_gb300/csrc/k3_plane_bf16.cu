@@ -840,7 +840,7 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_tc<OpsBF16><<<(unsigned)grid, WS_THREADS, WS_SMEM, st>>>(
         Y, reinterpret_cast<const uint4 *>(p.d_Gbf), reinterpret_cast<const uint4 *>(p.d_tcF) + 2 * TILE_BYTES / 16,
-        p.d_tcTw, d_plane, p.K, p.nb, p.L, n_items, n_groups, per, nullptr, l1flag, p.nb / PEAK_CHUNK, p.cfg.thr[0],
+        p.d_tcTw, d_plane, p.K, p.nb, p.L, n_items, n_groups, per, nullptr, l1flag, p.nb / PEAK_CHUNK, mark_threshold(p),
         p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 2;
@@ -876,7 +876,7 @@ cudaError_t launch_plane_f16(const Plan &p, const float2 *d_x, const float *d_sc
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_tc<OpsF16><<<(unsigned)grid, WS_THREADS, WS_SMEM, st>>>(
         Y, reinterpret_cast<const uint4 *>(p.d_Gh), reinterpret_cast<const uint4 *>(p.d_tcFh), p.d_tcTw, d_plane,
-        p.K, p.nb, p.L, n_items, n_groups, per, unscale, l1flag, p.nb / PEAK_CHUNK, p.cfg.thr[0], p.d_status);
+        p.K, p.nb, p.L, n_items, n_groups, per, unscale, l1flag, p.nb / PEAK_CHUNK, mark_threshold(p), p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 2;
     return cudaGetLastError();

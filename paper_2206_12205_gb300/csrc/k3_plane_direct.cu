@@ -539,7 +539,7 @@ cudaError_t launch_plane_direct_f8(const Plan &p, const float2 *d_x, const float
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_direct_f8<<<(unsigned)grid, D_WARPS * 32, smem, st>>>(d_x, d_scale, reinterpret_cast<const uint4 *>(p.d_dimg),
                                                                    p.d_dsig, d_plane, p.K, G, p.m, p.nb, n_tiles, per,
-                                                                   l1flag, p.nb / PEAK_CHUNK, p.cfg.thr[0], p.d_status);
+                                                                   l1flag, p.nb / PEAK_CHUNK, mark_threshold(p), p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 1;
     return cudaGetLastError();
@@ -592,7 +592,7 @@ cudaError_t launch_plane_direct(const Plan &p, const float2 *d_x, const float *d
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_direct<<<(unsigned)grid, D_WARPS * 32, smem, st>>>(Xb, reinterpret_cast<const uint4 *>(p.d_dimg), d_plane,
                                                                 p.K, Kpad, p.m, p.nb, n_tiles, per, cols, l1flag,
-                                                                p.nb / PEAK_CHUNK, p.cfg.thr[0], p.d_status);
+                                                                p.nb / PEAK_CHUNK, mark_threshold(p), p.d_status);
     p.prof.end(FDAS_STAGE_CORRELATE, st);
     p.prof.launches += 2;
     return cudaGetLastError();

@@ -354,7 +354,10 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_L1_MIN_BLOCKS) k4_l
                                                               unsigned int *__restrict__ ticket) {
     constexpr int CPW1 = Fmt<E>::EPV == 8 ? 4 : 2;
     const int lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ticket = 0;   // k4_scan_blocks' count
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        ticket[0] = 0;                               // k4_scan_blocks' count
+        ticket[2] = 0;                               // k4_levels_select's (int64 slot after the ticket)
+    }
     const int i = blockIdx.y;
     const int c0 = (blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * CPW1;
     if (c0 >= chunks1) return;                       // warp-uniform
@@ -395,7 +398,10 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32) k4_level1_marked(const E *_
                                                                     uint32_t *__restrict__ unit_mask,
                                                                     unsigned int *__restrict__ ticket) {
     const int lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;                      // k4_scan_blocks' count
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ticket[0] = 0;                               // k4_scan_blocks' count
+        ticket[2] = 0;                               // k4_levels_select's (int64 slot after the ticket)
+    }
     const int64_t u0 = ((int64_t)blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * 32;
     if (u0 >= n_units1) return;                      // warp-uniform
     const int64_t u = u0 + lane;
@@ -422,12 +428,31 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32) k4_level1_marked(const E *_
 // Levels 2 .. 16 of one (row i, CPW chunks from c0) of level 2's region: each warp re-reads S_1
 // of its chunks (interleaved bins, see add_level) and carries the running sums through the
 // levels in registers.
+//   With the plane kernel's unit marks (l2mark: the units holding a stored value above
+// mark_threshold <= thr[1] / 2), a chunk outside level 4's region whose unit and the two units of
+// its second harmonic are all unmarked is skipped: every P(r) and P(2 r) there is at most
+// thr[1] / 2, so S_2 = P(r) + P(2 r) rounds to at most thr[1] (rounded addition is monotone and
+// 2 (thr[1] / 2) is exact) and no cell can be a level-2 peak; its unit counts zero without reading
+// the plane.  On a noise plane (mean 2) about one 512-bin unit in a hundred holds a value above
+// thr[1] / 2 for the thresholds of the searches here, so most of these chunks are skipped.
 template <typename E>
 __device__ __forceinline__ void levels_group(const E *__restrict__ plane, int64_t nb, int zmax, int K,
                                              const LevelTable &lt, int chunks2, int i, int c0,
-                                             int32_t *__restrict__ unit_count, uint32_t *__restrict__ unit_mask) {
+                                             int32_t *__restrict__ unit_count, uint32_t *__restrict__ unit_mask,
+                                             const uint8_t *__restrict__ l2mark) {
     const int lane = threadIdx.x & 31;
     const int z = -zmax + 2 * i;
+    if (l2mark != nullptr && CPW == 1 &&
+        (lt.n_levels < 3 || !row_in_level(i, K, zmax, 4) || (int64_t)c0 * CB > lt.lev[2].rmax)) {
+        const int64_t chunks1 = lt.lev[0].chunks;
+        const int i2 = (2 * z + zmax) >> 1;
+        const int64_t mu = lane == 0 ? (int64_t)i * chunks1 + c0 : (int64_t)i2 * chunks1 + 2 * c0 + (lane - 1);
+        const bool marked = lane < 3 && __ldg(l2mark + mu) != 0;
+        if (!__any_sync(0xffffffffu, marked)) {
+            if (lane == 0) unit_count[(int)lt.lev[1].unit0 + (i - lt.lev[1].i_lo) * (int)lt.lev[1].chunks + c0] = 0;
+            return;
+        }
+    }
     const E *row = plane + (int64_t)i * nb;
     const E *row2 = plane + (int64_t)((2 * z + zmax) >> 1) * nb;      // harmonic 2
     const int64_t rmax2 = lt.lev[1].rmax;
@@ -459,10 +484,57 @@ template <typename E>
 __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_levels(const E *__restrict__ plane, int64_t nb, int zmax, int K,
                                                               LevelTable lt, int chunks2,
                                                               int32_t *__restrict__ unit_count,
-                                                              uint32_t *__restrict__ unit_mask) {
+                                                              uint32_t *__restrict__ unit_mask,
+                                                              const uint8_t *__restrict__ l2mark) {
     const int c0 = (blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * CPW;
     if (c0 >= chunks2) return;                       // warp-uniform
-    levels_group<E>(plane, nb, zmax, K, lt, chunks2, lt.lev[1].i_lo + blockIdx.y, c0, unit_count, unit_mask);
+    levels_group<E>(plane, nb, zmax, K, lt, chunks2, lt.lev[1].i_lo + blockIdx.y, c0, unit_count, unit_mask, l2mark);
+}
+
+// Whether chunk c of row i (in level 2's region) can hold a level-2 .. peak given the plane
+// kernel's unit marks: always inside level 4's region; outside it only when its unit or one of the
+// two units of its second harmonic is marked (see levels_group).
+__device__ __forceinline__ bool chunk_needs_search(const uint8_t *__restrict__ marks, int64_t chunks1, int zmax, int K,
+                                                   const LevelTable &lt, int i, int c) {
+    if (lt.n_levels >= 3 && row_in_level(i, K, zmax, 4) && (int64_t)c * CB <= lt.lev[2].rmax) return true;
+    const int i2 = (2 * (-zmax + 2 * i) + zmax) >> 1;
+    return __ldg(marks + (int64_t)i * chunks1 + c) | __ldg(marks + (int64_t)i2 * chunks1 + 2 * c) |
+           __ldg(marks + (int64_t)i2 * chunks1 + 2 * c + 1);
+}
+
+// The level search's work list: one thread per entry of the block order (row << 16 | 4-chunk
+// group); an entry is kept when any of its chunks needs the search (chunk_needs_search), else its
+// chunks' level-2 units count zero here.  Kept entries are appended per warp in the order's order
+// (ballot prefix, one atomic per warp), so the list keeps the ray order's locality; *count was
+// zeroed by the level-1 pass.
+__global__ void __launch_bounds__(256) k4_levels_select(const uint32_t *__restrict__ order, int64_t n_order,
+                                                        const uint8_t *__restrict__ marks, int zmax, int K,
+                                                        LevelTable lt, int chunks2, uint32_t *__restrict__ work,
+                                                        unsigned int *__restrict__ count,
+                                                        int32_t *__restrict__ unit_count) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool keep = false;
+    uint32_t o = 0;
+    if (k < n_order) {
+        o = __ldg(order + k);
+        const int a = (int)(o >> 16);
+        if (a < lt.lev[1].rows) {
+            const int i = lt.lev[1].i_lo + a;
+            const int64_t chunks1 = lt.lev[0].chunks;
+            const int c0 = (int)(o & 0xffffu) * DETECT_WARPS * CPW;
+            for (int w = 0; w < DETECT_WARPS * CPW && c0 + w < chunks2; w++)
+                keep |= chunk_needs_search(marks, chunks1, zmax, K, lt, i, c0 + w);
+            if (!keep)
+                for (int w = 0; w < DETECT_WARPS * CPW && c0 + w < chunks2; w++)
+                    unit_count[(int)lt.lev[1].unit0 + a * (int)lt.lev[1].chunks + c0 + w] = 0;
+        }
+    }
+    const uint32_t b = __ballot_sync(0xffffffffu, keep);
+    unsigned int base = 0;
+    if (lane == 0 && b) base = atomicAdd(count, (unsigned int)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) work[base + __popc(b & ((1u << lane) - 1u))] = o;
 }
 
 // Level 2's region in the ray order of upload_levels_order, each entry a (row << 16 | chunk
@@ -474,8 +546,11 @@ template <typename E>
 __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_levels_ordered(const E *__restrict__ plane, int64_t nb, int zmax, int K,
                                                                       LevelTable lt, int chunks2,
                                                                       const uint32_t *__restrict__ order, int64_t n_order,
+                                                                      const unsigned int *__restrict__ d_count,
                                                                       int32_t *__restrict__ unit_count,
-                                                                      uint32_t *__restrict__ unit_mask) {
+                                                                      uint32_t *__restrict__ unit_mask,
+                                                                      const uint8_t *__restrict__ l2mark) {
+    if (d_count != nullptr) n_order = *d_count;   // a work list (k4_levels_select), written before this launch
     int64_t idx = blockIdx.x;
     uint32_t next = idx < n_order ? __ldg(order + idx) : 0u;
     for (; idx < n_order; idx += gridDim.x) {
@@ -484,7 +559,8 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_leve
         if ((int)(o >> 16) >= lt.lev[1].rows) continue;                       // block-uniform
         const int c0 = ((int)(o & 0xffffu) * DETECT_WARPS + (threadIdx.x >> 5)) * CPW;
         if (c0 >= chunks2) continue;                                          // warp-uniform
-        levels_group<E>(plane, nb, zmax, K, lt, chunks2, lt.lev[1].i_lo + (int)(o >> 16), c0, unit_count, unit_mask);
+        levels_group<E>(plane, nb, zmax, K, lt, chunks2, lt.lev[1].i_lo + (int)(o >> 16), c0, unit_count, unit_mask,
+                        l2mark);
     }
 }
 
@@ -798,6 +874,8 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
     const int64_t n_units = p.n_units;
     const int64_t n_blocks = (n_units + SCAN_BLOCK - 1) / SCAN_BLOCK;
     unsigned int *ticket = reinterpret_cast<unsigned int *>(block_off + n_blocks);   // zeroed by level 1
+    // the plane kernel's unit marks (mark_threshold) bound the level-2 sums too
+    const uint8_t *l2mark = l1flag && lt.n_levels > 1 ? l1flag : nullptr;
     p.prof.begin(FDAS_STAGE_PEAKS, st);
     p.prof.launches += lt.n_levels > 1 ? 4 : 3;
     p.prof.begin(PROF_PEAKS_LEVEL1, st);
@@ -834,12 +912,24 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
             const int64_t blocks = sizeof(E) == 4 ? p.k4order_n
                                                   : std::min<int64_t>(p.k4order_n, (int64_t)std::max(sms, 1) * FDAS_K4_MIN_BLOCKS);
+            // with the marks: select the entries to search first (a list in the workspace), so that the
+            // skipped chunks cost one thread each instead of a warp's round trip in the search
+            const uint32_t *order = p.d_k4order;
+            unsigned int *wcount = nullptr;
+            if (l2mark != nullptr) {
+                uint32_t *work = reinterpret_cast<uint32_t *>(ws + p.ws_k4work);
+                wcount = ticket + 2;
+                k4_levels_select<<<(unsigned)((p.k4order_n + 255) / 256), 256, 0, st>>>(
+                    p.d_k4order, p.k4order_n, l2mark, p.cfg.zmax, p.K, lt, (int)chunks2, work, wcount, unit_count);
+                order = work;
+                p.prof.launches += 1;
+            }
             k4_levels_ordered<E><<<(unsigned)blocks, DETECT_WARPS * 32, 0, st>>>(
-                plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2, p.d_k4order, p.k4order_n, unit_count,
-                unit_mask);
+                plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2, order, p.k4order_n, wcount, unit_count,
+                unit_mask, l2mark);
         } else {
             k4_levels<E><<<levels_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2,
-                                                                     unit_count, unit_mask);
+                                                                     unit_count, unit_mask, l2mark);
         }
         p.prof.end(PROF_PEAKS_LEVELS, st);
     }
@@ -916,6 +1006,13 @@ bool levels_order(const Plan &p, std::vector<uint32_t> &order, bool anchored) {
     order.resize(items.size());
     for (size_t k = 0; k < items.size(); k++) order[k] = items[k].code;
     return true;
+}
+
+int64_t levels_order_size(const Plan &p) {
+    LevelDesc d{};
+    level_region(p, 2, false, d);
+    const int64_t per = DETECT_WARPS * CPW;
+    return (int64_t)d.rows * ((d.chunks + per - 1) / per);
 }
 
 cudaError_t upload_levels_order(Plan &p) {

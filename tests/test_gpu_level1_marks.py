@@ -1,10 +1,12 @@
 """The level-1 pass fused into the plane kernel (every precision but the split one): inside
 fdas_search the plane kernel marks every 512-bin unit of a row that holds a stored value above
-thr[0], and level 1 visits only those units instead of reading the whole plane.  The peak list
-must be the one the full level-1 pass (fdas_peaks on the same plane) gives, record for record --
-the full pass is the one the parity tests pin to the oracle -- for thresholds from "a handful of
-units" to "nearly all", every precision with marks, ragged segment tails and the last bins of the
-rows."""
+min(thr[0], thr[1] / 2); level 1 visits only those units instead of reading the whole plane, and
+the level search skips the chunks outside level 4's region whose level-2 sums the marks bound
+below thr[1] (the chunk's unit and its second harmonic's two units unmarked).  The peak list
+must be the one the full passes give (fdas_peaks on the same plane: no marks, every chunk
+searched), record for record -- the full passes are the ones the parity tests pin to the oracle
+-- for thresholds from "a handful of units" to "nearly all", every precision with marks, ragged
+segment tails and the last bins of the rows."""
 import numpy as np
 import pytest
 import torch
