@@ -12,8 +12,9 @@
 // [[Re w, -Im w], [Im w, Re w]], rows and columns permuted as described below).
 //
 // One persistent, warp-specialised CTA per SM walks a contiguous range of (segment, template
-// pair) items with producer, MMA and two epilogue roles overlapped through TMEM and shared-memory
-// buffers (layout below the helpers).  Every mbarrier wait is bounded; a timeout sets
+// pair) items, segments fastest (item = pair * n_seg + segment, so a CTA keeps one pair's template
+// spectra in registers across its items), with producer, MMA and two epilogue roles overlapped
+// through TMEM and shared-memory buffers (layout below the helpers).  Every mbarrier wait is bounded; a timeout sets
 // FDAS_DEV_TIMEOUT, all roles stop, the issued MMAs drain and the TMEM is released.
 #include <cmath>
 #include <cstring>
@@ -161,6 +162,10 @@ __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_f16(const float2 *
 // data as the A operand (M = 128 rows = two templates x 64) and a DFT matrix as B:
 //   stage 1  D1[(z,n2), (p,k1)] = A1[(z,n2), K1] . F1^T          A1 = x, in TMEM (K1: stage-1 order)
 //   stage 2  D2[(z,k1), (p,k2)] = A2[(z,k1), (s,n2)] . F2^T      A2 = W_S^{n2 k1} D1, shared memory
+// Stage-1 rows interleave the two templates within each 32-row TMEM quadrant q: row
+// 32 q + 16 z + (n2 mod 16) holds n2 = 16 q + (n2 mod 16), so the two threads of a warp that form
+// rows (0, n2) and (1, n2) load the same Yhat words and the warp's loads coalesce.  Stage-2 rows
+// are 64 z + k1 (the order epilogue 1 writes A2 in).
 // Accumulator columns are ordered (p, k): the 64 real parts, then the 64 imaginary parts, so a
 // thread's TMEM row yields 8 consecutive real (or imaginary) parts per 8 columns.  A2 is stored
 // MN-major: the 8 consecutive k1 of one (z, n2, s) are one 16-byte row of a core matrix, which is
@@ -278,9 +283,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
     const int64_t it0 = (int64_t)blockIdx.x * items_per_cta;
     const int64_t it1 = min(n_items, it0 + items_per_cta);
     const int64_t n_my = it1 - it0;
+    const int64_t n_seg = n_items / n_groups;           // items are pair * n_seg + segment
     const int quad = warp & 3;                          // TMEM lane quadrant this warp may access
     const int lrow = 32 * quad + lane;                  // TMEM lane = GEMM row
-    const int zl = lrow >> 6, idx = lrow & 63;          // (template in the pair, n2 or k1)
+    const int zl = lrow >> 6, idx = lrow & 63;          // stage-2 row: (template in the pair, k1)
     const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
 
     if (warp < WS_P0) {
@@ -341,21 +347,28 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
         __syncwarp();
     } else if (warp < WS_E1) {
         // ---------------------------------------------------------------- producer
-        // thread -> A1 row (zl, n2 = idx), columns 32 hp .. 32 hp + 31 (chunks 8 hp .. 8 hp + 7)
+        // thread -> A1 row (z1, n2) (interleaved order), columns 32 hp .. 32 hp + 31 (chunks 8 hp .. 8 hp + 7)
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_WIDE));
         const int hp = (warp - WS_P0) >> 2;
-        const uint4 *Yj = Y + (it0 / n_groups) * (TC_S_BF16 / 4) + 8 * hp * TC_R + idx;
-        int grp = (int)(it0 % n_groups);               // template pair of the current item
+        const int z1 = (lane >> 4) & 1, n2 = 16 * quad + (lane & 15);      // interleaved stage-1 row
+        const uint4 *Yb = Y + 8 * hp * TC_R + n2;
+        int64_t j = it0 % n_seg;                        // segment of the current item
+        int grp = (int)(it0 / n_seg);                   // its template pair
+        int gcur = -1;                                  // the pair whose spectrum gv holds
+        uint4 gv[8];
         for (int64_t k = 0; k < n_my; k++) {
-            const int z = grp * TC_G + zl;
+            const int z = grp * TC_G + z1;
             const int sl = (int)(k & 1);
-            const uint4 *Gz = G + (z < K ? z : 0) * (TC_S_BF16 / 4) + 8 * hp * TC_R + idx;
-            uint4 yv[8], gv[8];
+            if (grp != gcur) {
+                const uint4 *Gz = G + (z < K ? z : 0) * (TC_S_BF16 / 4) + 8 * hp * TC_R + n2;
 #pragma unroll
-            for (int c = 0; c < 8; c++) {
-                yv[c] = __ldg(Yj + c * TC_R);
-                gv[c] = z < K ? __ldg(Gz + c * TC_R) : make_uint4(0, 0, 0, 0);
+                for (int c = 0; c < 8; c++) gv[c] = z < K ? __ldg(Gz + c * TC_R) : make_uint4(0, 0, 0, 0);
+                gcur = grp;
             }
+            uint4 yv[8];
+            const uint4 *Yj = Yb + j * (TC_S_BF16 / 4);
+#pragma unroll
+            for (int c = 0; c < 8; c++) yv[c] = __ldg(Yj + c * TC_R);
             if (k >= 2 && !ws_wait(&bars->a1_free[sl], (uint32_t)(((k - 2) >> 1) & 1), abort_flag)) break;
             tc::fence_after_thread_sync();
             // conj(y) g: Re = yr gr + yi gi, Im = yr gi - yi gr, two n1 per packed pair; written in
@@ -383,20 +396,21 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
             tc::tmem_st_wait();
             tc::fence_before_thread_sync();
             mbar_arrive(&bars->a1_full[sl]);
-            if (++grp == n_groups) {
-                grp = 0;
-                Yj += TC_S_BF16 / 4;
+            if (++j == n_seg) {
+                j = 0;
+                grp++;
             }
         }
     } else if (warp < WS_E2) {
         // ---------------------------------------------------------------- epilogue 1
-        // thread -> D1 row (zl, n2 = idx), k1 in [32 h, 32 h + 32)
+        // thread -> D1 row (z1, n2) (interleaved order), k1 in [32 h, 32 h + 32)
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_WIDE));
         const int h = (warp - WS_E1) >> 2;
+        const int z1 = (lane >> 4) & 1, n2 = 16 * quad + (lane & 15);
         float2 wx[4], wy[4], nwy[4];                    // W_S^{n2 q}, q = 2 i, 2 i + 1
 #pragma unroll
         for (int i = 0; i < 4; i++) {
-            const float2 t0 = __ldg(tw + (2 * i) * TC_R + idx), t1 = __ldg(tw + (2 * i + 1) * TC_R + idx);
+            const float2 t0 = __ldg(tw + (2 * i) * TC_R + n2), t1 = __ldg(tw + (2 * i + 1) * TC_R + n2);
             wx[i] = make_float2(t0.x, t1.x);
             wy[i] = make_float2(t0.y, t1.y);
             nwy[i] = make_float2(-t0.y, -t1.y);
@@ -404,12 +418,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
         float bx[4], by[4];                             // W_S^{n2 k0}, k0 = 32 h + 8 g
 #pragma unroll
         for (int g = 0; g < 4; g++) {
-            const float2 b = __ldg(tw + (32 * h + 8 * g) * TC_R + idx);
+            const float2 b = __ldg(tw + (32 * h + 8 * g) * TC_R + n2);
             bx[g] = b.x;
             by[g] = b.y;
         }
-        // A2 byte offset of (m = 64 zl + 32 h, k = n2); k = 64 + n2 (imaginary part) is 8 A2_CK further
-        const uint32_t a2_row = (uint32_t)(8 * zl + 4 * h) * A2_CM + (uint32_t)(idx >> 3) * A2_CK + (idx & 7) * 16;
+        // A2 byte offset of (m = 64 z1 + 32 h, k = n2); k = 64 + n2 (imaginary part) is 8 A2_CK further
+        const uint32_t a2_row = (uint32_t)(8 * z1 + 4 * h) * A2_CM + (uint32_t)(n2 >> 3) * A2_CK + (n2 & 7) * 16;
         int s3 = 0, u3 = 0;                             // slot k mod 3 and its use count k / 3
         for (int64_t k = 0; k < n_my; k++) {
             const int sl = (int)(k & 1);
@@ -459,8 +473,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_E2));
         const int h = (warp - WS_E2) >> 2;
         const int kl = L / TC_R;                        // k2 < L / 64  <=>  bin t = k1 + 64 k2 < L
-        int64_t j = it0 / n_groups;
-        int grp = (int)(it0 % n_groups);
+        int64_t j = it0 % n_seg;
+        int grp = (int)(it0 / n_seg);
         int slot = 0, u3 = 0;                           // slot k mod 3 and its use count k / 3
         for (int64_t k = 0; k < n_my; k++) {
             const uint32_t dcol = (uint32_t)slot * TC_N;
@@ -469,9 +483,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
             const int z = grp * TC_G + zl;
             const int64_t r0 = j * L;
             const float us = unscale ? __ldg(unscale + j) : 1.0f;
-            if (++grp == n_groups) {                    // the next item
-                grp = 0;
-                j++;
+            if (++j == n_seg) {                         // the next item
+                j = 0;
+                grp++;
             }
             // stored k2 (this thread): k2 < kmax, from t < L, r0 + t < nb and z < K
             const int64_t rest = nb - r0 - idx;
@@ -504,12 +518,18 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
             }
             typename Ops::Out *prow = plane + (int64_t)(z < K ? z : 0) * nb + r0 + idx + 64 * 32 * h;
             // level-1 marks: the 512-bin units of row z holding a stored value above thr1 (rounding
-            // is monotone, so the largest value decides whether any does)
+            // is monotone, so the largest value decides whether any does; four interleaved chains
+            // keep the maximum's dependency chain short)
             if (l1flag != nullptr && kmax > 0) {
-                float vmax = pw[0];
+                float m0 = pw[0], m1 = pw[1], m2 = pw[2], m3 = pw[3];
 #pragma unroll
-                for (int i = 1; i < 32; i++) vmax = fmaxf(vmax, pw[i]);
-                if (Ops::stored(vmax, us) > thr1) {
+                for (int i = 4; i < 32; i += 4) {
+                    m0 = fmaxf(m0, pw[i]);
+                    m1 = fmaxf(m1, pw[i + 1]);
+                    m2 = fmaxf(m2, pw[i + 2]);
+                    m3 = fmaxf(m3, pw[i + 3]);
+                }
+                if (Ops::stored(fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)), us) > thr1) {
                     uint8_t *frow = l1flag + (int64_t)z * chunks1;
                     const int64_t b0 = r0 + idx + 64 * 32 * h;
 #pragma unroll
