@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_f16(const float2 *
 //   warps 20-27  epilogue 2: D2 -> |.|^2 -> plane (halves of k2)
 // TMEM (512 columns): three accumulator slots of 128 columns (item k uses slot k mod 3 for D1 and,
 // once epilogue 1 has drained it, for D2) and two A1 slots of 64 columns (item k: k mod 2).
-// Shared memory: F1, F2 (32 KB each) and two A2 slots (32 KB each, item k: k mod 2).
+// Shared memory: F1, F2 (32 KB each), two A2 slots (32 KB each, item k: k mod 2) and the W_S^{n2 k1} table.
 // Hand-offs are mbarriers, each with one signalling and one waiting role:
 //   a1_full[2]  producer -> MMA (256 arrivals)        a1_free[2]  MMA commit after stage 1 -> producer
 //   d1_full[3]  MMA commit after stage 1 -> epi 1      b2_full[2]  epi 1 -> MMA (256: A2 ready, D1 read)
@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_f16(const float2 *
 //   d_free[3]   epi 2 -> MMA (256 arrivals: accumulator slot drained)
 // The u-th use of a barrier waits for phase parity u & 1; a role can never be two phases behind
 // (the next phase of every barrier depends on the waiting role's own progress).  Every wait is
-// bounded and also gives up when another role has aborted.  The twiddle W_S^{n2 k1} with k1 = k0 + q (k0 a multiple of
-// 8) is applied as W_S^{n2 q} (per-thread pairs held in registers) then W_S^{n2 k0}.
+// bounded and also gives up when another role has aborted.  Epilogue 1 reads the twiddle W_S^{n2 k1}
+// from a shared-memory copy of the plan's table, one 16-byte word per pair of consecutive k1.
 constexpr int WS_P0 = 4;                                     // first producer warp
 constexpr int WS_PRODUCERS = 256;                            // warps 4-11
 constexpr int WS_E1 = WS_P0 + WS_PRODUCERS / 32;             // first epilogue-1 warp (12)
@@ -207,7 +207,9 @@ constexpr uint32_t F_LBO = TC_M * 16, F_SBO = 128;           // F1, F2: dense K-
 constexpr uint32_t OFF_F1 = 0, OFF_F2 = TILE_BYTES;
 constexpr uint32_t OFF_A2 = 2 * TILE_BYTES;                  // 2 slots
 constexpr uint32_t OFF_BAR = OFF_A2 + 2 * TILE_BYTES;
-constexpr uint32_t WS_SMEM = OFF_BAR + 256;
+// W_S^{n2 k1} for the k1 pairs (2 kp, 2 kp + 1) as float4 {Re, Re, Im, Im} at [kp][n2] (32 KB)
+constexpr uint32_t OFF_TWS = OFF_BAR + 256;
+constexpr uint32_t WS_SMEM = OFF_TWS + (TC_R / 2) * TC_R * 16;
 constexpr uint32_t WS_TMEM_COLS = 512;
 constexpr uint32_t COL_A1 = 3 * TC_N;                        // accumulator slots at 0, 128, 256
 
@@ -274,6 +276,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
     }
     for (int i = tid; i < (int)(2 * TILE_BYTES / 16); i += WS_THREADS)
         reinterpret_cast<uint4 *>(smem + OFF_F1)[i] = __ldg(Fimg + i);
+    for (int e = tid; e < (TC_R / 2) * TC_R; e += WS_THREADS) {
+        const int kp = e / TC_R, n2 = e % TC_R;
+        const float2 a = __ldg(tw + (2 * kp) * TC_R + n2), b = __ldg(tw + (2 * kp + 1) * TC_R + n2);
+        reinterpret_cast<float4 *>(smem + OFF_TWS)[e] = make_float4(a.x, b.x, a.y, b.y);
+    }
     tc::fence_proxy_async_smem();
     tc::fence_before_thread_sync();
     __syncthreads();
@@ -407,21 +414,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_WIDE));
         const int h = (warp - WS_E1) >> 2;
         const int z1 = (lane >> 4) & 1, n2 = 16 * quad + (lane & 15);
-        float2 wx[4], wy[4], nwy[4];                    // W_S^{n2 q}, q = 2 i, 2 i + 1
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const float2 t0 = __ldg(tw + (2 * i) * TC_R + n2), t1 = __ldg(tw + (2 * i + 1) * TC_R + n2);
-            wx[i] = make_float2(t0.x, t1.x);
-            wy[i] = make_float2(t0.y, t1.y);
-            nwy[i] = make_float2(-t0.y, -t1.y);
-        }
-        float bx[4], by[4];                             // W_S^{n2 k0}, k0 = 32 h + 8 g
-#pragma unroll
-        for (int g = 0; g < 4; g++) {
-            const float2 b = __ldg(tw + (32 * h + 8 * g) * TC_R + n2);
-            bx[g] = b.x;
-            by[g] = b.y;
-        }
+        // W_S^{n2 k1} for k1 = 32 h + 8 g + 2 i + {0, 1}: word (16 h + 4 g + i) * 64 + n2
+        const float4 *tws = reinterpret_cast<const float4 *>(smem + OFF_TWS) + 16 * h * TC_R + n2;
         // A2 byte offset of (m = 64 z1 + 32 h, k = n2); k = 64 + n2 (imaginary part) is 8 A2_CK further
         const uint32_t a2_row = (uint32_t)(8 * z1 + 4 * h) * A2_CM + (uint32_t)(n2 >> 3) * A2_CK + (n2 & 7) * 16;
         int s3 = 0, u3 = 0;                             // slot k mod 3 and its use count k / 3
@@ -441,17 +435,16 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
 #pragma unroll
                 for (int g2 = 0; g2 < 2; g2++) {
                     const int g = 2 * gg + g2;
-                    const float2 BX = make_float2(bx[g], bx[g]), BY = make_float2(by[g], by[g]);
-                    const float2 NBY = make_float2(-by[g], -by[g]);
                     uint32_t ore[4], oim[4];
 #pragma unroll
                     for (int i = 0; i < 4; i++) {
+                        const float4 t = tws[(4 * g + i) * TC_R];
+                        const float2 wx = make_float2(t.x, t.y), wy = make_float2(t.z, t.w);
                         const float2 dr = u2f2(rr[8 * g2 + 2 * i], rr[8 * g2 + 2 * i + 1]);
                         const float2 di = u2f2(ri[8 * g2 + 2 * i], ri[8 * g2 + 2 * i + 1]);
-                        const float2 er = __ffma2_rn(dr, wx[i], __fmul2_rn(di, nwy[i]));
-                        const float2 ei = __ffma2_rn(dr, wy[i], __fmul2_rn(di, wx[i]));
-                        const float2 yr = __ffma2_rn(er, BX, __fmul2_rn(ei, NBY));
-                        const float2 yi = __ffma2_rn(er, BY, __fmul2_rn(ei, BX));
+                        const float2 q = __fmul2_rn(di, wy);
+                        const float2 yr = __ffma2_rn(dr, wx, make_float2(-q.x, -q.y));
+                        const float2 yi = __ffma2_rn(dr, wy, __fmul2_rn(di, wx));
                         ore[i] = Ops::pack(yr.x, yr.y);
                         oim[i] = Ops::pack(yi.x, yi.y);
                     }
