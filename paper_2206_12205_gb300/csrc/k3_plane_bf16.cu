@@ -197,10 +197,11 @@ constexpr int WS_E1 = WS_P0 + WS_PRODUCERS / 32;             // first epilogue-1
 constexpr int WS_E2 = WS_E1 + 8;                             // first epilogue-2 warp (20)
 constexpr int WS_THREADS = (WS_E2 + 8) * 32;                 // 28 warps = 7 warpgroups
 // Registers: 72 a thread at launch (7 warps on each SM sub-partition).  Warpgroup 0 (the MMA
-// warp and three idle warps) and epilogue 2 give 16 and 8 back; the producers and epilogue 1
-// take 8 more: 128 x 56 + 256 x 80 + 256 x 80 + 256 x 64 = 896 x 72.
-constexpr int REG_LAUNCH = 72, REG_MMA = 56, REG_WIDE = 80, REG_E2 = 64;
-static_assert(128 * REG_MMA + 512 * REG_WIDE + 256 * REG_E2 == WS_THREADS * REG_LAUNCH,
+// warps and two idle warps) gives 16 back and epilogue 1 gives 8; the producers (the pair's
+// template spectrum held across items) and epilogue 2 (a whole accumulator row half loaded at
+// once) take 8 more: 128 x 56 + 256 x 80 + 256 x 64 + 256 x 80 = 896 x 72.
+constexpr int REG_LAUNCH = 72, REG_MMA = 56, REG_PROD = 80, REG_E1 = 64, REG_E2 = 80;
+static_assert(128 * REG_MMA + 256 * (REG_PROD + REG_E1 + REG_E2) == WS_THREADS * REG_LAUNCH,
               "register split must add up to the launch allocation");
 constexpr uint32_t A2_CM = 128, A2_CK = (TC_M / 8) * 128;    // A2 MN-major: core matrices along M, K
 constexpr uint32_t F_LBO = TC_M * 16, F_SBO = 128;           // F1, F2: dense K-major
@@ -232,6 +233,13 @@ __device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// max(a, b, c) in one instruction (three-input max.f32, sm_100 and later)
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
 
 __device__ __forceinline__ float2 u2f2(uint32_t a, uint32_t b) {
@@ -355,7 +363,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
     } else if (warp < WS_E1) {
         // ---------------------------------------------------------------- producer
         // thread -> A1 row (z1, n2) (interleaved order), columns 32 hp .. 32 hp + 31 (chunks 8 hp .. 8 hp + 7)
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_WIDE));
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_PROD));
         const int hp = (warp - WS_P0) >> 2;
         const int z1 = (lane >> 4) & 1, n2 = 16 * quad + (lane & 15);      // interleaved stage-1 row
         const uint4 *Yb = Y + 8 * hp * TC_R + n2;
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
     } else if (warp < WS_E2) {
         // ---------------------------------------------------------------- epilogue 1
         // thread -> D1 row (z1, n2) (interleaved order), k1 in [32 h, 32 h + 32)
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_WIDE));
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_E1));
         const int h = (warp - WS_E1) >> 2;
         const int z1 = (lane >> 4) & 1, n2 = 16 * quad + (lane & 15);
         // W_S^{n2 k1} for k1 = 32 h + 8 g + 2 i + {0, 1}: word (16 h + 4 g + i) * 64 + n2
@@ -463,7 +471,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
     } else {
         // ---------------------------------------------------------------- epilogue 2
         // thread -> D2 row (zl, k1 = idx), k2 in [32 h, 32 h + 32)
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_E2));
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_E2));
         const int h = (warp - WS_E2) >> 2;
         const int kl = L / TC_R;                        // k2 < L / 64  <=>  bin t = k1 + 64 k2 < L
         int64_t j = it0 % n_seg;
@@ -480,30 +488,39 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
                 j = 0;
                 grp++;
             }
-            // stored k2 (this thread): k2 < kmax, from t < L, r0 + t < nb and z < K
-            const int64_t rest = nb - r0 - idx;
-            const int64_t kr = (rest + TC_R - 1) / TC_R;
-            int kmax = rest <= 0 ? 0 : (kr < (int64_t)kl ? (int)kr : kl);
-            if (z >= K) kmax = 0;
+            // stored k2 (this thread): k2 < kmax, from t < L, r0 + t < nb and z < K (a segment wholly
+            // inside the row stores all L / 64)
+            int kmax = kl;
+            if (z >= K) {
+                kmax = 0;
+            } else if (r0 + L > nb) {
+                const int64_t rest = nb - r0 - idx;
+                const int64_t kr = (rest + TC_R - 1) / TC_R;
+                kmax = rest <= 0 ? 0 : (kr < (int64_t)kl ? (int)kr : kl);
+            }
             kmax -= 32 * h;
             float pw[32];
+            {
+                // the row half's 32 real and 32 imaginary parts in one round trip
+                uint32_t rr[2][16], ri[2][16];
 #pragma unroll
-            for (int gg = 0; gg < 2; gg++) {
-                uint32_t rr[16], ri[16];
-                tc::tmem_ld16(tbase + lane_base + dcol + 32 * h + 16 * gg, rr);
-                tc::tmem_ld16(tbase + lane_base + dcol + TC_R + 32 * h + 16 * gg, ri);
+                for (int gg = 0; gg < 2; gg++) {
+                    tc::tmem_ld16(tbase + lane_base + dcol + 32 * h + 16 * gg, rr[gg]);
+                    tc::tmem_ld16(tbase + lane_base + dcol + TC_R + 32 * h + 16 * gg, ri[gg]);
+                }
                 tc::tmem_ld_wait();
-                if (gg == 1) {                                           // accumulator slot drained
-                    tc::fence_before_thread_sync();
-                    mbar_arrive(&bars->d_free[slot]);
-                }
+                tc::fence_before_thread_sync();
+                mbar_arrive(&bars->d_free[slot]);                        // accumulator slot drained
 #pragma unroll
-                for (int i = 0; i < 8; i++) {
-                    const float2 re = u2f2(rr[2 * i], rr[2 * i + 1]), im = u2f2(ri[2 * i], ri[2 * i + 1]);
-                    const float2 p = __ffma2_rn(re, re, __fmul2_rn(im, im));
-                    pw[16 * gg + 2 * i] = p.x;
-                    pw[16 * gg + 2 * i + 1] = p.y;
-                }
+                for (int gg = 0; gg < 2; gg++)
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        const float2 re = u2f2(rr[gg][2 * i], rr[gg][2 * i + 1]);
+                        const float2 im = u2f2(ri[gg][2 * i], ri[gg][2 * i + 1]);
+                        const float2 p = __ffma2_rn(re, re, __fmul2_rn(im, im));
+                        pw[16 * gg + 2 * i] = p.x;
+                        pw[16 * gg + 2 * i + 1] = p.y;
+                    }
             }
             if (++slot == 3) {
                 slot = 0;
@@ -512,17 +529,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k3_plane_tc(const uint4 *__rest
             typename Ops::Out *prow = plane + (int64_t)(z < K ? z : 0) * nb + r0 + idx + 64 * 32 * h;
             // level-1 marks: the 512-bin units of row z holding a stored value above thr1 (rounding
             // is monotone, so the largest value decides whether any does; four interleaved chains
-            // keep the maximum's dependency chain short)
+            // of three-input maxima keep the maximum's dependency chain short)
             if (l1flag != nullptr && kmax > 0) {
-                float m0 = pw[0], m1 = pw[1], m2 = pw[2], m3 = pw[3];
+                float m[4];
 #pragma unroll
-                for (int i = 4; i < 32; i += 4) {
-                    m0 = fmaxf(m0, pw[i]);
-                    m1 = fmaxf(m1, pw[i + 1]);
-                    m2 = fmaxf(m2, pw[i + 2]);
-                    m3 = fmaxf(m3, pw[i + 3]);
-                }
-                if (Ops::stored(fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)), us) > thr1) {
+                for (int c = 0; c < 4; c++)          // chain c: pw[c + 4 i], i < 8
+                    m[c] = fmaxf(fmax3(fmax3(pw[c], pw[c + 4], pw[c + 8]), pw[c + 12], pw[c + 16]),
+                                 fmax3(pw[c + 20], pw[c + 24], pw[c + 28]));
+                if (Ops::stored(fmax3(fmaxf(m[0], m[1]), m[2], m[3]), us) > thr1) {
                     uint8_t *frow = l1flag + (int64_t)z * chunks1;
                     const int64_t b0 = r0 + idx + 64 * 32 * h;
 #pragma unroll
