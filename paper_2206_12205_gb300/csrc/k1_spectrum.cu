@@ -78,6 +78,45 @@ __global__ void __launch_bounds__(k1_groups_a(M1) * (M1 / 32), FDAS_K1A_MIN_BLOC
     }
 }
 
+// The block's sum of |X_k|^2 (acc: this thread's FP32 partial) to partial[blockIdx.x] in FP64;
+// the last block to finish sums the partials in a fixed order: sigma2 = sum / (Nb - 1) unless
+// fixed, scale = sqrt(2 / sigma2); a series with no power outside DC (sigma2 = 0) gets scale 0,
+// a zero spectrum and plane, as the local variant does for a block of median power 0.
+// NT = blockDim.x (a power of two); red: NT doubles of shared memory.
+template <int NT>
+__device__ __forceinline__ void k1_sum_and_finalize(float acc, double *red, double *__restrict__ partial,
+                                                    unsigned int *__restrict__ ticket, int64_t nb, double sigma2_fixed,
+                                                    double *__restrict__ sigma2_out, float *__restrict__ scale_out) {
+    red[threadIdx.x] = (double)acc;
+    __syncthreads();
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;                    // block-uniform
+    __threadfence();
+    double tot = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) tot += __ldcg(partial + i);
+    red[threadIdx.x] = tot;
+    __syncthreads();
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double sigma2 = sigma2_fixed > 0.0 ? sigma2_fixed : red[0] / (double)(nb - 1);
+        *sigma2_out = sigma2;
+        *scale_out = sigma2 > 0.0 ? (float)sqrt(2.0 / sigma2) : 0.f;
+    }
+}
+
 // Groups 0 .. C2-1 take rows a = p C2 + g; groups C2 .. 2 C2 - 1 their partners M1 - a (row 0,
 // its own partner, lends its partner slot to row M1/2, the other self-partnered row).
 template <int M2>
@@ -130,37 +169,7 @@ __global__ void __launch_bounds__(2 * k1_groups_b(M2) * (M2 / 32), FDAS_K1B_MIN_
         X[k] = xk;
         acc = fmaf(xk.x, xk.x, fmaf(xk.y, xk.y, acc));
     }
-    red[threadIdx.x] = (double)acc;
-    __syncthreads();
-    for (int s = G * T / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    // the last block to finish sums the partials in a fixed order: sigma2 = sum / (Nb - 1) unless
-    // fixed, scale = sqrt(2 / sigma2); a series with no power outside DC (sigma2 = 0) gets scale 0,
-    // a zero spectrum and plane, as the local variant does for a block of median power 0
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        partial[blockIdx.x] = red[0];
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;                    // block-uniform
-    __threadfence();
-    double tot = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += G * T) tot += __ldcg(partial + i);
-    red[threadIdx.x] = tot;
-    __syncthreads();
-    for (int s = G * T / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double sigma2 = sigma2_fixed > 0.0 ? sigma2_fixed : red[0] / (double)(nb - 1);
-        *sigma2_out = sigma2;
-        *scale_out = sigma2 > 0.0 ? (float)sqrt(2.0 / sigma2) : 0.f;
-    }
+    k1_sum_and_finalize<G * T>(acc, red, partial, ticket, nb, sigma2_fixed, sigma2_out, scale_out);
 }
 
 __global__ void k1_apply_scale(const float2 *__restrict__ X, const float *__restrict__ scale, float2 *__restrict__ out,

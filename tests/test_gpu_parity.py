@@ -59,7 +59,7 @@ def test_templates_match_oracle(zmax, m, S):
 
 
 # ------------------------------------------------------------------ spectrum (K1)
-@pytest.mark.parametrize("n", [1 << 11, 1 << 12, 1 << 13, 1 << 16, 1 << 20])
+@pytest.mark.parametrize("n", [1 << 11, 1 << 12, 1 << 13, 1 << 16, 1 << 20, 1 << 21, 1 << 24])
 def test_spectrum_matches_oracle(n):
     x = (synth.noise(n, synth.rng_for(50, n.bit_length())) + synth.chirp(n, 0.3, n / 7.3, 3.0)).astype(np.float32)
     x[: n // 3] += 5.0                                 # a DC offset and a step: DC must still vanish
@@ -71,6 +71,29 @@ def test_spectrum_matches_oracle(n):
     assert got[0] == 0
     assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max() + 2e-5
     assert abs(s.sigma2.item() - s2) <= 1e-5 * s2
+
+
+@pytest.mark.parametrize("n", [1 << 26, 1 << 27])
+def test_spectrum_long_transform_lengths(n):
+    """The four-step passes at transform lengths 8192 x 4096 (N = 2^26) and 8192 x 8192 (N = 2^27),
+    where the FP64 oracle takes a minute or more: every bin against an FP64 FFT with the spectrum's
+    definition applied (DC zeroed, scale sqrt(2 / sigma2)), and sigma2 against Parseval's identity,
+    sum_{k=1}^{N/2-1} |X_k|^2 = (N sum x^2 - X_0^2 - X_{N/2}^2) / 2, which needs no transform."""
+    x = (synth.noise(n, synth.rng_for(51, n.bit_length())) + synth.chirp(n, 0.3, n / 7.3, 3.0)).astype(np.float32)
+    s = _search(n, 8, 32, 1024)
+    xh = s.spectrum(_to_dev(x))
+    torch.cuda.synchronize()
+    got = xh.cpu().numpy().view(np.complex64).astype(np.complex128)
+    xd = x.astype(np.float64)
+    nb = n // 2
+    x0, xnyq = xd.sum(), xd[0::2].sum() - xd[1::2].sum()
+    s2 = (n * np.dot(xd, xd) - x0 * x0 - xnyq * xnyq) / 2.0 / (nb - 1)
+    assert abs(s.sigma2.item() - s2) <= 1e-5 * s2
+    ref = np.fft.rfft(xd)[:nb]
+    ref[0] = 0.0
+    ref *= np.sqrt(2.0 / s2)
+    assert got[0] == 0
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max() + 2e-5
 
 
 def test_spectrum_fixed_sigma2():
