@@ -166,12 +166,10 @@ fdas_status fdas_plan(const fdas_config *cfg, fdas_plan_t *plan, size_t *workspa
                                                            : sizeof(float2) * (size_t)p->n_seg * p->S;
     p->ws_y = off;     off = align_up(off + ybytes);
     p->ws_segscale = off; off = align_up(off + sizeof(float) * (size_t)p->n_seg);
-    const size_t n_scan_blocks = (size_t)((p->n_units + fdas::PEAK_SCAN_BLOCK - 1) / fdas::PEAK_SCAN_BLOCK);
+    // the non-empty unit list directly before the counts (the kernels find it from the counts)
+    off += sizeof(uint32_t) * fdas::PEAK_LIST_WORDS;
     p->ws_ucount = off; off = align_up(off + sizeof(int32_t) * (size_t)p->n_units);
-    p->ws_uoff = off;   off = align_up(off + sizeof(int32_t) * (size_t)p->n_units);
     p->ws_umask = off;  off = align_up(off + sizeof(uint32_t) * (fdas::PEAK_CHUNK / 32) * (size_t)p->n_units);
-    // block sums + the scan's ticket + the level search's work count
-    p->ws_ublock = off; off = align_up(off + sizeof(int64_t) * (n_scan_blocks + 2));
     p->ws_l1flag = off; off = align_up(off + (size_t)p->K * (size_t)(p->nb / fdas::PEAK_CHUNK));
     // the level search's work list (the entries of its block order that are not skipped)
     p->ws_k4work = off; off = align_up(off + sizeof(uint32_t) * (size_t)std::max<int64_t>(1, fdas::levels_order_size(*p)));
@@ -323,7 +321,8 @@ fdas_status fdas_search(fdas_plan_t plan, const float *d_series, void *d_workspa
     // the tensor-core plane kernels mark the level-1 units as they store the plane
     uint8_t *l1flag = fdas::level1_fusable(*p) ? reinterpret_cast<uint8_t *>(ws + p->ws_l1flag) : nullptr;
     if (e == cudaSuccess) e = launch_plane_any(p, x, scale, ws, d_plane, st, l1flag);
-    if (e == cudaSuccess) e = fdas::launch_peaks(*p, d_plane, plane_is_bf16(p), ws, d_peaks, d_npeaks, 0u, st, l1flag);
+    if (e == cudaSuccess)
+        e = fdas::launch_peaks(*p, d_plane, plane_is_bf16(p), ws, d_peaks, d_npeaks, 0u, st, l1flag, true);
     return record(p, e);
 }
 

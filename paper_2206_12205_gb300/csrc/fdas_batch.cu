@@ -523,7 +523,7 @@ fdas_status fdas_batch_search(fdas_batch_t b, const float *d_series, void *d_wor
             if (e == cudaSuccess)
                 e = fdas::launch_peaks(p, plane, p.cfg.precision == FDAS_BF16 || p.cfg.precision == FDAS_BF16_DIRECT,
                                        ws, d_peaks + b->peak_off[i],
-                                       d_npeaks + i, (uint32_t)i, st_l, l1flag);
+                                       d_npeaks + i, (uint32_t)i, st_l, l1flag, true);
         }
         // join: the capture stream waits for every lane
         for (int l = 0; l < b->lanes && e == cudaSuccess; l++) {

@@ -68,7 +68,7 @@ struct Plan {
     int n_levels;
     int64_t n_units;
     // workspace layout (byte offsets inside the caller's workspace)
-    size_t ws_x, ws_tmp, ws_part, ws_scale, ws_y, ws_segscale, ws_ucount, ws_uoff, ws_umask, ws_ublock, ws_l1flag,
+    size_t ws_x, ws_tmp, ws_part, ws_scale, ws_y, ws_segscale, ws_ucount, ws_umask, ws_l1flag,
         ws_k4work, ws_bytes;
     int n_part;
     // plan-owned device memory
@@ -99,11 +99,15 @@ struct Plan {
 };
 
 // Peak search geometry: tiles of PEAK_ROWS rows x PEAK_CHUNK bins; a unit is one
-// (level, row, chunk) with a count and a PEAK_CHUNK-bit mask; the offset scan works on blocks
-// of PEAK_SCAN_BLOCK units.
+// (level, row, chunk) with a count and a PEAK_CHUNK-bit mask.
 constexpr int PEAK_ROWS = 8;
 constexpr int PEAK_CHUNK = 512;
-constexpr int PEAK_SCAN_BLOCK = 4096;
+// The non-empty peak units, listed as the level kernels count them: a 4-word header (the list's
+// count, then the level search's work count) and up to PEAK_LIST_CAP unit numbers, placed in the
+// workspace directly before the unit counts.  When the list holds them all, the output block
+// orders and emits them; else it scans every unit's count.
+constexpr int PEAK_LIST_CAP = 1024;
+constexpr int PEAK_LIST_WORDS = 4 + PEAK_LIST_CAP;
 
 struct LevelDesc {
     int H;          // harmonic count
@@ -174,9 +178,11 @@ cudaError_t launch_plane_any(const Plan &p, const float2 *x, const float *scale,
 bool levels_order(const Plan &p, std::vector<uint32_t> &order, bool anchored = false);
 int64_t levels_order_size(const Plan &p);   // entries of the plain order (level 2's region)
 cudaError_t upload_levels_order(Plan &p);
+// list_cleared: the peak list's counters (PEAK_LIST_WORDS before the unit counts) were cleared
+// earlier on the stream (launch_spectrum does); else the peak search clears them itself.
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws,
                          fdas_peak *d_peaks, int32_t *d_npeaks, uint32_t series, cudaStream_t st,
-                         const uint8_t *l1flag = nullptr);
+                         const uint8_t *l1flag = nullptr, bool list_cleared = false);
 cudaError_t launch_band_max(const Plan &p, const void *d_plane, bool bf16, const int64_t *d_lo, const int64_t *d_hi,
                             int n_bands, int64_t max_width, unsigned long long *d_slot, float *d_value,
                             int64_t *d_r, int32_t *d_zi, cudaStream_t st);

@@ -55,14 +55,18 @@ __global__ void __launch_bounds__(k1_groups_a(M1) * (M1 / 32), FDAS_K1A_MIN_BLOC
                                                                      const float2 *__restrict__ lo,
                                                                      const float2 *__restrict__ hi,
                                                                      float2 *__restrict__ B, int M2,
-                                                                     unsigned int *__restrict__ ticket) {
+                                                                     unsigned int *__restrict__ ticket,
+                                                                     uint32_t *__restrict__ list_hdr) {
     constexpr int T = M1 / 32, C1 = k1_groups_a(M1);
     constexpr int E = fft_smem_entries(M1) + K1_GPAD;
     extern __shared__ float2 sm[];        // C1 * E entries
     __shared__ float2 wi[C1][32];         // W_N^{2 n2 T i} of each column
     const int g = threadIdx.x % C1, t = threadIdx.x / C1;
     const int n2 = blockIdx.x * C1 + g;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;   // pass B's block count, read after this kernel
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *ticket = 0;                      // pass B's block count, read after this kernel
+        list_hdr[0] = list_hdr[1] = 0;    // the peak search's list counters, for the same step
+    }
     for (int i = t; i < 32; i += T) wi[g][i] = twN(lo, hi, 2 * (int64_t)n2 * T * i);   // T < 32 for M1 < 1024
     float2 v[32];
 #pragma unroll
@@ -220,13 +224,14 @@ __global__ void __launch_bounds__(256) k1_local_norm(const float2 *__restrict__ 
 }
 
 template <int M1>
-cudaError_t run_pass_a(const Plan &p, const float2 *z, float2 *B, unsigned int *ticket, cudaStream_t st) {
+cudaError_t run_pass_a(const Plan &p, const float2 *z, float2 *B, unsigned int *ticket, uint32_t *list_hdr,
+                       cudaStream_t st) {
     constexpr int C1 = k1_groups_a(M1);
     const size_t smem = sizeof(float2) * C1 * (fft_smem_entries(M1) + K1_GPAD);
     auto kern = k1_pass_a<M1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<p.M2 / C1, C1 * (M1 / 32), smem, st>>>(z, p.d_tw, p.d_twn_lo, p.d_twn_hi, B, p.M2, ticket);
+    kern<<<p.M2 / C1, C1 * (M1 / 32), smem, st>>>(z, p.d_tw, p.d_twn_lo, p.d_twn_hi, B, p.M2, ticket, list_hdr);
     return cudaGetLastError();
 }
 
@@ -253,19 +258,20 @@ cudaError_t launch_spectrum(const Plan &p, const float *d_series, char *ws, cuda
     double *sigma2 = reinterpret_cast<double *>(ws + p.ws_scale);
     float *scale = reinterpret_cast<float *>(ws + p.ws_scale + 8);
     unsigned int *ticket = reinterpret_cast<unsigned int *>(ws + p.ws_scale + 12);
+    uint32_t *list_hdr = reinterpret_cast<uint32_t *>(ws + p.ws_ucount) - PEAK_LIST_WORDS;
     p.prof.begin(FDAS_STAGE_SPECTRUM, st);
     p.prof.launches += 2;
     cudaError_t e = cudaErrorInvalidValue;
     switch (p.M1) {
-        case 32: e = run_pass_a<32>(p, z, B, ticket, st); break;
-        case 64: e = run_pass_a<64>(p, z, B, ticket, st); break;
-        case 128: e = run_pass_a<128>(p, z, B, ticket, st); break;
-        case 256: e = run_pass_a<256>(p, z, B, ticket, st); break;
-        case 512: e = run_pass_a<512>(p, z, B, ticket, st); break;
-        case 1024: e = run_pass_a<1024>(p, z, B, ticket, st); break;
-        case 2048: e = run_pass_a<2048>(p, z, B, ticket, st); break;
-        case 4096: e = run_pass_a<4096>(p, z, B, ticket, st); break;
-        case 8192: e = run_pass_a<8192>(p, z, B, ticket, st); break;
+        case 32: e = run_pass_a<32>(p, z, B, ticket, list_hdr, st); break;
+        case 64: e = run_pass_a<64>(p, z, B, ticket, list_hdr, st); break;
+        case 128: e = run_pass_a<128>(p, z, B, ticket, list_hdr, st); break;
+        case 256: e = run_pass_a<256>(p, z, B, ticket, list_hdr, st); break;
+        case 512: e = run_pass_a<512>(p, z, B, ticket, list_hdr, st); break;
+        case 1024: e = run_pass_a<1024>(p, z, B, ticket, list_hdr, st); break;
+        case 2048: e = run_pass_a<2048>(p, z, B, ticket, list_hdr, st); break;
+        case 4096: e = run_pass_a<4096>(p, z, B, ticket, list_hdr, st); break;
+        case 8192: e = run_pass_a<8192>(p, z, B, ticket, list_hdr, st); break;
     }
     if (e != cudaSuccess) return e;
     e = cudaErrorInvalidValue;

@@ -19,14 +19,14 @@
 // lane tests its 16 values against the threshold through their maximum; only cells above it (a
 // handful per plane) recompute their 3x3 neighbourhood's sums to decide the peak.
 //
-// Output order (H, i, r) without a sort: a "unit" is (level, row, chunk of CB bins), units
-// are numbered in that order, and
+// Output order (H, i, r): a "unit" is (level, row, chunk of CB bins), units are numbered in
+// that order, and
 //   pass A (k4_level1 over the plane, k4_levels over level 2's region) writes each unit's peak
-//     count and, when non-zero, its CB-bit mask;
-//   pass B (k4_scan_blocks; its last block scans the block sums) turns the counts into exclusive
-//     offsets + total;
-//   pass C (k4_emit, one warp per unit, empty units skipped) recomputes S_H at the few
-//   marked cells and writes the records at offset + rank.
+//     count and, when non-zero, its CB-bit mask, and lists the non-empty units (in no order);
+//   pass B (k4_emit_listed, one block): when the list holds every non-empty unit (PEAK_LIST_CAP;
+//     the usual case) it sorts the list's unit numbers, scans their counts into offsets and
+//     writes the records; otherwise it scans every unit's count in order.  Either way a
+//     record's power is S_H recomputed at its cell, at offset + rank.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -40,7 +40,6 @@ namespace {
 constexpr int CB = PEAK_CHUNK;           // bins per unit (a warp's chunk)
 constexpr int LB = CB / 32;              // bins per lane (16)
 constexpr int WORDS = CB / 32;           // mask words per unit
-constexpr int SCAN_BLOCK = PEAK_SCAN_BLOCK;
 constexpr int DETECT_WARPS = 4;          // warps per k4_level1 / k4_levels block
 #ifndef FDAS_K4_CPW
 #define FDAS_K4_CPW 1                    // chunks per k4_levels warp
@@ -252,6 +251,26 @@ __device__ __noinline__ bool local_max(const E *plane, int64_t nb, int zmax, int
     return true;
 }
 
+// The non-empty unit list of the step: PEAK_LIST_WORDS words directly before the counts (word 0
+// the number of non-empty units, words 4 .. the first PEAK_LIST_CAP unit numbers, in no order).
+__device__ __forceinline__ unsigned int *unit_list(int32_t *unit_count) {
+    return reinterpret_cast<unsigned int *>(unit_count) - PEAK_LIST_WORDS;
+}
+__device__ __forceinline__ const unsigned int *unit_list(const int32_t *unit_count) {
+    return reinterpret_cast<const unsigned int *>(unit_count) - PEAK_LIST_WORDS;
+}
+// A unit's count, and the unit on the list when it holds peaks (one thread per unit; the list
+// append, a handful of times per plane, out of line so that it costs the callers no registers).
+__device__ __noinline__ void list_unit(int32_t *unit_count, int64_t u) {
+    unsigned int *list = unit_list(unit_count);
+    const unsigned int slot = atomicAdd(list, 1u);
+    if (slot < (unsigned int)PEAK_LIST_CAP) list[4 + slot] = (unsigned int)u;
+}
+__device__ __forceinline__ void count_unit(int32_t *__restrict__ unit_count, int64_t u, int cnt) {
+    unit_count[u] = cnt;
+    if (cnt > 0) list_unit(unit_count, u);
+}
+
 // One level H > 1 of one (row, chunk), lane bins rb + 32 e: S_H from S_{H/2}, then the unit's count
 // and mask (word e of the mask, bins 32 e .. 32 e + 31 of the chunk, is the warp's ballot of bit e).
 // Returns false when the chunk lies outside level H's region (the regions nest: stop there).
@@ -280,7 +299,7 @@ __device__ __forceinline__ bool level_step(const E *__restrict__ plane, int64_t 
         int cnt = __popc(pk);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if (lane == 0) unit_count[u] = cnt;
+        if (lane == 0) count_unit(unit_count, u, cnt);
         if (cnt > 0) {
             uint32_t word = 0;
 #pragma unroll
@@ -350,14 +369,9 @@ template <typename E>
 __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_L1_MIN_BLOCKS) k4_level1(const E *__restrict__ plane, int64_t nb, int zmax,
                                                               int K, LevelDesc d, int chunks1,
                                                               int32_t *__restrict__ unit_count,
-                                                              uint32_t *__restrict__ unit_mask,
-                                                              unsigned int *__restrict__ ticket) {
+                                                              uint32_t *__restrict__ unit_mask) {
     constexpr int CPW1 = Fmt<E>::EPV == 8 ? 4 : 2;
     const int lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        ticket[0] = 0;                               // k4_scan_blocks' count
-        ticket[2] = 0;                               // k4_levels_select's (int64 slot after the ticket)
-    }
     const int i = blockIdx.y;
     const int c0 = (blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * CPW1;
     if (c0 >= chunks1) return;                       // warp-uniform
@@ -378,7 +392,7 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_L1_MIN_BLOCKS) k4_l
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
             const uint32_t hi = __shfl_down_sync(0xffffffffu, pk, 1);
-            if (lane == 0) unit_count[u] = cnt;
+            if (lane == 0) count_unit(unit_count, u, cnt);
             if (cnt > 0 && !(lane & 1)) unit_mask[(int64_t)u * WORDS + (lane >> 1)] = pk | (hi << 16);
         } else if (lane == 0) {
             unit_count[u] = 0;
@@ -386,21 +400,70 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_L1_MIN_BLOCKS) k4_l
     }
 }
 
+// Whether chunk c of row i (in level 2's region) can hold a level-2 .. peak given the plane
+// kernel's unit marks: always inside level 4's region; outside it only when its unit or one of the
+// two units of its second harmonic is marked (see levels_group).
+__device__ __forceinline__ bool chunk_needs_search(const uint8_t *__restrict__ marks, int64_t chunks1, int zmax, int K,
+                                                   const LevelTable &lt, int i, int c) {
+    if (lt.n_levels >= 3 && row_in_level(i, K, zmax, 4) && (int64_t)c * CB <= lt.lev[2].rmax) return true;
+    const int i2 = (2 * (-zmax + 2 * i) + zmax) >> 1;
+    return __ldg(marks + (int64_t)i * chunks1 + c) | __ldg(marks + (int64_t)i2 * chunks1 + 2 * c) |
+           __ldg(marks + (int64_t)i2 * chunks1 + 2 * c + 1);
+}
+
+// The level search's work list: one thread per entry k of the block order (row << 16 | 4-chunk
+// group); an entry is kept when any of its chunks needs the search (chunk_needs_search), else its
+// chunks' level-2 units count zero here.  Kept entries are appended per warp in the order's order
+// (ballot prefix, one atomic per warp), so the list keeps the ray order's locality; *count
+// (word 1 of the unit list's header) was cleared before the peak search.  Whole warps call it.
+__device__ __noinline__ void select_entry(int64_t k, const uint32_t *__restrict__ order, int64_t n_order,
+                                             const uint8_t *__restrict__ marks, int zmax, int K, const LevelTable &lt,
+                                             int chunks2, uint32_t *__restrict__ work, unsigned int *__restrict__ count,
+                                             int32_t *__restrict__ unit_count) {
+    const int lane = threadIdx.x & 31;
+    bool keep = false;
+    uint32_t o = 0;
+    if (k < n_order) {
+        o = __ldg(order + k);
+        const int a = (int)(o >> 16);
+        if (a < lt.lev[1].rows) {
+            const int i = lt.lev[1].i_lo + a;
+            const int64_t chunks1 = lt.lev[0].chunks;
+            const int c0 = (int)(o & 0xffffu) * DETECT_WARPS * CPW;
+            for (int w = 0; w < DETECT_WARPS * CPW && c0 + w < chunks2; w++)
+                keep |= chunk_needs_search(marks, chunks1, zmax, K, lt, i, c0 + w);
+            if (!keep)
+                for (int w = 0; w < DETECT_WARPS * CPW && c0 + w < chunks2; w++)
+                    unit_count[(int)lt.lev[1].unit0 + a * (int)lt.lev[1].chunks + c0 + w] = 0;
+        }
+    }
+    const uint32_t b = __ballot_sync(0xffffffffu, keep);
+    unsigned int base = 0;
+    if (lane == 0 && b) base = atomicAdd(count, (unsigned int)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) work[base + __popc(b & ((1u << lane) - 1u))] = o;
+}
+
 // Level 1 after a plane kernel that marked its units (flags[u] != 0: the unit u = i chunks + c holds
 // a stored value above the threshold): a warp takes 32 units, writes a zero count for the unmarked
 // ones and runs the level-1 test of k4_level1 on each marked one (a handful per plane).  The
 // plane is not streamed; the result is the same as k4_level1's.
+// The blocks from l1_blocks on build the level search's work list instead (select_entry, one
+// thread per entry of the block order; n_order = 0: none): the list depends only on the marks.
 template <typename E>
 __global__ void __launch_bounds__(DETECT_WARPS * 32) k4_level1_marked(const E *__restrict__ plane, int64_t nb, int zmax,
                                                                     int K, LevelDesc d, int64_t n_units1,
                                                                     const uint8_t *__restrict__ flags,
                                                                     int32_t *__restrict__ unit_count,
                                                                     uint32_t *__restrict__ unit_mask,
-                                                                    unsigned int *__restrict__ ticket) {
+                                                                    int64_t l1_blocks,
+                                                                    const uint32_t *__restrict__ order, int64_t n_order,
+                                                                    LevelTable lt, int chunks2, uint32_t *__restrict__ work) {
     const int lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ticket[0] = 0;                               // k4_scan_blocks' count
-        ticket[2] = 0;                               // k4_levels_select's (int64 slot after the ticket)
+    if (blockIdx.x >= l1_blocks) {                   // block-uniform
+        select_entry((int64_t)(blockIdx.x - l1_blocks) * blockDim.x + threadIdx.x, order, n_order, flags, zmax, K, lt,
+                     chunks2, work, unit_list(unit_count) + 1, unit_count);
+        return;
     }
     const int64_t u0 = ((int64_t)blockIdx.x * DETECT_WARPS + (threadIdx.x >> 5)) * 32;
     if (u0 >= n_units1) return;                      // warp-uniform
@@ -420,7 +483,7 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32) k4_level1_marked(const E *_
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         const uint32_t hi = __shfl_down_sync(0xffffffffu, pk, 1);
-        if (lane == 0) unit_count[d.unit0 + uu] = cnt;
+        if (lane == 0) count_unit(unit_count, d.unit0 + uu, cnt);
         if (cnt > 0 && !(lane & 1)) unit_mask[(d.unit0 + uu) * WORDS + (lane >> 1)] = pk | (hi << 16);
     }
 }
@@ -491,52 +554,6 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_leve
     levels_group<E>(plane, nb, zmax, K, lt, chunks2, lt.lev[1].i_lo + blockIdx.y, c0, unit_count, unit_mask, l2mark);
 }
 
-// Whether chunk c of row i (in level 2's region) can hold a level-2 .. peak given the plane
-// kernel's unit marks: always inside level 4's region; outside it only when its unit or one of the
-// two units of its second harmonic is marked (see levels_group).
-__device__ __forceinline__ bool chunk_needs_search(const uint8_t *__restrict__ marks, int64_t chunks1, int zmax, int K,
-                                                   const LevelTable &lt, int i, int c) {
-    if (lt.n_levels >= 3 && row_in_level(i, K, zmax, 4) && (int64_t)c * CB <= lt.lev[2].rmax) return true;
-    const int i2 = (2 * (-zmax + 2 * i) + zmax) >> 1;
-    return __ldg(marks + (int64_t)i * chunks1 + c) | __ldg(marks + (int64_t)i2 * chunks1 + 2 * c) |
-           __ldg(marks + (int64_t)i2 * chunks1 + 2 * c + 1);
-}
-
-// The level search's work list: one thread per entry of the block order (row << 16 | 4-chunk
-// group); an entry is kept when any of its chunks needs the search (chunk_needs_search), else its
-// chunks' level-2 units count zero here.  Kept entries are appended per warp in the order's order
-// (ballot prefix, one atomic per warp), so the list keeps the ray order's locality; *count was
-// zeroed by the level-1 pass.
-__global__ void __launch_bounds__(256) k4_levels_select(const uint32_t *__restrict__ order, int64_t n_order,
-                                                        const uint8_t *__restrict__ marks, int zmax, int K,
-                                                        LevelTable lt, int chunks2, uint32_t *__restrict__ work,
-                                                        unsigned int *__restrict__ count,
-                                                        int32_t *__restrict__ unit_count) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    bool keep = false;
-    uint32_t o = 0;
-    if (k < n_order) {
-        o = __ldg(order + k);
-        const int a = (int)(o >> 16);
-        if (a < lt.lev[1].rows) {
-            const int i = lt.lev[1].i_lo + a;
-            const int64_t chunks1 = lt.lev[0].chunks;
-            const int c0 = (int)(o & 0xffffu) * DETECT_WARPS * CPW;
-            for (int w = 0; w < DETECT_WARPS * CPW && c0 + w < chunks2; w++)
-                keep |= chunk_needs_search(marks, chunks1, zmax, K, lt, i, c0 + w);
-            if (!keep)
-                for (int w = 0; w < DETECT_WARPS * CPW && c0 + w < chunks2; w++)
-                    unit_count[(int)lt.lev[1].unit0 + a * (int)lt.lev[1].chunks + c0 + w] = 0;
-        }
-    }
-    const uint32_t b = __ballot_sync(0xffffffffu, keep);
-    unsigned int base = 0;
-    if (lane == 0 && b) base = atomicAdd(count, (unsigned int)__popc(b));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (keep) work[base + __popc(b & ((1u << lane) - 1u))] = o;
-}
-
 // Level 2's region in the ray order of upload_levels_order, each entry a (row << 16 | chunk
 // group): block b takes the entries b, b + gridDim.x, ... (so the blocks in flight keep to a short
 // stretch of the order); with a persistent grid the next entry's code is loaded while the current
@@ -550,7 +567,7 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4_leve
                                                                       int32_t *__restrict__ unit_count,
                                                                       uint32_t *__restrict__ unit_mask,
                                                                       const uint8_t *__restrict__ l2mark) {
-    if (d_count != nullptr) n_order = *d_count;   // a work list (k4_levels_select), written before this launch
+    if (d_count != nullptr) n_order = *d_count;   // a work list (the level-1 pass's selection blocks), written before this launch
     int64_t idx = blockIdx.x;
     uint32_t next = idx < n_order ? __ldg(order + idx) : 0u;
     for (; idx < n_order; idx += gridDim.x) {
@@ -628,7 +645,7 @@ __device__ __forceinline__ void anch_unit(const E *__restrict__ plane, int64_t n
         int cnt = __popc(pk);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if (lane == 0) unit_count[u] = cnt;
+        if (lane == 0) count_unit(unit_count, u, cnt);
         if (cnt > 0) {
             uint32_t word = 0;
 #pragma unroll
@@ -696,92 +713,6 @@ __global__ void __launch_bounds__(DETECT_WARPS * 32, FDAS_K4_MIN_BLOCKS) k4a_lev
     anch_chunk<E>(plane, nb, zmax, K, lt, (int)(o >> 16), c, unit_count, unit_mask);
 }
 
-// Second level (the last block of k4_scan_blocks, 1024 threads, fixed order): block offsets in
-// place, total count, overflow flag.
-__device__ __forceinline__ void scan_top(int64_t *__restrict__ block_sum, int64_t nblocks, int32_t *__restrict__ npeaks,
-                                         int max_peaks, int32_t *__restrict__ status) {
-    __shared__ int64_t warp_tot[32];
-    __shared__ int64_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t b0 = 0; b0 < nblocks; b0 += 1024) {
-        const int64_t b = b0 + threadIdx.x;
-        const int64_t v = (b < nblocks) ? __ldcg(block_sum + b) : 0;
-        int64_t incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) warp_tot[warp] = incl;
-        __syncthreads();
-        int64_t before = carry;
-        for (int w = 0; w < warp; w++) before += warp_tot[w];
-        if (b < nblocks) block_sum[b] = before + incl - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = before + incl;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const int64_t total = carry;
-        *npeaks = (int32_t)(total < 0x7fffffff ? total : 0x7fffffff);
-        if (total > max_peaks) atomicOr(status, FDAS_DEV_PEAK_OVERFLOW);
-    }
-}
-
-// First-level scan: exclusive prefix of the counts inside each block of SCAN_BLOCK units.
-__global__ void __launch_bounds__(1024) k4_scan_blocks(const int32_t *__restrict__ cnt, int64_t n,
-                                                       int32_t *__restrict__ off, int64_t *__restrict__ block_sum,
-                                                       unsigned int *__restrict__ ticket, int32_t *__restrict__ npeaks,
-                                                       int max_peaks, int32_t *__restrict__ status) {
-    __shared__ int32_t warp_tot[32];
-    const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x * 4;
-    int32_t v[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) v[k] = (base + k < n) ? cnt[base + k] : 0;
-    const int32_t sum = v[0] + v[1] + v[2] + v[3];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) warp_tot[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int32_t t = warp_tot[lane], ti = t;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, ti, o);
-            if (lane >= o) ti += y;
-        }
-        warp_tot[lane] = ti - t;                 // exclusive warp offsets
-        if (lane == 31) {
-            block_sum[blockIdx.x] = ti;
-            __threadfence();                             // before this block's ticket below
-        }
-    }
-    __syncthreads();
-    int32_t run = warp_tot[warp] + incl - sum;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        if (base + k < n) off[base + k] = run;
-        run += v[k];
-    }
-    // the last block to finish scans the block sums (the second level)
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;                               // block-uniform
-    __threadfence();
-    scan_top(block_sum, (int64_t)gridDim.x, npeaks, max_peaks, status);
-}
-
 struct UnitRef {
     int l, row;
     int64_t chunk;
@@ -801,67 +732,148 @@ __device__ __forceinline__ UnitRef unit_of(const LevelTable &lt, int64_t u) {
     return ref;
 }
 
-// Records of the non-empty units at (block offset + in-block offset + rank).  A warp reads 32
-// units' counts at a time (one per lane) and then serves the non-empty ones one by one.
+// The records of one non-empty unit u, the first at out[base]: one warp, the unit's mask words
+// one per lane, the peaks in bin order (the order of the output within a unit).
 template <typename E>
-__global__ void __launch_bounds__(256) k4_emit(const E *__restrict__ plane, int64_t nb, int zmax, LevelTable lt,
-                                               int64_t n_units, const int32_t *__restrict__ unit_count,
-                                               const int32_t *__restrict__ unit_off,
-                                               const int64_t *__restrict__ block_off,
-                                               const uint32_t *__restrict__ unit_mask, fdas_peak *__restrict__ out,
-                                               int max_peaks, uint32_t series) {
+__device__ __forceinline__ void emit_unit(const E *__restrict__ plane, int64_t nb, int zmax, const LevelTable &lt,
+                                          int64_t u, int64_t base, const uint32_t *__restrict__ unit_mask,
+                                          fdas_peak *__restrict__ out, int max_peaks, uint32_t series) {
     const int lane = threadIdx.x & 31;
-    const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u0 = warp_id * 32; u0 < n_units; u0 += n_warps * 32) {
-        const int64_t mine = u0 + lane;
-        const int32_t my_cnt = mine < n_units ? unit_count[mine] : 0;
-        uint32_t busy = __ballot_sync(0xffffffffu, my_cnt != 0);
-        while (busy) {                                           // warp-uniform
-            const int j = __ffs(busy) - 1;
-            busy &= busy - 1;
-            const int64_t u = u0 + j;
-            const int64_t base = block_off[u / SCAN_BLOCK] + unit_off[u];
-            const UnitRef ref = unit_of(lt, u);
-            const int H = lt.lev[ref.l].H;
-            const uint32_t w = lane < WORDS ? unit_mask[u * WORDS + lane] : 0u;
-            int incl = __popc(w);
+    const UnitRef ref = unit_of(lt, u);
+    const int H = lt.lev[ref.l].H;
+    const uint32_t w = lane < WORDS ? unit_mask[u * WORDS + lane] : 0u;
+    int incl = __popc(w);
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            int64_t pos = base + incl - __popc(w);
-            uint32_t bits = w;
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                if (pos < max_peaks) {
-                    const int64_t r = ref.chunk * CB + lane * 32 + b;
-                    fdas_peak pk;
-                    pk.series = series;
-                    pk.r = (uint32_t)r;
-                    pk.zi = (int16_t)ref.row;
-                    pk.harm = (uint8_t)H;
-                    pk.pad = 0;
-                    pk.power = lt.anchored ? harm_sum_anch(plane, nb, zmax, H, ref.row, r)
-                                           : harm_sum(plane, nb, zmax, H, ref.row, r);
-                    out[pos] = pk;
-                }
-                pos++;
-            }
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    int64_t pos = base + incl - __popc(w);
+    uint32_t bits = w;
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        if (pos < max_peaks) {
+            const int64_t r = ref.chunk * CB + lane * 32 + b;
+            fdas_peak pk;
+            pk.series = series;
+            pk.r = (uint32_t)r;
+            pk.zi = (int16_t)ref.row;
+            pk.harm = (uint8_t)H;
+            pk.pad = 0;
+            pk.power = lt.anchored ? harm_sum_anch(plane, nb, zmax, H, ref.row, r)
+                                   : harm_sum(plane, nb, zmax, H, ref.row, r);
+            out[pos] = pk;
         }
+        pos++;
+    }
+}
+
+// Exclusive scan of one value per thread over a block of 1024 threads; *total = the block's sum.
+// warp_tot: 32 ints of shared memory.  Every thread calls it (two barriers).
+__device__ __forceinline__ int32_t block_excl_scan(int32_t c, int32_t *warp_tot, int32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int32_t wt = warp_tot[lane];
+        int32_t wi = wt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_tot[lane] = wi - wt;                        // exclusive warp offsets
+        if (lane == 31) warp_tot[32] = wi;
+    }
+    __syncthreads();
+    *total = warp_tot[32];
+    return warp_tot[warp] + incl - c;
+}
+
+// The step's peaks, one block of 1024 threads.  Usually the non-empty unit list holds every
+// non-empty unit (a handful to a few hundred of ~10^6): its unit numbers are sorted by rank (they
+// are distinct: rank = how many are smaller), their counts scanned in that order into output
+// offsets, and each unit's records emitted by one warp.  Units are numbered in (level, row, chunk)
+// order, so the records come out in (H, i, r) order.  When more than PEAK_LIST_CAP units hold
+// peaks (low thresholds), the block scans every unit's count in order, 4096 units a round, and
+// emits the non-empty ones as it goes (slower, the same records).  Then the total and the
+// overflow flag.
+template <typename E>
+__global__ void __launch_bounds__(1024) k4_emit_listed(const E *__restrict__ plane, int64_t nb, int zmax, LevelTable lt,
+                                                       int64_t n_units, const int32_t *__restrict__ unit_count,
+                                                       const uint32_t *__restrict__ unit_mask,
+                                                       fdas_peak *__restrict__ out, int max_peaks, uint32_t series,
+                                                       int32_t *__restrict__ npeaks, int32_t *__restrict__ status) {
+    __shared__ uint32_t key[PEAK_LIST_CAP], sorted[PEAK_LIST_CAP];
+    __shared__ int32_t offs[PEAK_LIST_CAP];
+    __shared__ int32_t warp_tot[33];
+    const int t = threadIdx.x, warp = t >> 5;
+    const unsigned int *list = unit_list(unit_count);
+    const int n = (int)*list;
+    int64_t total = 0;
+    if (n <= PEAK_LIST_CAP) {                            // block-uniform
+        if (t < n) key[t] = list[4 + t];
+        __syncthreads();
+        if (t < n) {
+            const uint32_t k = key[t];
+            int rank = 0;
+            for (int j = 0; j < n; j++) rank += key[j] < k;
+            sorted[rank] = k;
+        }
+        __syncthreads();
+        // at most 1024 units x 512 peaks: 32-bit offsets
+        const int32_t c = t < n ? unit_count[sorted[t]] : 0;
+        int32_t tot;
+        const int32_t ex = block_excl_scan(c, warp_tot, &tot);
+        if (t < n) offs[t] = ex;
+        total = tot;
+        __syncthreads();
+        for (int k = warp; k < n; k += 32)
+            emit_unit<E>(plane, nb, zmax, lt, (int64_t)sorted[k], offs[k], unit_mask, out, max_peaks, series);
+    } else {
+        for (int64_t u0 = 0; u0 < n_units; u0 += 4 * 1024) {
+            const int64_t b0 = u0 + 4 * t;               // this thread's 4 units
+            int32_t v[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) v[k] = b0 + k < n_units ? unit_count[b0 + k] : 0;
+            int32_t tot;
+            int32_t run = block_excl_scan(v[0] + v[1] + v[2] + v[3], warp_tot, &tot);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int32_t mine = run;                // offset (in the round) of unit b0 + k
+                run += v[k];
+                uint32_t busy = __ballot_sync(0xffffffffu, v[k] != 0);
+                while (busy) {                           // warp-uniform
+                    const int j = __ffs(busy) - 1;
+                    busy &= busy - 1;
+                    const int32_t off_j = __shfl_sync(0xffffffffu, mine, j);
+                    emit_unit<E>(plane, nb, zmax, lt, u0 + 4 * (32 * warp + j) + k, total + off_j, unit_mask, out,
+                                 max_peaks, series);
+                }
+            }
+            total += tot;
+            __syncthreads();                             // warp_tot is reused by the next round
+        }
+    }
+    if (t == 0) {
+        *npeaks = (int32_t)(total < 0x7fffffff ? total : 0x7fffffff);
+        if (total > max_peaks) atomicOr(status, FDAS_DEV_PEAK_OVERFLOW);
     }
 }
 
 template <typename E>
 cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks, int32_t *npeaks, uint32_t series,
-                      cudaStream_t st, const uint8_t *l1flag) {
+                      cudaStream_t st, const uint8_t *l1flag, bool list_cleared) {
     const LevelTable lt = make_levels(p);
     int32_t *unit_count = reinterpret_cast<int32_t *>(ws + p.ws_ucount);
-    int32_t *unit_off = reinterpret_cast<int32_t *>(ws + p.ws_uoff);
     uint32_t *unit_mask = reinterpret_cast<uint32_t *>(ws + p.ws_umask);
-    int64_t *block_off = reinterpret_cast<int64_t *>(ws + p.ws_ublock);
     const int64_t chunks1 = lt.lev[0].chunks;
     constexpr int CPW1 = Fmt<E>::EPV == 8 ? 4 : 2;
     const dim3 level1_grid((unsigned)((chunks1 + DETECT_WARPS * CPW1 - 1) / (DETECT_WARPS * CPW1)), (unsigned)p.K);
@@ -872,22 +884,35 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
         (!p.d_k4order || p.k4order_n != (int64_t)lt.lev[1].rows * ((chunks2 + DETECT_WARPS * CPW - 1) / (DETECT_WARPS * CPW))))
         return cudaErrorInvalidValue;                // the block order was not built for this region
     const int64_t n_units = p.n_units;
-    const int64_t n_blocks = (n_units + SCAN_BLOCK - 1) / SCAN_BLOCK;
-    unsigned int *ticket = reinterpret_cast<unsigned int *>(block_off + n_blocks);   // zeroed by level 1
     // the plane kernel's unit marks (mark_threshold) bound the level-2 sums too
     const uint8_t *l2mark = l1flag && lt.n_levels > 1 ? l1flag : nullptr;
     p.prof.begin(FDAS_STAGE_PEAKS, st);
-    p.prof.launches += lt.n_levels > 1 ? 4 : 3;
+    // the non-empty unit list starts empty (its counter: the word PEAK_LIST_WORDS before the counts)
+    // and so does the level search's work count (the next word); a search's long FFT has cleared
+    // both already (list_cleared)
+    uint32_t *list_hdr = reinterpret_cast<uint32_t *>(unit_count) - PEAK_LIST_WORDS;
+    if (!list_cleared) {
+        cudaError_t e0 = cudaMemsetAsync(list_hdr, 0, 2 * sizeof(uint32_t), st);
+        if (e0 != cudaSuccess) return e0;
+    }
+    p.prof.launches += lt.n_levels > 1 ? 3 : 2;
+    // with the marks, the level search's work list is built by extra blocks of the level-1 pass
+    const bool select_list = l2mark != nullptr && lt.n_levels > 1 && !lt.anchored && (sizeof(E) == 4 || FDAS_K4_RAY_BF16);
+    uint32_t *work = reinterpret_cast<uint32_t *>(ws + p.ws_k4work);
+    unsigned int *wcount = select_list ? list_hdr + 1 : nullptr;
     p.prof.begin(PROF_PEAKS_LEVEL1, st);
     if (l1flag) {
         const int64_t n1 = (int64_t)p.K * chunks1;
         const int64_t blocks = (n1 + DETECT_WARPS * 32 - 1) / (DETECT_WARPS * 32);
-        k4_level1_marked<E><<<(unsigned)blocks, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt.lev[0], n1,
-                                                                          l1flag, unit_count, unit_mask, ticket);
+        const int64_t n_sel = select_list ? p.k4order_n : 0;
+        const int64_t sel_blocks = (n_sel + DETECT_WARPS * 32 - 1) / (DETECT_WARPS * 32);
+        k4_level1_marked<E><<<(unsigned)(blocks + sel_blocks), DETECT_WARPS * 32, 0, st>>>(
+            plane, p.nb, p.cfg.zmax, p.K, lt.lev[0], n1, l1flag, unit_count, unit_mask, blocks, p.d_k4order, n_sel,
+            lt, (int)chunks2, work);
         p.prof.level1_fused++;
     } else {
         k4_level1<E><<<level1_grid, DETECT_WARPS * 32, 0, st>>>(plane, p.nb, p.cfg.zmax, p.K, lt.lev[0], (int)chunks1,
-                                                                 unit_count, unit_mask, ticket);
+                                                                 unit_count, unit_mask);
     }
     p.prof.end(PROF_PEAKS_LEVEL1, st);
     if (lt.n_levels > 1 && lt.anchored) {
@@ -914,16 +939,8 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
                                                   : std::min<int64_t>(p.k4order_n, (int64_t)std::max(sms, 1) * FDAS_K4_MIN_BLOCKS);
             // with the marks: select the entries to search first (a list in the workspace), so that the
             // skipped chunks cost one thread each instead of a warp's round trip in the search
-            const uint32_t *order = p.d_k4order;
-            unsigned int *wcount = nullptr;
-            if (l2mark != nullptr) {
-                uint32_t *work = reinterpret_cast<uint32_t *>(ws + p.ws_k4work);
-                wcount = ticket + 2;
-                k4_levels_select<<<(unsigned)((p.k4order_n + 255) / 256), 256, 0, st>>>(
-                    p.d_k4order, p.k4order_n, l2mark, p.cfg.zmax, p.K, lt, (int)chunks2, work, wcount, unit_count);
-                order = work;
-                p.prof.launches += 1;
-            }
+            // (the work list from the level-1 pass's extra blocks, when the marks exist)
+            const uint32_t *order = select_list ? work : p.d_k4order;
             k4_levels_ordered<E><<<(unsigned)blocks, DETECT_WARPS * 32, 0, st>>>(
                 plane, p.nb, p.cfg.zmax, p.K, lt, (int)chunks2, order, p.k4order_n, wcount, unit_count,
                 unit_mask, l2mark);
@@ -933,11 +950,8 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
         }
         p.prof.end(PROF_PEAKS_LEVELS, st);
     }
-    k4_scan_blocks<<<(unsigned)n_blocks, 1024, 0, st>>>(unit_count, n_units, unit_off, block_off, ticket, npeaks,
-                                                       p.cfg.max_peaks, p.d_status);
-    const int64_t emit_blocks = std::min<int64_t>((n_units + 255) / 256, 152 * 8);
-    k4_emit<E><<<(unsigned)emit_blocks, 256, 0, st>>>(plane, p.nb, p.cfg.zmax, lt, n_units, unit_count, unit_off,
-                                                       block_off, unit_mask, peaks, p.cfg.max_peaks, series);
+    k4_emit_listed<E><<<1, 1024, 0, st>>>(plane, p.nb, p.cfg.zmax, lt, n_units, unit_count, unit_mask, peaks,
+                                          p.cfg.max_peaks, series, npeaks, p.d_status);
     p.prof.end(FDAS_STAGE_PEAKS, st);
     return cudaGetLastError();
 }
@@ -1033,11 +1047,12 @@ cudaError_t upload_levels_order(Plan &p) {
 }
 
 cudaError_t launch_peaks(const Plan &p, const void *d_plane, bool bf16, char *ws, fdas_peak *d_peaks,
-                         int32_t *d_npeaks, uint32_t series, cudaStream_t st, const uint8_t *l1flag) {
+                         int32_t *d_npeaks, uint32_t series, cudaStream_t st, const uint8_t *l1flag, bool list_cleared) {
     if (bf16)
         return run_peaks<__nv_bfloat16>(p, reinterpret_cast<const __nv_bfloat16 *>(d_plane), ws, d_peaks, d_npeaks,
-                                        series, st, l1flag);
-    return run_peaks<float>(p, reinterpret_cast<const float *>(d_plane), ws, d_peaks, d_npeaks, series, st, l1flag);
+                                        series, st, l1flag, list_cleared);
+    return run_peaks<float>(p, reinterpret_cast<const float *>(d_plane), ws, d_peaks, d_npeaks, series, st, l1flag,
+                            list_cleared);
 }
 
 }  // namespace fdas

@@ -223,6 +223,33 @@ def test_peaks_ties_plateaus_and_overflow():
     assert fd.fdas_device_status(s.plan) == 0         # cleared by the previous read
 
 
+@pytest.mark.parametrize("thr1", [20.0, 14.0, 13.0, 8.0])
+def test_peaks_listed_and_full_scan_paths(thr1):
+    """The peak list's two output paths: when at most 1024 units (level, row, 512-bin chunk)
+    hold peaks, one block orders the listed units and writes the records; beyond that the full
+    offset scan does.  Exponential noise planes (mean 2, the normalised plane's noise law) at
+    thresholds that put the non-empty unit count on both sides of 1024: bit-exact against the
+    oracle either way, with the true count."""
+    n, zmax, m, S = 1 << 16, 32, 64, 1024
+    K, nb = zmax + 1, n // 2
+    rng = np.random.default_rng(9000 + int(thr1))
+    pl = rng.exponential(2.0, size=(K, nb)).astype(np.float32)
+    thr = (thr1, thr1 * 1.6)
+    s = _search(n, zmax, m, S, max_harm=2, thr=thr, max_peaks=1 << 17)
+    s.plane.copy_(torch.from_numpy(pl.ravel()))
+    s.find_peaks()
+    torch.cuda.synchronize()
+    want, cnt = oracle.peaks_f32(pl, zmax, 2, thr, max_out=1 << 17)
+    units = {(int(w["h"]), int(w["zi"]), int(w["r"]) // 512) for w in want}
+    if thr1 >= 14.0:                                   # 51 and 799 non-empty units: the listed path
+        assert 0 < len(units) <= 1024
+    else:                                              # 1177 and 2654: the full scan
+        assert len(units) > 1024
+    assert int(s.npeaks.item()) == cnt
+    _peaks_equal(s.peak_list(), want)
+    assert fd.fdas_device_status(s.plan) == 0
+
+
 def test_bf16_plane_peaks_quick_cast():
     """The peak kernel widens BF16 planes by bit placement (Sec. 3.1 quick cast): given the
     same values, BF16 and FP32 planes give the same peaks."""
