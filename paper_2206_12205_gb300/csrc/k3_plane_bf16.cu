@@ -79,15 +79,19 @@ struct OpsF16 {
 };
 
 // Segment FFTs (FP32 CUDA-core block FFT), stored as BF16 pairs in the stage-1 order.
+// It also clears the plane kernel's unit marks (zero16: n_zero16 16-byte words, or none), which
+// saves the plane kernel a separate clearing launch.
 __global__ void __launch_bounds__(TC_S_BF16 / 32) k2_segments_bf16(const float2 *__restrict__ X,
                                                                    const float *__restrict__ scale_ptr,
                                                                    const float2 *__restrict__ tw,
                                                                    uint4 *__restrict__ Y, int64_t nb, int L,
-                                                                   int half_m) {
+                                                                   int half_m, uint4 *__restrict__ zero16,
+                                                                   int64_t n_zero16) {
     constexpr int S = TC_S_BF16, T = S / 32;
     extern __shared__ float2 sm[];
     const int t = threadIdx.x;
     const int64_t j = blockIdx.x;
+    for (int64_t w = j * T + t; w < n_zero16; w += (int64_t)gridDim.x * T) zero16[w] = make_uint4(0u, 0u, 0u, 0u);
     const float scale = scale_ptr ? __ldg(scale_ptr) : 1.0f;
     const int64_t base = j * L - half_m;
     float2 v[32];
@@ -850,8 +854,12 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
     if (e != cudaSuccess) return e;
     e = prepare_plane_tc<OpsBF16>();
     if (e != cudaSuccess) return e;
+    // the unit marks are cleared by the segment kernel: their workspace slot is 256-byte aligned
+    // and padded to 256 bytes, so whole 16-byte words cover it
+    const int64_t n_zero16 = l1flag ? ((int64_t)p.K * (p.nb / PEAK_CHUNK) + 15) / 16 : 0;
     p.prof.begin(FDAS_STAGE_SEGMENTS, st);
-    k2_segments_bf16<<<(unsigned)p.n_seg, TC_S_BF16 / 32, smem2, st>>>(d_x, d_scale, p.d_tw, Y, p.nb, p.L, p.m / 2);
+    k2_segments_bf16<<<(unsigned)p.n_seg, TC_S_BF16 / 32, smem2, st>>>(d_x, d_scale, p.d_tw, Y, p.nb, p.L, p.m / 2,
+                                                                      reinterpret_cast<uint4 *>(l1flag), n_zero16);
     p.prof.end(FDAS_STAGE_SEGMENTS, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -862,8 +870,6 @@ cudaError_t launch_plane_bf16(const Plan &p, const float2 *d_x, const float *d_s
     const int64_t ctas = std::min<int64_t>(n_items, (int64_t)sms);     // one persistent CTA per SM
     const int64_t per = (n_items + ctas - 1) / ctas;
     const int64_t grid = (n_items + per - 1) / per;
-    e = clear_marks(p, l1flag, st);
-    if (e != cudaSuccess) return e;
     p.prof.begin(FDAS_STAGE_CORRELATE, st);
     k3_plane_tc<OpsBF16><<<(unsigned)grid, WS_THREADS, WS_SMEM, st>>>(
         Y, reinterpret_cast<const uint4 *>(p.d_Gbf), reinterpret_cast<const uint4 *>(p.d_tcF) + 2 * TILE_BYTES / 16,
