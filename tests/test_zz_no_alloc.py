@@ -42,12 +42,17 @@ def test_static_plane_matches_workspace_plane_twice(n, zmax, m, S):
              + synth.chirp(n, 0.1 + 0.05 * call, n / 11.0 + 100 * call, 4.0 * call)).astype(np.float32)
         xhat = s.spectrum(torch.from_numpy(x).cuda()).clone()
         s.plane_from_spectrum(xhat)
+        torch.cuda.synchronize()
+        free0, torch0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         # through the C-ABI directly
         st = fd.load().fdas_plane_static(
             s.plan.handle, ctypes.c_void_p(xhat.data_ptr()), ctypes.c_void_p(out_static.data_ptr()),
             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         assert st == fb.FDAS_OK, fd.load().fdas_last_error(s.plan.handle)
         torch.cuda.synchronize()
+        if call == 1:                          # after the first call (which may load the module): no allocation
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_allocated() == torch0
         ref = s.plane.cpu().numpy().astype(np.float64)
         got = out_static.cpu().numpy().astype(np.float64)
         assert _floor_err(got, ref) <= 1e-5
