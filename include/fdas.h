@@ -223,6 +223,10 @@ fdas_status fdas_plane_static(fdas_plan_t plan, const float *d_xhat, void *d_pla
  * in row-major (i, r) order, or equal for later ones).  Peaks are written to d_peaks in
  * (harm, zi, r) order, at most max_peaks of them; *d_npeaks (device int32) receives the
  * true count, and a count above max_peaks also sets FDAS_DEV_PEAK_OVERFLOW.
+ * The records are written from the list of (level, row, 512-bin chunk) units that hold peaks by
+ * one block; when more than 1024 units hold peaks (low thresholds) one block per SM scans every
+ * unit's count instead (5.8 million peaks at N = 2^23, 85 templates: about 0.4 ms for the
+ * output, beside 8.5 ms for the harmonic sums' local-maximum tests).
  * Errors: FDAS_E_INVALID, FDAS_E_STATE, FDAS_E_CUDA.
  */
 fdas_status fdas_peaks(fdas_plan_t plan, const void *d_plane, void *d_workspace,

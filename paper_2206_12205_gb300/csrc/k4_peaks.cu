@@ -797,14 +797,16 @@ __device__ __forceinline__ int32_t block_excl_scan(int32_t c, int32_t *warp_tot,
     return warp_tot[warp] + incl - c;
 }
 
-// The step's peaks, one block of 1024 threads.  Usually the non-empty unit list holds every
-// non-empty unit (a handful to a few hundred of ~10^6): its unit numbers are sorted by rank (they
-// are distinct: rank = how many are smaller), their counts scanned in that order into output
-// offsets, and each unit's records emitted by one warp.  Units are numbered in (level, row, chunk)
-// order, so the records come out in (H, i, r) order.  When more than PEAK_LIST_CAP units hold
-// peaks (low thresholds), the block scans every unit's count in order, 4096 units a round, and
-// emits the non-empty ones as it goes (slower, the same records).  Then the total and the
-// overflow flag.
+// The step's peaks, blocks of 1024 threads.  Usually the non-empty unit list holds every
+// non-empty unit (a handful to a few hundred of ~10^6): block 0 alone sorts its unit numbers by
+// rank (they are distinct: rank = how many are smaller), scans their counts in that order into
+// output offsets and emits each unit's records with one warp; the other blocks return at once.
+// Units are numbered in (level, row, chunk) order, so the records come out in (H, i, r) order.
+// When more than PEAK_LIST_CAP units hold peaks (low thresholds, up to millions of peaks), every
+// block takes a contiguous range of units: it sums the counts before its range (its first output
+// offset; a few MB read from L2 per block, no communication between blocks), then scans its
+// range 4096 units a round and emits the non-empty units as it goes.  The last block (or block 0
+// on the listed path) writes the total and the overflow flag.
 template <typename E>
 __global__ void __launch_bounds__(1024) k4_emit_listed(const E *__restrict__ plane, int64_t nb, int zmax, LevelTable lt,
                                                        int64_t n_units, const int32_t *__restrict__ unit_count,
@@ -818,7 +820,10 @@ __global__ void __launch_bounds__(1024) k4_emit_listed(const E *__restrict__ pla
     const unsigned int *list = unit_list(unit_count);
     const int n = (int)*list;
     int64_t total = 0;
-    if (n <= PEAK_LIST_CAP) {                            // block-uniform
+    bool writer = false;                                 // the block that writes the total
+    if (n <= PEAK_LIST_CAP) {                            // grid-uniform
+        if (blockIdx.x != 0) return;
+        writer = true;
         if (t < n) key[t] = list[4 + t];
         __syncthreads();
         if (t < n) {
@@ -838,11 +843,29 @@ __global__ void __launch_bounds__(1024) k4_emit_listed(const E *__restrict__ pla
         for (int k = warp; k < n; k += 32)
             emit_unit<E>(plane, nb, zmax, lt, (int64_t)sorted[k], offs[k], unit_mask, out, max_peaks, series);
     } else {
-        for (int64_t u0 = 0; u0 < n_units; u0 += 4 * 1024) {
+        // this block's units [ub, ue) (whole rounds of 4096) and the count before them
+        const int64_t rounds = (n_units + 4095) / 4096;
+        const int64_t per = (rounds + gridDim.x - 1) / gridDim.x;
+        const int64_t ub = min(n_units, (int64_t)blockIdx.x * per * 4096);
+        const int64_t ue = min(n_units, ub + per * 4096);
+        writer = blockIdx.x == gridDim.x - 1;
+        {
+            __shared__ unsigned long long pre_tot;       // counts are non-negative
+            if (t == 0) pre_tot = 0ull;
+            __syncthreads();
+            unsigned long long acc = 0ull;
+            for (int64_t u = t; u < ub; u += 1024) acc += (unsigned long long)unit_count[u];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if ((t & 31) == 0) atomicAdd(&pre_tot, acc);
+            __syncthreads();
+            total = (int64_t)pre_tot;
+        }
+        for (int64_t u0 = ub; u0 < ue; u0 += 4 * 1024) {
             const int64_t b0 = u0 + 4 * t;               // this thread's 4 units
             int32_t v[4];
 #pragma unroll
-            for (int k = 0; k < 4; k++) v[k] = b0 + k < n_units ? unit_count[b0 + k] : 0;
+            for (int k = 0; k < 4; k++) v[k] = b0 + k < ue ? unit_count[b0 + k] : 0;
             int32_t tot;
             int32_t run = block_excl_scan(v[0] + v[1] + v[2] + v[3], warp_tot, &tot);
 #pragma unroll
@@ -862,7 +885,7 @@ __global__ void __launch_bounds__(1024) k4_emit_listed(const E *__restrict__ pla
             __syncthreads();                             // warp_tot is reused by the next round
         }
     }
-    if (t == 0) {
+    if (writer && t == 0) {
         *npeaks = (int32_t)(total < 0x7fffffff ? total : 0x7fffffff);
         if (total > max_peaks) atomicOr(status, FDAS_DEV_PEAK_OVERFLOW);
     }
@@ -950,8 +973,11 @@ cudaError_t run_peaks(const Plan &p, const E *plane, char *ws, fdas_peak *peaks,
         }
         p.prof.end(PROF_PEAKS_LEVELS, st);
     }
-    k4_emit_listed<E><<<1, 1024, 0, st>>>(plane, p.nb, p.cfg.zmax, lt, n_units, unit_count, unit_mask, peaks,
-                                          p.cfg.max_peaks, series, npeaks, p.d_status);
+    // one block per SM: block 0 serves the usual (listed) case, all of them the overflowing one
+    int sms_out = 152;
+    cudaDeviceGetAttribute(&sms_out, cudaDevAttrMultiProcessorCount, p.device >= 0 ? p.device : 0);
+    k4_emit_listed<E><<<(unsigned)std::max(1, sms_out), 1024, 0, st>>>(
+        plane, p.nb, p.cfg.zmax, lt, n_units, unit_count, unit_mask, peaks, p.cfg.max_peaks, series, npeaks, p.d_status);
     p.prof.end(FDAS_STAGE_PEAKS, st);
     return cudaGetLastError();
 }
