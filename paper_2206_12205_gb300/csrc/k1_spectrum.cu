@@ -30,8 +30,10 @@ __device__ __forceinline__ float2 twN(const float2 *__restrict__ lo, const float
 }
 
 // FFTs of one CTA: groups per CTA (bounded by 1024 threads and the shared memory) and the
-// padding between the groups' shared-memory regions (16 words: groups interleaved in a warp
-// fall on different banks).
+// padding between the groups' shared-memory regions.  The G groups interleave in a warp (lane
+// l serves group l mod G), so a half-warp's 8-byte accesses cover 16 / G consecutive entries of
+// each group: the regions must start 32 / G banks apart, i.e. a region of E entries with
+// E = 16 / G (mod 16).
 #ifndef FDAS_K1A_GROUPS
 #define FDAS_K1A_GROUPS 4                // pass-A columns per CTA for FFT lengths up to 2048
 #endif
@@ -40,7 +42,10 @@ __device__ __forceinline__ float2 twN(const float2 *__restrict__ lo, const float
 #endif
 constexpr int k1_groups_a(int S) { return S >= 8192 ? 1 : (S >= 4096 ? 2 : FDAS_K1A_GROUPS); }
 constexpr int k1_groups_b(int S) { return S >= 8192 ? 1 : (S >= 4096 ? 2 : FDAS_K1B_GROUPS); }
-constexpr int K1_GPAD = 8;
+constexpr int k1_gpad(int S, int G) { return (16 / G - fft_smem_entries(S) % 16 + 16) % 16; }
+constexpr int k1_region(int S, int G) { return fft_smem_entries(S) + k1_gpad(S, G); }
+static_assert(2 * k1_region(2048, 4) % 32 == 8 && 2 * k1_region(4096, 2) % 32 == 16 && 2 * k1_region(256, 4) % 32 == 8,
+              "group regions 32 / G banks apart");
 #ifndef FDAS_K1A_MIN_BLOCKS
 #define FDAS_K1A_MIN_BLOCKS 1            // resident pass-A blocks per SM the registers must allow
 #endif
@@ -58,9 +63,10 @@ __global__ void __launch_bounds__(k1_groups_a(M1) * (M1 / 32), FDAS_K1A_MIN_BLOC
                                                                      unsigned int *__restrict__ ticket,
                                                                      uint32_t *__restrict__ list_hdr) {
     constexpr int T = M1 / 32, C1 = k1_groups_a(M1);
-    constexpr int E = fft_smem_entries(M1) + K1_GPAD;
+    constexpr int E = k1_region(M1, C1);
     extern __shared__ float2 sm[];        // C1 * E entries
-    __shared__ float2 wi[C1][32];         // W_N^{2 n2 T i} of each column
+    __shared__ float2 wi[C1][33];         // W_N^{2 n2 T i} of each column (rows padded: the groups of a
+                                          // warp read one entry each, on different banks)
     const int g = threadIdx.x % C1, t = threadIdx.x / C1;
     const int n2 = blockIdx.x * C1 + g;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(2 * k1_groups_b(M2) * (M2 / 32), FDAS_K1B_MIN_
                                                                          double sigma2_fixed, double *__restrict__ sigma2_out,
                                                                          float *__restrict__ scale_out) {
     constexpr int T = M2 / 32, C2 = k1_groups_b(M2), G = 2 * C2;
-    constexpr int E = fft_smem_entries(M2) + K1_GPAD;
+    constexpr int E = k1_region(M2, G);
     extern __shared__ float2 smb[];       // G * E entries
     __shared__ double red[G * T];
     const int g = threadIdx.x % G, t = threadIdx.x / G;
@@ -227,7 +233,7 @@ template <int M1>
 cudaError_t run_pass_a(const Plan &p, const float2 *z, float2 *B, unsigned int *ticket, uint32_t *list_hdr,
                        cudaStream_t st) {
     constexpr int C1 = k1_groups_a(M1);
-    const size_t smem = sizeof(float2) * C1 * (fft_smem_entries(M1) + K1_GPAD);
+    const size_t smem = sizeof(float2) * C1 * k1_region(M1, C1);
     auto kern = k1_pass_a<M1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -239,7 +245,7 @@ template <int M2>
 cudaError_t run_pass_b(const Plan &p, const float2 *B, float2 *X, double *partial, unsigned int *ticket,
                        double *sigma2, float *scale, cudaStream_t st) {
     constexpr int C2 = k1_groups_b(M2);
-    const size_t smem = 2 * C2 * sizeof(float2) * (fft_smem_entries(M2) + K1_GPAD);
+    const size_t smem = 2 * C2 * sizeof(float2) * k1_region(M2, 2 * C2);
     auto kern = k1_pass_b<M2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
